@@ -1,0 +1,191 @@
+/*
+ * libihdg -- the element-parallel iHDG sweep on one GB300 (sm_103a), behind a C ABI.
+ *
+ * The method (Muralikrishnan, Tran, Bui-Thanh, "iHDG: An Iterative HDG Framework for
+ * Partial Differential Equations"):
+ *   * Section 2, Eqs. (HDGlocal), (HDGeqn), (RiemannFluxBoth): upwind HDG for
+ *     sum_k d_k(A_k u) + C u = f on a mesh of elements K with skeleton E_h.
+ *   * Section 2, Eqs. (iHDGlocal), (iHDGtrace), Algorithm 1: the iteration.  Every element
+ *     solves its local equation with the weighted trace of iterate k, independently of all
+ *     others; the weighted trace of iterate k+1 is then formed face by face; the loop stops
+ *     when ||u^{k+1} - u^k||_{L2} < tol (Section 6.1, Eq. (tolerancecriteriarelerror)).
+ *   * Section 3: scalar transport (Eqs. transportLocalk1, transportLocale) and linearized
+ *     shallow water with backward Euler (Eq. localSolverDD and the trace formula below it).
+ *   * Section 4.1: convection-diffusion in first-order form (Eqs. ErrorDDMCD1, ErrorDDMCD2,
+ *     the flux general_flux_convdiff with gamma = 1, alpha = sqrt((beta.n)^2 + 4)).
+ *
+ * Discretisation choices where the paper is silent: uniform box meshes of congruent
+ * elements; tensor-product Q^p (p = 1..4) with a Gauss-Lobatto-Legendre (GLL) nodal basis;
+ * Gauss-Legendre quadrature with q = p+2 points per direction for the forcing and the
+ * boundary data; Dirichlet traces are the L2 projection of g onto each boundary face.
+ *
+ * Conventions used by every call:
+ *   * Elements are numbered lexicographically, x index fastest.  Inside an element, nodes
+ *     (GLL, (p+1)^d) and quadrature points (Gauss, q^d) are lexicographic, x fastest.
+ *   * Faces: all x-normal faces first (i + (nx+1)*(j + ny*k)), then y-normal
+ *     (i + nx*(j + (ny+1)*k)), then z-normal (i + nx*(j + ny*k)).  Points on a face are
+ *     lexicographic over the tangential axes in increasing axis order.  Boundary faces are
+ *     numbered in global face order.
+ *   * Volume components: transport (u); convection-diffusion (sigma_1..sigma_d, u);
+ *     shallow water (phi, u, v).  One scalar trace per face node: u_hat, u_hat, phi_hat.
+ *   * Host pointers are owned by the caller, read during the call only, and outputs are
+ *     written only when the returned status is IHDG_OK, IHDG_NOT_CONVERGED or
+ *     IHDG_DIVERGED.  A context is not thread-safe: use one per thread.
+ *   * Every call returns a status; ihdg_last_error() gives a one-line reason.
+ *   * No call falls back to the CPU.  Without a usable GPU, ihdg_create() fails with
+ *     IHDG_ERR_CUDA.
+ */
+#ifndef IHDG_H
+#define IHDG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  IHDG_OK = 0,
+  IHDG_ERR_INVALID = 1,      /* bad argument: null pointer, size, coefficient */
+  IHDG_ERR_NOMEM = 2,        /* workspace too small or device allocation failed */
+  IHDG_ERR_CUDA = 3,         /* a CUDA call failed; see ihdg_last_error() */
+  IHDG_NOT_CONVERGED = 4,    /* max_iters sweeps ran without meeting tol (outputs valid) */
+  IHDG_DIVERGED = 5,         /* residual non-finite or grew by diverge_factor (outputs valid) */
+  IHDG_ERR_BUSY = 6,         /* serving: request not finished / no room admitted */
+  IHDG_ERR_TIMEOUT = 7,      /* a bounded device wait ran out; the context stays usable */
+  IHDG_ERR_UNSUPPORTED = 8   /* (pde, dim, p, precision) combination not built */
+} ihdg_status;
+
+typedef enum { IHDG_TRANSPORT = 0, IHDG_CONVDIFF = 1, IHDG_SWE = 2 } ihdg_pde;
+
+/* Arithmetic of the sweep.  FP64: every step in float64.  MIXED_*: defect correction --
+ * float64 outer sweeps form the residual r = S(E) - E and its float64 norm; inner sweeps on
+ * the correction equation e = r + G(e) run in float32 (CUDA cores), TF32 or BF16 (tcgen05
+ * tensor cores, float32 accumulation); E += e; repeat until the float64 norm < tol. */
+typedef enum {
+  IHDG_FP64 = 0,
+  IHDG_MIXED_FP32 = 1,
+  IHDG_MIXED_TF32 = 2,
+  IHDG_MIXED_BF16 = 3
+} ihdg_precision;
+
+/* Uniform box mesh of n[0] x n[1] (x n[2]) congruent elements on [lo, hi], order p. */
+typedef struct {
+  int dim;          /* 2 or 3 (shallow water: 2) */
+  int n[3];         /* elements per direction, >= 1 (n[2] ignored when dim = 2) */
+  double lo[3], hi[3];
+  int p;            /* polynomial order, 1..4 */
+} ihdg_mesh;
+
+typedef struct {
+  ihdg_pde pde;
+  double beta[3];       /* transport / convection-diffusion velocity (constant) */
+  double kappa;         /* convection-diffusion diffusivity, > 0 */
+  double nu;            /* convection-diffusion reaction, >= 0 */
+  double Phi;           /* shallow water mean geopotential, > 0 */
+  double coriolis_f;    /* shallow water Coriolis parameter (constant) */
+  double friction;      /* shallow water bottom friction gamma >= 0 */
+  double dt;            /* shallow water backward-Euler step, > 0 */
+} ihdg_coeffs;
+
+typedef struct {
+  double tol;              /* stop when ||u^k - u^{k-1}||_{L2} < tol (absolute) */
+  int max_iters;           /* sweep budget (default 2000 when <= 0) */
+  ihdg_precision prec;
+  double diverge_factor;   /* DIVERGED when residual > factor * its running minimum;
+                              <= 0 disables the check (default 1e6 when == 0) */
+  int inner_max;           /* mixed: inner sweeps per outer step cap (0 = automatic) */
+  double inner_rtol;       /* mixed: inner stop when step norm <= inner_rtol * ||r|| (0 = auto) */
+  const double* u0;        /* optional initial guess, volume layout (host for ihdg_solve,
+                              device for ihdg_solve_device); NULL = zero */
+} ihdg_options;
+
+typedef struct {
+  int iterations;          /* sweeps executed (plain: the paper's count K; mixed: all) */
+  int fp64_sweeps;         /* of which float64 */
+  int lowp_sweeps;         /* of which low precision */
+  double residual;         /* last float64 ||u^k - u^{k-1}|| */
+  ihdg_status status;
+  double setup_ms;         /* host operator build + uploads (0 when cached) */
+  double solve_ms;         /* device time of the sweep loop and reconstruction */
+} ihdg_result;
+
+typedef struct {
+  long long n_el;          /* elements */
+  int nvol;                /* volume values per element = ncomp * (p+1)^dim */
+  int ncomp;               /* volume components */
+  int nqv;                 /* forcing values per element (q^dim, q = p+2); 0 for SWE */
+  long long n_bface;       /* boundary faces */
+  int nqf;                 /* boundary values per boundary face (q^(dim-1)); 0 for SWE */
+  long long n_face;        /* all faces */
+  int nface_nodes;         /* trace values per face ((p+1)^(dim-1)) */
+  int n_exp;               /* exported trace values per element (device state) */
+  int n_in;                /* gathered trace inputs per element */
+} ihdg_sizes;
+
+typedef struct ihdg_ctx ihdg_ctx;
+
+/* Create a context bound to CUDA device `device`.  Fails with IHDG_ERR_CUDA when no such
+ * device exists or it is not sm_103.  *out receives the context (caller destroys it). */
+ihdg_status ihdg_create(ihdg_ctx** out, int device);
+void ihdg_destroy(ihdg_ctx* ctx);
+/* One-line description of the last failure on this context ("" when none).  Never NULL. */
+const char* ihdg_last_error(const ihdg_ctx* ctx);
+
+/* Sizes of every array for this problem (host-only; validates mesh and coefficients). */
+ihdg_status ihdg_problem_sizes(const ihdg_mesh* mesh, const ihdg_coeffs* coeffs, ihdg_sizes* out);
+
+/* Physical coordinates of the quadrature points where the caller samples f and g
+ * (host-only).  vol_xyz: [n_el][nqv][dim]; bnd_xyz: [n_bface][nqf][dim]; either may be
+ * NULL.  The library samples nothing itself: the forcing and boundary data are inputs. */
+ihdg_status ihdg_quadrature_points(const ihdg_mesh* mesh, double* vol_xyz, double* bnd_xyz);
+
+/* Physical coordinates of the GLL nodes, [n_el][(p+1)^dim][dim] (host-only). */
+ihdg_status ihdg_node_points(const ihdg_mesh* mesh, double* xyz);
+
+/* Steady solve (transport, convection-diffusion) by the iHDG iteration, host buffers.
+ *   f_qp      [n_el][nqv]        forcing f at the quadrature points
+ *   g_qp      [n_bface][nqf]     Dirichlet / inflow data g at boundary quadrature points
+ *                                (transport reads it on inflow faces only)
+ *   u_out     [n_el][nvol]       volume solution u^K at the GLL nodes
+ *   trace_out [n_face][nface_nodes] trace u_hat^K at the face GLL nodes (NULL = skip)
+ * Copies inputs to the device, runs, copies outputs back (all inside the call). */
+ihdg_status ihdg_solve(ihdg_ctx* ctx, const ihdg_mesh* mesh, const ihdg_coeffs* coeffs,
+                       const double* f_qp, const double* g_qp, const ihdg_options* opts,
+                       double* u_out, double* trace_out, ihdg_result* res);
+
+/* Device workspace the device-pointer calls need for this problem and precision. */
+ihdg_status ihdg_workspace_bytes(const ihdg_mesh* mesh, const ihdg_coeffs* coeffs,
+                                 const ihdg_options* opts, size_t* bytes);
+
+/* As ihdg_solve, but every array (including opts->u0) is DEVICE memory of the context's
+ * device, workspace is caller-allocated device memory of at least ihdg_workspace_bytes(),
+ * 256-byte aligned, and all work is ordered on `stream` (a cudaStream_t; NULL = legacy
+ * default stream).  Returns after the solve has finished on the device. */
+ihdg_status ihdg_solve_device(ihdg_ctx* ctx, const ihdg_mesh* mesh, const ihdg_coeffs* coeffs,
+                              const double* d_f_qp, const double* d_g_qp,
+                              const ihdg_options* opts, double* d_u_out, double* d_trace_out,
+                              void* d_workspace, size_t workspace_bytes, void* stream,
+                              ihdg_result* res);
+
+/* Linearized shallow water (Section 3, Eq. localSolverDD), walls on the whole boundary:
+ * advance q (in/out, [n_el][3][(p+1)^2] volume layout (phi, u, v), host) by nsteps
+ * backward-Euler steps of coeffs->dt; each step runs the iHDG iteration warm-started from
+ * the previous step.  iters_per_step (host, length nsteps) may be NULL.  res reports the
+ * totals and the status of the worst step. */
+ihdg_status ihdg_swe_steps(ihdg_ctx* ctx, const ihdg_mesh* mesh, const ihdg_coeffs* coeffs,
+                           double* q_inout, int nsteps, const ihdg_options* opts,
+                           int* iters_per_step, ihdg_result* res);
+
+/* Device-pointer form of ihdg_swe_steps (q and iters_per_step on the host as above are
+ * replaced by device q; iters_per_step stays a host array). */
+ihdg_status ihdg_swe_steps_device(ihdg_ctx* ctx, const ihdg_mesh* mesh,
+                                  const ihdg_coeffs* coeffs, double* d_q_inout, int nsteps,
+                                  const ihdg_options* opts, int* iters_per_step,
+                                  void* d_workspace, size_t workspace_bytes, void* stream,
+                                  ihdg_result* res);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IHDG_H */

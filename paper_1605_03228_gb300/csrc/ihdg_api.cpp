@@ -1,0 +1,540 @@
+// C-ABI of libihdg: argument checks, operator plans, workspace layout and the solve drivers.
+// Every step of the iteration runs in the CUDA kernels of ihdg_kernels.cu / ihdg_mixed.cu;
+// this file only validates, builds the float64 operators once per problem (host), moves
+// data and decides when to launch.  There is no CPU fallback: without a device every
+// entry point that computes fails with IHDG_ERR_CUDA.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "../../include/ihdg.h"
+#include "ihdg_dev.h"
+#include "ihdg_kernels.h"
+#include "ihdg_mixed.h"
+#include "ihdg_ops.h"
+
+using namespace ihdg;
+
+namespace {
+
+struct Plan {
+  ihdg_mesh mesh{};
+  ihdg_coeffs co{};
+  Ops ops;
+  DevGeo g{};
+  OpsDev op{};
+  void* dbuf = nullptr;
+  size_t dbytes = 0;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+bool same_problem(const ihdg_mesh& a, const ihdg_mesh& b, const ihdg_coeffs& ca, const ihdg_coeffs& cb) {
+  return std::memcmp(&a, &b, sizeof(ihdg_mesh)) == 0 && std::memcmp(&ca, &cb, sizeof(ihdg_coeffs)) == 0;
+}
+
+}  // namespace
+
+struct ihdg_ctx {
+  int device = 0;
+  std::string err;
+  std::vector<std::unique_ptr<Plan>> plans;
+  // device scratch of the host-pointer calls (inputs, outputs, workspace)
+  void* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  Ctrl* h_ctrl = nullptr;   // pinned readback of the loop state
+};
+
+namespace {
+
+ihdg_status fail(ihdg_ctx* c, ihdg_status st, const std::string& msg) {
+  if (c) c->err = msg;
+  return st;
+}
+ihdg_status cuda_fail(ihdg_ctx* c, cudaError_t e, const char* where) {
+  std::ostringstream os;
+  os << where << ": " << cudaGetErrorString(e);
+  return fail(c, IHDG_ERR_CUDA, os.str());
+}
+#define CK(call, where)                                     \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); \
+  } while (0)
+
+void fill_geo(const ihdg_mesh& m, const Ops& o, DevGeo& g) {
+  std::memset(&g, 0, sizeof(g));
+  g.dim = m.dim;
+  g.nf = o.nf;
+  g.nlf = o.nlf;
+  g.n_in = o.n_in;
+  g.n_exp = o.n_exp;
+  g.nvol = o.nvol;
+  g.nqv = o.nqv;
+  g.nqf = o.nqf;
+  g.nb = o.nb;
+  g.n[0] = m.n[0];
+  g.n[1] = m.n[1];
+  g.n[2] = m.dim == 3 ? m.n[2] : 1;
+  g.nel = (long long)g.n[0] * g.n[1] * g.n[2];
+  g.ld = (g.nel + 31) / 32 * 32;
+  g.stride[0] = 1;
+  g.stride[1] = g.n[0];
+  g.stride[2] = (long long)g.n[0] * g.n[1];
+  g.nbf_off[0] = 0;
+  g.nbf_off[1] = 2LL * g.n[1] * g.n[2];
+  g.nbf_off[2] = g.nbf_off[1] + 2LL * g.n[0] * g.n[2];
+  for (int f = 0; f < 6; ++f) {
+    g.kind[f] = f < o.nlf ? o.face_kind[f] : 0;
+    g.own_off[f] = o.own_off[f] < 0 ? 0 : o.own_off[f];
+    g.nbr_off[f] = o.nbr_off[f] < 0 ? 0 : o.nbr_off[f];
+  }
+  g.bc_mirror = o.bc_mirror;
+  g.steady = o.pde != IHDG_SWE;
+}
+
+// Build (or find) the plan of a problem: host float64 operators and their device copies.
+ihdg_status get_plan(ihdg_ctx* ctx, const ihdg_mesh& m, const ihdg_coeffs& co, Plan*& out, double* setup_ms) {
+  for (auto& p : ctx->plans)
+    if (same_problem(p->mesh, m, p->co, co)) { out = p.get(); if (setup_ms) *setup_ms = 0.0; return IHDG_OK; }
+  auto t0 = std::chrono::steady_clock::now();
+  auto pl = std::make_unique<Plan>();
+  pl->mesh = m;
+  pl->co = co;
+  std::string err;
+  ihdg_status st = build_ops(m, co, pl->ops, err);
+  if (st != IHDG_OK) return fail(ctx, st, err);
+  const Ops& o = pl->ops;
+  if (!shape_supported(m.dim, o.nf))
+    return fail(ctx, IHDG_ERR_UNSUPPORTED, "this (dim, p) has no compiled sweep kernel (built: 2D p=1..4, 3D p=1..2)");
+  fill_geo(m, o, pl->g);
+  // pack all operators into one host image, then one upload
+  std::vector<double> img;
+  std::vector<size_t> off;
+  auto put = [&](const std::vector<double>& v) { off.push_back(img.size()); img.insert(img.end(), v.begin(), v.end()); size_t pad = (32 - img.size() % 32) % 32; img.insert(img.end(), pad, 0.0); };
+  std::vector<double> Qp;
+  for (int i = 0; i < o.n_in; ++i)
+    for (int j = i; j < o.n_in; ++j) Qp.push_back(o.Q[i * o.n_in + j] * (i == j ? 1.0 : 2.0));
+  std::vector<double> empty(1, 0.0);
+  put(o.LE); put(Qp); put(o.Lvol); put(o.R); put(o.Mn);
+  put(o.PF.empty() ? empty : o.PF); put(o.PV.empty() ? empty : o.PV);
+  for (int f = 0; f < 6; ++f) put(o.PFb[f].empty() ? empty : o.PFb[f]);
+  for (int f = 0; f < 6; ++f) put(o.PVb[f].empty() ? empty : o.PVb[f]);
+  put(o.Pg.empty() ? empty : o.Pg);
+  put(o.PqF.empty() ? empty : o.PqF); put(o.PqV.empty() ? empty : o.PqV);
+  put(o.facevol);
+  size_t nd = img.size();
+  std::vector<float> le32(o.LE.begin(), o.LE.end());
+  size_t bytes = align256(nd * sizeof(double)) + align256(le32.size() * sizeof(float));
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  CK(cudaMalloc(&pl->dbuf, bytes), "cudaMalloc(operators)");
+  pl->dbytes = bytes;
+  CK(cudaMemcpy(pl->dbuf, img.data(), nd * sizeof(double), cudaMemcpyHostToDevice), "upload operators");
+  float* d32 = reinterpret_cast<float*>(static_cast<char*>(pl->dbuf) + align256(nd * sizeof(double)));
+  CK(cudaMemcpy(d32, le32.data(), le32.size() * sizeof(float), cudaMemcpyHostToDevice), "upload operators");
+  const double* b = static_cast<const double*>(pl->dbuf);
+  size_t k = 0;
+  OpsDev& op = pl->op;
+  op.LE = b + off[k++]; op.Qp = b + off[k++]; op.Lvol = b + off[k++]; op.R = b + off[k++]; op.Mn = b + off[k++];
+  op.PF = b + off[k++]; op.PV = b + off[k++];
+  for (int f = 0; f < 6; ++f) op.PFb[f] = b + off[k++];
+  for (int f = 0; f < 6; ++f) op.PVb[f] = b + off[k++];
+  op.Pg = b + off[k++]; op.PqF = b + off[k++]; op.PqV = b + off[k++]; op.facevol = b + off[k++];
+  op.LE32 = d32;
+  if (ctx->plans.size() >= 16) {
+    cudaFree(ctx->plans.front()->dbuf);
+    ctx->plans.erase(ctx->plans.begin());
+  }
+  out = pl.get();
+  ctx->plans.push_back(std::move(pl));
+  if (setup_ms) *setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return IHDG_OK;
+}
+
+// Workspace layout of one solve (offsets in bytes from the workspace base).
+struct Layout {
+  size_t ctrl, partials, res_hist, F, ring, qnext, mixed, total;
+  MixedLayout mx;
+};
+
+Layout layout_for(const DevGeo& g, const ihdg_options& o, bool swe) {
+  Layout L{};
+  size_t at = 0;
+  auto take = [&](size_t bytes) { size_t r = at; at += align256(bytes); return r; };
+  int maxit = o.max_iters > 0 ? o.max_iters : 2000;
+  L.ctrl = take(sizeof(Ctrl));
+  L.partials = take(sizeof(double) * (size_t)partials_needed(g.nel));
+  L.res_hist = take(sizeof(double) * (size_t)(maxit + 2));
+  L.F = take(sizeof(double) * (size_t)g.n_exp * g.ld);
+  L.ring = take(3 * sizeof(double) * (size_t)g.n_exp * g.ld);
+  L.qnext = swe ? take(sizeof(double) * (size_t)g.nvol * g.nel) : 0;
+  if (o.prec != IHDG_FP64) {
+    L.mx = mixed_layout(g, o.prec);
+    L.mixed = take(L.mx.total);
+  }
+  L.total = at;
+  return L;
+}
+
+ihdg_options defaults(const ihdg_options* o) {
+  ihdg_options r{};
+  if (o) r = *o;
+  if (r.max_iters <= 0) r.max_iters = 2000;
+  if (r.diverge_factor == 0.0) r.diverge_factor = 1e6;
+  if (r.inner_max <= 0) r.inner_max = 400;
+  if (r.inner_rtol <= 0.0) r.inner_rtol = r.prec == IHDG_MIXED_BF16 ? 1e-2 : (r.prec == IHDG_MIXED_TF32 ? 1e-3 : 1e-4);
+  return r;
+}
+
+ihdg_status check_opts(ihdg_ctx* ctx, const ihdg_options& o) {
+  if (!(o.tol >= 0.0) || !std::isfinite(o.tol)) return fail(ctx, IHDG_ERR_INVALID, "opts.tol must be finite and >= 0");
+  if (o.prec < IHDG_FP64 || o.prec > IHDG_MIXED_BF16) return fail(ctx, IHDG_ERR_INVALID, "opts.prec is not a known precision");
+  if (o.max_iters > 100000000) return fail(ctx, IHDG_ERR_INVALID, "opts.max_iters too large");
+  return IHDG_OK;
+}
+
+// One solve of the iteration on the device: forcing, first sweep, sweep loop (float64 or
+// mixed), reconstruction of u^K and the trace.  `u0` (device, may be null) is the initial
+// guess; for shallow water src.q holds q^m and u0 == src.q (warm start).
+ihdg_status device_iterate(ihdg_ctx* ctx, Plan* pl, const ihdg_options& o, const SrcDev& src, const double* u0,
+                           double* d_u, double* d_tr, char* ws, const Layout& L, cudaStream_t stream,
+                           ihdg_result* res) {
+  LaunchArgs a{};
+  a.g = pl->g;
+  a.op = pl->op;
+  a.src = src;
+  a.u0 = u0;
+  a.F = reinterpret_cast<double*>(ws + L.F);
+  a.ring = reinterpret_cast<double*>(ws + L.ring);
+  a.ring_stride = (long long)pl->g.n_exp * pl->g.ld;
+  a.ctrl = reinterpret_cast<Ctrl*>(ws + L.ctrl);
+  a.partials = reinterpret_cast<double*>(ws + L.partials);
+  a.res_hist = reinterpret_cast<double*>(ws + L.res_hist);
+  a.stream = stream;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0), "cudaEventCreate");
+  CK(cudaEventCreate(&e1), "cudaEventCreate");
+  CK(cudaEventRecord(e0, stream), "cudaEventRecord");
+  CK(launch_ctrl_init(a, o.tol, o.diverge_factor, o.max_iters, o.inner_max, o.inner_rtol), "ctrl init");
+  CK(launch_forcing(a), "forcing kernel");
+  CK(launch_export0(a, u0, a.ring), "initial export kernel");
+  CK(launch_first(a), "first sweep kernel");
+  Ctrl* hc = ctx->h_ctrl;
+  bool mixed = o.prec != IHDG_FP64;
+  const double* Eu = nullptr;     // exports whose traces fed the final local solve
+  const double* Eu2 = nullptr;    //   (+ a second array, added; mixed path)
+  const double* Et = nullptr;     // exports of u^K
+  const double* Et2 = nullptr;
+  if (!mixed) {
+    int batch = 2;
+    for (;;) {
+      CK(cudaMemcpyAsync(hc, a.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, stream), "ctrl readback");
+      CK(cudaStreamSynchronize(stream), "sweep loop");
+      if (hc->done) break;
+      int left = hc->max_iters - hc->iter;
+      int n = batch < left ? batch : left;
+      if (n <= 0) break;
+      CK(launch_sweep64(a, n), "sweep kernel");
+      if (batch < 32) batch *= 2;
+    }
+    int K = hc->iter;
+    Et = a.ring + (long long)(K % 3) * a.ring_stride;
+    Eu = a.ring + (long long)((K + 2) % 3) * a.ring_stride;
+  } else {
+    MixedArgs m{};
+    m.base = a;
+    mixed_bind(m, ws + L.mixed, L.mx, o.prec);
+    ihdg_status st = run_mixed(ctx->h_ctrl, m, o, &Eu, &Eu2, &Et, &Et2, ctx->err);
+    if (st != IHDG_OK) return fail(ctx, st, ctx->err);
+  }
+  if (d_u) CK(launch_reconstruct(a, Eu, Eu2, d_u), "reconstruct kernel");
+  if (d_tr) {
+    double beta[3] = {pl->co.beta[0], pl->co.beta[1], pl->co.beta[2]};
+    long long nface = count_faces(pl->mesh, nullptr);
+    CK(launch_trace_out(a, Et, Et2, d_u, (int)pl->co.pde, beta, pl->ops.alpha_axis, nface, d_tr), "trace kernel");
+  }
+  CK(cudaEventRecord(e1, stream), "cudaEventRecord");
+  CK(cudaMemcpyAsync(hc, a.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, stream), "ctrl readback");
+  CK(cudaStreamSynchronize(stream), "solve");
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (res) {
+    res->iterations = hc->iter;
+    res->fp64_sweeps = hc->fp64_sweeps;
+    res->lowp_sweeps = hc->lowp_sweeps;
+    res->residual = hc->res;
+    res->status = (ihdg_status)hc->status;
+    res->solve_ms = ms;
+  }
+  return IHDG_OK;
+}
+
+ihdg_status ensure_scratch(ihdg_ctx* ctx, size_t bytes) {
+  if (ctx->scratch_bytes >= bytes) return IHDG_OK;
+  if (ctx->scratch) cudaFree(ctx->scratch);
+  ctx->scratch = nullptr;
+  ctx->scratch_bytes = 0;
+  cudaError_t e = cudaMalloc(&ctx->scratch, bytes);
+  if (e != cudaSuccess) return fail(ctx, IHDG_ERR_NOMEM, std::string("device scratch allocation failed: ") + cudaGetErrorString(e));
+  ctx->scratch_bytes = bytes;
+  return IHDG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ihdg_status ihdg_create(ihdg_ctx** out, int device) {
+  if (!out) return IHDG_ERR_INVALID;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return IHDG_ERR_CUDA;
+  cudaDeviceProp pr;
+  if (cudaGetDeviceProperties(&pr, device) != cudaSuccess) return IHDG_ERR_CUDA;
+  if (pr.major != 10 || pr.minor != 3) return IHDG_ERR_CUDA;   // built for sm_103a only
+  auto* c = new ihdg_ctx();
+  c->device = device;
+  if (cudaSetDevice(device) != cudaSuccess || cudaMallocHost(&c->h_ctrl, sizeof(Ctrl)) != cudaSuccess) {
+    delete c;
+    return IHDG_ERR_CUDA;
+  }
+  *out = c;
+  return IHDG_OK;
+}
+
+void ihdg_destroy(ihdg_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  for (auto& p : ctx->plans) cudaFree(p->dbuf);
+  if (ctx->scratch) cudaFree(ctx->scratch);
+  if (ctx->h_ctrl) cudaFreeHost(ctx->h_ctrl);
+  delete ctx;
+}
+
+const char* ihdg_last_error(const ihdg_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+ihdg_status ihdg_problem_sizes(const ihdg_mesh* mesh, const ihdg_coeffs* co, ihdg_sizes* out) {
+  if (!mesh || !co || !out) return IHDG_ERR_INVALID;
+  std::string err;
+  Ops o;
+  ihdg_status st = build_ops(*mesh, *co, o, err);
+  if (st != IHDG_OK) return st;
+  std::memset(out, 0, sizeof(*out));
+  out->n_el = 1;
+  for (int a = 0; a < mesh->dim; ++a) out->n_el *= mesh->n[a];
+  out->nvol = o.nvol;
+  out->ncomp = o.ncomp;
+  out->nqv = co->pde == IHDG_SWE ? 0 : o.nqv;
+  out->nqf = co->pde == IHDG_SWE ? 0 : o.nqf;
+  out->n_face = count_faces(*mesh, &out->n_bface);
+  out->nface_nodes = o.nf;
+  out->n_exp = o.n_exp;
+  out->n_in = o.n_in;
+  return IHDG_OK;
+}
+
+ihdg_status ihdg_quadrature_points(const ihdg_mesh* mesh, double* vol_xyz, double* bnd_xyz) {
+  if (!mesh) return IHDG_ERR_INVALID;
+  std::string err;
+  ihdg_status st = validate(*mesh, nullptr, err);
+  if (st != IHDG_OK) return st;
+  quadrature_points(*mesh, vol_xyz, bnd_xyz);
+  return IHDG_OK;
+}
+
+ihdg_status ihdg_node_points(const ihdg_mesh* mesh, double* xyz) {
+  if (!mesh || !xyz) return IHDG_ERR_INVALID;
+  std::string err;
+  ihdg_status st = validate(*mesh, nullptr, err);
+  if (st != IHDG_OK) return st;
+  node_points(*mesh, xyz);
+  return IHDG_OK;
+}
+
+ihdg_status ihdg_workspace_bytes(const ihdg_mesh* mesh, const ihdg_coeffs* co, const ihdg_options* opts, size_t* bytes) {
+  if (!mesh || !co || !bytes) return IHDG_ERR_INVALID;
+  std::string err;
+  Ops o;
+  ihdg_status st = build_ops(*mesh, *co, o, err);
+  if (st != IHDG_OK) return st;
+  DevGeo g;
+  fill_geo(*mesh, o, g);
+  *bytes = layout_for(g, defaults(opts), co->pde == IHDG_SWE).total;
+  return IHDG_OK;
+}
+
+ihdg_status ihdg_solve_device(ihdg_ctx* ctx, const ihdg_mesh* mesh, const ihdg_coeffs* co, const double* d_f,
+                              const double* d_g, const ihdg_options* opts, double* d_u, double* d_tr,
+                              void* d_ws, size_t ws_bytes, void* stream, ihdg_result* res) {
+  if (!ctx) return IHDG_ERR_INVALID;
+  if (!mesh || !co || !d_f || !d_g || !d_ws || !d_u) return fail(ctx, IHDG_ERR_INVALID, "null argument");
+  if (co->pde == IHDG_SWE) return fail(ctx, IHDG_ERR_INVALID, "shallow water is solved by ihdg_swe_steps*");
+  if (reinterpret_cast<uintptr_t>(d_ws) % 256 != 0) return fail(ctx, IHDG_ERR_INVALID, "workspace must be 256-byte aligned");
+  ihdg_options o = defaults(opts);
+  ihdg_status st = check_opts(ctx, o);
+  if (st != IHDG_OK) return st;
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  Plan* pl = nullptr;
+  double setup_ms = 0.0;
+  st = get_plan(ctx, *mesh, *co, pl, &setup_ms);
+  if (st != IHDG_OK) return st;
+  Layout L = layout_for(pl->g, o, false);
+  if (ws_bytes < L.total) return fail(ctx, IHDG_ERR_NOMEM, "workspace smaller than ihdg_workspace_bytes()");
+  SrcDev src{d_f, d_g, nullptr};
+  st = device_iterate(ctx, pl, o, src, o.u0, d_u, d_tr, static_cast<char*>(d_ws), L, static_cast<cudaStream_t>(stream), res);
+  if (st == IHDG_OK && res) res->setup_ms = setup_ms;
+  ctx->err.clear();
+  return st;
+}
+
+ihdg_status ihdg_solve(ihdg_ctx* ctx, const ihdg_mesh* mesh, const ihdg_coeffs* co, const double* f_qp,
+                       const double* g_qp, const ihdg_options* opts, double* u_out, double* trace_out,
+                       ihdg_result* res) {
+  if (!ctx) return IHDG_ERR_INVALID;
+  if (!mesh || !co || !f_qp || !g_qp || !u_out) return fail(ctx, IHDG_ERR_INVALID, "null argument");
+  if (co->pde == IHDG_SWE) return fail(ctx, IHDG_ERR_INVALID, "shallow water is solved by ihdg_swe_steps*");
+  ihdg_sizes sz;
+  ihdg_status st = ihdg_problem_sizes(mesh, co, &sz);
+  if (st != IHDG_OK) {
+    std::string err;
+    validate(*mesh, co, err);
+    return fail(ctx, st, err.empty() ? "invalid problem" : err);
+  }
+  ihdg_options o = defaults(opts);
+  st = check_opts(ctx, o);
+  if (st != IHDG_OK) return st;
+  size_t ws = 0;
+  ihdg_workspace_bytes(mesh, co, &o, &ws);
+  size_t bf = align256(sizeof(double) * sz.n_el * sz.nqv), bg = align256(sizeof(double) * sz.n_bface * sz.nqf);
+  size_t bu = align256(sizeof(double) * sz.n_el * sz.nvol), bt = align256(sizeof(double) * sz.n_face * sz.nface_nodes);
+  size_t bu0 = o.u0 ? bu : 0;
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  st = ensure_scratch(ctx, bf + bg + bu + bt + bu0 + ws);
+  if (st != IHDG_OK) return st;
+  char* s = static_cast<char*>(ctx->scratch);
+  double* d_f = reinterpret_cast<double*>(s);
+  double* d_g = reinterpret_cast<double*>(s + bf);
+  double* d_u = reinterpret_cast<double*>(s + bf + bg);
+  double* d_t = reinterpret_cast<double*>(s + bf + bg + bu);
+  double* d_u0 = o.u0 ? reinterpret_cast<double*>(s + bf + bg + bu + bt) : nullptr;
+  char* d_ws = s + bf + bg + bu + bt + bu0;
+  cudaStream_t stream = nullptr;
+  CK(cudaMemcpyAsync(d_f, f_qp, sizeof(double) * sz.n_el * sz.nqv, cudaMemcpyHostToDevice, stream), "copy f");
+  CK(cudaMemcpyAsync(d_g, g_qp, sizeof(double) * sz.n_bface * sz.nqf, cudaMemcpyHostToDevice, stream), "copy g");
+  if (o.u0) CK(cudaMemcpyAsync(d_u0, o.u0, sizeof(double) * sz.n_el * sz.nvol, cudaMemcpyHostToDevice, stream), "copy u0");
+  ihdg_options od = o;
+  od.u0 = d_u0;
+  st = ihdg_solve_device(ctx, mesh, co, d_f, d_g, &od, d_u, trace_out ? d_t : nullptr, d_ws, ws, stream, res);
+  if (st != IHDG_OK) return st;
+  CK(cudaMemcpy(u_out, d_u, sizeof(double) * sz.n_el * sz.nvol, cudaMemcpyDeviceToHost), "copy u");
+  if (trace_out) CK(cudaMemcpy(trace_out, d_t, sizeof(double) * sz.n_face * sz.nface_nodes, cudaMemcpyDeviceToHost), "copy trace");
+  return IHDG_OK;
+}
+
+ihdg_status ihdg_swe_steps_device(ihdg_ctx* ctx, const ihdg_mesh* mesh, const ihdg_coeffs* co, double* d_q,
+                                  int nsteps, const ihdg_options* opts, int* iters_per_step, void* d_ws,
+                                  size_t ws_bytes, void* stream, ihdg_result* res) {
+  if (!ctx) return IHDG_ERR_INVALID;
+  if (!mesh || !co || !d_q || !d_ws) return fail(ctx, IHDG_ERR_INVALID, "null argument");
+  if (co->pde != IHDG_SWE) return fail(ctx, IHDG_ERR_INVALID, "ihdg_swe_steps* needs coeffs.pde = IHDG_SWE");
+  if (nsteps < 0) return fail(ctx, IHDG_ERR_INVALID, "nsteps must be >= 0");
+  if (reinterpret_cast<uintptr_t>(d_ws) % 256 != 0) return fail(ctx, IHDG_ERR_INVALID, "workspace must be 256-byte aligned");
+  ihdg_options o = defaults(opts);
+  ihdg_status st = check_opts(ctx, o);
+  if (st != IHDG_OK) return st;
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  Plan* pl = nullptr;
+  double setup_ms = 0.0;
+  st = get_plan(ctx, *mesh, *co, pl, &setup_ms);
+  if (st != IHDG_OK) return st;
+  Layout L = layout_for(pl->g, o, true);
+  if (ws_bytes < L.total) return fail(ctx, IHDG_ERR_NOMEM, "workspace smaller than ihdg_workspace_bytes()");
+  char* ws = static_cast<char*>(d_ws);
+  double* qn = reinterpret_cast<double*>(ws + L.qnext);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ihdg_result tot{};
+  tot.status = IHDG_OK;
+  size_t qbytes = sizeof(double) * (size_t)pl->g.nel * pl->g.nvol;
+  for (int m = 0; m < nsteps; ++m) {
+    SrcDev src{nullptr, nullptr, d_q};
+    ihdg_result r{};
+    st = device_iterate(ctx, pl, o, src, d_q, qn, nullptr, ws, L, s, &r);
+    if (st != IHDG_OK) return st;
+    CK(cudaMemcpyAsync(d_q, qn, qbytes, cudaMemcpyDeviceToDevice, s), "copy q");
+    if (iters_per_step) iters_per_step[m] = r.iterations;
+    tot.iterations += r.iterations;
+    tot.fp64_sweeps += r.fp64_sweeps;
+    tot.lowp_sweeps += r.lowp_sweeps;
+    tot.solve_ms += r.solve_ms;
+    tot.residual = r.residual;
+    if (r.status > tot.status) tot.status = r.status;
+  }
+  CK(cudaStreamSynchronize(s), "swe steps");
+  tot.setup_ms = setup_ms;
+  if (res) *res = tot;
+  ctx->err.clear();
+  return IHDG_OK;
+}
+
+ihdg_status ihdg_swe_steps(ihdg_ctx* ctx, const ihdg_mesh* mesh, const ihdg_coeffs* co, double* q, int nsteps,
+                           const ihdg_options* opts, int* iters_per_step, ihdg_result* res) {
+  if (!ctx) return IHDG_ERR_INVALID;
+  if (!mesh || !co || !q) return fail(ctx, IHDG_ERR_INVALID, "null argument");
+  ihdg_sizes sz;
+  ihdg_status st = ihdg_problem_sizes(mesh, co, &sz);
+  if (st != IHDG_OK) {
+    std::string err;
+    validate(*mesh, co, err);
+    return fail(ctx, st, err.empty() ? "invalid problem" : err);
+  }
+  ihdg_options o = defaults(opts);
+  size_t ws = 0;
+  ihdg_workspace_bytes(mesh, co, &o, &ws);
+  size_t bq = align256(sizeof(double) * sz.n_el * sz.nvol);
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  st = ensure_scratch(ctx, bq + ws);
+  if (st != IHDG_OK) return st;
+  double* d_q = static_cast<double*>(ctx->scratch);
+  CK(cudaMemcpy(d_q, q, sizeof(double) * sz.n_el * sz.nvol, cudaMemcpyHostToDevice), "copy q");
+  st = ihdg_swe_steps_device(ctx, mesh, co, d_q, nsteps, &o, iters_per_step, static_cast<char*>(ctx->scratch) + bq, ws, nullptr, res);
+  if (st != IHDG_OK) return st;
+  CK(cudaMemcpy(q, d_q, sizeof(double) * sz.n_el * sz.nvol, cudaMemcpyDeviceToHost), "copy q");
+  return IHDG_OK;
+}
+
+// Host-only inspection of the float64 operators of a problem (no device needed).
+// which: 0 L_E, 1 Q, 2 L_vol, 3 R, 4 PF, 5 PV.  rows/cols receive the shape; data may be
+// NULL to query the shape only.
+ihdg_status ihdg_host_operator(const ihdg_mesh* mesh, const ihdg_coeffs* co, int which, int* rows, int* cols,
+                               double* data) {
+  if (!mesh || !co || !rows || !cols) return IHDG_ERR_INVALID;
+  std::string err;
+  Ops o;
+  ihdg_status st = build_ops(*mesh, *co, o, err);
+  if (st != IHDG_OK) return st;
+  const std::vector<double>* v = nullptr;
+  int r = 0, c = 0;
+  switch (which) {
+    case 0: v = &o.LE; r = o.n_exp; c = o.n_in; break;
+    case 1: v = &o.Q; r = o.n_in; c = o.n_in; break;
+    case 2: v = &o.Lvol; r = o.nvol; c = o.n_in; break;
+    case 3: v = &o.R; r = o.n_exp; c = o.nvol; break;
+    case 4: v = &o.PF; r = o.n_exp; c = o.nqv; break;
+    case 5: v = &o.PV; r = o.nvol; c = o.nqv; break;
+    default: return IHDG_ERR_INVALID;
+  }
+  *rows = r;
+  *cols = c;
+  if (data && v->size() == (size_t)r * c) std::memcpy(data, v->data(), sizeof(double) * v->size());
+  return IHDG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,401 @@
+// CUDA kernels of the element-parallel iHDG sweep (sm_103a).
+//
+// One sweep of Algorithm 1 (Section 2) on the export state E (see ihdg_ops.h):
+//   a1  gather the traces every element needs from its own and its neighbours' exports of
+//       iterate k, combined by the upwind flux (transport: upwind value, Eq. transportLocale;
+//       convection-diffusion: (h^- + h^+)/alpha, Section 4.1; shallow water: h^- + h^+, or
+//       2h^- at a wall, the trace formula under Eq. localSolverDD);
+//   a2  the per-sweep right-hand side is only the trace-dependent part: forcing, boundary
+//       data and time-step data are folded once per solve into F (k_forcing);
+//   a3  apply the precomputed local solve, E^{k+1} = F + L_E t^k;
+//   a4  write E^{k+1} (three-slot ring) and accumulate the stopping residual
+//       ||u^{k+1} - u^k||^2 = dt^T Q dt with dt = t(E^k) - t(E^{k-1});
+//   a5  the last block to finish sums the per-block partial sums in a fixed order
+//       (deterministic, no floating-point atomics) and takes the loop decision on the device.
+//
+// Layout: every per-element array is slot-major, x[slot * ld + element], so a warp of
+// consecutive elements reads consecutive addresses for every slot (neighbours along x are
+// one element away, along y n0, along z n0*n1).  Elements are numbered x fastest.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+
+#include "ihdg_dev.h"
+#include "ihdg_kernels.h"
+#include "ihdg_common.cuh"
+
+namespace ihdg {
+
+namespace {
+
+// Volume data of element K in float64: forcing/boundary (steady) or time-step data (SWE).
+// Writes V[i] = (A^{-1} b)_i for i < nvol through `put`.
+template <typename Out>
+__device__ __forceinline__ void volume_source(const DevGeo& g, const OpsDev& op, const SrcDev& src,
+                                              long long K, const int* c, Out&& put) {
+  for (int i = 0; i < g.nvol; ++i) {
+    double v = 0.0;
+    if (g.steady) {
+      const double* fk = src.f + K * g.nqv;
+      const double* row = op.PV + (long long)i * g.nqv;
+      for (int q = 0; q < g.nqv; ++q) v += row[q] * fk[q];
+      for (int f = 0; f < g.nlf; ++f) {
+        if (!on_bnd(g, c, f)) continue;
+        const double* gb = src.g + bface_of(g, c, f) * g.nqf;
+        const double* rb = op.PVb[f] + (long long)i * g.nqf;
+        for (int q = 0; q < g.nqf; ++q) v += rb[q] * gb[q];
+      }
+    } else {
+      const double* qk = src.q + K * g.nvol;
+      const double* row = op.PqV + (long long)i * g.nvol;
+      for (int q = 0; q < g.nvol; ++q) v += row[q] * qk[q];
+    }
+    put(i, v);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// a2 (once per solve / per time step): export forcing F = R A^{-1} b.
+__global__ void __launch_bounds__(BS) k_forcing(DevGeo g, OpsDev op, SrcDev src, double* __restrict__ F) {
+  const long long K = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (K >= g.nel) return;
+  int c[3];
+  coords(g, K, c);
+  for (int e = 0; e < g.n_exp; ++e) {
+    double v = 0.0;
+    if (g.steady) {
+      const double* fk = src.f + K * g.nqv;
+      const double* row = op.PF + (long long)e * g.nqv;
+      for (int q = 0; q < g.nqv; ++q) v += row[q] * fk[q];
+      for (int f = 0; f < g.nlf; ++f) {
+        if (!on_bnd(g, c, f)) continue;
+        const double* gb = src.g + bface_of(g, c, f) * g.nqf;
+        const double* rb = op.PFb[f] + (long long)e * g.nqf;
+        for (int q = 0; q < g.nqf; ++q) v += rb[q] * gb[q];
+      }
+    } else {
+      const double* qk = src.q + K * g.nvol;
+      const double* row = op.PqF + (long long)e * g.nvol;
+      for (int q = 0; q < g.nvol; ++q) v += row[q] * qk[q];
+    }
+    F[(long long)e * g.ld + K] = v;
+  }
+}
+
+// Initial export E^0 = R u^0 (u^0 in the volume layout [nel][nvol]).
+__global__ void __launch_bounds__(BS) k_export0(DevGeo g, OpsDev op, const double* __restrict__ u0,
+                                                double* __restrict__ E0) {
+  const long long K = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (K >= g.nel) return;
+  for (int e = 0; e < g.n_exp; ++e) {
+    double v = 0.0;
+    if (u0) {
+      const double* row = op.R + (long long)e * g.nvol;
+      for (int i = 0; i < g.nvol; ++i) v += row[i] * u0[K * g.nvol + i];
+    }
+    E0[(long long)e * g.ld + K] = v;
+  }
+}
+
+// First sweep (k = 0 -> 1): E^1 = F + L_E t(E^0), and the residual ||u^1 - u^0|| on the
+// full volume state (u^0 is the initial guess, not a previous local solve).
+template <int NF, int NLF>
+__global__ void __launch_bounds__(BS) k_first(DevGeo g, OpsDev op, SrcDev src, const double* __restrict__ u0,
+                                              const double* __restrict__ F, double* ring, long long ring_stride,
+                                              Ctrl* ctrl, double* partials, double* res_hist) {
+  constexpr int NIN = NF * NLF;
+  __shared__ double ws[BS / 32];
+  extern __shared__ double sdyn[];
+  double* du = sdyn + threadIdx.x;    // per-thread column of nvol doubles, stride BS
+  const long long K = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double acc = 0.0;
+  if (K < g.nel) {
+    int c[3];
+    coords(g, K, c);
+    double t[NIN];
+    gather<NF, NLF, double, double>(g, ring, K, c, [&](int s, double v) { t[s] = v; });
+    double* E1 = ring + ring_stride;
+    for (int e = 0; e < g.n_exp; ++e) {
+      double v = F[(long long)e * g.ld + K];
+      const double* row = op.LE + (long long)e * NIN;
+#pragma unroll
+      for (int s = 0; s < NIN; ++s) v += row[s] * t[s];
+      E1[(long long)e * g.ld + K] = v;
+    }
+    volume_source(g, op, src, K, c, [&](int i, double v) { du[i * BS] = v; });
+    for (int i = 0; i < g.nvol; ++i) {
+      double v = du[i * BS];
+      const double* row = op.Lvol + (long long)i * NIN;
+#pragma unroll
+      for (int s = 0; s < NIN; ++s) v += row[s] * t[s];
+      if (u0) v -= u0[K * g.nvol + i];
+      du[i * BS] = v;
+    }
+    for (int i = 0; i < g.nvol; ++i) {
+      double s = 0.0;
+      const double* row = op.Mn + (long long)i * g.nvol;
+      for (int j = 0; j < g.nvol; ++j) s += row[j] * du[j * BS];
+      acc += du[i * BS] * s;
+    }
+  }
+  double tot;
+  if (arrive(ctrl, partials, acc, ws, &tot) && threadIdx.x == 0) decide(ctrl, tot, res_hist, true);
+}
+
+// Plain sweep in float64 (k -> k+1, k >= 1): a1..a5.  E^k in ring slot k%3, E^{k-1} in
+// (k+2)%3, E^{k+1} written to (k+1)%3.  The operators L_E (n_exp x NIN) and the packed upper
+// triangle of Q (off-diagonals doubled) are staged in shared memory; the gathered traces
+// live in a per-thread shared-memory column, their increments in registers.
+template <int NF, int NLF>
+__global__ void __launch_bounds__(BS) k_sweep64(DevGeo g, OpsDev op, const double* __restrict__ F,
+                                                double* ring, long long ring_stride, Ctrl* ctrl,
+                                                double* partials, double* res_hist) {
+  constexpr int NIN = NF * NLF;
+  constexpr int NQ = NIN * (NIN + 1) / 2;
+  __shared__ double ws[BS / 32];
+  extern __shared__ double sdyn[];
+  if (ctrl_done(ctrl)) return;
+  const int it = ctrl_iter(ctrl);
+  double* sLE = sdyn;                       // n_exp * NIN
+  double* sQ = sLE + g.n_exp * NIN;         // NQ
+  double* st = sQ + NQ + threadIdx.x;       // per-thread trace column, stride BS
+  for (int i = threadIdx.x; i < g.n_exp * NIN; i += BS) sLE[i] = op.LE[i];
+  for (int i = threadIdx.x; i < NQ; i += BS) sQ[i] = op.Qp[i];
+  __syncthreads();
+  const double* Ecur = ring + (long long)(it % 3) * ring_stride;
+  const double* Eprv = ring + (long long)((it + 2) % 3) * ring_stride;
+  double* Enxt = ring + (long long)((it + 1) % 3) * ring_stride;
+  const long long K = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double acc = 0.0;
+  if (K < g.nel) {
+    int c[3];
+    coords(g, K, c);
+    double d[NIN];
+    gather<NF, NLF, double, double>(g, Ecur, K, c, [&](int s, double v) { st[s * BS] = v; d[s] = v; });
+    gather<NF, NLF, double, double>(g, Eprv, K, c, [&](int s, double v) { d[s] -= v; });
+    // a4 residual: dt^T Q dt with Q packed upper-triangular, off-diagonals doubled
+    int q = 0;
+#pragma unroll
+    for (int s = 0; s < NIN; ++s) {
+      double r = 0.0;
+#pragma unroll
+      for (int u = s; u < NIN; ++u) r += sQ[q + u - s] * d[u];
+      q += NIN - s;
+      acc += d[s] * r;
+    }
+    // a3: E^{k+1} = F + L_E t^k
+    for (int e = 0; e < g.n_exp; ++e) {
+      double v = F[(long long)e * g.ld + K];
+      const double* row = sLE + e * NIN;
+#pragma unroll
+      for (int s = 0; s < NIN; ++s) v += row[s] * st[s * BS];
+      Enxt[(long long)e * g.ld + K] = v;
+    }
+  }
+  double tot;
+  if (arrive(ctrl, partials, acc, ws, &tot) && threadIdx.x == 0) decide(ctrl, tot, res_hist, true);
+}
+
+// Volume reconstruction u = A^{-1} b + L_vol t(E) (+ L_vol t(E2) when E2 is given).
+template <int NF, int NLF>
+__global__ void __launch_bounds__(BS) k_reconstruct(DevGeo g, OpsDev op, SrcDev src, const double* __restrict__ E,
+                                                    const double* __restrict__ E2, double* __restrict__ u) {
+  constexpr int NIN = NF * NLF;
+  const long long K = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (K >= g.nel) return;
+  int c[3];
+  coords(g, K, c);
+  double t[NIN];
+  gather<NF, NLF, double, double>(g, E, K, c, [&](int s, double v) { t[s] = v; });
+  if (E2) gather<NF, NLF, double, double>(g, E2, K, c, [&](int s, double v) { t[s] += v; });
+  volume_source(g, op, src, K, c, [&](int i, double v) {
+    const double* row = op.Lvol + (long long)i * NIN;
+#pragma unroll
+    for (int s = 0; s < NIN; ++s) v += row[s] * t[s];
+    u[K * g.nvol + i] = v;
+  });
+}
+
+// Trace output on every face node (Algorithm 1 step 3 applied to the final iterate):
+// transport: the upwind export (inflow boundary: projected g; beta.n = 0: {{u}});
+// convection-diffusion: (h^- + h^+)/alpha inside, projected g on the boundary;
+// shallow water: h^- + h^+ inside, 2 h^- at walls.
+__global__ void __launch_bounds__(BS) k_trace_out(DevGeo g, OpsDev op, SrcDev src, const double* __restrict__ E,
+                                                  const double* __restrict__ E2, const double* __restrict__ u,
+                                                  int pde, double beta0, double beta1, double beta2,
+                                                  double al0, double al1, double al2, long long nface,
+                                                  double* __restrict__ tr) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nface * g.nf) return;
+  const long long fc = idx / g.nf;
+  const int j = (int)(idx % g.nf);
+  const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
+  const long long cnt0 = (long long)(n0 + 1) * n1 * n2;
+  const long long cnt1 = (long long)n0 * (n1 + 1) * n2;
+  int a;
+  long long loc;
+  if (fc < cnt0) { a = 0; loc = fc; } else if (fc < cnt0 + cnt1) { a = 1; loc = fc - cnt0; } else { a = 2; loc = fc - cnt0 - cnt1; }
+  int ci, cj, ck;
+  long long L = -1, R = -1, bf = -1;
+  auto eid = [&](long long i, long long jj, long long k) { return i + (long long)n0 * (jj + (long long)n1 * k); };
+  if (a == 0) {
+    ci = (int)(loc % (n0 + 1)); cj = (int)((loc / (n0 + 1)) % n1); ck = (int)(loc / ((long long)(n0 + 1) * n1));
+    if (ci > 0) L = eid(ci - 1, cj, ck);
+    if (ci < n0) R = eid(ci, cj, ck);
+    if (ci == 0 || ci == n0) bf = 2LL * (cj + (long long)n1 * ck) + (ci == n0);
+  } else if (a == 1) {
+    ci = (int)(loc % n0); cj = (int)((loc / n0) % (n1 + 1)); ck = (int)(loc / ((long long)n0 * (n1 + 1)));
+    if (cj > 0) L = eid(ci, cj - 1, ck);
+    if (cj < n1) R = eid(ci, cj, ck);
+    if (cj == 0 || cj == n1) bf = g.nbf_off[1] + (long long)ck * 2 * n0 + (long long)(cj == n1) * n0 + ci;
+  } else {
+    ci = (int)(loc % n0); cj = (int)((loc / n0) % n1); ck = (int)(loc / ((long long)n0 * n1));
+    if (ck > 0) L = eid(ci, cj, ck - 1);
+    if (ck < n2) R = eid(ci, cj, ck);
+    if (ck == 0 || ck == n2) bf = g.nbf_off[2] + (long long)(ck == n2) * n0 * n1 + (long long)cj * n0 + ci;
+  }
+  const int fL = 2 * a + 1, fR = 2 * a;   // the face as seen from its left / right element
+  auto ex = [&](long long el, int f) {
+    double v = E[(long long)(g.own_off[f] + j) * g.ld + el];
+    if (E2) v += E2[(long long)(g.own_off[f] + j) * g.ld + el];
+    return v;
+  };
+  auto proj_g = [&]() {
+    double v = 0.0;
+    for (int q = 0; q < g.nqf; ++q) v += op.Pg[j * g.nqf + q] * src.g[bf * g.nqf + q];
+    return v;
+  };
+  double v = 0.0;
+  if (pde == 0) {
+    const double b = a == 0 ? beta0 : (a == 1 ? beta1 : beta2);
+    if (b > 0) v = (L >= 0) ? ex(L, fL) : proj_g();
+    else if (b < 0) v = (R >= 0) ? ex(R, fR) : proj_g();
+    else {
+      const double* fvL = op.facevol + fL * g.nf;
+      const double* fvR = op.facevol + fR * g.nf;
+      if (L >= 0 && R >= 0) v = 0.5 * (u[L * g.nvol + (int)fvL[j]] + u[R * g.nvol + (int)fvR[j]]);
+      else if (L >= 0) v = u[L * g.nvol + (int)fvL[j]];
+      else v = u[R * g.nvol + (int)fvR[j]];
+    }
+  } else if (pde == 1) {
+    const double al = a == 0 ? al0 : (a == 1 ? al1 : al2);
+    if (L >= 0 && R >= 0) v = (ex(L, fL) + ex(R, fR)) / al;
+    else v = proj_g();
+  } else {
+    if (L >= 0 && R >= 0) v = ex(L, fL) + ex(R, fR);
+    else if (L >= 0) v = 2.0 * ex(L, fL);
+    else v = 2.0 * ex(R, fR);
+  }
+  tr[idx] = v;
+}
+
+__global__ void k_ctrl_init(Ctrl* c, double tol, double div, int max_iters, int inner_max, double inner_rtol) {
+  c->ticket = 0u;
+  c->done = 0;
+  c->status = 4;
+  c->iter = 0;
+  c->fp64_sweeps = 0;
+  c->lowp_sweeps = 0;
+  c->inner_done = 0;
+  c->inner_iter = 0;
+  c->outer = 0;
+  c->max_iters = max_iters;
+  c->inner_max = inner_max;
+  c->tol = tol;
+  c->diverge_factor = div;
+  c->inner_rtol = inner_rtol;
+  c->res = 0.0;
+  c->res_min = 1e300;
+  c->rnorm = 0.0;
+  c->inner_step = 0.0;
+}
+
+inline unsigned grid_for(long long n) { return (unsigned)((n + BS - 1) / BS); }
+
+template <int NF, int NLF>
+cudaError_t run_first_t(const LaunchArgs& a) {
+  size_t smem = (size_t)a.g.nvol * BS * sizeof(double);
+  auto kern = k_first<NF, NLF>;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  kern<<<grid_for(a.g.nel), BS, smem, a.stream>>>(a.g, a.op, a.src, a.u0, a.F, a.ring, a.ring_stride, a.ctrl, a.partials, a.res_hist);
+  return cudaGetLastError();
+}
+
+template <int NF, int NLF>
+cudaError_t run_sweep64_t(const LaunchArgs& a, int count) {
+  constexpr int NIN = NF * NLF;
+  size_t smem = ((size_t)a.g.n_exp * NIN + NIN * (NIN + 1) / 2 + (size_t)NIN * BS) * sizeof(double);
+  auto kern = k_sweep64<NF, NLF>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  for (int i = 0; i < count; ++i)
+    kern<<<grid_for(a.g.nel), BS, smem, a.stream>>>(a.g, a.op, a.F, a.ring, a.ring_stride, a.ctrl, a.partials, a.res_hist);
+  return cudaGetLastError();
+}
+
+template <int NF, int NLF>
+cudaError_t run_reconstruct_t(const LaunchArgs& a, const double* E, const double* E2, double* u) {
+  k_reconstruct<NF, NLF><<<grid_for(a.g.nel), BS, 0, a.stream>>>(a.g, a.op, a.src, E, E2, u);
+  return cudaGetLastError();
+}
+
+// dispatch over the built (dim, p) shapes
+template <template <int, int> class Fn, typename... Args>
+cudaError_t dispatch(const DevGeo& g, Args&&... args) {
+  if (g.dim == 2) {
+    switch (g.nf) {
+      case 2: return Fn<2, 4>::run(args...);
+      case 3: return Fn<3, 4>::run(args...);
+      case 4: return Fn<4, 4>::run(args...);
+      case 5: return Fn<5, 4>::run(args...);
+    }
+  } else {
+    switch (g.nf) {
+      case 4: return Fn<4, 6>::run(args...);
+      case 9: return Fn<9, 6>::run(args...);
+    }
+  }
+  return cudaErrorNotSupported;
+}
+
+template <int NF, int NLF> struct FirstFn { static cudaError_t run(const LaunchArgs& a) { return run_first_t<NF, NLF>(a); } };
+template <int NF, int NLF> struct Sweep64Fn { static cudaError_t run(const LaunchArgs& a, int n) { return run_sweep64_t<NF, NLF>(a, n); } };
+template <int NF, int NLF> struct ReconFn {
+  static cudaError_t run(const LaunchArgs& a, const double* E, const double* E2, double* u) { return run_reconstruct_t<NF, NLF>(a, E, E2, u); }
+};
+
+}  // namespace
+
+bool shape_supported(int dim, int nf) {
+  return (dim == 2 && nf >= 2 && nf <= 5) || (dim == 3 && (nf == 4 || nf == 9));
+}
+
+cudaError_t launch_ctrl_init(const LaunchArgs& a, double tol, double div, int max_iters, int inner_max, double inner_rtol) {
+  k_ctrl_init<<<1, 1, 0, a.stream>>>(a.ctrl, tol, div, max_iters, inner_max, inner_rtol);
+  return cudaGetLastError();
+}
+cudaError_t launch_forcing(const LaunchArgs& a) {
+  k_forcing<<<grid_for(a.g.nel), BS, 0, a.stream>>>(a.g, a.op, a.src, a.F);
+  return cudaGetLastError();
+}
+cudaError_t launch_export0(const LaunchArgs& a, const double* u0, double* E0) {
+  k_export0<<<grid_for(a.g.nel), BS, 0, a.stream>>>(a.g, a.op, u0, E0);
+  return cudaGetLastError();
+}
+cudaError_t launch_first(const LaunchArgs& a) { return dispatch<FirstFn>(a.g, a); }
+cudaError_t launch_sweep64(const LaunchArgs& a, int count) { return dispatch<Sweep64Fn>(a.g, a, count); }
+cudaError_t launch_reconstruct(const LaunchArgs& a, const double* E, const double* E2, double* u) {
+  return dispatch<ReconFn>(a.g, a, E, E2, u);
+}
+cudaError_t launch_trace_out(const LaunchArgs& a, const double* E, const double* E2, const double* u, int pde,
+                             const double* beta, const double* alpha, long long nface, double* tr) {
+  long long n = nface * a.g.nf;
+  k_trace_out<<<grid_for(n), BS, 0, a.stream>>>(a.g, a.op, a.src, E, E2, u, pde, beta[0], beta[1], beta[2],
+                                                alpha[0], alpha[1], alpha[2], nface, tr);
+  return cudaGetLastError();
+}
+int partials_needed(long long nel) { return (int)grid_for(nel); }
+
+}  // namespace ihdg

@@ -1,0 +1,60 @@
+// Kernel launch interface of the iHDG sweep (internal header).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "ihdg_dev.h"
+
+namespace ihdg {
+
+// Device copies of the float64 operators (see Ops in ihdg_ops.h), row-major.
+struct OpsDev {
+  const double* LE;      // n_exp x n_in
+  const double* Qp;      // packed upper triangle of Q, off-diagonals doubled
+  const double* Lvol;    // nvol x n_in
+  const double* R;       // n_exp x nvol
+  const double* Mn;      // nvol x nvol
+  const double* PF;      // n_exp x nqv
+  const double* PV;      // nvol x nqv
+  const double* PFb[6];  // n_exp x nqf
+  const double* PVb[6];  // nvol x nqf
+  const double* Pg;      // nf x nqf
+  const double* PqF;     // n_exp x nvol
+  const double* PqV;     // nvol x nvol
+  const double* facevol; // nlf x nf
+  const float* LE32;     // n_exp x n_in, float32 copy for the low-precision sweeps
+};
+
+// Problem data: steady forcing/boundary data, or shallow-water step data q^m.
+struct SrcDev {
+  const double* f;   // [nel][nqv]
+  const double* g;   // [n_bface][nqf]
+  const double* q;   // [nel][nvol]
+};
+
+struct LaunchArgs {
+  DevGeo g;
+  OpsDev op;
+  SrcDev src;
+  const double* u0;       // initial guess (volume layout) or nullptr
+  double* F;              // export forcing, n_exp x ld
+  double* ring;           // three export slots of n_exp x ld
+  long long ring_stride;  // = n_exp * ld
+  Ctrl* ctrl;
+  double* partials;       // one per block of the element kernels
+  double* res_hist;       // residual after each sweep (index = sweep number), or nullptr
+  cudaStream_t stream;
+};
+
+bool shape_supported(int dim, int nf);
+int partials_needed(long long nel);
+
+cudaError_t launch_ctrl_init(const LaunchArgs& a, double tol, double div, int max_iters, int inner_max, double inner_rtol);
+cudaError_t launch_forcing(const LaunchArgs& a);
+cudaError_t launch_export0(const LaunchArgs& a, const double* u0, double* E0);
+cudaError_t launch_first(const LaunchArgs& a);
+cudaError_t launch_sweep64(const LaunchArgs& a, int count);
+cudaError_t launch_reconstruct(const LaunchArgs& a, const double* E, const double* E2, double* u);
+cudaError_t launch_trace_out(const LaunchArgs& a, const double* E, const double* E2, const double* u, int pde,
+                             const double* beta, const double* alpha, long long nface, double* tr);
+
+}  // namespace ihdg

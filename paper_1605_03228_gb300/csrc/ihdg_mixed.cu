@@ -1,0 +1,321 @@
+// Mixed-precision iHDG sweep loop: float64 defect correction around low-precision inner
+// sweeps (see ihdg_mixed.h for the scheme).  The inner sweep is the same a1..a5 pass as the
+// float64 one, on the correction equation, with low-precision storage of e and r and
+// float32 arithmetic; its loop decision is a step-size test in the export space.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "ihdg_common.cuh"
+#include "ihdg_dev.h"
+#include "ihdg_kernels.h"
+#include "ihdg_mixed.h"
+
+namespace ihdg {
+
+namespace {
+
+template <typename T> __device__ __forceinline__ float to_f(T v);
+template <> __device__ __forceinline__ float to_f<float>(float v) { return v; }
+template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <typename T> __device__ __forceinline__ T from_f(float v);
+template <> __device__ __forceinline__ float from_f<float>(float v) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
+// gather from a low-precision array, widening to TA
+template <int NF, int NLF, typename TL, typename TA, typename Out>
+__device__ __forceinline__ void gather_lp(const DevGeo& g, const TL* __restrict__ E, long long K, const int* c, Out&& put) {
+#pragma unroll
+  for (int f = 0; f < NLF; ++f) {
+    const int kind = g.kind[f];
+    const bool bnd = on_bnd(g, c, f);
+    const long long Kn = nbr_of(g, K, f);
+    const TL* own = E + (long long)g.own_off[f] * g.ld + K;
+    const TL* nb = E + (long long)g.nbr_off[f] * g.ld + Kn;
+#pragma unroll
+    for (int j = 0; j < NF; ++j) {
+      TA v = TA(0);
+      if (kind == FK_OWN_D) {
+        v = (TA)to_f(own[(long long)j * g.ld]);
+      } else if (kind == FK_NBR_D) {
+        if (!bnd) v = (TA)to_f(nb[(long long)j * g.ld]);
+      } else if (kind == FK_SUM_D) {
+        const TA o = (TA)to_f(own[(long long)j * g.ld]);
+        if (!bnd) v = o + (TA)to_f(nb[(long long)j * g.ld]);
+        else if (g.bc_mirror) v = o + o;
+      }
+      put(f * NF + j, v);
+    }
+  }
+}
+
+// Outer float64 sweep: E' = E + e (own and gathered), r = F + L_E t(E') - E'.
+template <int NF, int NLF, typename TL>
+__global__ void __launch_bounds__(BS) k_outer64(DevGeo g, OpsDev op, const double* __restrict__ F, double* E64,
+                                                long long es, double* __restrict__ r64, TL* __restrict__ rlp,
+                                                TL* e0, TL* e1, int has_e, Ctrl* ctrl, double* partials) {
+  constexpr int NIN = NF * NLF;
+  __shared__ double ws[BS / 32];
+  extern __shared__ double sdyn[];
+  if (ctrl_done(ctrl)) return;
+  const int o = *(volatile const int*)&ctrl->outer;
+  const int j = *(volatile const int*)&ctrl->inner_iter;
+  double* sLE = sdyn;
+  double* st = sLE + g.n_exp * NIN + threadIdx.x;
+  for (int i = threadIdx.x; i < g.n_exp * NIN; i += BS) sLE[i] = op.LE[i];
+  __syncthreads();
+  const double* Ecur = E64 + (long long)(o & 1) * es;
+  double* Enx = E64 + (long long)((o + 1) & 1) * es;
+  const TL* ecur = (j & 1) ? e1 : e0;
+  const long long K = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double acc = 0.0;
+  if (K < g.nel) {
+    int c[3];
+    coords(g, K, c);
+    gather<NF, NLF, double, double>(g, Ecur, K, c, [&](int s, double v) { st[s * BS] = v; });
+    if (has_e) gather_lp<NF, NLF, TL, double>(g, ecur, K, c, [&](int s, double v) { st[s * BS] += v; });
+    for (int e = 0; e < g.n_exp; ++e) {
+      const long long at = (long long)e * g.ld + K;
+      double own = Ecur[at];
+      if (has_e) own += (double)to_f(ecur[at]);
+      double v = F[at];
+      const double* row = sLE + e * NIN;
+#pragma unroll
+      for (int s = 0; s < NIN; ++s) v += row[s] * st[s * BS];
+      const double r = v - own;
+      Enx[at] = own;
+      r64[at] = r;
+      rlp[at] = from_f<TL>((float)r);
+      acc += r * r;
+    }
+  }
+  double tot;
+  if (arrive(ctrl, partials, acc, ws, &tot) && threadIdx.x == 0) {
+    ctrl->rnorm = sqrt(tot);
+    ctrl->outer = o + 1;
+    ctrl->iter += 1;
+    ctrl->fp64_sweeps += 1;
+  }
+}
+
+// Float64 stopping residual of the next exact sweep, sqrt(t(r)^T Q t(r)), fused with the
+// first useful inner sweep e = r + L_E t(r) (low precision).
+template <int NF, int NLF, typename TL>
+__global__ void __launch_bounds__(BS) k_inner_first(DevGeo g, OpsDev op, const double* __restrict__ r64, TL* e0,
+                                                    Ctrl* ctrl, double* partials, double* res_hist) {
+  constexpr int NIN = NF * NLF;
+  constexpr int NQ = NIN * (NIN + 1) / 2;
+  __shared__ double ws[BS / 32];
+  extern __shared__ double sdyn[];
+  if (ctrl_done(ctrl)) return;
+  double* sQ = sdyn;
+  float* sL = reinterpret_cast<float*>(sQ + NQ);
+  for (int i = threadIdx.x; i < NQ; i += BS) sQ[i] = op.Qp[i];
+  for (int i = threadIdx.x; i < g.n_exp * NIN; i += BS) sL[i] = op.LE32[i];
+  __syncthreads();
+  const long long K = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double acc = 0.0;
+  if (K < g.nel) {
+    int c[3];
+    coords(g, K, c);
+    double d[NIN];
+    gather<NF, NLF, double, double>(g, r64, K, c, [&](int s, double v) { d[s] = v; });
+    int q = 0;
+#pragma unroll
+    for (int s = 0; s < NIN; ++s) {
+      double r = 0.0;
+#pragma unroll
+      for (int u = s; u < NIN; ++u) r += sQ[q + u - s] * d[u];
+      q += NIN - s;
+      acc += d[s] * r;
+    }
+    for (int e = 0; e < g.n_exp; ++e) {
+      const long long at = (long long)e * g.ld + K;
+      float v = (float)r64[at];
+      const float* row = sL + e * NIN;
+#pragma unroll
+      for (int s = 0; s < NIN; ++s) v = fmaf(row[s], (float)d[s], v);
+      e0[at] = from_f<TL>(v);
+    }
+  }
+  double tot;
+  if (arrive(ctrl, partials, acc, ws, &tot) && threadIdx.x == 0) {
+    decide(ctrl, tot, res_hist, false);
+    ctrl->inner_iter = 0;
+    ctrl->inner_done = 0;
+  }
+}
+
+// Inner low-precision sweep on the correction equation: e_{j+1} = r + L_E t(e_j).
+template <int NF, int NLF, typename TL>
+__global__ void __launch_bounds__(BS) k_inner(DevGeo g, OpsDev op, const TL* __restrict__ rlp, TL* e0, TL* e1,
+                                              Ctrl* ctrl, double* partials) {
+  constexpr int NIN = NF * NLF;
+  __shared__ double ws[BS / 32];
+  extern __shared__ float sf[];
+  if (ctrl_done(ctrl) || *(volatile const int*)&ctrl->inner_done) return;
+  const int j = *(volatile const int*)&ctrl->inner_iter;
+  for (int i = threadIdx.x; i < g.n_exp * NIN; i += BS) sf[i] = op.LE32[i];
+  __syncthreads();
+  const TL* ec = (j & 1) ? e1 : e0;
+  TL* en = (j & 1) ? e0 : e1;
+  const long long K = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  float acc = 0.f;
+  if (K < g.nel) {
+    int c[3];
+    coords(g, K, c);
+    float t[NIN];
+    gather_lp<NF, NLF, TL, float>(g, ec, K, c, [&](int s, float v) { t[s] = v; });
+    for (int e = 0; e < g.n_exp; ++e) {
+      const long long at = (long long)e * g.ld + K;
+      float v = to_f(rlp[at]);
+      const float* row = sf + e * NIN;
+#pragma unroll
+      for (int s = 0; s < NIN; ++s) v = fmaf(row[s], t[s], v);
+      const TL nv = from_f<TL>(v);
+      const float dlt = to_f(nv) - to_f(ec[at]);
+      acc = fmaf(dlt, dlt, acc);
+      en[at] = nv;
+    }
+  }
+  double tot;
+  if (arrive(ctrl, partials, (double)acc, ws, &tot) && threadIdx.x == 0) {
+    const int jn = j + 1;
+    ctrl->inner_iter = jn;
+    ctrl->iter += 1;
+    ctrl->lowp_sweeps += 1;
+    const double step = sqrt(tot);
+    ctrl->inner_step = step;
+    if (step <= ctrl->inner_rtol * ctrl->rnorm || jn >= ctrl->inner_max || ctrl->iter >= ctrl->max_iters ||
+        !(step == step) || isinf(step))
+      ctrl->inner_done = 1;
+  }
+}
+
+inline unsigned grid_for(long long n) { return (unsigned)((n + BS - 1) / BS); }
+
+template <typename TL>
+struct MixedRunner {
+  template <int NF, int NLF>
+  struct Fn {
+    static cudaError_t run(MixedArgs& m, int which, int has_e, int count) {
+      constexpr int NIN = NF * NLF;
+      const LaunchArgs& a = m.base;
+      TL* e0 = static_cast<TL*>(m.e[0]);
+      TL* e1 = static_cast<TL*>(m.e[1]);
+      TL* rl = static_cast<TL*>(m.rlp);
+      if (which == 0) {
+        size_t smem = ((size_t)a.g.n_exp * NIN + (size_t)NIN * BS) * sizeof(double);
+        auto k = k_outer64<NF, NLF, TL>;
+        if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k<<<grid_for(a.g.nel), BS, smem, a.stream>>>(a.g, a.op, a.F, m.E64, a.ring_stride, m.r64, rl, e0, e1, has_e,
+                                                      a.ctrl, a.partials);
+      } else if (which == 1) {
+        size_t smem = (size_t)NIN * (NIN + 1) / 2 * sizeof(double) + (size_t)a.g.n_exp * NIN * sizeof(float);
+        auto k = k_inner_first<NF, NLF, TL>;
+        if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k<<<grid_for(a.g.nel), BS, smem, a.stream>>>(a.g, a.op, m.r64, e0, a.ctrl, a.partials, a.res_hist);
+      } else {
+        size_t smem = (size_t)a.g.n_exp * NIN * sizeof(float);
+        for (int i = 0; i < count; ++i)
+          k_inner<NF, NLF, TL><<<grid_for(a.g.nel), BS, smem, a.stream>>>(a.g, a.op, rl, e0, e1, a.ctrl, a.partials);
+      }
+      return cudaGetLastError();
+    }
+  };
+};
+
+template <typename TL>
+cudaError_t mixed_launch(MixedArgs& m, int which, int has_e, int count) {
+  const DevGeo& g = m.base.g;
+  using R = MixedRunner<TL>;
+  if (g.dim == 2) {
+    switch (g.nf) {
+      case 2: return R::template Fn<2, 4>::run(m, which, has_e, count);
+      case 3: return R::template Fn<3, 4>::run(m, which, has_e, count);
+      case 4: return R::template Fn<4, 4>::run(m, which, has_e, count);
+      case 5: return R::template Fn<5, 4>::run(m, which, has_e, count);
+    }
+  } else {
+    switch (g.nf) {
+      case 4: return R::template Fn<4, 6>::run(m, which, has_e, count);
+      case 9: return R::template Fn<9, 6>::run(m, which, has_e, count);
+    }
+  }
+  return cudaErrorNotSupported;
+}
+
+cudaError_t mlaunch(MixedArgs& m, int which, int has_e, int count) {
+  if (m.prec == IHDG_MIXED_BF16) return mixed_launch<__nv_bfloat16>(m, which, has_e, count);
+  return mixed_launch<float>(m, which, has_e, count);
+}
+
+size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+MixedLayout mixed_layout(const DevGeo& g, int prec) {
+  MixedLayout L{};
+  L.lp_bytes = prec == IHDG_MIXED_BF16 ? 2 : 4;
+  size_t one = a256((size_t)g.n_exp * g.ld * L.lp_bytes);
+  L.rlp = 0;
+  L.e0 = one;
+  L.e1 = 2 * one;
+  L.total = 3 * one;
+  return L;
+}
+
+void mixed_bind(MixedArgs& m, char* region, const MixedLayout& L, int prec) {
+  m.prec = prec;
+  m.E64 = m.base.ring + m.base.ring_stride;   // ring slots 1 and 2
+  m.r64 = m.base.ring;                        // ring slot 0 (E^0 is dead once the outer loop runs)
+  m.rlp = region + L.rlp;
+  m.e[0] = region + L.e0;
+  m.e[1] = region + L.e1;
+}
+
+ihdg_status run_mixed(Ctrl* hc, MixedArgs& m, const ihdg_options& o, const double** Eu, const double** Eu2,
+                      const double** Et, const double** Et2, std::string& err) {
+  const LaunchArgs& a = m.base;
+  auto ck = [&](cudaError_t e, const char* where) {
+    if (e != cudaSuccess) { err = std::string(where) + ": " + cudaGetErrorString(e); return false; }
+    return true;
+  };
+  if (o.prec == IHDG_MIXED_TF32) { err = "TF32 inner sweeps need the tensor-core kernel, not built in this library"; return IHDG_ERR_UNSUPPORTED; }
+  if (!ck(cudaMemcpyAsync(hc, a.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, a.stream), "ctrl readback") ||
+      !ck(cudaStreamSynchronize(a.stream), "first sweep"))
+    return IHDG_ERR_CUDA;
+  if (hc->done) {   // the first float64 sweep already met the tolerance (or failed)
+    *Eu = a.ring;
+    *Eu2 = nullptr;
+    *Et = a.ring + a.ring_stride;
+    *Et2 = nullptr;
+    return IHDG_OK;
+  }
+  MixedArgs mm = m;
+  int has_e = 0;
+  for (int outer = 0; outer < 1000000; ++outer) {
+    if (!ck(mlaunch(mm, 0, has_e, 1), "outer sweep kernel") || !ck(mlaunch(mm, 1, 0, 1), "residual kernel"))
+      return IHDG_ERR_CUDA;
+    has_e = 1;
+    int batch = 4;
+    for (;;) {
+      if (!ck(mlaunch(mm, 2, 0, batch), "inner sweep kernel") ||
+          !ck(cudaMemcpyAsync(hc, a.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, a.stream), "ctrl readback") ||
+          !ck(cudaStreamSynchronize(a.stream), "inner loop"))
+        return IHDG_ERR_CUDA;
+      if (hc->done || hc->inner_done) break;
+      if (batch < 64) batch *= 2;
+    }
+    if (hc->done) break;
+  }
+  const double* Ecur = mm.E64 + (long long)(hc->outer & 1) * a.ring_stride;
+  *Eu = Ecur;
+  *Eu2 = nullptr;
+  *Et = Ecur;
+  *Et2 = mm.r64;
+  return IHDG_OK;
+}
+
+}  // namespace ihdg

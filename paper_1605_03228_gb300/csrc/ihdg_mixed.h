@@ -1,0 +1,38 @@
+// Mixed-precision iHDG sweep loop (internal header).
+//
+// Defect correction around the float64 iteration E <- S(E) = F + L_E t(E):
+//   outer (float64):  E' = E + e,  r = S(E') - E'                      (k_outer64)
+//   check (float64):  res = ||u(S(E')) - u(E')|| = sqrt(t(r)^T Q t(r))  (k_inner_first)
+//   inner (low):      e <- r + L_E t(e), from e = r, until the step is small  (k_inner)
+// The float64 residual is the paper's stopping quantity (Section 6.1) evaluated for the
+// next exact sweep from the current state; the output is u(E') with the trace of S(E').
+#pragma once
+#include <string>
+
+#include "../../include/ihdg.h"
+#include "ihdg_kernels.h"
+
+namespace ihdg {
+
+struct MixedLayout {
+  size_t rlp, e0, e1, total;   // byte offsets inside the mixed region
+  int lp_bytes;                // bytes per low-precision value
+};
+
+struct MixedArgs {
+  LaunchArgs base;
+  double* E64;          // two float64 export slots (ring slots 1 and 2), stride base.ring_stride
+  double* r64;          // float64 residual (ring slot 0)
+  void* rlp;            // low-precision residual
+  void* e[2];           // low-precision correction, ping-pong
+  int prec;
+};
+
+MixedLayout mixed_layout(const DevGeo& g, int prec);
+void mixed_bind(MixedArgs& m, char* region, const MixedLayout& L, int prec);
+// Runs the outer/inner loop after the first float64 sweep.  On return, (Eu, Eu2) are the
+// exports whose traces feed the final local solve, and (Et, Et2) the exports of u^K.
+ihdg_status run_mixed(Ctrl* h_ctrl, MixedArgs& m, const ihdg_options& o, const double** Eu, const double** Eu2,
+                      const double** Et, const double** Et2, std::string& err);
+
+}  // namespace ihdg

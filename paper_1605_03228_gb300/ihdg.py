@@ -1,0 +1,263 @@
+"""Python binding of libihdg (ctypes).  Argument marshalling only: every step of the iHDG
+sweep runs in the library's CUDA kernels.  There is no CPU fallback; if the library or a
+GPU is missing, the calls raise.
+
+The names follow include/ihdg.h.  Arrays are numpy float64 (host calls) or raw device
+pointers (the *_device calls), e.g. from torch tensors via tensor.data_ptr().
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OK, ERR_INVALID, ERR_NOMEM, ERR_CUDA, NOT_CONVERGED, DIVERGED, ERR_BUSY, ERR_TIMEOUT, ERR_UNSUPPORTED = range(9)
+STATUS_NAMES = {0: "OK", 1: "ERR_INVALID", 2: "ERR_NOMEM", 3: "ERR_CUDA", 4: "NOT_CONVERGED", 5: "DIVERGED",
+                6: "ERR_BUSY", 7: "ERR_TIMEOUT", 8: "ERR_UNSUPPORTED"}
+TRANSPORT, CONVDIFF, SWE = 0, 1, 2
+FP64, MIXED_FP32, MIXED_TF32, MIXED_BF16 = 0, 1, 2, 3
+
+
+class Mesh(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("lo", ctypes.c_double * 3),
+                ("hi", ctypes.c_double * 3), ("p", ctypes.c_int)]
+
+
+class Coeffs(ctypes.Structure):
+    _fields_ = [("pde", ctypes.c_int), ("beta", ctypes.c_double * 3), ("kappa", ctypes.c_double),
+                ("nu", ctypes.c_double), ("Phi", ctypes.c_double), ("coriolis_f", ctypes.c_double),
+                ("friction", ctypes.c_double), ("dt", ctypes.c_double)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iters", ctypes.c_int), ("prec", ctypes.c_int),
+                ("diverge_factor", ctypes.c_double), ("inner_max", ctypes.c_int),
+                ("inner_rtol", ctypes.c_double), ("u0", ctypes.c_void_p)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("fp64_sweeps", ctypes.c_int), ("lowp_sweeps", ctypes.c_int),
+                ("residual", ctypes.c_double), ("status", ctypes.c_int), ("setup_ms", ctypes.c_double),
+                ("solve_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Sizes(ctypes.Structure):
+    _fields_ = [("n_el", ctypes.c_longlong), ("nvol", ctypes.c_int), ("ncomp", ctypes.c_int), ("nqv", ctypes.c_int),
+                ("n_bface", ctypes.c_longlong), ("nqf", ctypes.c_int), ("n_face", ctypes.c_longlong),
+                ("nface_nodes", ctypes.c_int), ("n_exp", ctypes.c_int), ("n_in", ctypes.c_int)]
+
+
+EXPORTED = ["ihdg_create", "ihdg_destroy", "ihdg_last_error", "ihdg_problem_sizes", "ihdg_quadrature_points",
+            "ihdg_node_points", "ihdg_solve", "ihdg_workspace_bytes", "ihdg_solve_device", "ihdg_swe_steps",
+            "ihdg_swe_steps_device", "ihdg_host_operator"]
+
+_lib = None
+
+
+def lib_path():
+    return _build.LIB
+
+
+def load(build_if_missing=True):
+    """Load libihdg.so (building it first when missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError("libihdg.so is not built; run paper_1605_03228_gb300/build.py")
+    L = ctypes.CDLL(_build.LIB)
+    P, VP, I, D, SZ = ctypes.POINTER, ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    dp = P(ctypes.c_double)
+    L.ihdg_create.argtypes = [P(VP), I]
+    L.ihdg_destroy.argtypes = [VP]
+    L.ihdg_destroy.restype = None
+    L.ihdg_last_error.argtypes = [VP]
+    L.ihdg_last_error.restype = ctypes.c_char_p
+    L.ihdg_problem_sizes.argtypes = [P(Mesh), P(Coeffs), P(Sizes)]
+    L.ihdg_quadrature_points.argtypes = [P(Mesh), dp, dp]
+    L.ihdg_node_points.argtypes = [P(Mesh), dp]
+    L.ihdg_solve.argtypes = [VP, P(Mesh), P(Coeffs), dp, dp, P(Options), dp, dp, P(Result)]
+    L.ihdg_workspace_bytes.argtypes = [P(Mesh), P(Coeffs), P(Options), P(SZ)]
+    L.ihdg_solve_device.argtypes = [VP, P(Mesh), P(Coeffs), VP, VP, P(Options), VP, VP, VP, SZ, VP, P(Result)]
+    L.ihdg_swe_steps.argtypes = [VP, P(Mesh), P(Coeffs), dp, I, P(Options), P(I), P(Result)]
+    L.ihdg_swe_steps_device.argtypes = [VP, P(Mesh), P(Coeffs), VP, I, P(Options), P(I), VP, SZ, VP, P(Result)]
+    L.ihdg_host_operator.argtypes = [P(Mesh), P(Coeffs), I, P(I), P(I), dp]
+    for name in EXPORTED:
+        if getattr(L, name).restype is None and name != "ihdg_destroy":
+            pass
+    for name in EXPORTED:
+        f = getattr(L, name)
+        if name not in ("ihdg_destroy", "ihdg_last_error"):
+            f.restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def make_mesh(dim, n, p, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0)):
+    m = Mesh()
+    m.dim = dim
+    for a in range(3):
+        m.n[a] = int(n[a]) if a < len(n) else 1
+        m.lo[a] = float(lo[a]) if a < len(lo) else 0.0
+        m.hi[a] = float(hi[a]) if a < len(hi) else 1.0
+    m.p = p
+    return m
+
+
+def make_coeffs(pde, beta=(0.0, 0.0, 0.0), kappa=0.0, nu=0.0, Phi=0.0, coriolis_f=0.0, friction=0.0, dt=0.0):
+    c = Coeffs()
+    c.pde = pde
+    for a in range(3):
+        c.beta[a] = float(beta[a]) if a < len(beta) else 0.0
+    c.kappa, c.nu, c.Phi, c.coriolis_f, c.friction, c.dt = kappa, nu, Phi, coriolis_f, friction, dt
+    return c
+
+
+def make_options(tol, max_iters=2000, prec=FP64, diverge_factor=0.0, inner_max=0, inner_rtol=0.0, u0=None):
+    o = Options()
+    o.tol, o.max_iters, o.prec, o.diverge_factor = tol, max_iters, prec, diverge_factor
+    o.inner_max, o.inner_rtol = inner_max, inner_rtol
+    o.u0 = u0
+    return o
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if a is not None else None
+
+
+class IHDGError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def problem_sizes(mesh, coeffs):
+    L = load()
+    s = Sizes()
+    st = L.ihdg_problem_sizes(ctypes.byref(mesh), ctypes.byref(coeffs), ctypes.byref(s))
+    if st != OK:
+        raise IHDGError(st, "ihdg_problem_sizes")
+    return s
+
+
+def quadrature_points(mesh, coeffs):
+    s = problem_sizes(mesh, coeffs)
+    L = load()
+    q = (mesh.p + 2)
+    nqv, nqf = q ** mesh.dim, q ** (mesh.dim - 1)
+    vol = np.zeros((s.n_el, nqv, mesh.dim))
+    bnd = np.zeros((s.n_bface, nqf, mesh.dim))
+    st = L.ihdg_quadrature_points(ctypes.byref(mesh), _dptr(vol), _dptr(bnd))
+    if st != OK:
+        raise IHDGError(st, "ihdg_quadrature_points")
+    return vol, bnd
+
+
+def node_points(mesh, coeffs):
+    s = problem_sizes(mesh, coeffs)
+    L = load()
+    nb = (mesh.p + 1) ** mesh.dim
+    xyz = np.zeros((s.n_el, nb, mesh.dim))
+    st = L.ihdg_node_points(ctypes.byref(mesh), _dptr(xyz))
+    if st != OK:
+        raise IHDGError(st, "ihdg_node_points")
+    return xyz
+
+
+def host_operator(mesh, coeffs, which):
+    """Float64 operator of the library's host precompute: 0 L_E, 1 Q, 2 L_vol, 3 R, 4 PF, 5 PV."""
+    L = load()
+    r, c = ctypes.c_int(), ctypes.c_int()
+    st = L.ihdg_host_operator(ctypes.byref(mesh), ctypes.byref(coeffs), which, ctypes.byref(r), ctypes.byref(c), None)
+    if st != OK:
+        raise IHDGError(st, "ihdg_host_operator")
+    out = np.zeros((r.value, c.value))
+    L.ihdg_host_operator(ctypes.byref(mesh), ctypes.byref(coeffs), which, ctypes.byref(r), ctypes.byref(c), _dptr(out))
+    return out
+
+
+def workspace_bytes(mesh, coeffs, opts):
+    L = load()
+    n = ctypes.c_size_t()
+    st = L.ihdg_workspace_bytes(ctypes.byref(mesh), ctypes.byref(coeffs), ctypes.byref(opts), ctypes.byref(n))
+    if st != OK:
+        raise IHDGError(st, "ihdg_workspace_bytes")
+    return n.value
+
+
+class Context:
+    """An ihdg_ctx bound to one CUDA device."""
+
+    def __init__(self, device=0):
+        self.L = load()
+        self.h = ctypes.c_void_p()
+        st = self.L.ihdg_create(ctypes.byref(self.h), device)
+        if st != OK:
+            raise IHDGError(st, f"ihdg_create(device={device}) failed: no usable sm_103 GPU")
+
+    def close(self):
+        if self.h:
+            self.L.ihdg_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def last_error(self):
+        return self.L.ihdg_last_error(self.h).decode()
+
+    def _check(self, st, name, allow_nonconverged=True):
+        if st != OK:
+            raise IHDGError(st, f"{name}: {self.last_error()}")
+
+    def solve(self, mesh, coeffs, f_qp, g_qp, opts, want_trace=True):
+        """Host-buffer solve.  Returns (u [n_el, nvol], trace or None, Result)."""
+        s = problem_sizes(mesh, coeffs)
+        f = np.ascontiguousarray(f_qp, dtype=np.float64)
+        g = np.ascontiguousarray(g_qp, dtype=np.float64)
+        u = np.zeros((s.n_el, s.nvol))
+        tr = np.zeros((s.n_face, s.nface_nodes)) if want_trace else None
+        res = Result()
+        st = self.L.ihdg_solve(self.h, ctypes.byref(mesh), ctypes.byref(coeffs), _dptr(f), _dptr(g),
+                               ctypes.byref(opts), _dptr(u), _dptr(tr), ctypes.byref(res))
+        self._check(st, "ihdg_solve")
+        return u, tr, res
+
+    def solve_device(self, mesh, coeffs, d_f, d_g, opts, d_u, d_tr, d_ws, ws_bytes, stream=0):
+        """Device-pointer solve (integer pointers).  Returns Result."""
+        res = Result()
+        st = self.L.ihdg_solve_device(self.h, ctypes.byref(mesh), ctypes.byref(coeffs), ctypes.c_void_p(d_f),
+                                      ctypes.c_void_p(d_g), ctypes.byref(opts), ctypes.c_void_p(d_u),
+                                      ctypes.c_void_p(d_tr) if d_tr else None, ctypes.c_void_p(d_ws),
+                                      ctypes.c_size_t(ws_bytes), ctypes.c_void_p(stream), ctypes.byref(res))
+        self._check(st, "ihdg_solve_device")
+        return res
+
+    def swe_steps(self, mesh, coeffs, q, nsteps, opts):
+        """Host-buffer shallow-water stepping; q is updated in place.  Returns (iters, Result)."""
+        qq = np.ascontiguousarray(q, dtype=np.float64)
+        its = (ctypes.c_int * max(nsteps, 1))()
+        res = Result()
+        st = self.L.ihdg_swe_steps(self.h, ctypes.byref(mesh), ctypes.byref(coeffs), _dptr(qq), nsteps,
+                                   ctypes.byref(opts), its, ctypes.byref(res))
+        self._check(st, "ihdg_swe_steps")
+        q[...] = qq
+        return list(its)[:nsteps], res
+
+    def swe_steps_device(self, mesh, coeffs, d_q, nsteps, opts, d_ws, ws_bytes, stream=0):
+        its = (ctypes.c_int * max(nsteps, 1))()
+        res = Result()
+        st = self.L.ihdg_swe_steps_device(self.h, ctypes.byref(mesh), ctypes.byref(coeffs), ctypes.c_void_p(d_q),
+                                          nsteps, ctypes.byref(opts), its, ctypes.c_void_p(d_ws),
+                                          ctypes.c_size_t(ws_bytes), ctypes.c_void_p(stream), ctypes.byref(res))
+        self._check(st, "ihdg_swe_steps_device")
+        return list(its)[:nsteps], res

@@ -1,0 +1,367 @@
+"""GPU parity: libihdg's CUDA path against the float64 oracle, through the C ABI.
+
+Bars (written here, derived in the design notes):
+  * float64 path: the same iteration count K as the oracle (an integer decided by float64
+    residuals on both sides; a residual within 1e-9 relative of tol may land one sweep
+    apart), and relative L2 difference of u^K <= 1e-10;
+  * mixed path (float32 / bf16 inner sweeps, float64 refinement): relative L2 difference
+    <= 1e-6 from the oracle's float64 solution at the same tolerance;
+  * divergence is an integer outcome too: the same status at the same sweep.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import BoxMesh, ConvDiff, Discretisation, ShallowWater, Transport
+from oracle.ihdg import STATUS_DIVERGED, STATUS_OK
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1605_03228_gb300 import ihdg
+    c = ihdg.Context(0)
+    yield c
+    c.close()
+
+
+def ih():
+    from paper_1605_03228_gb300 import ihdg
+    return ihdg
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def oracle_trace_at_nodes(disc, T):
+    """Oracle traces are at face Gauss points; the library reports face GLL nodes.  Fit the
+    degree-p face polynomial (exact: q = p+2 points) with the oracle's own Lagrange tables."""
+    from oracle.refelem import lagrange_matrix
+    ref = disc.ref
+    B1 = lagrange_matrix(ref.nodes1, ref.xq1)
+    B = B1 if disc.d == 2 else np.kron(B1, B1)
+    coef, *_ = np.linalg.lstsq(B, T.T, rcond=None)
+    return coef.T
+
+
+def check_iteration_count(K_gpu, K_or, hist_or, tol):
+    if K_gpu == K_or:
+        return
+    assert abs(K_gpu - K_or) == 1, (K_gpu, K_or)
+    k = min(K_gpu, K_or)
+    assert abs(hist_or[k - 1] - tol) < 1e-9 * tol, "counts differ away from the tolerance boundary"
+
+
+# ------------------------------------------------------------------------------ transport
+@pytest.mark.parametrize("n,p,beta", [((8, 8), 2, (1.0, 0.5)), ((7, 5), 3, (-0.6, 1.0)),
+                                      ((6, 9), 1, (0.8, -0.3)), ((5, 6), 4, (-1.0, -0.4))])
+def test_transport2d_fp64(ctx, n, p, beta):
+    ihdg = ih()
+    mesh = ihdg.make_mesh(2, n, p)
+    co = ihdg.make_coeffs(ihdg.TRANSPORT, beta=beta)
+    vol, bnd = ihdg.quadrature_points(mesh, co)
+    f = W.transport2d_forcing(vol, beta)
+    g = W.transport2d_exact(bnd)
+    tol = 1e-10
+    u, tr, res = ctx.solve(mesh, co, f, g, ihdg.make_options(tol))
+    om = BoxMesh(2, n)
+    disc = Discretisation(om, p)
+    U, T, K, r, st, hist = Transport(disc, np.array(beta)).iterate(f, g, tol, history=True)
+    assert res.status == ihdg.OK and st == STATUS_OK
+    check_iteration_count(res.iterations, K, hist, tol)
+    assert rel(u, U.reshape(om.nel, -1)) < 1e-10
+    assert rel(tr, oracle_trace_at_nodes(disc, T)) < 1e-10
+
+
+@pytest.mark.parametrize("n,p,beta", [((4, 3, 5), 2, (1.0, 1.0, 1.0)), ((3, 4, 3), 1, (0.5, -0.8, 0.3)),
+                                      ((3, 3, 3), 2, (-0.3, 0.6, -0.9))])
+def test_transport3d_fp64(ctx, n, p, beta):
+    ihdg = ih()
+    b = np.array(beta) / np.linalg.norm(beta)
+    mesh = ihdg.make_mesh(3, n, p)
+    co = ihdg.make_coeffs(ihdg.TRANSPORT, beta=tuple(b))
+    vol, bnd = ihdg.quadrature_points(mesh, co)
+    f = W.transport3d_forcing(vol, tuple(b))
+    g = W.transport3d_exact(bnd)
+    tol = 1e-10
+    u, tr, res = ctx.solve(mesh, co, f, g, ihdg.make_options(tol))
+    om = BoxMesh(3, n)
+    disc = Discretisation(om, p)
+    U, T, K, r, st, hist = Transport(disc, b).iterate(f, g, tol, history=True)
+    check_iteration_count(res.iterations, K, hist, tol)
+    assert rel(u, U.reshape(om.nel, -1)) < 1e-10
+    assert rel(tr, oracle_trace_at_nodes(disc, T)) < 1e-10
+
+
+def test_transport_beta_axis_aligned(ctx):
+    """beta . n = 0 on the y faces: zero-weight faces, trace reported as {{u}}."""
+    ihdg = ih()
+    n, p, beta = (5, 4), 2, (1.0, 0.0)
+    mesh = ihdg.make_mesh(2, n, p)
+    co = ihdg.make_coeffs(ihdg.TRANSPORT, beta=beta)
+    vol, bnd = ihdg.quadrature_points(mesh, co)
+    f, g = W.transport2d_forcing(vol, beta), W.transport2d_exact(bnd)
+    u, tr, res = ctx.solve(mesh, co, f, g, ihdg.make_options(1e-11))
+    om = BoxMesh(2, n)
+    disc = Discretisation(om, p)
+    U, T, K, r, st = Transport(disc, np.array(beta)).iterate(f, g, 1e-11)
+    assert res.iterations == K
+    assert rel(u, U.reshape(om.nel, -1)) < 1e-10
+    assert rel(tr, oracle_trace_at_nodes(disc, T)) < 1e-10
+
+
+# ------------------------------------------------------------------------------ conv.-diff.
+@pytest.mark.parametrize("n,p,kappa,beta,nu", [((6, 7), 3, 1e-4, (1.0, 1.0), 0.0),
+                                                ((5, 4), 2, 1e-3, (-1.0, 0.5), 1.0),
+                                                ((4, 4), 4, 1e-5, (0.3, -1.0), 0.0)])
+def test_convdiff2d_fp64(ctx, n, p, kappa, beta, nu):
+    ihdg = ih()
+    mesh = ihdg.make_mesh(2, n, p)
+    co = ihdg.make_coeffs(ihdg.CONVDIFF, beta=beta, kappa=kappa, nu=nu)
+    vol, bnd = ihdg.quadrature_points(mesh, co)
+    f = W.convdiff_forcing(vol, kappa, beta, nu)
+    g = W.convdiff_exact(bnd)
+    tol = 1e-10
+    u, tr, res = ctx.solve(mesh, co, f, g, ihdg.make_options(tol, max_iters=3000))
+    om = BoxMesh(2, n)
+    disc = Discretisation(om, p)
+    U, T, K, r, st, hist = ConvDiff(disc, np.array(beta), kappa, nu).iterate(f, g, tol, max_iters=3000, history=True)
+    assert st == STATUS_OK and res.status == ihdg.OK
+    check_iteration_count(res.iterations, K, hist, tol)
+    assert rel(u, U.reshape(om.nel, -1)) < 1e-10
+    assert rel(tr, oracle_trace_at_nodes(disc, T)) < 1e-10
+
+
+def test_convdiff_diverges_like_oracle(ctx):
+    """kappa = 1e-2 at h = 1/256 (the 2D convection-diffusion workload's element size): the
+    iteration diverges; both sides stop with DIVERGED at the same sweep, same iterate."""
+    ihdg = ih()
+    n, p, h = (6, 6), 3, 1.0 / 256
+    mesh = ihdg.make_mesh(2, n, p, hi=(n[0] * h, n[1] * h))
+    co = ihdg.make_coeffs(ihdg.CONVDIFF, beta=(1.0, 1.0), kappa=1e-2)
+    vol, bnd = ihdg.quadrature_points(mesh, co)
+    f, g = W.convdiff_forcing(vol, 1e-2), W.convdiff_exact(bnd)
+    u, tr, res = ctx.solve(mesh, co, f, g, ihdg.make_options(1e-8))
+    om = BoxMesh(2, n, hi=[n[0] * h, n[1] * h])
+    disc = Discretisation(om, p)
+    U, T, K, r, st = ConvDiff(disc, np.array([1.0, 1.0]), 1e-2).iterate(f, g, 1e-8)
+    assert st == STATUS_DIVERGED and res.status == ihdg.DIVERGED
+    assert res.iterations == K
+    assert rel(u, U.reshape(om.nel, -1)) < 1e-9
+
+
+def test_convdiff3d_fp64(ctx):
+    ihdg = ih()
+    n, p, kappa, beta = (3, 4, 3), 2, 1e-4, (0.6, 0.5, -0.7)
+    mesh = ihdg.make_mesh(3, n, p)
+    co = ihdg.make_coeffs(ihdg.CONVDIFF, beta=beta, kappa=kappa, nu=0.5)
+    vol, bnd = ihdg.quadrature_points(mesh, co)
+    rng = np.random.default_rng(5)
+    f = rng.standard_normal(vol.shape[:2])
+    g = rng.standard_normal(bnd.shape[:2])
+    u, tr, res = ctx.solve(mesh, co, f, g, ihdg.make_options(1e-10, max_iters=3000))
+    om = BoxMesh(3, n)
+    disc = Discretisation(om, p)
+    U, T, K, r, st, hist = ConvDiff(disc, np.array(beta), kappa, 0.5).iterate(f, g, 1e-10, max_iters=3000, history=True)
+    check_iteration_count(res.iterations, K, hist, 1e-10)
+    assert rel(u, U.reshape(om.nel, -1)) < 1e-10
+
+
+# ------------------------------------------------------------------------------ edge cases
+def test_single_element_and_zero_data(ctx):
+    ihdg = ih()
+    mesh = ihdg.make_mesh(2, (1, 1), 2)
+    co = ihdg.make_coeffs(ihdg.TRANSPORT, beta=(1.0, 0.5))
+    vol, bnd = ihdg.quadrature_points(mesh, co)
+    u, tr, res = ctx.solve(mesh, co, np.zeros(vol.shape[:2]), np.zeros(bnd.shape[:2]), ihdg.make_options(1e-10))
+    assert res.status == ihdg.OK and res.iterations == 1 and np.abs(u).max() == 0.0
+    f, g = W.transport2d_forcing(vol), W.transport2d_exact(bnd)
+    u, tr, res = ctx.solve(mesh, co, f, g, ihdg.make_options(1e-12))
+    om = BoxMesh(2, (1, 1))
+    disc = Discretisation(om, 2)
+    U, T, K, r, st = Transport(disc, np.array([1.0, 0.5])).iterate(f, g, 1e-12)
+    assert res.iterations == K and rel(u, U.reshape(1, -1)) < 1e-12
+
+
+def test_max_iters_and_initial_guess(ctx):
+    ihdg = ih()
+    n, p = (9, 4), 2
+    mesh = ihdg.make_mesh(2, n, p)
+    co = ihdg.make_coeffs(ihdg.TRANSPORT, beta=(1.0, 0.5))
+    vol, bnd = ihdg.quadrature_points(mesh, co)
+    f, g = W.transport2d_forcing(vol), W.transport2d_exact(bnd)
+    om = BoxMesh(2, n)
+    disc = Discretisation(om, p)
+    pr = Transport(disc, np.array([1.0, 0.5]))
+    u, tr, res = ctx.solve(mesh, co, f, g, ihdg.make_options(1e-14, max_iters=7))
+    U, T, K, r, st = pr.iterate(f, g, 1e-14, max_iters=7)
+    assert res.status == ihdg.NOT_CONVERGED and res.iterations == 7 == K
+    assert rel(u, U.reshape(om.nel, -1)) < 1e-12
+    u0 = np.random.default_rng(2).standard_normal((om.nel, disc.nb))
+    o = ihdg.make_options(1e-10)
+    o.u0 = u0.ctypes.data
+    u, tr, res = ctx.solve(mesh, co, f, g, o)
+    U, T, K, r, st = pr.iterate(f, g, 1e-10, U0=u0.reshape(om.nel, 1, -1))
+    assert res.iterations == K and rel(u, U.reshape(om.nel, -1)) < 1e-10
+
+
+# ------------------------------------------------------------------------------ shallow water
+@pytest.mark.parametrize("n,p,ratio,fc,gam", [((8, 8), 2, 0.5, 0.0, 0.0), ((6, 7), 3, 1.0, 0.4, 0.05)])
+def test_swe_steps_fp64(ctx, n, p, ratio, fc, gam):
+    ihdg = ih()
+    h = 1.0 / n[0]
+    dt = ratio * h / ((p + 1) * (p + 2))
+    mesh = ihdg.make_mesh(2, n, p)
+    co = ihdg.make_coeffs(ihdg.SWE, Phi=1.0, dt=dt, coriolis_f=fc, friction=gam)
+    nodes = ihdg.node_points(mesh, co)
+    q0 = W.swe_bump(nodes, seed=0, width=0.15)
+    q = q0.reshape(q0.shape[0], -1).copy()
+    its, res = ctx.swe_steps(mesh, co, q, 3, ihdg.make_options(1e-10))
+    om = BoxMesh(2, n)
+    disc = Discretisation(om, p)
+    pr = ShallowWater(disc, 1.0, dt, fc, gam)
+    U = q0.copy()
+    for s in range(3):
+        U, T, K, r, st = pr.step(U, 1e-10)
+        assert its[s] == K
+    assert rel(q, U.reshape(om.nel, -1)) < 1e-10
+
+
+# ------------------------------------------------------------------------------ mixed precision
+@pytest.mark.parametrize("prec_name", ["MIXED_FP32", "MIXED_BF16"])
+def test_mixed_transport2d(ctx, prec_name):
+    ihdg = ih()
+    n, p, beta = (24, 24), 2, (1.0, 0.5)
+    mesh = ihdg.make_mesh(2, n, p)
+    co = ihdg.make_coeffs(ihdg.TRANSPORT, beta=beta)
+    vol, bnd = ihdg.quadrature_points(mesh, co)
+    f, g = W.transport2d_forcing(vol), W.transport2d_exact(bnd)
+    u, tr, res = ctx.solve(mesh, co, f, g, ihdg.make_options(1e-10, prec=getattr(ihdg, prec_name)))
+    om = BoxMesh(2, n)
+    disc = Discretisation(om, p)
+    U, T, K, r, st = Transport(disc, np.array(beta)).iterate(f, g, 1e-10)
+    assert res.status == ihdg.OK, res.as_dict()
+    assert res.fp64_sweeps >= 2 and res.lowp_sweeps > 0
+    assert rel(u, U.reshape(om.nel, -1)) < 1e-6
+    assert rel(tr, oracle_trace_at_nodes(disc, T)) < 1e-6
+
+
+@pytest.mark.parametrize("prec_name", ["MIXED_FP32", "MIXED_BF16"])
+def test_mixed_transport3d(ctx, prec_name):
+    ihdg = ih()
+    n, p = (6, 6, 6), 2
+    b = tuple(np.ones(3) / np.sqrt(3))
+    mesh = ihdg.make_mesh(3, n, p)
+    co = ihdg.make_coeffs(ihdg.TRANSPORT, beta=b)
+    vol, bnd = ihdg.quadrature_points(mesh, co)
+    f, g = W.transport3d_forcing(vol, b), W.transport3d_exact(bnd)
+    u, tr, res = ctx.solve(mesh, co, f, g, ihdg.make_options(1e-8, prec=getattr(ihdg, prec_name)))
+    om = BoxMesh(3, n)
+    disc = Discretisation(om, p)
+    U, T, K, r, st = Transport(disc, np.array(b)).iterate(f, g, 1e-8)
+    assert res.status == ihdg.OK, res.as_dict()
+    assert rel(u, U.reshape(om.nel, -1)) < 1e-6
+
+
+def test_mixed_convdiff(ctx):
+    ihdg = ih()
+    n, p, kappa = (12, 10), 3, 1e-4
+    mesh = ihdg.make_mesh(2, n, p)
+    co = ihdg.make_coeffs(ihdg.CONVDIFF, beta=(1.0, 1.0), kappa=kappa)
+    vol, bnd = ihdg.quadrature_points(mesh, co)
+    f, g = W.convdiff_forcing(vol, kappa), W.convdiff_exact(bnd)
+    u, tr, res = ctx.solve(mesh, co, f, g, ihdg.make_options(1e-8, prec=ihdg.MIXED_FP32))
+    om = BoxMesh(2, n)
+    disc = Discretisation(om, p)
+    U, T, K, r, st = ConvDiff(disc, np.array([1.0, 1.0]), kappa).iterate(f, g, 1e-8)
+    assert res.status == ihdg.OK, res.as_dict()
+    assert rel(u, U.reshape(om.nel, -1)) < 1e-6
+
+
+# ------------------------------------------------------------------------------ device API
+def test_device_api_matches_host_api(ctx):
+    ihdg = ih()
+    n, p, beta = (16, 12), 3, (0.7, 1.0)
+    mesh = ihdg.make_mesh(2, n, p)
+    co = ihdg.make_coeffs(ihdg.TRANSPORT, beta=beta)
+    vol, bnd = ihdg.quadrature_points(mesh, co)
+    f, g = W.transport2d_forcing(vol, beta), W.transport2d_exact(bnd)
+    opts = ihdg.make_options(1e-10)
+    u_h, tr_h, res_h = ctx.solve(mesh, co, f, g, opts)
+    s = ihdg.problem_sizes(mesh, co)
+    dev = torch.device("cuda:0")
+    df = torch.from_numpy(np.ascontiguousarray(f)).to(dev)
+    dg = torch.from_numpy(np.ascontiguousarray(g)).to(dev)
+    du = torch.empty((s.n_el, s.nvol), dtype=torch.float64, device=dev)
+    dt = torch.empty((s.n_face, s.nface_nodes), dtype=torch.float64, device=dev)
+    nws = ihdg.workspace_bytes(mesh, co, opts)
+    ws = torch.empty(nws + 256, dtype=torch.uint8, device=dev)
+    base = (ws.data_ptr() + 255) // 256 * 256
+    stream = torch.cuda.current_stream().cuda_stream
+    res = ctx.solve_device(mesh, co, df.data_ptr(), dg.data_ptr(), opts, du.data_ptr(), dt.data_ptr(), base, nws, stream)
+    assert res.iterations == res_h.iterations
+    assert np.array_equal(du.cpu().numpy(), u_h) and np.array_equal(dt.cpu().numpy(), tr_h)
+
+
+# ------------------------------------------------------------------------------ full size, sampled
+def patch_oracle_sweeps(kind, nfull, p, h, k, centers, coeff, f_fun, g_fun):
+    """u^k at sampled elements by the oracle on a patch that holds every element within k
+    of the sample (after k sweeps nothing farther away can reach it)."""
+    out = []
+    d = len(nfull)
+    for c in centers:
+        lo_i = [max(0, c[a] - k - 1) for a in range(d)]
+        hi_i = [min(nfull[a], c[a] + k + 2) for a in range(d)]
+        nn = [hi_i[a] - lo_i[a] for a in range(d)]
+        om = BoxMesh(d, nn, lo=[lo_i[a] * h for a in range(d)], hi=[hi_i[a] * h for a in range(d)])
+        disc = Discretisation(om, p)
+        pr = coeff(disc)
+        f = f_fun(disc.volume_points())
+        g = g_fun(disc.boundary_points())
+        U, T, K, r, st = pr.iterate(f, g, 0.0, max_iters=k, diverge_factor=np.inf)
+        loc = sum((c[a] - lo_i[a]) * int(np.prod(nn[:a])) for a in range(d))
+        out.append(U[loc].ravel())
+    return np.array(out)
+
+
+def test_full_size_convdiff_sampled(ctx):
+    """The 2D convection-diffusion workload at full size (256^2, p = 3), k float64 sweeps,
+    sampled elements against the oracle on dependency patches."""
+    ihdg = ih()
+    n, p, kappa, k = (256, 256), 3, 1e-2, 4
+    mesh = ihdg.make_mesh(2, n, p)
+    co = ihdg.make_coeffs(ihdg.CONVDIFF, beta=(1.0, 1.0), kappa=kappa)
+    vol, bnd = ihdg.quadrature_points(mesh, co)
+    f, g = W.convdiff_forcing(vol, kappa), W.convdiff_exact(bnd)
+    u, tr, res = ctx.solve(mesh, co, f, g, ihdg.make_options(0.0, max_iters=k, diverge_factor=-1.0))
+    assert res.iterations == k
+    rng = np.random.default_rng(0)
+    centers = [(0, 0), (255, 255), (0, 200), (128, 3)] + [tuple(rng.integers(0, 256, 2)) for _ in range(4)]
+    ref = patch_oracle_sweeps("cd", n, p, 1 / 256, k, centers,
+                              lambda disc: ConvDiff(disc, np.array([1.0, 1.0]), kappa),
+                              lambda X: W.convdiff_forcing(X, kappa), W.convdiff_exact)
+    got = np.array([u[c[0] + 256 * c[1]] for c in centers])
+    assert rel(got, ref) < 1e-10
+
+
+def test_full_size_transport3d_sampled(ctx):
+    """The 3D transport workload at full size (64^3, p = 2), k float64 sweeps, sampled."""
+    ihdg = ih()
+    n, p, k = (64, 64, 64), 2, 3
+    b = tuple(np.ones(3) / np.sqrt(3))
+    mesh = ihdg.make_mesh(3, n, p)
+    co = ihdg.make_coeffs(ihdg.TRANSPORT, beta=b)
+    vol, bnd = ihdg.quadrature_points(mesh, co)
+    f, g = W.transport3d_forcing(vol, b), W.transport3d_exact(bnd)
+    u, tr, res = ctx.solve(mesh, co, f, g, ihdg.make_options(0.0, max_iters=k, diverge_factor=-1.0))
+    centers = [(0, 0, 0), (63, 63, 63), (5, 40, 63), (31, 2, 17)]
+    ref = patch_oracle_sweeps("tr", n, p, 1 / 64, k, centers, lambda disc: Transport(disc, np.array(b)),
+                              lambda X: W.transport3d_forcing(X, b), W.transport3d_exact)
+    got = np.array([u[c[0] + 64 * (c[1] + 64 * c[2])] for c in centers])
+    assert rel(got, ref) < 1e-10

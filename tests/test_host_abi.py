@@ -1,0 +1,184 @@
+"""CPU tests of libihdg's host side: the library loads and exports every symbol the header
+declares; geometry queries agree with the oracle's own point generators; argument checks;
+and the library's float64 operators (built independently of the oracle) reproduce one
+oracle sweep when applied on the CPU in the export form.  No compute call needs a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import BoxMesh, ConvDiff, Discretisation, ShallowWater, Transport
+from paper_1605_03228_gb300 import ihdg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_symbols():
+    src = open(os.path.join(ROOT, "include", "ihdg.h")).read()
+    return sorted(set(re.findall(r"\b(ihdg_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = ihdg.load()
+    syms = header_symbols()
+    assert len(syms) >= 11
+    for s in syms:
+        assert hasattr(L, s), s
+
+
+def test_create_without_gpu_fails_cleanly():
+    try:
+        import torch
+        has_gpu = torch.cuda.is_available()
+    except Exception:
+        has_gpu = False
+    if has_gpu:
+        pytest.skip("a GPU is present")
+    with pytest.raises(ihdg.IHDGError) as e:
+        ihdg.Context(0)
+    assert e.value.status == ihdg.ERR_CUDA
+
+
+@pytest.mark.parametrize("dim,n,p", [(2, (3, 2), 2), (3, (2, 3, 2), 1)])
+def test_points_match_oracle(dim, n, p):
+    mesh = ihdg.make_mesh(dim, n, p, lo=(0.1, -0.2, 0.3), hi=(1.3, 0.7, 0.9))
+    co = ihdg.make_coeffs(ihdg.TRANSPORT, beta=(1.0, 0.5, 0.3))
+    vol, bnd = ihdg.quadrature_points(mesh, co)
+    nodes = ihdg.node_points(mesh, co)
+    om = BoxMesh(dim, n, lo=[0.1, -0.2, 0.3][:dim], hi=[1.3, 0.7, 0.9][:dim])
+    disc = Discretisation(om, p)
+    assert np.abs(vol - disc.volume_points()).max() < 1e-14
+    assert np.abs(bnd - disc.boundary_points()).max() < 1e-14
+    assert np.abs(nodes - disc.node_points()).max() < 1e-14
+
+
+def test_sizes():
+    mesh = ihdg.make_mesh(2, (256, 256), 3)
+    co = ihdg.make_coeffs(ihdg.CONVDIFF, beta=(1, 1), kappa=1e-2)
+    s = ihdg.problem_sizes(mesh, co)
+    assert (s.n_el, s.nvol, s.ncomp, s.nqv, s.nqf) == (65536, 48, 3, 25, 5)
+    assert s.n_face == 2 * 257 * 256 and s.n_bface == 4 * 256
+    assert (s.n_exp, s.n_in, s.nface_nodes) == (16, 16, 4)
+
+
+def test_invalid_arguments_rejected():
+    L = ihdg.load()
+    s = ihdg.Sizes()
+    bad = [
+        (ihdg.make_mesh(4, (2, 2), 2), ihdg.make_coeffs(ihdg.TRANSPORT, beta=(1, 1))),
+        (ihdg.make_mesh(2, (0, 2), 2), ihdg.make_coeffs(ihdg.TRANSPORT, beta=(1, 1))),
+        (ihdg.make_mesh(2, (2, 2), 2, hi=(0.0, 1.0)), ihdg.make_coeffs(ihdg.TRANSPORT, beta=(1, 1))),
+        (ihdg.make_mesh(2, (2, 2), 2), ihdg.make_coeffs(ihdg.CONVDIFF, beta=(1, 1), kappa=0.0)),
+        (ihdg.make_mesh(2, (2, 2), 2), ihdg.make_coeffs(ihdg.SWE, Phi=1.0, dt=0.0)),
+        (ihdg.make_mesh(2, (2, 2), 2), ihdg.make_coeffs(ihdg.TRANSPORT, beta=(0, 0))),
+    ]
+    for m, c in bad:
+        assert L.ihdg_problem_sizes(ctypes.byref(m), ctypes.byref(c), ctypes.byref(s)) == ihdg.ERR_INVALID
+    m3 = ihdg.make_mesh(3, (2, 2, 2), 2)
+    c3 = ihdg.make_coeffs(ihdg.SWE, Phi=1.0, dt=0.1)
+    assert L.ihdg_problem_sizes(ctypes.byref(m3), ctypes.byref(c3), ctypes.byref(s)) == ihdg.ERR_UNSUPPORTED
+    m = ihdg.make_mesh(2, (2, 2), 5)
+    c = ihdg.make_coeffs(ihdg.TRANSPORT, beta=(1, 1))
+    assert L.ihdg_problem_sizes(ctypes.byref(m), ctypes.byref(c), ctypes.byref(s)) == ihdg.ERR_UNSUPPORTED
+    assert L.ihdg_problem_sizes(None, ctypes.byref(c), ctypes.byref(s)) == ihdg.ERR_INVALID
+
+
+# ---------------------------------------------------------------- export-form sweep on the CPU
+def export_gather(E, om, kinds, own_off, nbr_off, nf, mirror):
+    """Trace inputs t (nel, 2d*nf) from exports E (nel, n_exp), as the sweep's step a1."""
+    nel, d = om.nel, om.d
+    t = np.zeros((nel, 2 * d * nf))
+    for K in range(nel):
+        for f in range(2 * d):
+            nb = om.nbr[K, f]
+            for j in range(nf):
+                s = f * nf + j
+                if kinds[f] == "own":
+                    t[K, s] = E[K, own_off[f] + j]
+                elif kinds[f] == "nbr":
+                    t[K, s] = E[nb, nbr_off[f] + j] if nb >= 0 else 0.0
+                elif kinds[f] == "sum":
+                    o = E[K, own_off[f] + j]
+                    t[K, s] = o + E[nb, nbr_off[f] + j] if nb >= 0 else (2 * o if mirror else 0.0)
+    return t
+
+
+def check_one_sweep(mesh, co, problem, kinds, own_off, nbr_off, mirror, U_prev=None):
+    Lvol = ihdg.host_operator(mesh, co, 2)
+    R = ihdg.host_operator(mesh, co, 3)
+    LE = ihdg.host_operator(mesh, co, 0)
+    Q = ihdg.host_operator(mesh, co, 1)
+    assert np.abs(LE - R @ Lvol).max() < 1e-12 * max(1, np.abs(LE).max())
+    om, disc = problem.mesh, problem.disc
+    rng = np.random.default_rng(3)
+    U = rng.standard_normal((om.nel, problem.nc, disc.nb))
+    E = U.reshape(om.nel, -1) @ R.T
+    t = export_gather(E, om, kinds, own_off, nbr_off, disc.ref.nb1 ** (om.d - 1), mirror)
+    u_lib = t @ Lvol.T
+    if problem.__class__ is ShallowWater:
+        zero = np.zeros_like(U)
+        u_or = problem.sweep(U, None, None, U_prev=zero)
+    else:
+        f = np.zeros((om.nel, disc.nq))
+        g = np.zeros((om.nbface, disc.nqf))
+        u_or = problem.sweep(U, f, g)
+    assert np.abs(u_lib - u_or.reshape(om.nel, -1)).max() < 1e-11 * max(1.0, np.abs(u_or).max())
+    # the stopping-norm operator: ||L_vol dt||^2 in the problem's norm equals dt^T Q dt
+    dt = rng.standard_normal((om.nel, Lvol.shape[1]))
+    du = (dt @ Lvol.T).reshape(om.nel, problem.nc, disc.nb)
+    assert abs(np.einsum("ki,ij,kj->", dt, Q, dt) - problem.norm2(du)) < 1e-10 * problem.norm2(du)
+
+
+@pytest.mark.parametrize("p", [1, 3])
+def test_export_form_matches_oracle_transport(p):
+    beta = (1.0, 0.5)
+    mesh = ihdg.make_mesh(2, (3, 3), p)
+    co = ihdg.make_coeffs(ihdg.TRANSPORT, beta=beta)
+    om = BoxMesh(2, (3, 3))
+    pr = Transport(Discretisation(om, p), np.array(beta))
+    nf = p + 1
+    kinds = ["nbr", "own", "nbr", "own"]          # beta > 0: -x, -y inflow; +x, +y outflow
+    own_off = [0, 0, 0, nf]
+    nbr_off = [0, 0, nf, 0]
+    check_one_sweep(mesh, co, pr, kinds, own_off, nbr_off, False)
+    # forcing part: u^1 from u^0 = 0 with g = 0 is PV f
+    PV = ihdg.host_operator(mesh, co, 5)
+    f = np.random.default_rng(1).standard_normal((om.nel, pr.disc.nq))
+    u1 = pr.sweep(np.zeros((om.nel, 1, pr.disc.nb)), f, np.zeros((om.nbface, pr.disc.nqf)))
+    assert np.abs(f @ PV.T - u1.reshape(om.nel, -1)).max() < 1e-12
+
+
+@pytest.mark.parametrize("p", [1, 3])
+def test_export_form_matches_oracle_convdiff(p):
+    beta, kappa, nu = (1.0, -0.7), 0.05, 0.3
+    mesh = ihdg.make_mesh(2, (3, 3), p)
+    co = ihdg.make_coeffs(ihdg.CONVDIFF, beta=beta, kappa=kappa, nu=nu)
+    om = BoxMesh(2, (3, 3))
+    pr = ConvDiff(Discretisation(om, p), np.array(beta), kappa, nu)
+    nf = p + 1
+    kinds = ["sum"] * 4
+    own_off = [f * nf for f in range(4)]
+    nbr_off = [(f ^ 1) * nf for f in range(4)]
+    check_one_sweep(mesh, co, pr, kinds, own_off, nbr_off, False)
+
+
+def test_export_form_matches_oracle_convdiff_3d():
+    beta, kappa = (0.6, -0.4, 0.7), 0.1
+    mesh = ihdg.make_mesh(3, (2, 2, 2), 1)
+    co = ihdg.make_coeffs(ihdg.CONVDIFF, beta=beta, kappa=kappa)
+    om = BoxMesh(3, (2, 2, 2))
+    pr = ConvDiff(Discretisation(om, 1), np.array(beta), kappa, 0.0)
+    nf = 4
+    check_one_sweep(mesh, co, pr, ["sum"] * 6, [f * nf for f in range(6)], [(f ^ 1) * nf for f in range(6)], False)
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_export_form_matches_oracle_swe(p):
+    mesh = ihdg.make_mesh(2, (3, 3), p)
+    co = ihdg.make_coeffs(ihdg.SWE, Phi=1.5, dt=0.01, coriolis_f=0.3, friction=0.1)
+    om = BoxMesh(2, (3, 3))
+    pr = ShallowWater(Discretisation(om, p), 1.5, 0.01, 0.3, 0.1)
+    nf = p + 1
+    check_one_sweep(mesh, co, pr, ["sum"] * 4, [f * nf for f in range(4)], [(f ^ 1) * nf for f in range(4)], True)
