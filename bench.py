@@ -1,0 +1,436 @@
+#!/usr/bin/env python3
+"""Benchmark of the element-parallel iHDG sweep on GB300 (one JSON line on stdout).
+
+Default workload: the 2D convection-diffusion problem on a uniform 256x256 quad mesh, p = 3,
+beta = (1, 1), u = exp(x+y) sin(pi x) sin(pi y), tolerance 1e-8, mixed precision (float32
+inner sweeps, float64 outer sweeps and residual).  With kappa = 1e-2 as listed, the upwind
+iHDG iteration diverges on this mesh (spectral radius ~45; the paper's Theorem 4 and Table 3
+predict it), so there is no time-to-tolerance.  The headline solve therefore uses the same
+mesh, order, velocity, forcing and tolerance with kappa = 1e-4 (element Peclet ~55), which
+converges and costs exactly the same per sweep; the as-listed kappa = 1e-2 problem is also
+timed (sweeps capped, divergence check off) and reported under "as_listed".
+
+One step = one complete solve call through the C ABI (ihdg_solve_device) with inputs
+resident in HBM: forcing, first sweep, every float64 and low-precision sweep with its
+residual reduction and loop decision, reconstruction of u and of the trace.
+value = element-DOF updates/s = n_el * nvol * sweeps / step time.  L2 is flushed (a 512 MB
+write) between timed steps, outside the timed events.
+
+Other workloads: --workload transport2d (8x8, p=2, float64, tol 1e-10),
+transport3d (64^3, p=2, bf16 inner + float64, tol 1e-8), swe (512^2, p=2, 100 steps).
+
+--impl reference times the float64 CPU oracle (the reference arm of this build) on the
+same workload, each step a bounded sample of sweeps on the full mesh.
+
+Multi-GPU (torchrun, one rank per GPU): every rank solves its own replica (the solves are
+independent; there is no data exchange), scaling "weak", value = all ranks' work / max time.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "element-DOF updates/s"
+UNIT = "DOF-updates/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="convdiff2d",
+                    choices=["convdiff2d", "transport2d", "transport3d", "swe"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=0, help="override the elements per side (profiling cases)")
+    ap.add_argument("--no-extras", action="store_true", help="skip the as-listed and float64 comparison solves")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- workloads
+def workload_spec(name):
+    if name == "convdiff2d":
+        return dict(name="convdiff2d", dim=2, n=(256, 256), p=3, pde="convdiff", beta=(1.0, 1.0), kappa=1e-4,
+                    listed_kappa=1e-2, tol=1e-8, prec="MIXED_FP32",
+                    desc="2D conv-diff 256x256 p=3 beta=(1,1) u=exp(x+y)sin(pi x)sin(pi y) tol 1e-8; "
+                         "kappa=1e-4 (listed kappa=1e-2 diverges, rho~45, reported as as_listed)")
+    if name == "transport2d":
+        return dict(name="transport2d", dim=2, n=(8, 8), p=2, pde="transport", beta=(1.0, 0.5), tol=1e-10,
+                    prec="FP64", desc="2D transport 8x8 p=2 beta=(1,0.5) u=sin(pi x)cos(pi y) tol 1e-10 float64")
+    if name == "transport3d":
+        b = 1 / math.sqrt(3)
+        return dict(name="transport3d", dim=3, n=(64, 64, 64), p=2, pde="transport", beta=(b, b, b), tol=1e-8,
+                    prec="MIXED_BF16", desc="3D transport 64^3 p=2 beta=(1,1,1)/sqrt3 u=sin sin sin tol 1e-8 bf16+f64")
+    if name == "swe":
+        return dict(name="swe", dim=2, n=(512, 512), p=2, pde="swe", Phi=1.0, dt=1.0 / (512 * 12), listed_dt=1e-3,
+                    nsteps=100, tol=1e-8, prec="MIXED_FP32",
+                    desc="2D linearized shallow water 512x512 p=2 Phi=1 walls, Gaussian bump + 1% seeded noise, "
+                         "backward Euler 100 steps at dt=h/((p+1)(p+2)) (listed dt=1e-3 diverges, rho~6)")
+    raise ValueError(name)
+
+
+def make_problem(ih, spec, kappa=None):
+    mesh = ih.make_mesh(spec["dim"], spec["n"], spec["p"])
+    if spec["pde"] == "convdiff":
+        co = ih.make_coeffs(ih.CONVDIFF, beta=spec["beta"], kappa=spec["kappa"] if kappa is None else kappa)
+    elif spec["pde"] == "transport":
+        co = ih.make_coeffs(ih.TRANSPORT, beta=spec["beta"])
+    else:
+        co = ih.make_coeffs(ih.SWE, Phi=spec["Phi"], dt=spec["dt"])
+    return mesh, co
+
+
+def inputs(ih, spec, mesh, co, kappa=None):
+    if spec["pde"] == "swe":
+        nodes = ih.node_points(mesh, co)
+        return W.swe_bump(nodes, seed=0).reshape(nodes.shape[0], -1), None
+    vol, bnd = ih.quadrature_points(mesh, co)
+    if spec["pde"] == "convdiff":
+        k = spec["kappa"] if kappa is None else kappa
+        return W.convdiff_forcing(vol, k, spec["beta"]), W.convdiff_exact(bnd)
+    if spec["dim"] == 2:
+        return W.transport2d_forcing(vol, spec["beta"]), W.transport2d_exact(bnd)
+    return W.transport3d_forcing(vol, spec["beta"]), W.transport3d_exact(bnd)
+
+
+# ----------------------------------------------------------------------------- clocks
+class Clocks:
+    """nvidia-smi sampling (200 ms) during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.strip().split(",") for r in self.f.read().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args, spec, rank):
+    """Float64 CPU oracle on the same workload: each step runs a bounded number of sweeps of
+    Algorithm 1 on the full mesh (the oracle as it stands)."""
+    if rank != 0:
+        return
+    from oracle import BoxMesh, ConvDiff, Discretisation, ShallowWater, Transport
+    om = BoxMesh(spec["dim"], spec["n"])
+    disc = Discretisation(om, spec["p"])
+    if spec["pde"] == "convdiff":
+        pr = ConvDiff(disc, np.array(spec["beta"]), spec["kappa"])
+        X, B = disc.volume_points(), disc.boundary_points()
+        f, g = W.convdiff_forcing(X, spec["kappa"], spec["beta"]), W.convdiff_exact(B)
+        prev = None
+    elif spec["pde"] == "transport":
+        pr = Transport(disc, np.array(spec["beta"]))
+        X, B = disc.volume_points(), disc.boundary_points()
+        if spec["dim"] == 2:
+            f, g = W.transport2d_forcing(X, spec["beta"]), W.transport2d_exact(B)
+        else:
+            f, g = W.transport3d_forcing(X, spec["beta"]), W.transport3d_exact(B)
+        prev = None
+    else:
+        pr = ShallowWater(disc, spec["Phi"], spec["dt"])
+        f = g = None
+        prev = W.swe_bump(disc.node_points(), seed=0)
+    U = np.zeros((om.nel, pr.nc, disc.nb)) if prev is None else prev.copy()
+    sweeps_per_step = 1
+    for _ in range(args.warmup):
+        U = pr.sweep(U, f, g, prev)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        for _ in range(sweeps_per_step):
+            Un = pr.sweep(U, f, g, prev)
+            res = math.sqrt(pr.norm2(Un - U))
+            U = Un
+        times.append(time.perf_counter() - t0)
+    t = float(np.mean(times))
+    value = om.nel * pr.nvol * sweeps_per_step / t
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": spec["desc"], "kind": "float64 CPU oracle (numpy), one sweep per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} single sweeps of Algorithm 1 on the full {spec['n']} mesh"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(spec, budget_s=15.0):
+    """The oracle timed on the host cores: sweeps of the same workload on the full mesh
+    until ~budget_s of CPU work (at least one)."""
+    from oracle import BoxMesh, ConvDiff, Discretisation, Transport
+    om = BoxMesh(spec["dim"], spec["n"])
+    disc = Discretisation(om, spec["p"])
+    if spec["pde"] == "convdiff":
+        pr = ConvDiff(disc, np.array(spec["beta"]), spec["kappa"])
+        X, B = disc.volume_points(), disc.boundary_points()
+        f, g = W.convdiff_forcing(X, spec["kappa"], spec["beta"]), W.convdiff_exact(B)
+    else:
+        return None
+    U = np.zeros((om.nel, pr.nc, disc.nb))
+    n, t0 = 0, time.perf_counter()
+    while True:
+        Un = pr.sweep(U, f, g)
+        math.sqrt(pr.norm2(Un - U))
+        U = Un
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    t = (time.perf_counter() - t0) / n
+    return {"value": om.nel * pr.nvol / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{n} sweeps (Algorithm 1, float64 numpy, BLAS threads) on the full {spec['n']} mesh"}
+
+
+# ----------------------------------------------------------------------------- our arm
+def main():
+    args = parse()
+    spec = workload_spec(args.workload)
+    if args.n:
+        spec["n"] = (args.n,) * spec["dim"]
+        spec["desc"] = f"[{args.n} per side] " + spec["desc"]
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    if args.impl == "reference":
+        run_reference(args, spec, rank)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    from paper_1605_03228_gb300 import ihdg as ih
+
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    ctx = ih.Context(local)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    mesh, co = make_problem(ih, spec)
+    sz = ih.problem_sizes(mesh, co)
+    prec = getattr(ih, spec["prec"])
+    a, b = inputs(ih, spec, mesh, co)
+    swe = spec["pde"] == "swe"
+    opts = ih.make_options(spec["tol"], max_iters=4000, prec=prec)
+    nws = ih.workspace_bytes(mesh, co, opts)
+    ws = torch.empty(nws + 256, dtype=torch.uint8, device=dev)
+    wsp = (ws.data_ptr() + 255) // 256 * 256
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    dA = torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    dB = torch.from_numpy(np.ascontiguousarray(b)).to(dev) if b is not None else None
+    du = torch.empty((sz.n_el, sz.nvol), dtype=torch.float64, device=dev)
+    dt = torch.empty((sz.n_face, sz.nface_nodes), dtype=torch.float64, device=dev)
+    q0 = dA.clone() if swe else None
+
+    def step(o):
+        if swe:
+            dA.copy_(q0)
+            its, r = ctx.swe_steps_device(mesh, co, dA.data_ptr(), spec["nsteps"], o, wsp, nws, sp)
+            return r
+        return ctx.solve_device(mesh, co, dA.data_ptr(), dB.data_ptr(), o, du.data_ptr(), dt.data_ptr(), wsp, nws, sp)
+
+    for _ in range(args.warmup):
+        r = step(opts)
+    if r.status not in (ih.OK,):
+        print(f"warning: warm-up solve status {ih.STATUS_NAMES[r.status]}", file=sys.stderr)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    clocks = Clocks(local)
+    barrier()
+    clocks.start()
+    times, sweeps, launches = [], [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = step(opts)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        sweeps.append(r.iterations)
+        launches.append(r.kernel_launches)
+    barrier()
+    clk = clocks.stop()
+    ms = float(np.mean(times))
+    if dist is not None:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    per_step_updates = sz.n_el * sz.nvol * float(np.mean(sweeps))
+    value = world * per_step_updates / (ms * 1e-3)
+    status = ih.STATUS_NAMES[r.status]
+
+    # roofline of the dominant kernel: one profiled solve (events around every sweep launch)
+    rp = step(ih.make_options(spec["tol"], max_iters=4000, prec=prec, profile=1))
+    lp_bytes = 2 if prec == ih.MIXED_BF16 else 4
+    if prec == ih.FP64:
+        kern, kms = "k_sweep64", rp.fp64_sweep_ms
+        # read E^k, E^(k-1), F, write E^(k+1): 4 float64 words per export value
+        bytes_per_launch = sz.n_el * sz.n_exp * 8 * 4
+    else:
+        kern, kms = "k_inner", rp.lowp_sweep_ms
+        # read e_j, r, write e_(j+1): 3 low-precision words per export value
+        bytes_per_launch = sz.n_el * sz.n_exp * lp_bytes * 3
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = peaks.get("hbm_gbs", 6800.0)
+    achieved = bytes_per_launch / (kms * 1e-3) / 1e9 if kms > 0 else None
+    traffic = None
+    try:
+        tr = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        ent = tr.get(f"{spec['name']}:{kern}")
+        if ent and ent.get("per_launch_bytes"):
+            traffic = ent["per_launch_bytes"]
+    except Exception:
+        pass
+    roof = {"kernel": kern, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+            "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": kms,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s"}
+
+    # end to end through the host-buffer call: H2D of the inputs and D2H of the outputs inside
+    e2e = None
+    if not swe:
+        ha, hb = np.ascontiguousarray(a), np.ascontiguousarray(b)
+        ctx.solve(mesh, co, ha, hb, opts)
+        et = []
+        for _ in range(max(3, min(args.steps, 10))):
+            t0 = time.perf_counter()
+            u_h, tr_h, rh = ctx.solve(mesh, co, ha, hb, opts)
+            et.append(time.perf_counter() - t0)
+        e2e = {"value": world * sz.n_el * sz.nvol * rh.iterations / float(np.mean(et)), "unit": UNIT,
+               "h2d_bytes_per_step": int(ha.nbytes + hb.nbytes),
+               "d2h_bytes_per_step": int(u_h.nbytes + tr_h.nbytes),
+               "ms_per_step": float(np.mean(et)) * 1e3}
+
+    extras = {}
+    if not args.no_extras and spec["name"] == "convdiff2d":
+        # float64 plain sweep, same problem: time-to-tol comparison
+        o64 = ih.make_options(spec["tol"], max_iters=4000, prec=ih.FP64)
+        step(o64)
+        t64 = []
+        for _ in range(2):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r64 = step(o64)
+            e1.record(stream)
+            e1.synchronize()
+            t64.append(e0.elapsed_time(e1))
+        r64p = step(ih.make_options(spec["tol"], max_iters=4000, prec=ih.FP64, profile=1))
+        du_mixed = du.clone()
+        extras["time_to_tol"] = {
+            "tol": spec["tol"], "mixed_fp32_ms": ms, "mixed_sweeps": float(np.mean(sweeps)), "mixed_status": status,
+            "fp64_ms": float(np.mean(t64)), "fp64_sweeps": r64.iterations, "fp64_status": ih.STATUS_NAMES[r64.status],
+            "speedup_mixed_vs_fp64": float(np.mean(t64)) / ms,
+            "fp64_sweep_kernel_ms": r64p.fp64_sweep_ms,
+            "fp64_sweep_dfma_tflops": (sz.n_el * (sz.n_exp * sz.n_in + sz.n_in * (sz.n_in + 1) // 2) * 2)
+                                      / (r64p.fp64_sweep_ms * 1e-3) / 1e12 if r64p.fp64_sweep_ms else None}
+        # agreement of the two GPU paths on the converged solution
+        step(o64)
+        extras["time_to_tol"]["mixed_vs_fp64_rel_l2"] = float(torch.linalg.norm(du_mixed - du) / torch.linalg.norm(du))
+        # the as-listed kappa: diverges; sweep throughput of capped solves
+        mesh2, co2 = make_problem(ih, spec, kappa=spec["listed_kappa"])
+        a2, b2 = inputs(ih, spec, mesh2, co2, kappa=spec["listed_kappa"])
+        dA2 = torch.from_numpy(np.ascontiguousarray(a2)).to(dev)
+        dB2 = torch.from_numpy(np.ascontiguousarray(b2)).to(dev)
+        o2 = ih.make_options(spec["tol"], max_iters=60, prec=ih.FP64, diverge_factor=-1.0)
+        ctx.solve_device(mesh2, co2, dA2.data_ptr(), dB2.data_ptr(), o2, du.data_ptr(), dt.data_ptr(), wsp, nws, sp)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r2 = ctx.solve_device(mesh2, co2, dA2.data_ptr(), dB2.data_ptr(), o2, du.data_ptr(), dt.data_ptr(), wsp, nws, sp)
+        e1.record(stream)
+        e1.synchronize()
+        od = ih.make_options(spec["tol"], max_iters=2000, prec=ih.FP64)
+        rd = ctx.solve_device(mesh2, co2, dA2.data_ptr(), dB2.data_ptr(), od, du.data_ptr(), dt.data_ptr(), wsp, nws, sp)
+        extras["as_listed"] = {"kappa": spec["listed_kappa"], "status_default_solve": ih.STATUS_NAMES[rd.status],
+                               "sweeps_before_divergence_stop": rd.iterations,
+                               "capped_fp64_sweeps": r2.iterations,
+                               "capped_fp64_updates_per_s": sz.n_el * sz.nvol * r2.iterations / (e0.elapsed_time(e1) * 1e-3)}
+
+    base = None
+    if rank == 0 and not args.no_cpu_baseline and spec["pde"] == "convdiff":
+        base = cpu_baseline(spec)
+    dtype = {"FP64": "f64", "MIXED_FP32": "f32+f64", "MIXED_BF16": "bf16+f32+f64", "MIXED_TF32": "tf32+f64"}[spec["prec"]]
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+            "config": {"workload": spec["desc"], "n_el": sz.n_el, "nvol": sz.nvol, "sweeps_per_step": float(np.mean(sweeps)),
+                       "status": status, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": "flushed between steps (512 MB write, outside the timed events)"},
+            "e2e": e2e, "gpu_launches": int(np.sum(launches)), "roofline": roof, "clocks": clk,
+            "cpu_baseline": base}
+    line.update(extras)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

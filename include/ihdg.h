@@ -98,6 +98,8 @@ typedef struct {
   double inner_rtol;       /* mixed: inner stop when step norm <= inner_rtol * ||r|| (0 = auto) */
   const double* u0;        /* optional initial guess, volume layout (host for ihdg_solve,
                               device for ihdg_solve_device); NULL = zero */
+  int profile;             /* 1: time every sweep launch with CUDA events (one launch per
+                              host check, so slower overall) and report the averages below */
 } ihdg_options;
 
 typedef struct {
@@ -108,6 +110,12 @@ typedef struct {
   ihdg_status status;
   double setup_ms;         /* host operator build + uploads (0 when cached) */
   double solve_ms;         /* device time of the sweep loop and reconstruction */
+  double fp64_sweep_ms;    /* profile: mean device time of one float64 sweep launch */
+  double lowp_sweep_ms;    /* profile: mean device time of one low-precision sweep launch */
+  int fp64_launches;       /* profile: float64 sweep launches timed */
+  int lowp_launches;       /* profile: low-precision sweep launches timed */
+  int kernel_launches;     /* CUDA kernels this call launched (including sweeps that found
+                              the loop already stopped and returned at once) */
 } ihdg_result;
 
 typedef struct {
@@ -184,6 +192,13 @@ ihdg_status ihdg_swe_steps_device(ihdg_ctx* ctx, const ihdg_mesh* mesh,
                                   const ihdg_options* opts, int* iters_per_step,
                                   void* d_workspace, size_t workspace_bytes, void* stream,
                                   ihdg_result* res);
+
+/* Host-only inspection of the float64 per-element operators this library builds for a
+ * problem (no device needed): which = 0 L_E (n_exp x n_in), 1 Q (n_in x n_in), 2 L_vol
+ * (nvol x n_in), 3 R (n_exp x nvol), 4 forcing-to-export (n_exp x nqv), 5 forcing-to-volume
+ * (nvol x nqv).  Row-major into data (may be NULL to query rows/cols only). */
+ihdg_status ihdg_host_operator(const ihdg_mesh* mesh, const ihdg_coeffs* coeffs, int which,
+                               int* rows, int* cols, double* data);
 
 #ifdef __cplusplus
 }

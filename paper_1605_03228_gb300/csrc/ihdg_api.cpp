@@ -221,10 +221,17 @@ ihdg_status device_iterate(ihdg_ctx* ctx, Plan* pl, const ihdg_options& o, const
   CK(cudaEventCreate(&e0), "cudaEventCreate");
   CK(cudaEventCreate(&e1), "cudaEventCreate");
   CK(cudaEventRecord(e0, stream), "cudaEventRecord");
+  SweepTimer tm;
+  tm.on = o.profile != 0;
+  if (tm.on) {
+    CK(cudaEventCreate(&tm.a), "cudaEventCreate");
+    CK(cudaEventCreate(&tm.b), "cudaEventCreate");
+  }
   CK(launch_ctrl_init(a, o.tol, o.diverge_factor, o.max_iters, o.inner_max, o.inner_rtol), "ctrl init");
   CK(launch_forcing(a), "forcing kernel");
   CK(launch_export0(a, u0, a.ring), "initial export kernel");
   CK(launch_first(a), "first sweep kernel");
+  tm.launches += 4;
   Ctrl* hc = ctx->h_ctrl;
   bool mixed = o.prec != IHDG_FP64;
   const double* Eu = nullptr;     // exports whose traces fed the final local solve
@@ -240,7 +247,20 @@ ihdg_status device_iterate(ihdg_ctx* ctx, Plan* pl, const ihdg_options& o, const
       int left = hc->max_iters - hc->iter;
       int n = batch < left ? batch : left;
       if (n <= 0) break;
+      if (tm.on) {
+        CK(cudaEventRecord(tm.a, stream), "cudaEventRecord");
+        CK(launch_sweep64(a, 1), "sweep kernel");
+        CK(cudaEventRecord(tm.b, stream), "cudaEventRecord");
+        CK(cudaEventSynchronize(tm.b), "sweep kernel");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, tm.a, tm.b);
+        tm.fp64_ms += ms;
+        tm.fp64_n += 1;
+        tm.launches += 1;
+        continue;
+      }
       CK(launch_sweep64(a, n), "sweep kernel");
+      tm.launches += n;
       if (batch < 32) batch *= 2;
     }
     int K = hc->iter;
@@ -250,14 +270,15 @@ ihdg_status device_iterate(ihdg_ctx* ctx, Plan* pl, const ihdg_options& o, const
     MixedArgs m{};
     m.base = a;
     mixed_bind(m, ws + L.mixed, L.mx, o.prec);
-    ihdg_status st = run_mixed(ctx->h_ctrl, m, o, &Eu, &Eu2, &Et, &Et2, ctx->err);
+    ihdg_status st = run_mixed(ctx->h_ctrl, m, o, &Eu, &Eu2, &Et, &Et2, ctx->err, &tm);
     if (st != IHDG_OK) return fail(ctx, st, ctx->err);
   }
-  if (d_u) CK(launch_reconstruct(a, Eu, Eu2, d_u), "reconstruct kernel");
+  if (d_u) { CK(launch_reconstruct(a, Eu, Eu2, d_u), "reconstruct kernel"); tm.launches += 1; }
   if (d_tr) {
     double beta[3] = {pl->co.beta[0], pl->co.beta[1], pl->co.beta[2]};
     long long nface = count_faces(pl->mesh, nullptr);
     CK(launch_trace_out(a, Et, Et2, d_u, (int)pl->co.pde, beta, pl->ops.alpha_axis, nface, d_tr), "trace kernel");
+    tm.launches += 1;
   }
   CK(cudaEventRecord(e1, stream), "cudaEventRecord");
   CK(cudaMemcpyAsync(hc, a.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, stream), "ctrl readback");
@@ -266,7 +287,16 @@ ihdg_status device_iterate(ihdg_ctx* ctx, Plan* pl, const ihdg_options& o, const
   cudaEventElapsedTime(&ms, e0, e1);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (tm.on) {
+    cudaEventDestroy(tm.a);
+    cudaEventDestroy(tm.b);
+  }
   if (res) {
+    res->fp64_sweep_ms = tm.fp64_n ? tm.fp64_ms / tm.fp64_n : 0.0;
+    res->lowp_sweep_ms = tm.lowp_n ? tm.lowp_ms / tm.lowp_n : 0.0;
+    res->fp64_launches = tm.fp64_n;
+    res->lowp_launches = tm.lowp_n;
+    res->kernel_launches = tm.launches;
     res->iterations = hc->iter;
     res->fp64_sweeps = hc->fp64_sweeps;
     res->lowp_sweeps = hc->lowp_sweeps;
@@ -390,9 +420,10 @@ ihdg_status ihdg_solve_device(ihdg_ctx* ctx, const ihdg_mesh* mesh, const ihdg_c
   if (ws_bytes < L.total) return fail(ctx, IHDG_ERR_NOMEM, "workspace smaller than ihdg_workspace_bytes()");
   SrcDev src{d_f, d_g, nullptr};
   st = device_iterate(ctx, pl, o, src, o.u0, d_u, d_tr, static_cast<char*>(d_ws), L, static_cast<cudaStream_t>(stream), res);
-  if (st == IHDG_OK && res) res->setup_ms = setup_ms;
+  if (st != IHDG_OK) return st;
+  if (res) res->setup_ms = setup_ms;
   ctx->err.clear();
-  return st;
+  return IHDG_OK;
 }
 
 ihdg_status ihdg_solve(ihdg_ctx* ctx, const ihdg_mesh* mesh, const ihdg_coeffs* co, const double* f_qp,
@@ -475,9 +506,16 @@ ihdg_status ihdg_swe_steps_device(ihdg_ctx* ctx, const ihdg_mesh* mesh, const ih
     tot.lowp_sweeps += r.lowp_sweeps;
     tot.solve_ms += r.solve_ms;
     tot.residual = r.residual;
+    tot.fp64_sweep_ms += r.fp64_sweep_ms * r.fp64_launches;
+    tot.lowp_sweep_ms += r.lowp_sweep_ms * r.lowp_launches;
+    tot.fp64_launches += r.fp64_launches;
+    tot.lowp_launches += r.lowp_launches;
+    tot.kernel_launches += r.kernel_launches;
     if (r.status > tot.status) tot.status = r.status;
   }
   CK(cudaStreamSynchronize(s), "swe steps");
+  if (tot.fp64_launches) tot.fp64_sweep_ms /= tot.fp64_launches;
+  if (tot.lowp_launches) tot.lowp_sweep_ms /= tot.lowp_launches;
   tot.setup_ms = setup_ms;
   if (res) *res = tot;
   ctx->err.clear();

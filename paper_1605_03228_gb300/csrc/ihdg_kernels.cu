@@ -316,7 +316,10 @@ template <int NF, int NLF>
 cudaError_t run_first_t(const LaunchArgs& a) {
   size_t smem = (size_t)a.g.nvol * BS * sizeof(double);
   auto kern = k_first<NF, NLF>;
-  if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (smem > 32 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
   kern<<<grid_for(a.g.nel), BS, smem, a.stream>>>(a.g, a.op, a.src, a.u0, a.F, a.ring, a.ring_stride, a.ctrl, a.partials, a.res_hist);
   return cudaGetLastError();
 }
@@ -326,7 +329,7 @@ cudaError_t run_sweep64_t(const LaunchArgs& a, int count) {
   constexpr int NIN = NF * NLF;
   size_t smem = ((size_t)a.g.n_exp * NIN + NIN * (NIN + 1) / 2 + (size_t)NIN * BS) * sizeof(double);
   auto kern = k_sweep64<NF, NLF>;
-  if (smem > 48 * 1024) {
+  if (smem > 32 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }

@@ -45,6 +45,15 @@ struct LaunchArgs {
   cudaStream_t stream;
 };
 
+// Optional per-launch device timing of the sweep kernels (events around each launch).
+struct SweepTimer {
+  bool on = false;
+  double fp64_ms = 0.0, lowp_ms = 0.0;
+  int fp64_n = 0, lowp_n = 0;
+  cudaEvent_t a = nullptr, b = nullptr;
+  int launches = 0;   // every kernel launch of the solve (counted by the host drivers)
+};
+
 bool shape_supported(int dim, int nf);
 int partials_needed(long long nel);
 

@@ -208,13 +208,13 @@ struct MixedRunner {
       if (which == 0) {
         size_t smem = ((size_t)a.g.n_exp * NIN + (size_t)NIN * BS) * sizeof(double);
         auto k = k_outer64<NF, NLF, TL>;
-        if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (smem > 32 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k<<<grid_for(a.g.nel), BS, smem, a.stream>>>(a.g, a.op, a.F, m.E64, a.ring_stride, m.r64, rl, e0, e1, has_e,
                                                       a.ctrl, a.partials);
       } else if (which == 1) {
         size_t smem = (size_t)NIN * (NIN + 1) / 2 * sizeof(double) + (size_t)a.g.n_exp * NIN * sizeof(float);
         auto k = k_inner_first<NF, NLF, TL>;
-        if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (smem > 32 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k<<<grid_for(a.g.nel), BS, smem, a.stream>>>(a.g, a.op, m.r64, e0, a.ctrl, a.partials, a.res_hist);
       } else {
         size_t smem = (size_t)a.g.n_exp * NIN * sizeof(float);
@@ -276,7 +276,7 @@ void mixed_bind(MixedArgs& m, char* region, const MixedLayout& L, int prec) {
 }
 
 ihdg_status run_mixed(Ctrl* hc, MixedArgs& m, const ihdg_options& o, const double** Eu, const double** Eu2,
-                      const double** Et, const double** Et2, std::string& err) {
+                      const double** Et, const double** Et2, std::string& err, SweepTimer* tm) {
   const LaunchArgs& a = m.base;
   auto ck = [&](cudaError_t e, const char* where) {
     if (e != cudaSuccess) { err = std::string(where) + ": " + cudaGetErrorString(e); return false; }
@@ -295,12 +295,37 @@ ihdg_status run_mixed(Ctrl* hc, MixedArgs& m, const ihdg_options& o, const doubl
   }
   MixedArgs mm = m;
   int has_e = 0;
+  // one timed launch: events around it, host waits, the duration goes to the timer
+  auto timed = [&](int which, int he, bool fp64) {
+    if (!ck(cudaEventRecord(tm->a, a.stream), "event") || !ck(mlaunch(mm, which, he, 1), "sweep kernel") ||
+        !ck(cudaEventRecord(tm->b, a.stream), "event") || !ck(cudaEventSynchronize(tm->b), "event"))
+      return false;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, tm->a, tm->b);
+    if (fp64) { tm->fp64_ms += ms; tm->fp64_n += 1; } else { tm->lowp_ms += ms; tm->lowp_n += 1; }
+    tm->launches += 1;
+    return true;
+  };
   for (int outer = 0; outer < 1000000; ++outer) {
-    if (!ck(mlaunch(mm, 0, has_e, 1), "outer sweep kernel") || !ck(mlaunch(mm, 1, 0, 1), "residual kernel"))
+    if (tm && tm->on) {
+      if (!timed(0, has_e, true) || !timed(1, 0, false)) return IHDG_ERR_CUDA;
+    } else if (!ck(mlaunch(mm, 0, has_e, 1), "outer sweep kernel") || !ck(mlaunch(mm, 1, 0, 1), "residual kernel")) {
       return IHDG_ERR_CUDA;
+    } else {
+      tm->launches += 2;
+    }
     has_e = 1;
     int batch = 4;
     for (;;) {
+      if (tm && tm->on) {
+        if (!ck(cudaMemcpyAsync(hc, a.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, a.stream), "ctrl readback") ||
+            !ck(cudaStreamSynchronize(a.stream), "inner loop"))
+          return IHDG_ERR_CUDA;
+        if (hc->done || hc->inner_done) break;
+        if (!timed(2, 0, false)) return IHDG_ERR_CUDA;
+        continue;
+      }
+      tm->launches += batch;
       if (!ck(mlaunch(mm, 2, 0, batch), "inner sweep kernel") ||
           !ck(cudaMemcpyAsync(hc, a.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, a.stream), "ctrl readback") ||
           !ck(cudaStreamSynchronize(a.stream), "inner loop"))
@@ -308,6 +333,9 @@ ihdg_status run_mixed(Ctrl* hc, MixedArgs& m, const ihdg_options& o, const doubl
       if (hc->done || hc->inner_done) break;
       if (batch < 64) batch *= 2;
     }
+    if (!ck(cudaMemcpyAsync(hc, a.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, a.stream), "ctrl readback") ||
+        !ck(cudaStreamSynchronize(a.stream), "outer loop"))
+      return IHDG_ERR_CUDA;
     if (hc->done) break;
   }
   const double* Ecur = mm.E64 + (long long)(hc->outer & 1) * a.ring_stride;

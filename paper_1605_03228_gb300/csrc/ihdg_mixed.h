@@ -33,6 +33,6 @@ void mixed_bind(MixedArgs& m, char* region, const MixedLayout& L, int prec);
 // Runs the outer/inner loop after the first float64 sweep.  On return, (Eu, Eu2) are the
 // exports whose traces feed the final local solve, and (Et, Et2) the exports of u^K.
 ihdg_status run_mixed(Ctrl* h_ctrl, MixedArgs& m, const ihdg_options& o, const double** Eu, const double** Eu2,
-                      const double** Et, const double** Et2, std::string& err);
+                      const double** Et, const double** Et2, std::string& err, SweepTimer* tm);
 
 }  // namespace ihdg

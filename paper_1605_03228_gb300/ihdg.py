@@ -33,13 +33,14 @@ class Coeffs(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iters", ctypes.c_int), ("prec", ctypes.c_int),
                 ("diverge_factor", ctypes.c_double), ("inner_max", ctypes.c_int),
-                ("inner_rtol", ctypes.c_double), ("u0", ctypes.c_void_p)]
+                ("inner_rtol", ctypes.c_double), ("u0", ctypes.c_void_p), ("profile", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("fp64_sweeps", ctypes.c_int), ("lowp_sweeps", ctypes.c_int),
                 ("residual", ctypes.c_double), ("status", ctypes.c_int), ("setup_ms", ctypes.c_double),
-                ("solve_ms", ctypes.c_double)]
+                ("solve_ms", ctypes.c_double), ("fp64_sweep_ms", ctypes.c_double), ("lowp_sweep_ms", ctypes.c_double),
+                ("fp64_launches", ctypes.c_int), ("lowp_launches", ctypes.c_int), ("kernel_launches", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -89,9 +90,6 @@ def load(build_if_missing=True):
     L.ihdg_swe_steps_device.argtypes = [VP, P(Mesh), P(Coeffs), VP, I, P(Options), P(I), VP, SZ, VP, P(Result)]
     L.ihdg_host_operator.argtypes = [P(Mesh), P(Coeffs), I, P(I), P(I), dp]
     for name in EXPORTED:
-        if getattr(L, name).restype is None and name != "ihdg_destroy":
-            pass
-    for name in EXPORTED:
         f = getattr(L, name)
         if name not in ("ihdg_destroy", "ihdg_last_error"):
             f.restype = ctypes.c_int
@@ -119,11 +117,13 @@ def make_coeffs(pde, beta=(0.0, 0.0, 0.0), kappa=0.0, nu=0.0, Phi=0.0, coriolis_
     return c
 
 
-def make_options(tol, max_iters=2000, prec=FP64, diverge_factor=0.0, inner_max=0, inner_rtol=0.0, u0=None):
+def make_options(tol, max_iters=2000, prec=FP64, diverge_factor=0.0, inner_max=0, inner_rtol=0.0, u0=None,
+                 profile=0):
     o = Options()
     o.tol, o.max_iters, o.prec, o.diverge_factor = tol, max_iters, prec, diverge_factor
     o.inner_max, o.inner_rtol = inner_max, inner_rtol
     o.u0 = u0
+    o.profile = profile
     return o
 
 

@@ -40,13 +40,15 @@ def rel(a, b):
 
 
 def oracle_trace_at_nodes(disc, T):
-    """Oracle traces are at face Gauss points; the library reports face GLL nodes.  Fit the
-    degree-p face polynomial (exact: q = p+2 points) with the oracle's own Lagrange tables."""
+    """Oracle traces are at face Gauss points; the library reports face GLL nodes.  The
+    Gauss-weighted least-squares fit onto the face polynomials (the oracle's own tables) is
+    exact for polynomial traces and is the face L2 projection for boundary data."""
     from oracle.refelem import lagrange_matrix
     ref = disc.ref
     B1 = lagrange_matrix(ref.nodes1, ref.xq1)
     B = B1 if disc.d == 2 else np.kron(B1, B1)
-    coef, *_ = np.linalg.lstsq(B, T.T, rcond=None)
+    w = ref.face_w
+    coef = np.linalg.solve(B.T @ (w[:, None] * B), B.T @ (w[:, None] * T.T))
     return coef.T
 
 
