@@ -7,6 +7,7 @@
 
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <sstream>
@@ -129,6 +130,7 @@ ihdg_status get_plan(ihdg_ctx* ctx, const ihdg_mesh& m, const ihdg_coeffs& co, P
   put(o.Pg.empty() ? empty : o.Pg);
   put(o.PqF.empty() ? empty : o.PqF); put(o.PqV.empty() ? empty : o.PqV);
   put(o.facevol);
+  put(o.Mb);
   size_t nd = img.size();
   std::vector<float> le32(o.LE.begin(), o.LE.end());
   size_t bytes = align256(nd * sizeof(double)) + align256(le32.size() * sizeof(float));
@@ -146,6 +148,8 @@ ihdg_status get_plan(ihdg_ctx* ctx, const ihdg_mesh& m, const ihdg_coeffs& co, P
   for (int f = 0; f < 6; ++f) op.PFb[f] = b + off[k++];
   for (int f = 0; f < 6; ++f) op.PVb[f] = b + off[k++];
   op.Pg = b + off[k++]; op.PqF = b + off[k++]; op.PqV = b + off[k++]; op.facevol = b + off[k++];
+  op.Mb = b + off[k++];
+  for (int c = 0; c < 4; ++c) op.wcomp[c] = o.wcomp[c];
   op.LE32 = d32;
   if (ctx->plans.size() >= 16) {
     cudaFree(ctx->plans.front()->dbuf);
@@ -270,6 +274,11 @@ ihdg_status device_iterate(ihdg_ctx* ctx, Plan* pl, const ihdg_options& o, const
     MixedArgs m{};
     m.base = a;
     mixed_bind(m, ws + L.mixed, L.mx, o.prec);
+    // IHDG_PERSISTENT_GRID caps the persistent kernel's grid (tuning and grid-stride tests)
+    if (const char* cap = std::getenv("IHDG_PERSISTENT_GRID")) {
+      int v = std::atoi(cap);
+      if (v > 0) m.max_grid = v;
+    }
     ihdg_status st = run_mixed(ctx->h_ctrl, m, o, &Eu, &Eu2, &Et, &Et2, ctx->err, &tm);
     if (st != IHDG_OK) return fail(ctx, st, ctx->err);
   }

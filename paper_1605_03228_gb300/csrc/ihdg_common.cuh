@@ -11,6 +11,7 @@ namespace ihdg {
 namespace {
 
 constexpr int BS = 128;   // threads per block of the element kernels
+constexpr int PBS = 256;  // threads per block of the persistent kernels
 
 __device__ __forceinline__ void coords(const DevGeo& g, long long K, int* c) {
   c[0] = (int)(K % g.n[0]);

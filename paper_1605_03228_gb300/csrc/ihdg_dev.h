@@ -30,7 +30,9 @@ struct Ctrl {
   int outer;              // mixed: outer steps completed
   int max_iters;
   int inner_max;
-  int pad_;
+  int timeout;            // a bounded device wait ran out (the loop stops, status ERR_TIMEOUT)
+  unsigned int bar_count; // grid barrier of the persistent kernels: arrivals
+  unsigned int bar_gen;   //   and generation
   double tol, diverge_factor, inner_rtol;
   double res;             // last float64 stopping residual
   double res_min;

@@ -131,11 +131,19 @@ __global__ void __launch_bounds__(BS) k_first(DevGeo g, OpsDev op, SrcDev src, c
       if (u0) v -= u0[K * g.nvol + i];
       du[i * BS] = v;
     }
-    for (int i = 0; i < g.nvol; ++i) {
-      double s = 0.0;
-      const double* row = op.Mn + (long long)i * g.nvol;
-      for (int j = 0; j < g.nvol; ++j) s += row[j] * du[j * BS];
-      acc += du[i * BS] * s;
+    // ||du||^2 in the stopping norm: sum over components c of w_c du_c^T M du_c
+    for (int comp = 0; comp < g.nvol / g.nb; ++comp) {
+      const double w = op.wcomp[comp];
+      if (w == 0.0) continue;
+      const double* dc = du + comp * g.nb * BS;
+      double sc = 0.0;
+      for (int i = 0; i < g.nb; ++i) {
+        double s = 0.0;
+        const double* row = op.Mb + (long long)i * g.nb;
+        for (int j = 0; j < g.nb; ++j) s += row[j] * dc[j * BS];
+        sc += dc[i * BS] * s;
+      }
+      acc += w * sc;
     }
   }
   double tot;
@@ -183,13 +191,24 @@ __global__ void __launch_bounds__(BS) k_sweep64(DevGeo g, OpsDev op, const doubl
       q += NIN - s;
       acc += d[s] * r;
     }
-    // a3: E^{k+1} = F + L_E t^k
-    for (int e = 0; e < g.n_exp; ++e) {
-      double v = F[(long long)e * g.ld + K];
-      const double* row = sLE + e * NIN;
+    // a3: E^{k+1} = F + L_E t^k, in chunks whose forcing loads are issued together
+    constexpr int CH = 8;
 #pragma unroll
-      for (int s = 0; s < NIN; ++s) v += row[s] * st[s * BS];
-      Enxt[(long long)e * g.ld + K] = v;
+    for (int c0 = 0; c0 < NIN; c0 += CH) {
+      double fv[CH];
+#pragma unroll
+      for (int i = 0; i < CH; ++i) fv[i] = (c0 + i < g.n_exp) ? F[(long long)(c0 + i) * g.ld + K] : 0.0;
+#pragma unroll
+      for (int i = 0; i < CH; ++i) {
+        const int e = c0 + i;
+        if (e < g.n_exp) {
+          double v = fv[i];
+          const double* row = sLE + e * NIN;
+#pragma unroll
+          for (int s = 0; s < NIN; ++s) v += row[s] * st[s * BS];
+          Enxt[(long long)e * g.ld + K] = v;
+        }
+      }
     }
   }
   double tot;
@@ -301,6 +320,9 @@ __global__ void k_ctrl_init(Ctrl* c, double tol, double div, int max_iters, int 
   c->outer = 0;
   c->max_iters = max_iters;
   c->inner_max = inner_max;
+  c->timeout = 0;
+  c->bar_count = 0u;
+  c->bar_gen = 0u;
   c->tol = tol;
   c->diverge_factor = div;
   c->inner_rtol = inner_rtol;
@@ -399,6 +421,6 @@ cudaError_t launch_trace_out(const LaunchArgs& a, const double* E, const double*
                                                 alpha[0], alpha[1], alpha[2], nface, tr);
   return cudaGetLastError();
 }
-int partials_needed(long long nel) { return (int)grid_for(nel); }
+int partials_needed(long long nel) { return 2 * (int)grid_for(nel) + 2; }
 
 }  // namespace ihdg

@@ -22,6 +22,8 @@ struct OpsDev {
   const double* PqV;     // nvol x nvol
   const double* facevol; // nlf x nf
   const float* LE32;     // n_exp x n_in, float32 copy for the low-precision sweeps
+  const double* Mb;      // nb x nb element mass matrix
+  double wcomp[4];       // per-component weight of the stopping norm
 };
 
 // Problem data: steady forcing/boundary data, or shallow-water step data q^m.

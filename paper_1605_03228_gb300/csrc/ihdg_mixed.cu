@@ -50,11 +50,13 @@ __device__ __forceinline__ void gather_lp(const DevGeo& g, const TL* __restrict_
   }
 }
 
+constexpr int CH = 8;   // outputs per chunk: their loads are issued together, then stored
+
 // Outer float64 sweep: E' = E + e (own and gathered), r = F + L_E t(E') - E'.
 template <int NF, int NLF, typename TL>
 __global__ void __launch_bounds__(BS) k_outer64(DevGeo g, OpsDev op, const double* __restrict__ F, double* E64,
                                                 long long es, double* __restrict__ r64, TL* __restrict__ rlp,
-                                                TL* e0, TL* e1, int has_e, Ctrl* ctrl, double* partials) {
+                                                const TL* e0, const TL* e1, int has_e, Ctrl* ctrl, double* partials) {
   constexpr int NIN = NF * NLF;
   __shared__ double ws[BS / 32];
   extern __shared__ double sdyn[];
@@ -75,19 +77,36 @@ __global__ void __launch_bounds__(BS) k_outer64(DevGeo g, OpsDev op, const doubl
     coords(g, K, c);
     gather<NF, NLF, double, double>(g, Ecur, K, c, [&](int s, double v) { st[s * BS] = v; });
     if (has_e) gather_lp<NF, NLF, TL, double>(g, ecur, K, c, [&](int s, double v) { st[s * BS] += v; });
-    for (int e = 0; e < g.n_exp; ++e) {
-      const long long at = (long long)e * g.ld + K;
-      double own = Ecur[at];
-      if (has_e) own += (double)to_f(ecur[at]);
-      double v = F[at];
-      const double* row = sLE + e * NIN;
 #pragma unroll
-      for (int s = 0; s < NIN; ++s) v += row[s] * st[s * BS];
-      const double r = v - own;
-      Enx[at] = own;
-      r64[at] = r;
-      rlp[at] = from_f<TL>((float)r);
-      acc += r * r;
+    for (int c0 = 0; c0 < NIN; c0 += CH) {
+      double own[CH], fv[CH];
+#pragma unroll
+      for (int i = 0; i < CH; ++i) {
+        const int e = c0 + i;
+        own[i] = 0.0;
+        fv[i] = 0.0;
+        if (e < g.n_exp) {
+          const long long at = (long long)e * g.ld + K;
+          own[i] = Ecur[at] + (has_e ? (double)to_f(ecur[at]) : 0.0);
+          fv[i] = F[at];
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < CH; ++i) {
+        const int e = c0 + i;
+        if (e < g.n_exp) {
+          const long long at = (long long)e * g.ld + K;
+          double v = fv[i];
+          const double* row = sLE + e * NIN;
+#pragma unroll
+          for (int s = 0; s < NIN; ++s) v += row[s] * st[s * BS];
+          const double r = v - own[i];
+          Enx[at] = own[i];
+          r64[at] = r;
+          rlp[at] = from_f<TL>((float)r);
+          acc += r * r;
+        }
+      }
     }
   }
   double tot;
@@ -102,8 +121,9 @@ __global__ void __launch_bounds__(BS) k_outer64(DevGeo g, OpsDev op, const doubl
 // Float64 stopping residual of the next exact sweep, sqrt(t(r)^T Q t(r)), fused with the
 // first useful inner sweep e = r + L_E t(r) (low precision).
 template <int NF, int NLF, typename TL>
-__global__ void __launch_bounds__(BS) k_inner_first(DevGeo g, OpsDev op, const double* __restrict__ r64, TL* e0,
-                                                    Ctrl* ctrl, double* partials, double* res_hist) {
+__global__ void __launch_bounds__(BS) k_inner_first(DevGeo g, OpsDev op, const double* __restrict__ r64,
+                                                    TL* __restrict__ e0, Ctrl* ctrl, double* partials,
+                                                    double* res_hist) {
   constexpr int NIN = NF * NLF;
   constexpr int NQ = NIN * (NIN + 1) / 2;
   __shared__ double ws[BS / 32];
@@ -130,13 +150,25 @@ __global__ void __launch_bounds__(BS) k_inner_first(DevGeo g, OpsDev op, const d
       q += NIN - s;
       acc += d[s] * r;
     }
-    for (int e = 0; e < g.n_exp; ++e) {
-      const long long at = (long long)e * g.ld + K;
-      float v = (float)r64[at];
-      const float* row = sL + e * NIN;
+    float df[NIN];
 #pragma unroll
-      for (int s = 0; s < NIN; ++s) v = fmaf(row[s], (float)d[s], v);
-      e0[at] = from_f<TL>(v);
+    for (int s = 0; s < NIN; ++s) df[s] = (float)d[s];
+#pragma unroll
+    for (int c0 = 0; c0 < NIN; c0 += CH) {
+      float rv[CH];
+#pragma unroll
+      for (int i = 0; i < CH; ++i) rv[i] = (c0 + i < g.n_exp) ? (float)r64[(long long)(c0 + i) * g.ld + K] : 0.f;
+#pragma unroll
+      for (int i = 0; i < CH; ++i) {
+        const int e = c0 + i;
+        if (e < g.n_exp) {
+          float v = rv[i];
+          const float* row = sL + e * NIN;
+#pragma unroll
+          for (int s = 0; s < NIN; ++s) v = fmaf(row[s], df[s], v);
+          e0[(long long)e * g.ld + K] = from_f<TL>(v);
+        }
+      }
     }
   }
   double tot;
@@ -147,49 +179,114 @@ __global__ void __launch_bounds__(BS) k_inner_first(DevGeo g, OpsDev op, const d
   }
 }
 
-// Inner low-precision sweep on the correction equation: e_{j+1} = r + L_E t(e_j).
+// Grid-wide barrier of a cooperative launch (all blocks co-resident).  The wait is bounded
+// by ~1 s of SM clock; on expiry the block sets ctrl->timeout and leaves the barrier, and
+// every block stops its loop at the next check.
+__device__ __forceinline__ void grid_barrier(Ctrl* ctrl) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* gen = &ctrl->bar_gen;
+    const unsigned int g0 = *gen;
+    __threadfence();
+    const unsigned int a = atomicAdd(&ctrl->bar_count, 1u);
+    if (a == gridDim.x - 1) {
+      ctrl->bar_count = 0u;
+      __threadfence();
+      atomicExch(&ctrl->bar_gen, g0 + 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*gen == g0) {
+        if (clock64() - t0 > 2000000000LL) { atomicExch(&ctrl->timeout, 1); break; }
+        __nanosleep(20);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+// Persistent inner loop on the correction equation: e_{j+1} = r + L_E t(e_j), until the
+// step norm falls below inner_rtol * ||r||, inner_max sweeps, or the sweep budget.  One
+// cooperative launch runs many sweeps; each sweep ends with a grid barrier after which every
+// block sums the per-block partials in the same fixed order, so all blocks take the same
+// decision.  Block 0 records the loop state.
 template <int NF, int NLF, typename TL>
-__global__ void __launch_bounds__(BS) k_inner(DevGeo g, OpsDev op, const TL* __restrict__ rlp, TL* e0, TL* e1,
-                                              Ctrl* ctrl, double* partials) {
+__global__ void __launch_bounds__(PBS) k_inner_persist(DevGeo g, OpsDev op, const TL* __restrict__ rlp, TL* e0,
+                                                       TL* e1, Ctrl* ctrl, double* partials) {
   constexpr int NIN = NF * NLF;
-  __shared__ double ws[BS / 32];
+  __shared__ double ws[PBS / 32];
+  __shared__ double s_tot;
   extern __shared__ float sf[];
   if (ctrl_done(ctrl) || *(volatile const int*)&ctrl->inner_done) return;
-  const int j = *(volatile const int*)&ctrl->inner_iter;
-  for (int i = threadIdx.x; i < g.n_exp * NIN; i += BS) sf[i] = op.LE32[i];
+  int j = *(volatile const int*)&ctrl->inner_iter;
+  const int iter0 = *(volatile const int*)&ctrl->iter;
+  const int max_iters = ctrl->max_iters, inner_max = ctrl->inner_max;
+  const double lim = ctrl->inner_rtol * ctrl->rnorm;
+  for (int i = threadIdx.x; i < g.n_exp * NIN; i += PBS) sf[i] = op.LE32[i];
   __syncthreads();
-  const TL* ec = (j & 1) ? e1 : e0;
-  TL* en = (j & 1) ? e0 : e1;
-  const long long K = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  float acc = 0.f;
-  if (K < g.nel) {
-    int c[3];
-    coords(g, K, c);
-    float t[NIN];
-    gather_lp<NF, NLF, TL, float>(g, ec, K, c, [&](int s, float v) { t[s] = v; });
-    for (int e = 0; e < g.n_exp; ++e) {
-      const long long at = (long long)e * g.ld + K;
-      float v = to_f(rlp[at]);
-      const float* row = sf + e * NIN;
+  const long long stride = (long long)gridDim.x * PBS;
+  for (int s = 0;; ++s) {
+    const TL* __restrict__ ec = (j & 1) ? e1 : e0;
+    TL* __restrict__ en = (j & 1) ? e0 : e1;
+    float acc = 0.f;
+    for (long long K = (long long)blockIdx.x * PBS + threadIdx.x; K < g.nel; K += stride) {
+      int c[3];
+      coords(g, K, c);
+      float t[NIN];
+      gather_lp<NF, NLF, TL, float>(g, ec, K, c, [&](int q, float v) { t[q] = v; });
 #pragma unroll
-      for (int s = 0; s < NIN; ++s) v = fmaf(row[s], t[s], v);
-      const TL nv = from_f<TL>(v);
-      const float dlt = to_f(nv) - to_f(ec[at]);
-      acc = fmaf(dlt, dlt, acc);
-      en[at] = nv;
+      for (int c0 = 0; c0 < NIN; c0 += CH) {
+        float rv[CH], ov[CH];
+#pragma unroll
+        for (int i = 0; i < CH; ++i) {
+          const int e = c0 + i;
+          rv[i] = 0.f;
+          ov[i] = 0.f;
+          if (e < g.n_exp) {
+            const long long at = (long long)e * g.ld + K;
+            rv[i] = to_f(rlp[at]);
+            ov[i] = to_f(ec[at]);
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < CH; ++i) {
+          const int e = c0 + i;
+          if (e < g.n_exp) {
+            float v = rv[i];
+            const float* row = sf + e * NIN;
+#pragma unroll
+            for (int q = 0; q < NIN; ++q) v = fmaf(row[q], t[q], v);
+            const TL nv = from_f<TL>(v);
+            const float dl = to_f(nv) - ov[i];
+            acc = fmaf(dl, dl, acc);
+            en[(long long)e * g.ld + K] = nv;
+          }
+        }
+      }
     }
-  }
-  double tot;
-  if (arrive(ctrl, partials, (double)acc, ws, &tot) && threadIdx.x == 0) {
-    const int jn = j + 1;
-    ctrl->inner_iter = jn;
-    ctrl->iter += 1;
-    ctrl->lowp_sweeps += 1;
-    const double step = sqrt(tot);
-    ctrl->inner_step = step;
-    if (step <= ctrl->inner_rtol * ctrl->rnorm || jn >= ctrl->inner_max || ctrl->iter >= ctrl->max_iters ||
-        !(step == step) || isinf(step))
-      ctrl->inner_done = 1;
+    double* part = partials + (long long)(s & 1) * gridDim.x;
+    const double bs = block_sum((double)acc, ws);
+    if (threadIdx.x == 0) part[blockIdx.x] = bs;
+    __threadfence();
+    grid_barrier(ctrl);
+    if (*(volatile int*)&ctrl->timeout) break;
+    double v = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += PBS) v += __ldcg(part + i);
+    const double tot = block_sum(v, ws);
+    if (threadIdx.x == 0) s_tot = tot;
+    __syncthreads();
+    const double step = sqrt(s_tot);
+    j += 1;
+    const int it = iter0 + s + 1;
+    const bool stop = step <= lim || j >= inner_max || it >= max_iters || !(step == step) || isinf(step);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      ctrl->inner_iter = j;
+      ctrl->iter = it;
+      ctrl->lowp_sweeps += 1;
+      ctrl->inner_step = step;
+      if (stop) ctrl->inner_done = 1;
+    }
+    if (stop) break;
   }
 }
 
@@ -208,18 +305,42 @@ struct MixedRunner {
       if (which == 0) {
         size_t smem = ((size_t)a.g.n_exp * NIN + (size_t)NIN * BS) * sizeof(double);
         auto k = k_outer64<NF, NLF, TL>;
-        if (smem > 32 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (smem > 32 * 1024) {
+          cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+          if (e != cudaSuccess) return e;
+        }
         k<<<grid_for(a.g.nel), BS, smem, a.stream>>>(a.g, a.op, a.F, m.E64, a.ring_stride, m.r64, rl, e0, e1, has_e,
                                                       a.ctrl, a.partials);
       } else if (which == 1) {
         size_t smem = (size_t)NIN * (NIN + 1) / 2 * sizeof(double) + (size_t)a.g.n_exp * NIN * sizeof(float);
         auto k = k_inner_first<NF, NLF, TL>;
-        if (smem > 32 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (smem > 32 * 1024) {
+          cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+          if (e != cudaSuccess) return e;
+        }
         k<<<grid_for(a.g.nel), BS, smem, a.stream>>>(a.g, a.op, m.r64, e0, a.ctrl, a.partials, a.res_hist);
       } else {
+        // persistent cooperative launch: as many co-resident blocks as the elements need
         size_t smem = (size_t)a.g.n_exp * NIN * sizeof(float);
-        for (int i = 0; i < count; ++i)
-          k_inner<NF, NLF, TL><<<grid_for(a.g.nel), BS, smem, a.stream>>>(a.g, a.op, rl, e0, e1, a.ctrl, a.partials);
+        auto k = k_inner_persist<NF, NLF, TL>;
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, PBS, smem);
+        if (e != cudaSuccess) return e;
+        if (per < 1) return cudaErrorInvalidConfiguration;
+        long long need = (a.g.nel + PBS - 1) / PBS;
+        long long cap = (long long)per * sms;
+        int grid = (int)(need < cap ? need : cap);
+        if (grid > m.max_grid) grid = m.max_grid;
+        DevGeo gg = a.g;
+        OpsDev oo = a.op;
+        const TL* rlc = rl;
+        Ctrl* ct = a.ctrl;
+        double* pp = a.partials;
+        void* args[] = {&gg, &oo, &rlc, &e0, &e1, &ct, &pp};
+        e = cudaLaunchCooperativeKernel((const void*)k, dim3(grid), dim3(PBS), args, smem, a.stream);
+        if (e != cudaSuccess) return e;
       }
       return cudaGetLastError();
     }
@@ -295,47 +416,34 @@ ihdg_status run_mixed(Ctrl* hc, MixedArgs& m, const ihdg_options& o, const doubl
   }
   MixedArgs mm = m;
   int has_e = 0;
-  // one timed launch: events around it, host waits, the duration goes to the timer
-  auto timed = [&](int which, int he, bool fp64) {
-    if (!ck(cudaEventRecord(tm->a, a.stream), "event") || !ck(mlaunch(mm, which, he, 1), "sweep kernel") ||
-        !ck(cudaEventRecord(tm->b, a.stream), "event") || !ck(cudaEventSynchronize(tm->b), "event"))
+  // one launch, optionally timed with events; the timer gets the duration per sweep
+  auto launch = [&](int which, int he, bool fp64) {
+    if (tm->on && !ck(cudaEventRecord(tm->a, a.stream), "event")) return false;
+    const int before = hc->iter;
+    if (!ck(mlaunch(mm, which, he, 1), which == 0 ? "outer sweep kernel" : which == 1 ? "residual kernel" : "inner sweep kernel"))
+      return false;
+    tm->launches += 1;
+    if (!tm->on) return true;
+    if (!ck(cudaEventRecord(tm->b, a.stream), "event") || !ck(cudaEventSynchronize(tm->b), "event") ||
+        !ck(cudaMemcpy(hc, a.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost), "ctrl readback"))
       return false;
     float ms = 0.f;
     cudaEventElapsedTime(&ms, tm->a, tm->b);
-    if (fp64) { tm->fp64_ms += ms; tm->fp64_n += 1; } else { tm->lowp_ms += ms; tm->lowp_n += 1; }
-    tm->launches += 1;
+    const int n = which == 2 ? hc->iter - before : 1;
+    if (fp64) { tm->fp64_ms += ms; tm->fp64_n += 1; }
+    else if (n > 0) { tm->lowp_ms += ms; tm->lowp_n += n; }
     return true;
   };
   for (int outer = 0; outer < 1000000; ++outer) {
-    if (tm && tm->on) {
-      if (!timed(0, has_e, true) || !timed(1, 0, false)) return IHDG_ERR_CUDA;
-    } else if (!ck(mlaunch(mm, 0, has_e, 1), "outer sweep kernel") || !ck(mlaunch(mm, 1, 0, 1), "residual kernel")) {
-      return IHDG_ERR_CUDA;
-    } else {
-      tm->launches += 2;
-    }
+    if (!launch(0, has_e, true) || !launch(1, 0, false)) return IHDG_ERR_CUDA;
     has_e = 1;
-    int batch = 4;
-    for (;;) {
-      if (tm && tm->on) {
-        if (!ck(cudaMemcpyAsync(hc, a.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, a.stream), "ctrl readback") ||
-            !ck(cudaStreamSynchronize(a.stream), "inner loop"))
-          return IHDG_ERR_CUDA;
-        if (hc->done || hc->inner_done) break;
-        if (!timed(2, 0, false)) return IHDG_ERR_CUDA;
-        continue;
-      }
-      tm->launches += batch;
-      if (!ck(mlaunch(mm, 2, 0, batch), "inner sweep kernel") ||
-          !ck(cudaMemcpyAsync(hc, a.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, a.stream), "ctrl readback") ||
-          !ck(cudaStreamSynchronize(a.stream), "inner loop"))
-        return IHDG_ERR_CUDA;
-      if (hc->done || hc->inner_done) break;
-      if (batch < 64) batch *= 2;
-    }
+    // the persistent inner kernel runs until the inner loop stops (it returns at once when
+    // the residual check above already ended the solve)
+    if (!launch(2, 0, false)) return IHDG_ERR_CUDA;
     if (!ck(cudaMemcpyAsync(hc, a.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, a.stream), "ctrl readback") ||
-        !ck(cudaStreamSynchronize(a.stream), "outer loop"))
+        !ck(cudaStreamSynchronize(a.stream), "inner loop"))
       return IHDG_ERR_CUDA;
+    if (hc->timeout) { err = "persistent inner sweep: a grid barrier wait ran out"; return IHDG_ERR_TIMEOUT; }
     if (hc->done) break;
   }
   const double* Ecur = mm.E64 + (long long)(hc->outer & 1) * a.ring_stride;

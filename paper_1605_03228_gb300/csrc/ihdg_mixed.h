@@ -26,6 +26,7 @@ struct MixedArgs {
   void* rlp;            // low-precision residual
   void* e[2];           // low-precision correction, ping-pong
   int prec;
+  int max_grid = 1 << 30;   // cap on the persistent kernel's grid (tests shrink it)
 };
 
 MixedLayout mixed_layout(const DevGeo& g, int prec);

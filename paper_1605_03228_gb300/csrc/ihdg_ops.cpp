@@ -568,6 +568,10 @@ ihdg_status build_ops(const ihdg_mesh& m, const ihdg_coeffs& co, Ops& o, std::st
     }
   }
   o.R = R;
+  o.Mb = M;
+  if (co.pde == IHDG_TRANSPORT) o.wcomp[0] = 1.0;
+  else if (co.pde == IHDG_CONVDIFF) o.wcomp[d] = 1.0;
+  else { o.wcomp[0] = 1.0; o.wcomp[1] = co.Phi; o.wcomp[2] = co.Phi; }
 
   // Lvol = A^{-1} G
   o.Lvol = G;

@@ -42,6 +42,8 @@ struct Ops {
   std::vector<double> Q;      // n_in x n_in
   std::vector<double> R;      // n_exp x nvol   volume -> export
   std::vector<double> Mn;     // nvol x nvol    norm of the stopping test
+  std::vector<double> Mb;     // nb x nb element mass matrix
+  double wcomp[4] = {0, 0, 0, 0}; // Mn = blockdiag(wcomp[c] * Mb)
   std::vector<double> PF, PV; // n_exp x nqv, nvol x nqv    forcing -> export / volume
   std::vector<double> PFb[6], PVb[6];  // n_exp x nqf, nvol x nqf per local face (boundary data)
   std::vector<double> Pg;     // nf x nqf   boundary data -> L2-projected face nodal values

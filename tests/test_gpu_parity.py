@@ -271,6 +271,23 @@ def test_mixed_transport3d(ctx, prec_name):
     assert rel(u, U.reshape(om.nel, -1)) < 1e-6
 
 
+def test_mixed_persistent_grid_stride(ctx, monkeypatch):
+    """The persistent inner kernel with a grid far smaller than the elements (every thread
+    loops over several elements) gives the same answer as the one-element-per-thread grid."""
+    ihdg = ih()
+    n, p, beta = (40, 30), 2, (0.8, 1.0)
+    mesh = ihdg.make_mesh(2, n, p)
+    co = ihdg.make_coeffs(ihdg.TRANSPORT, beta=beta)
+    vol, bnd = ihdg.quadrature_points(mesh, co)
+    f, g = W.transport2d_forcing(vol, beta), W.transport2d_exact(bnd)
+    opts = ihdg.make_options(1e-10, prec=ihdg.MIXED_FP32)
+    u_a, _, ra = ctx.solve(mesh, co, f, g, opts)
+    monkeypatch.setenv("IHDG_PERSISTENT_GRID", "2")
+    u_b, _, rb = ctx.solve(mesh, co, f, g, opts)
+    assert ra.status == rb.status == ihdg.OK and ra.iterations == rb.iterations
+    assert np.array_equal(u_a, u_b)
+
+
 def test_mixed_convdiff(ctx):
     ihdg = ih()
     n, p, kappa = (12, 10), 3, 1e-4
