@@ -28,6 +28,7 @@ struct Plan {
   ihdg_mesh mesh{};
   ihdg_coeffs co{};
   Ops ops;
+  std::vector<float> le32;   // host float32 copy of L_E (kernel parameter of the tile kernel)
   DevGeo g{};
   OpsDev op{};
   void* dbuf = nullptr;
@@ -98,6 +99,11 @@ void fill_geo(const ihdg_mesh& m, const Ops& o, DevGeo& g) {
   }
   g.bc_mirror = o.bc_mirror;
   g.steady = o.pde != IHDG_SWE;
+  g.per_axis = o.layout_per_axis;
+  g.live = 0ull;
+  for (int f = 0; f < o.nlf; ++f)
+    if (o.face_kind[f] == FK_OWN || o.face_kind[f] == FK_SUM)
+      for (int j = 0; j < o.nf; ++j) g.live |= 1ull << (o.own_off[f] + j);
 }
 
 // Build (or find) the plan of a problem: host float64 operators and their device copies.
@@ -132,7 +138,8 @@ ihdg_status get_plan(ihdg_ctx* ctx, const ihdg_mesh& m, const ihdg_coeffs& co, P
   put(o.facevol);
   put(o.Mb);
   size_t nd = img.size();
-  std::vector<float> le32(o.LE.begin(), o.LE.end());
+  pl->le32.assign(o.LE.begin(), o.LE.end());
+  const std::vector<float>& le32 = pl->le32;
   size_t bytes = align256(nd * sizeof(double)) + align256(le32.size() * sizeof(float));
   CK(cudaSetDevice(ctx->device), "cudaSetDevice");
   CK(cudaMalloc(&pl->dbuf, bytes), "cudaMalloc(operators)");
@@ -279,6 +286,9 @@ ihdg_status device_iterate(ihdg_ctx* ctx, Plan* pl, const ihdg_options& o, const
       int v = std::atoi(cap);
       if (v > 0) m.max_grid = v;
     }
+    // IHDG_INNER_KERNEL=global selects the global-memory persistent kernel over the tile one
+    if (const char* ker = std::getenv("IHDG_INNER_KERNEL")) m.no_tile = std::strcmp(ker, "global") == 0;
+    m.LE32h = pl->le32.data();
     ihdg_status st = run_mixed(ctx->h_ctrl, m, o, &Eu, &Eu2, &Et, &Et2, ctx->err, &tm);
     if (st != IHDG_OK) return fail(ctx, st, ctx->err);
   }

@@ -63,6 +63,9 @@ __device__ __forceinline__ void gather(const DevGeo& g, const TE* __restrict__ E
   }
 }
 
+// Export slot e carries a value (transport: the axis has an outflow face).
+__device__ __forceinline__ bool row_live(const DevGeo& g, int e, int /*nf*/) { return (g.live >> e) & 1ull; }
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);

@@ -15,6 +15,8 @@ struct DevGeo {
   int kind[6], own_off[6], nbr_off[6];
   int bc_mirror;
   int steady;             // 1: forcing from (f, g); 0: shallow-water step data q^m
+  int per_axis;           // export slot = axis * nf + node (transport) / face * nf + node
+  unsigned long long live;  // bit e: export slot e carries a value (n_exp <= 64)
 };
 
 // Loop state of one solve, in device memory.  Written only by the last block of each

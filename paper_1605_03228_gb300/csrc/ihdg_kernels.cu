@@ -62,6 +62,7 @@ __global__ void __launch_bounds__(BS) k_forcing(DevGeo g, OpsDev op, SrcDev src,
   int c[3];
   coords(g, K, c);
   for (int e = 0; e < g.n_exp; ++e) {
+    if (!row_live(g, e, g.nf)) continue;
     double v = 0.0;
     if (g.steady) {
       const double* fk = src.f + K * g.nqv;
@@ -88,6 +89,7 @@ __global__ void __launch_bounds__(BS) k_export0(DevGeo g, OpsDev op, const doubl
   const long long K = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (K >= g.nel) return;
   for (int e = 0; e < g.n_exp; ++e) {
+    if (!row_live(g, e, g.nf)) continue;
     double v = 0.0;
     if (u0) {
       const double* row = op.R + (long long)e * g.nvol;
@@ -116,6 +118,7 @@ __global__ void __launch_bounds__(BS) k_first(DevGeo g, OpsDev op, SrcDev src, c
     gather<NF, NLF, double, double>(g, ring, K, c, [&](int s, double v) { t[s] = v; });
     double* E1 = ring + ring_stride;
     for (int e = 0; e < g.n_exp; ++e) {
+      if (!row_live(g, e, NF)) continue;
       double v = F[(long long)e * g.ld + K];
       const double* row = op.LE + (long long)e * NIN;
 #pragma unroll
@@ -197,11 +200,11 @@ __global__ void __launch_bounds__(BS) k_sweep64(DevGeo g, OpsDev op, const doubl
     for (int c0 = 0; c0 < NIN; c0 += CH) {
       double fv[CH];
 #pragma unroll
-      for (int i = 0; i < CH; ++i) fv[i] = (c0 + i < g.n_exp) ? F[(long long)(c0 + i) * g.ld + K] : 0.0;
+      for (int i = 0; i < CH; ++i) fv[i] = (c0 + i < g.n_exp && row_live(g, c0 + i, NF)) ? F[(long long)(c0 + i) * g.ld + K] : 0.0;
 #pragma unroll
       for (int i = 0; i < CH; ++i) {
         const int e = c0 + i;
-        if (e < g.n_exp) {
+        if (e < g.n_exp && row_live(g, e, NF)) {
           double v = fv[i];
           const double* row = sLE + e * NIN;
 #pragma unroll

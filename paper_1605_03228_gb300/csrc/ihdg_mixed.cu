@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(BS) k_outer64(DevGeo g, OpsDev op, const doubl
         const int e = c0 + i;
         own[i] = 0.0;
         fv[i] = 0.0;
-        if (e < g.n_exp) {
+        if (e < g.n_exp && row_live(g, e, NF)) {
           const long long at = (long long)e * g.ld + K;
           own[i] = Ecur[at] + (has_e ? (double)to_f(ecur[at]) : 0.0);
           fv[i] = F[at];
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(BS) k_outer64(DevGeo g, OpsDev op, const doubl
 #pragma unroll
       for (int i = 0; i < CH; ++i) {
         const int e = c0 + i;
-        if (e < g.n_exp) {
+        if (e < g.n_exp && row_live(g, e, NF)) {
           const long long at = (long long)e * g.ld + K;
           double v = fv[i];
           const double* row = sLE + e * NIN;
@@ -157,11 +157,11 @@ __global__ void __launch_bounds__(BS) k_inner_first(DevGeo g, OpsDev op, const d
     for (int c0 = 0; c0 < NIN; c0 += CH) {
       float rv[CH];
 #pragma unroll
-      for (int i = 0; i < CH; ++i) rv[i] = (c0 + i < g.n_exp) ? (float)r64[(long long)(c0 + i) * g.ld + K] : 0.f;
+      for (int i = 0; i < CH; ++i) rv[i] = (c0 + i < g.n_exp && row_live(g, c0 + i, NF)) ? (float)r64[(long long)(c0 + i) * g.ld + K] : 0.f;
 #pragma unroll
       for (int i = 0; i < CH; ++i) {
         const int e = c0 + i;
-        if (e < g.n_exp) {
+        if (e < g.n_exp && row_live(g, e, NF)) {
           float v = rv[i];
           const float* row = sL + e * NIN;
 #pragma unroll
@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(PBS) k_inner_persist(DevGeo g, OpsDev op, cons
           const int e = c0 + i;
           rv[i] = 0.f;
           ov[i] = 0.f;
-          if (e < g.n_exp) {
+          if (e < g.n_exp && row_live(g, e, NF)) {
             const long long at = (long long)e * g.ld + K;
             rv[i] = to_f(rlp[at]);
             ov[i] = to_f(ec[at]);
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(PBS) k_inner_persist(DevGeo g, OpsDev op, cons
 #pragma unroll
         for (int i = 0; i < CH; ++i) {
           const int e = c0 + i;
-          if (e < g.n_exp) {
+          if (e < g.n_exp && row_live(g, e, NF)) {
             float v = rv[i];
             const float* row = sf + e * NIN;
 #pragma unroll
@@ -290,6 +290,181 @@ __global__ void __launch_bounds__(PBS) k_inner_persist(DevGeo g, OpsDev op, cons
   }
 }
 
+// Low-precision operator passed by value: the kernel reads it from the parameter (constant)
+// bank, so every multiply-add takes its matrix entry straight from there.
+template <int NF, int NLF, bool PER_AXIS>
+struct LTile {
+  static constexpr int NIN = NF * NLF;
+  static constexpr int NEXP = PER_AXIS ? NF * (NLF / 2) : NF * NLF;
+  float L[NEXP][NIN];
+};
+
+constexpr int TBS = 512;   // threads per block of the tile kernel
+
+// Persistent inner loop with block-resident state.  Block b owns elements
+// [b*epb, b*epb + epb); their own exports e_j and the residual r stay in shared memory
+// (TL precision, the values the neighbours see), with each element's boundary-face mask.
+// Per sweep only the neighbours' exports are read from global memory, and e_{j+1} is
+// written back for them.  The loop decision is the same as k_inner_persist's.
+template <int NF, int NLF, bool PER_AXIS, typename TL>
+__global__ void __launch_bounds__(TBS) k_inner_tile(const DevGeo g, const TL* __restrict__ rlp, TL* e0, TL* e1,
+                                                    Ctrl* ctrl, double* partials, const int epb,
+                                                    const LTile<NF, NLF, PER_AXIS> Lp) {
+  constexpr int NIN = NF * NLF;
+  constexpr int NEXP = LTile<NF, NLF, PER_AXIS>::NEXP;
+  __shared__ double ws[TBS / 32];
+  __shared__ double s_tot;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  if (ctrl_done(ctrl) || *(volatile const int*)&ctrl->inner_done) return;
+  int j = *(volatile const int*)&ctrl->inner_iter;
+  const int iter0 = *(volatile const int*)&ctrl->iter;
+  const int max_iters = ctrl->max_iters, inner_max = ctrl->inner_max;
+  const double lim = ctrl->inner_rtol * ctrl->rnorm;
+  TL* ev = reinterpret_cast<TL*>(smraw);        // [NEXP][epb]
+  TL* rv = ev + (size_t)NEXP * epb;             // [NEXP][epb]
+  unsigned char* bm = reinterpret_cast<unsigned char*>(rv + (size_t)NEXP * epb);
+  const int ld = (int)g.ld;
+  const int K0 = blockIdx.x * epb;
+  const int cnt = min(epb, (int)g.nel - K0);
+  int dlt[NLF];
+#pragma unroll
+  for (int f = 0; f < NLF; ++f) dlt[f] = (f & 1) ? (int)g.stride[f >> 1] : -(int)g.stride[f >> 1];
+  {
+    const TL* ec = (j & 1) ? e1 : e0;
+    for (int le = threadIdx.x; le < cnt; le += TBS) {
+      const int K = K0 + le;
+      int c[3];
+      coords(g, K, c);
+      unsigned m = 0;
+#pragma unroll
+      for (int f = 0; f < NLF; ++f) m |= (on_bnd(g, c, f) ? 1u : 0u) << f;
+      bm[le] = (unsigned char)m;
+#pragma unroll
+      for (int e = 0; e < NEXP; ++e) {
+        if ((g.live >> e) & 1ull) {
+          ev[e * epb + le] = ec[e * ld + K];
+          rv[e * epb + le] = rlp[e * ld + K];
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (int s = 0;; ++s) {
+    const TL* __restrict__ ec = (j & 1) ? e1 : e0;
+    TL* __restrict__ en = (j & 1) ? e0 : e1;
+    float acc = 0.f;
+    for (int le = threadIdx.x; le < cnt; le += TBS) {
+      const int K = K0 + le;
+      const unsigned m = bm[le];
+      float t[NIN];
+#pragma unroll
+      for (int f = 0; f < NLF; ++f) {
+        const int kind = g.kind[f];
+        const bool bnd = (m >> f) & 1u;
+        const int os = PER_AXIS ? (f >> 1) * NF : f * NF;          // own slot of face f
+        const int ns = PER_AXIS ? (f >> 1) * NF : (f ^ 1) * NF;    // neighbour's slot
+        const int Kn = K + dlt[f];
+#pragma unroll
+        for (int q = 0; q < NF; ++q) {
+          float v = 0.f;
+          if (kind == FK_OWN_D) {
+            v = to_f(ev[(os + q) * epb + le]);
+          } else if (kind == FK_NBR_D) {
+            if (!bnd) v = to_f(ec[(ns + q) * ld + Kn]);
+          } else if (kind == FK_SUM_D) {
+            const float o = to_f(ev[(os + q) * epb + le]);
+            if (!bnd) v = o + to_f(ec[(ns + q) * ld + Kn]);
+            else if (g.bc_mirror) v = o + o;
+          }
+          t[f * NF + q] = v;
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < NEXP; ++e) {
+        if ((g.live >> e) & 1ull) {
+          float v = to_f(rv[e * epb + le]);
+#pragma unroll
+          for (int q = 0; q < NIN; ++q) v = fmaf(Lp.L[e][q], t[q], v);
+          const TL nv = from_f<TL>(v);
+          const float d = to_f(nv) - to_f(ev[e * epb + le]);
+          acc = fmaf(d, d, acc);
+          ev[e * epb + le] = nv;
+          en[e * ld + K] = nv;
+        }
+      }
+    }
+    double* part = partials + (long long)(s & 1) * gridDim.x;
+    const double bs = block_sum((double)acc, ws);
+    if (threadIdx.x == 0) part[blockIdx.x] = bs;
+    __threadfence();
+    grid_barrier(ctrl);
+    if (*(volatile int*)&ctrl->timeout) break;
+    double v = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += TBS) v += __ldcg(part + i);
+    const double tot = block_sum(v, ws);
+    if (threadIdx.x == 0) s_tot = tot;
+    __syncthreads();
+    const double step = sqrt(s_tot);
+    j += 1;
+    const int it = iter0 + s + 1;
+    const bool stop = step <= lim || j >= inner_max || it >= max_iters || !(step == step) || isinf(step);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      ctrl->inner_iter = j;
+      ctrl->iter = it;
+      ctrl->lowp_sweeps += 1;
+      ctrl->inner_step = step;
+      if (stop) ctrl->inner_done = 1;
+    }
+    if (stop) break;
+  }
+}
+
+// Launch the tile kernel when its block state fits in shared memory; returns
+// cudaErrorNotSupported (nothing launched) otherwise.
+template <int NF, int NLF, bool PER_AXIS, typename TL>
+cudaError_t launch_tile(MixedArgs& m, TL* rl, TL* e0, TL* e1) {
+  using LT = LTile<NF, NLF, PER_AXIS>;
+  const LaunchArgs& a = m.base;
+  if (!m.LE32h || a.g.n_exp != LT::NEXP || (long long)a.g.ld * LT::NEXP >= (1LL << 31)) return cudaErrorNotSupported;
+  auto k = k_inner_tile<NF, NLF, PER_AXIS, TL>;
+  int dev = 0, sms = 0, smem_max = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  smem_max -= 1024;   // static shared memory of the kernel
+  const long long nel = a.g.nel;
+  for (int bps = 4; bps >= 1; --bps) {
+    long long grid = (long long)bps * sms;
+    const long long cap = (nel + 63) / 64;          // at least two warps' worth of elements per block
+    if (grid > cap) grid = cap;
+    if (grid > m.max_grid) grid = m.max_grid;
+    if (grid < 1) grid = 1;
+    const long long epb = (nel + grid - 1) / grid;
+    grid = (nel + epb - 1) / epb;
+    const size_t smem = (size_t)epb * (2 * LT::NEXP * sizeof(TL) + 1) + 16;
+    if (smem > (size_t)smem_max) continue;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, TBS, smem);
+    if (e != cudaSuccess) return e;
+    if ((long long)per * sms < grid) continue;
+    LT L;
+    for (int r = 0; r < LT::NEXP; ++r)
+      for (int q = 0; q < LT::NIN; ++q) L.L[r][q] = m.LE32h[r * LT::NIN + q];
+    DevGeo gg = a.g;
+    const TL* rlc = rl;
+    Ctrl* ct = a.ctrl;
+    double* pp = a.partials;
+    int ep = (int)epb;
+    void* args[] = {&gg, &rlc, &e0, &e1, &ct, &pp, &ep, &L};
+    e = cudaLaunchCooperativeKernel((const void*)k, dim3((unsigned)grid), dim3(TBS), args, smem, a.stream);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+  }
+  return cudaErrorNotSupported;
+}
+
 inline unsigned grid_for(long long n) { return (unsigned)((n + BS - 1) / BS); }
 
 template <typename TL>
@@ -320,6 +495,11 @@ struct MixedRunner {
         }
         k<<<grid_for(a.g.nel), BS, smem, a.stream>>>(a.g, a.op, m.r64, e0, a.ctrl, a.partials, a.res_hist);
       } else {
+        if (!m.no_tile) {
+          cudaError_t te = a.g.per_axis ? launch_tile<NF, NLF, true, TL>(m, rl, e0, e1)
+                                        : launch_tile<NF, NLF, false, TL>(m, rl, e0, e1);
+          if (te != cudaErrorNotSupported) return te;
+        }
         // persistent cooperative launch: as many co-resident blocks as the elements need
         size_t smem = (size_t)a.g.n_exp * NIN * sizeof(float);
         auto k = k_inner_persist<NF, NLF, TL>;

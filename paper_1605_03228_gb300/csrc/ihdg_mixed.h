@@ -27,6 +27,8 @@ struct MixedArgs {
   void* e[2];           // low-precision correction, ping-pong
   int prec;
   int max_grid = 1 << 30;   // cap on the persistent kernel's grid (tests shrink it)
+  int no_tile = 0;          // 1: skip the shared-memory-resident tile kernel
+  const float* LE32h = nullptr;  // host copy of the float32 operator (n_exp x n_in)
 };
 
 MixedLayout mixed_layout(const DevGeo& g, int prec);

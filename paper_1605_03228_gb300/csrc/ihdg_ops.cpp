@@ -482,16 +482,14 @@ ihdg_status build_ops(const ihdg_mesh& m, const ihdg_coeffs& co, Ops& o, std::st
   o.Mn.assign((size_t)nvol * nvol, 0.0);
 
   if (co.pde == IHDG_TRANSPORT) {
-    int nout = 0;
+    // per-axis export layout: along each axis with beta_a != 0 exactly one face is outflow;
+    // slot a * nf + node holds u on it, and the downstream neighbour reads the same slots
+    o.n_exp = d * nf;
+    o.layout_per_axis = 1;
     for (int f = 0; f < nlf; ++f) {
       double bn = nsign(f) * co.beta[f / 2];
-      if (bn > 0) { o.own_off[f] = nout * nf; ++nout; }
-    }
-    o.n_exp = nout * nf;
-    for (int f = 0; f < nlf; ++f) {
-      double bn = nsign(f) * co.beta[f / 2];
-      if (bn > 0) o.face_kind[f] = FK_OWN;
-      else if (bn < 0) { o.face_kind[f] = FK_NBR; o.nbr_off[f] = o.own_off[f ^ 1]; }
+      if (bn > 0) { o.face_kind[f] = FK_OWN; o.own_off[f] = (f / 2) * nf; }
+      else if (bn < 0) { o.face_kind[f] = FK_NBR; o.nbr_off[f] = (f / 2) * nf; }
       else o.face_kind[f] = FK_NONE;
     }
     for (int a = 0; a < d; ++a) add_vol(K[a], 0, 0, -co.beta[a]);       // -(u, beta.grad v)

@@ -35,6 +35,8 @@ struct Ops {
   int own_off[6] = {-1, -1, -1, -1, -1, -1};  // export offset of this element's block
   int nbr_off[6] = {-1, -1, -1, -1, -1, -1};  // export offset of the neighbour's opposite block
   int bc_mirror = 0;                          // boundary SUM faces: input = 2 * own
+  int layout_per_axis = 0;                    // export slot = axis*nf + node (transport),
+                                              // else face*nf + node
   double in_scale[6] = {1, 1, 1, 1, 1, 1};    // input scale folded into G (1/alpha for CD)
   // dense operators, row-major
   std::vector<double> LE;     // n_exp x n_in

@@ -271,21 +271,26 @@ def test_mixed_transport3d(ctx, prec_name):
     assert rel(u, U.reshape(om.nel, -1)) < 1e-6
 
 
-def test_mixed_persistent_grid_stride(ctx, monkeypatch):
-    """The persistent inner kernel with a grid far smaller than the elements (every thread
-    loops over several elements) gives the same answer as the one-element-per-thread grid."""
+@pytest.mark.parametrize("kernel,grid", [("tile", "2"), ("global", "2"), ("global", "")])
+def test_mixed_inner_kernel_variants(ctx, monkeypatch, kernel, grid):
+    """The inner loop's kernel variants (block-resident tile state or global state) and grid
+    sizes far smaller than the element count (every thread loops over several elements)
+    reach the same solution as the default launch.  The inner stopping test sums per-block
+    partials, so the inner sweep count may differ by a sweep: compare at 1e-9."""
     ihdg = ih()
     n, p, beta = (40, 30), 2, (0.8, 1.0)
     mesh = ihdg.make_mesh(2, n, p)
     co = ihdg.make_coeffs(ihdg.TRANSPORT, beta=beta)
     vol, bnd = ihdg.quadrature_points(mesh, co)
     f, g = W.transport2d_forcing(vol, beta), W.transport2d_exact(bnd)
-    opts = ihdg.make_options(1e-10, prec=ihdg.MIXED_FP32)
+    opts = ihdg.make_options(1e-11, prec=ihdg.MIXED_FP32)
     u_a, _, ra = ctx.solve(mesh, co, f, g, opts)
-    monkeypatch.setenv("IHDG_PERSISTENT_GRID", "2")
+    if grid:
+        monkeypatch.setenv("IHDG_PERSISTENT_GRID", grid)
+    monkeypatch.setenv("IHDG_INNER_KERNEL", kernel)
     u_b, _, rb = ctx.solve(mesh, co, f, g, opts)
-    assert ra.status == rb.status == ihdg.OK and ra.iterations == rb.iterations
-    assert np.array_equal(u_a, u_b)
+    assert ra.status == rb.status == ihdg.OK
+    assert rel(u_b, u_a) < 1e-9
 
 
 def test_mixed_convdiff(ctx):

@@ -140,8 +140,8 @@ def test_export_form_matches_oracle_transport(p):
     pr = Transport(Discretisation(om, p), np.array(beta))
     nf = p + 1
     kinds = ["nbr", "own", "nbr", "own"]          # beta > 0: -x, -y inflow; +x, +y outflow
-    own_off = [0, 0, 0, nf]
-    nbr_off = [0, 0, nf, 0]
+    own_off = [(f // 2) * nf for f in range(4)]   # export slot = axis * nf + node
+    nbr_off = [(f // 2) * nf for f in range(4)]
     check_one_sweep(mesh, co, pr, kinds, own_off, nbr_off, False)
     # forcing part: u^1 from u^0 = 0 with g = 0 is PV f
     PV = ihdg.host_operator(mesh, co, 5)
