@@ -179,30 +179,47 @@ __global__ void __launch_bounds__(BS) k_inner_first(DevGeo g, OpsDev op, const d
   }
 }
 
-// Grid-wide barrier of a cooperative launch (all blocks co-resident).  The wait is bounded
-// by ~1 s of SM clock; on expiry the block sets ctrl->timeout and leaves the barrier, and
-// every block stops its loop at the next check.
-__device__ __forceinline__ void grid_barrier(Ctrl* ctrl) {
+// Flag-slot barrier with reduction, for cooperative launches.  Slot b (64 bits) holds the
+// float partial sum of block b in its low half and a tag in its high half; tags are the
+// solve's sweep numbers, so a slot written in sweep s is recognised without resetting it
+// (the slots are cleared before every launch).  Thread 0 publishes the block's slot with a
+// release store after the block's writes (bar.sync orders them before it); every block then
+// acquire-polls all slots until they carry the tag and sums the partials in slot order, so
+// all blocks obtain the same total.  Each poll is bounded by ~1 s of SM clock; on expiry
+// the block sets ctrl->timeout and every block stops at its next check.
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+template <int NT>
+__device__ double flag_reduce(unsigned long long* slots, double block_partial, unsigned tag, Ctrl* ctrl,
+                              double* ws, double* s_out) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned int* gen = &ctrl->bar_gen;
-    const unsigned int g0 = *gen;
-    __threadfence();
-    const unsigned int a = atomicAdd(&ctrl->bar_count, 1u);
-    if (a == gridDim.x - 1) {
-      ctrl->bar_count = 0u;
-      __threadfence();
-      atomicExch(&ctrl->bar_gen, g0 + 1u);
-    } else {
-      const long long t0 = clock64();
-      while (*gen == g0) {
-        if (clock64() - t0 > 2000000000LL) { atomicExch(&ctrl->timeout, 1); break; }
-        __nanosleep(20);
-      }
-    }
-    __threadfence();
+    const unsigned long long pk =
+        ((unsigned long long)tag << 32) | (unsigned long long)__float_as_uint((float)block_partial);
+    st_release_u64(slots + blockIdx.x, pk);
   }
+  double v = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += NT) {
+    const long long t0 = clock64();
+    unsigned long long x;
+    for (;;) {
+      x = ld_acquire_u64(slots + i);
+      if ((unsigned)(x >> 32) == tag) break;
+      if (clock64() - t0 > 2000000000LL) { atomicExch(&ctrl->timeout, 1); break; }
+    }
+    v += (double)__uint_as_float((unsigned)(x & 0xffffffffull));
+  }
+  const double tot = block_sum(v, ws);
+  if (threadIdx.x == 0) *s_out = tot;
   __syncthreads();
+  return *s_out;
 }
 
 // Persistent inner loop on the correction equation: e_{j+1} = r + L_E t(e_j), until the
@@ -264,20 +281,12 @@ __global__ void __launch_bounds__(PBS) k_inner_persist(DevGeo g, OpsDev op, cons
         }
       }
     }
-    double* part = partials + (long long)(s & 1) * gridDim.x;
-    const double bs = block_sum((double)acc, ws);
-    if (threadIdx.x == 0) part[blockIdx.x] = bs;
-    __threadfence();
-    grid_barrier(ctrl);
-    if (*(volatile int*)&ctrl->timeout) break;
-    double v = 0.0;
-    for (int i = threadIdx.x; i < (int)gridDim.x; i += PBS) v += __ldcg(part + i);
-    const double tot = block_sum(v, ws);
-    if (threadIdx.x == 0) s_tot = tot;
-    __syncthreads();
-    const double step = sqrt(s_tot);
-    j += 1;
     const int it = iter0 + s + 1;
+    const double bs = block_sum((double)acc, ws);
+    const double tot = flag_reduce<PBS>(reinterpret_cast<unsigned long long*>(partials), bs, (unsigned)it, ctrl, ws, &s_tot);
+    if (*(volatile int*)&ctrl->timeout) break;
+    const double step = sqrt(tot);
+    j += 1;
     const bool stop = step <= lim || j >= inner_max || it >= max_iters || !(step == step) || isinf(step);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       ctrl->inner_iter = j;
@@ -393,20 +402,12 @@ __global__ void __launch_bounds__(TBS) k_inner_tile(const DevGeo g, const TL* __
         }
       }
     }
-    double* part = partials + (long long)(s & 1) * gridDim.x;
-    const double bs = block_sum((double)acc, ws);
-    if (threadIdx.x == 0) part[blockIdx.x] = bs;
-    __threadfence();
-    grid_barrier(ctrl);
-    if (*(volatile int*)&ctrl->timeout) break;
-    double v = 0.0;
-    for (int i = threadIdx.x; i < (int)gridDim.x; i += TBS) v += __ldcg(part + i);
-    const double tot = block_sum(v, ws);
-    if (threadIdx.x == 0) s_tot = tot;
-    __syncthreads();
-    const double step = sqrt(s_tot);
-    j += 1;
     const int it = iter0 + s + 1;
+    const double bs = block_sum((double)acc, ws);
+    const double tot = flag_reduce<TBS>(reinterpret_cast<unsigned long long*>(partials), bs, (unsigned)it, ctrl, ws, &s_tot);
+    if (*(volatile int*)&ctrl->timeout) break;
+    const double step = sqrt(tot);
+    j += 1;
     const bool stop = step <= lim || j >= inner_max || it >= max_iters || !(step == step) || isinf(step);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       ctrl->inner_iter = j;
@@ -495,6 +496,9 @@ struct MixedRunner {
         }
         k<<<grid_for(a.g.nel), BS, smem, a.stream>>>(a.g, a.op, m.r64, e0, a.ctrl, a.partials, a.res_hist);
       } else {
+        // the flag slots of the persistent kernels start cleared (tags are sweep numbers)
+        cudaError_t ze = cudaMemsetAsync(a.partials, 0, sizeof(unsigned long long) * (size_t)m.slots, a.stream);
+        if (ze != cudaSuccess) return ze;
         if (!m.no_tile) {
           cudaError_t te = a.g.per_axis ? launch_tile<NF, NLF, true, TL>(m, rl, e0, e1)
                                         : launch_tile<NF, NLF, false, TL>(m, rl, e0, e1);

@@ -28,6 +28,7 @@ struct MixedArgs {
   int prec;
   int max_grid = 1 << 30;   // cap on the persistent kernel's grid (tests shrink it)
   int no_tile = 0;          // 1: skip the shared-memory-resident tile kernel
+  int slots = 0;            // length of the partials array (64-bit slots)
   const float* LE32h = nullptr;  // host copy of the float32 operator (n_exp x n_in)
 };
 
