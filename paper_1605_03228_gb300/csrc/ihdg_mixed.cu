@@ -308,20 +308,64 @@ struct LTile {
   float L[NEXP][NIN];
 };
 
-constexpr int TBS = 512;   // threads per block of the tile kernel
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid barrier plus sum of one double per block, for cooperative launches.  The arrival
+// counter only grows (cleared before the launch): barrier number b completes when it
+// reaches (b+1) * gridDim.x.  Thread 0 publishes the block's partial, arrives with a
+// release add and polls with acquire loads (bounded by ~1 s of SM clock, then
+// ctrl->timeout); warp 0 then sums the partials in block order with a fixed shuffle tree,
+// so every block obtains the same total.
+template <int NT>
+__device__ double barrier_sum(double* part, unsigned* count, unsigned nb, double mine, Ctrl* ctrl, double* s_out) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = mine;
+    red_release_add(count, 1u);
+    const unsigned target = nb * gridDim.x;
+    const long long t0 = clock64();
+    while (ld_acquire_u32(count) < target) {
+      if (clock64() - t0 > 2000000000LL) { atomicExch(&ctrl->timeout, 1); break; }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += 32) v += __ldcg(part + i);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) *s_out = v;
+  }
+  __syncthreads();
+  return *s_out;
+}
 
 // Persistent inner loop with block-resident state.  Block b owns elements
 // [b*epb, b*epb + epb); their own exports e_j and the residual r stay in shared memory
-// (TL precision, the values the neighbours see), with each element's boundary-face mask.
-// Per sweep only the neighbours' exports are read from global memory, and e_{j+1} is
-// written back for them.  The loop decision is the same as k_inner_persist's.
-template <int NF, int NLF, bool PER_AXIS, typename TL>
-__global__ void __launch_bounds__(TBS) k_inner_tile(const DevGeo g, const TL* __restrict__ rlp, TL* e0, TL* e1,
-                                                    Ctrl* ctrl, double* partials, const int epb,
-                                                    const LTile<NF, NLF, PER_AXIS> Lp) {
+// (TL precision: the values the neighbours see), with each element's boundary-face mask.
+// LPE lanes of a warp share one element: lane l gathers the traces of the faces
+// f = l, l + LPE, ... (own exports from shared memory, the neighbour's from global memory),
+// the lanes exchange them by shuffles, and lane l computes the export rows of its faces
+// (per-face layout) or axes (per-axis layout), reading the operator from the parameter
+// bank.  Per sweep only neighbours' exports cross global memory; the loop decision is the
+// same as k_inner_persist's.
+template <int NF, int NLF, bool PER_AXIS, typename TL, int NT, int LPE>
+__global__ void __launch_bounds__(NT) k_inner_tile(const DevGeo g, const TL* __restrict__ rlp, TL* e0, TL* e1,
+                                                   Ctrl* ctrl, double* partials, const int epb,
+                                                   const LTile<NF, NLF, PER_AXIS> Lp) {
   constexpr int NIN = NF * NLF;
   constexpr int NEXP = LTile<NF, NLF, PER_AXIS>::NEXP;
-  __shared__ double ws[TBS / 32];
+  constexpr int FPL = NLF / LPE;                    // faces per lane
+  constexpr int NBLK = PER_AXIS ? NLF / 2 : NLF;    // export row blocks (axes or faces)
+  constexpr int EPP = NT / LPE;                     // elements per pass
+  static_assert(NLF % LPE == 0 && 32 % LPE == 0, "lanes per element must divide faces and warps");
   __shared__ double s_tot;
   extern __shared__ __align__(16) unsigned char smraw[];
   if (ctrl_done(ctrl) || *(volatile const int*)&ctrl->inner_done) return;
@@ -335,12 +379,10 @@ __global__ void __launch_bounds__(TBS) k_inner_tile(const DevGeo g, const TL* __
   const int ld = (int)g.ld;
   const int K0 = blockIdx.x * epb;
   const int cnt = min(epb, (int)g.nel - K0);
-  int dlt[NLF];
-#pragma unroll
-  for (int f = 0; f < NLF; ++f) dlt[f] = (f & 1) ? (int)g.stride[f >> 1] : -(int)g.stride[f >> 1];
+  unsigned* count = &ctrl->bar_count;
   {
     const TL* ec = (j & 1) ? e1 : e0;
-    for (int le = threadIdx.x; le < cnt; le += TBS) {
+    for (int le = threadIdx.x; le < cnt; le += NT) {
       const int K = K0 + le;
       int c[3];
       coords(g, K, c);
@@ -350,61 +392,95 @@ __global__ void __launch_bounds__(TBS) k_inner_tile(const DevGeo g, const TL* __
       bm[le] = (unsigned char)m;
 #pragma unroll
       for (int e = 0; e < NEXP; ++e) {
-        if ((g.live >> e) & 1ull) {
-          ev[e * epb + le] = ec[e * ld + K];
-          rv[e * epb + le] = rlp[e * ld + K];
-        }
+        ev[e * epb + le] = ((g.live >> e) & 1ull) ? ec[e * ld + K] : from_f<TL>(0.f);
+        rv[e * epb + le] = ((g.live >> e) & 1ull) ? rlp[e * ld + K] : from_f<TL>(0.f);
       }
     }
   }
   __syncthreads();
+  const int lane = threadIdx.x & (LPE - 1);
+  const int wl = threadIdx.x & 31;
+  const int gbase = wl & ~(LPE - 1);
+  const int npass = (cnt + EPP - 1) / EPP;
   for (int s = 0;; ++s) {
     const TL* __restrict__ ec = (j & 1) ? e1 : e0;
     TL* __restrict__ en = (j & 1) ? e0 : e1;
     float acc = 0.f;
-    for (int le = threadIdx.x; le < cnt; le += TBS) {
+    for (int pass = 0; pass < npass; ++pass) {
+      const int le = pass * EPP + threadIdx.x / LPE;
+      const bool valid = le < cnt;
       const int K = K0 + le;
-      const unsigned m = bm[le];
-      float t[NIN];
+      const unsigned m = valid ? bm[le] : 0u;
+      // a1: this lane's faces
+      float lt[FPL][NF];
 #pragma unroll
-      for (int f = 0; f < NLF; ++f) {
+      for (int i = 0; i < FPL; ++i) {
+        const int f = i * LPE + lane;                 // runtime face of this lane
         const int kind = g.kind[f];
         const bool bnd = (m >> f) & 1u;
-        const int os = PER_AXIS ? (f >> 1) * NF : f * NF;          // own slot of face f
-        const int ns = PER_AXIS ? (f >> 1) * NF : (f ^ 1) * NF;    // neighbour's slot
-        const int Kn = K + dlt[f];
+        const int a = f >> 1;
+        const int os = PER_AXIS ? a * NF : f * NF;
+        const int ns = PER_AXIS ? a * NF : (f ^ 1) * NF;
+        const int Kn = K + ((f & 1) ? (int)g.stride[a] : -(int)g.stride[a]);
 #pragma unroll
         for (int q = 0; q < NF; ++q) {
           float v = 0.f;
-          if (kind == FK_OWN_D) {
-            v = to_f(ev[(os + q) * epb + le]);
-          } else if (kind == FK_NBR_D) {
-            if (!bnd) v = to_f(ec[(ns + q) * ld + Kn]);
-          } else if (kind == FK_SUM_D) {
-            const float o = to_f(ev[(os + q) * epb + le]);
-            if (!bnd) v = o + to_f(ec[(ns + q) * ld + Kn]);
-            else if (g.bc_mirror) v = o + o;
+          if (valid) {
+            if (kind == FK_OWN_D) {
+              v = to_f(ev[(os + q) * epb + le]);
+            } else if (kind == FK_NBR_D) {
+              if (!bnd) v = to_f(ec[(ns + q) * ld + Kn]);
+            } else if (kind == FK_SUM_D) {
+              const float o = to_f(ev[(os + q) * epb + le]);
+              if (!bnd) v = o + to_f(ec[(ns + q) * ld + Kn]);
+              else if (g.bc_mirror) v = o + o;
+            }
           }
-          t[f * NF + q] = v;
+          lt[i][q] = v;
         }
       }
+      // exchange: every lane of the element obtains all NIN traces
+      float t[NIN];
 #pragma unroll
-      for (int e = 0; e < NEXP; ++e) {
-        if ((g.live >> e) & 1ull) {
-          float v = to_f(rv[e * epb + le]);
+      for (int f = 0; f < NLF; ++f)
 #pragma unroll
-          for (int q = 0; q < NIN; ++q) v = fmaf(Lp.L[e][q], t[q], v);
-          const TL nv = from_f<TL>(v);
-          const float d = to_f(nv) - to_f(ev[e * epb + le]);
-          acc = fmaf(d, d, acc);
-          ev[e * epb + le] = nv;
-          en[e * ld + K] = nv;
+        for (int q = 0; q < NF; ++q) {
+          if constexpr (LPE == 1) t[f * NF + q] = lt[f][q];
+          else t[f * NF + q] = __shfl_sync(0xffffffffu, lt[f / LPE][q], gbase + (f % LPE));
+        }
+      if constexpr (LPE > 1) __syncwarp();
+      // a3/a4: this lane's export rows
+      if (valid) {
+#pragma unroll
+        for (int rb = 0; rb < NBLK; ++rb) {
+          if (LPE > 1 && rb % LPE != lane) continue;
+#pragma unroll
+          for (int q = 0; q < NF; ++q) {
+            const int e = rb * NF + q;
+            float v = to_f(rv[e * epb + le]);
+#pragma unroll
+            for (int k = 0; k < NIN; ++k) v = fmaf(Lp.L[e][k], t[k], v);
+            const TL nv = from_f<TL>(v);
+            const float d = to_f(nv) - to_f(ev[e * epb + le]);
+            acc = fmaf(d, d, acc);
+            ev[e * epb + le] = nv;
+            if ((g.live >> e) & 1ull) en[e * ld + K] = nv;
+          }
         }
       }
+      if constexpr (LPE > 1) __syncwarp();
     }
     const int it = iter0 + s + 1;
-    const double bs = block_sum((double)acc, ws);
-    const double tot = flag_reduce<TBS>(reinterpret_cast<unsigned long long*>(partials), bs, (unsigned)it, ctrl, ws, &s_tot);
+    double bs = (double)acc;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bs += __shfl_down_sync(0xffffffffu, bs, o);
+    __shared__ double wsum[NT / 32];
+    if (wl == 0) wsum[threadIdx.x >> 5] = bs;
+    __syncthreads();
+    double blk = 0.0;
+    if (threadIdx.x == 0)
+      for (int w = 0; w < NT / 32; ++w) blk += wsum[w];
+    const double tot = barrier_sum<NT>(partials + (size_t)(s & 1) * gridDim.x, count, (unsigned)(s + 1), blk, ctrl, &s_tot);
     if (*(volatile int*)&ctrl->timeout) break;
     const double step = sqrt(tot);
     j += 1;
@@ -422,32 +498,33 @@ __global__ void __launch_bounds__(TBS) k_inner_tile(const DevGeo g, const TL* __
 
 // Launch the tile kernel when its block state fits in shared memory; returns
 // cudaErrorNotSupported (nothing launched) otherwise.
-template <int NF, int NLF, bool PER_AXIS, typename TL>
-cudaError_t launch_tile(MixedArgs& m, TL* rl, TL* e0, TL* e1) {
+template <int NF, int NLF, bool PER_AXIS, typename TL, int NT, int LPE>
+cudaError_t launch_tile_v(MixedArgs& m, TL* rl, TL* e0, TL* e1) {
   using LT = LTile<NF, NLF, PER_AXIS>;
   const LaunchArgs& a = m.base;
   if (!m.LE32h || a.g.n_exp != LT::NEXP || (long long)a.g.ld * LT::NEXP >= (1LL << 31)) return cudaErrorNotSupported;
-  auto k = k_inner_tile<NF, NLF, PER_AXIS, TL>;
+  auto k = k_inner_tile<NF, NLF, PER_AXIS, TL, NT, LPE>;
   int dev = 0, sms = 0, smem_max = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   smem_max -= 1024;   // static shared memory of the kernel
   const long long nel = a.g.nel;
-  for (int bps = 4; bps >= 1; --bps) {
+  for (int bps = 2; bps >= 1; --bps) {
     long long grid = (long long)bps * sms;
-    const long long cap = (nel + 63) / 64;          // at least two warps' worth of elements per block
+    const long long cap = (nel + 63) / 64;          // at least 64 elements per block
     if (grid > cap) grid = cap;
     if (grid > m.max_grid) grid = m.max_grid;
     if (grid < 1) grid = 1;
     const long long epb = (nel + grid - 1) / grid;
     grid = (nel + epb - 1) / epb;
+    if (grid > m.slots / 2) continue;
     const size_t smem = (size_t)epb * (2 * LT::NEXP * sizeof(TL) + 1) + 16;
     if (smem > (size_t)smem_max) continue;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, TBS, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, NT, smem);
     if (e != cudaSuccess) return e;
     if ((long long)per * sms < grid) continue;
     LT L;
@@ -458,12 +535,24 @@ cudaError_t launch_tile(MixedArgs& m, TL* rl, TL* e0, TL* e1) {
     Ctrl* ct = a.ctrl;
     double* pp = a.partials;
     int ep = (int)epb;
+    e = cudaMemsetAsync(&a.ctrl->bar_count, 0, sizeof(unsigned), a.stream);
+    if (e != cudaSuccess) return e;
     void* args[] = {&gg, &rlc, &e0, &e1, &ct, &pp, &ep, &L};
-    e = cudaLaunchCooperativeKernel((const void*)k, dim3((unsigned)grid), dim3(TBS), args, smem, a.stream);
+    e = cudaLaunchCooperativeKernel((const void*)k, dim3((unsigned)grid), dim3(NT), args, smem, a.stream);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
   }
   return cudaErrorNotSupported;
+}
+
+// Tile kernel shape: one element per thread (default) or, with IHDG_TILE_LPE=4 on 2D
+// meshes, four lanes per element (one face each) with shuffled traces.
+template <int NF, int NLF, bool PER_AXIS, typename TL>
+cudaError_t launch_tile(MixedArgs& m, TL* rl, TL* e0, TL* e1) {
+  if constexpr (NLF == 4) {
+    if (m.tile_lpe == 4) return launch_tile_v<NF, NLF, PER_AXIS, TL, 1024, 4>(m, rl, e0, e1);
+  }
+  return launch_tile_v<NF, NLF, PER_AXIS, TL, 512, 1>(m, rl, e0, e1);
 }
 
 inline unsigned grid_for(long long n) { return (unsigned)((n + BS - 1) / BS); }

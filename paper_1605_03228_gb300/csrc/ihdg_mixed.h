@@ -29,6 +29,7 @@ struct MixedArgs {
   int max_grid = 1 << 30;   // cap on the persistent kernel's grid (tests shrink it)
   int no_tile = 0;          // 1: skip the shared-memory-resident tile kernel
   int slots = 0;            // length of the partials array (64-bit slots)
+  int tile_lpe = 1;         // lanes per element of the tile kernel (1, or 4 on 2D meshes)
   const float* LE32h = nullptr;  // host copy of the float32 operator (n_exp x n_in)
 };
 
