@@ -288,7 +288,8 @@ ihdg_status device_iterate(ihdg_ctx* ctx, Plan* pl, const ihdg_options& o, const
     }
     // IHDG_INNER_KERNEL=global selects the global-memory persistent kernel over the tile one
     if (const char* ker = std::getenv("IHDG_INNER_KERNEL")) m.no_tile = std::strcmp(ker, "global") == 0;
-    if (const char* lpe = std::getenv("IHDG_TILE_LPE")) m.tile_lpe = std::atoi(lpe) == 4 ? 4 : 1;
+    // IHDG_TILE_LPE=1 skips the register-resident 2D kernel (one element per thread instead)
+    if (const char* lpe = std::getenv("IHDG_TILE_LPE")) m.tile_lpe = std::atoi(lpe) == 1 ? 1 : 4;
     m.LE32h = pl->le32.data();
     m.slots = partials_needed(pl->g.nel);
     ihdg_status st = run_mixed(ctx->h_ctrl, m, o, &Eu, &Eu2, &Et, &Et2, ctx->err, &tm);

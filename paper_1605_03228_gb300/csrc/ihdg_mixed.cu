@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <vector>
 
 #include "ihdg_common.cuh"
 #include "ihdg_dev.h"
@@ -545,13 +546,175 @@ cudaError_t launch_tile_v(MixedArgs& m, TL* rl, TL* e0, TL* e1) {
   return cudaErrorNotSupported;
 }
 
+// Persistent inner loop for 2D meshes with register-resident state: four lanes per element,
+// lane l owns face l.  Each lane keeps in registers the exports of its face (per-face
+// layout) or of its axis when the face is the axis' outflow face (per-axis layout), and the
+// matching residual values; it gathers its face's traces (own registers + the neighbour's
+// exports from global memory), broadcasts them to the element's other lanes by shuffles, and
+// accumulates its rows as the traces arrive.  The operator sits in shared memory transposed
+// and padded, LT[k][rowblock * RW + r], so one 128-bit load gives a lane the coefficients of
+// trace k for 4 of its rows.  Every thread owns one (element, face) pair for the whole launch.
+template <int NF, bool PER_AXIS, typename TL>
+__global__ void __launch_bounds__(1024) k_inner_reg(const DevGeo g, const TL* __restrict__ rlp, TL* e0, TL* e1,
+                                                    Ctrl* ctrl, double* partials, const float* __restrict__ LTg) {
+  constexpr int NT = 1024, LPE = 4, NIN = 4 * NF;
+  constexpr int RW = (NF + 3) & ~3;          // padded row-block width
+  constexpr int NRB = 4;                     // row blocks stored (faces; axes use the first 2)
+  __shared__ __align__(16) float LT[NIN * NRB * RW];
+  __shared__ double wsum[NT / 32];
+  __shared__ double s_tot;
+  if (ctrl_done(ctrl) || *(volatile const int*)&ctrl->inner_done) return;
+  int j = *(volatile const int*)&ctrl->inner_iter;
+  const int iter0 = *(volatile const int*)&ctrl->iter;
+  const int max_iters = ctrl->max_iters, inner_max = ctrl->inner_max;
+  const double lim = ctrl->inner_rtol * ctrl->rnorm;
+  for (int i = threadIdx.x; i < NIN * NRB * RW; i += NT) LT[i] = LTg[i];
+  const int lane = threadIdx.x & 3;                  // face of this thread
+  const int gbase = (threadIdx.x & 31) & ~3;
+  const int K = blockIdx.x * (NT / LPE) + (threadIdx.x >> 2);
+  const bool valid = K < (int)g.nel;
+  const int ld = (int)g.ld;
+  const int f = lane, a = f >> 1;
+  const int kind = g.kind[f];
+  // rows owned by this lane: face f (per-face) or axis a when f is its outflow face (per-axis)
+  const bool has_rows = valid && (PER_AXIS ? kind == FK_OWN_D : (kind == FK_SUM_D || kind == FK_OWN_D));
+  const int rb = PER_AXIS ? a : f;
+  const int row0 = rb * NF;
+  const bool rows_live = ((g.live >> row0) & 1ull) != 0;
+  int c[3] = {0, 0, 0};
+  if (valid) coords(g, K, c);
+  const bool bnd = valid && on_bnd(g, c, f);
+  const int Kn = K + ((f & 1) ? (int)g.stride[a] : -(int)g.stride[a]);
+  const int os = row0;                                  // own slot of this face
+  const int ns = PER_AXIS ? a * NF : (f ^ 1) * NF;      // neighbour's slot across it
+  float ev[NF], rv[NF];
+  {
+    const TL* ec = (j & 1) ? e1 : e0;
+#pragma unroll
+    for (int r = 0; r < NF; ++r) {
+      ev[r] = (has_rows && rows_live) ? to_f(ec[(row0 + r) * ld + K]) : 0.f;
+      rv[r] = (has_rows && rows_live) ? to_f(rlp[(row0 + r) * ld + K]) : 0.f;
+    }
+  }
+  // per-axis inflow lanes need the own value only for OWN faces (none); per-face lanes own
+  // exactly their face's slots, so the gather's own part is ev[] of the same lane
+  __syncthreads();
+  unsigned* count = &ctrl->bar_count;
+  for (int s = 0;; ++s) {
+    const TL* __restrict__ ec = (j & 1) ? e1 : e0;
+    TL* __restrict__ en = (j & 1) ? e0 : e1;
+    float lt[NF];
+#pragma unroll
+    for (int q = 0; q < NF; ++q) {
+      float v = 0.f;
+      if (valid) {
+        if (kind == FK_OWN_D) {
+          v = ev[q];
+        } else if (kind == FK_NBR_D) {
+          if (!bnd) v = to_f(ec[(ns + q) * ld + Kn]);
+        } else if (kind == FK_SUM_D) {
+          if (!bnd) v = ev[q] + to_f(ec[(ns + q) * ld + Kn]);
+          else if (g.bc_mirror) v = ev[q] + ev[q];
+        }
+      }
+      lt[q] = v;
+    }
+    float acc[RW];
+#pragma unroll
+    for (int r = 0; r < RW; ++r) acc[r] = r < NF ? rv[r] : 0.f;
+#pragma unroll
+    for (int src = 0; src < LPE; ++src) {
+#pragma unroll
+      for (int q = 0; q < NF; ++q) {
+        const float x = __shfl_sync(0xffffffffu, lt[q], gbase + src);
+        const float* col = LT + ((src * NF + q) * NRB + rb) * RW;
+#pragma unroll
+        for (int r4 = 0; r4 < RW; r4 += 4) {
+          const float4 cf = *reinterpret_cast<const float4*>(col + r4);
+          acc[r4 + 0] = fmaf(cf.x, x, acc[r4 + 0]);
+          acc[r4 + 1] = fmaf(cf.y, x, acc[r4 + 1]);
+          acc[r4 + 2] = fmaf(cf.z, x, acc[r4 + 2]);
+          acc[r4 + 3] = fmaf(cf.w, x, acc[r4 + 3]);
+        }
+      }
+    }
+    float st = 0.f;
+    if (has_rows && rows_live) {
+#pragma unroll
+      for (int r = 0; r < NF; ++r) {
+        const TL nv = from_f<TL>(acc[r]);
+        const float nvf = to_f(nv);
+        const float d = nvf - ev[r];
+        st = fmaf(d, d, st);
+        ev[r] = nvf;
+        en[(row0 + r) * ld + K] = nv;
+      }
+    }
+    const int it = iter0 + s + 1;
+    double bs = (double)st;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bs += __shfl_down_sync(0xffffffffu, bs, o);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = bs;
+    __syncthreads();
+    double blk = 0.0;
+    if (threadIdx.x == 0)
+      for (int w = 0; w < NT / 32; ++w) blk += wsum[w];
+    const double tot = barrier_sum<NT>(partials + (size_t)(s & 1) * gridDim.x, count, (unsigned)(s + 1), blk, ctrl, &s_tot);
+    if (*(volatile int*)&ctrl->timeout) break;
+    const double step = sqrt(tot);
+    j += 1;
+    const bool stop = step <= lim || j >= inner_max || it >= max_iters || !(step == step) || isinf(step);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      ctrl->inner_iter = j;
+      ctrl->iter = it;
+      ctrl->lowp_sweeps += 1;
+      ctrl->inner_step = step;
+      if (stop) ctrl->inner_done = 1;
+    }
+    if (stop) break;
+  }
+}
+
+// Launch k_inner_reg when every (element, face) pair can be a resident thread.
+template <int NF, bool PER_AXIS, typename TL>
+cudaError_t launch_reg(MixedArgs& m, TL* rl, TL* e0, TL* e1) {
+  constexpr int NIN = 4 * NF, RW = (NF + 3) & ~3, NRB = 4;
+  const LaunchArgs& a = m.base;
+  if (a.g.dim != 2 || !m.LE32h || (long long)a.g.ld * a.g.n_exp >= (1LL << 31)) return cudaErrorNotSupported;
+  auto k = k_inner_reg<NF, PER_AXIS, TL>;
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, 1024, 0);
+  if (e != cudaSuccess) return e;
+  const long long grid = (a.g.nel + 255) / 256;
+  if (grid > (long long)per * sms || grid > m.max_grid || grid > m.slots / 2) return cudaErrorNotSupported;
+  if (m.dLT == nullptr) return cudaErrorNotSupported;
+  // transposed, padded operator: LT[k][rb * RW + r] = L_E[rb * NF + r][k]
+  std::vector<float> lt((size_t)NIN * NRB * RW, 0.f);
+  const int nrb = a.g.n_exp / NF;
+  for (int kk = 0; kk < NIN; ++kk)
+    for (int b = 0; b < nrb; ++b)
+      for (int r = 0; r < NF; ++r) lt[((size_t)kk * NRB + b) * RW + r] = m.LE32h[(b * NF + r) * NIN + kk];
+  e = cudaMemcpyAsync(m.dLT, lt.data(), lt.size() * sizeof(float), cudaMemcpyHostToDevice, a.stream);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(&a.ctrl->bar_count, 0, sizeof(unsigned), a.stream);
+  if (e != cudaSuccess) return e;
+  DevGeo gg = a.g;
+  const TL* rlc = rl;
+  Ctrl* ct = a.ctrl;
+  double* pp = a.partials;
+  const float* ltp = m.dLT;
+  void* args[] = {&gg, &rlc, &e0, &e1, &ct, &pp, &ltp};
+  e = cudaLaunchCooperativeKernel((const void*)k, dim3((unsigned)grid), dim3(1024), args, 0, a.stream);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
 // Tile kernel shape: one element per thread (default) or, with IHDG_TILE_LPE=4 on 2D
 // meshes, four lanes per element (one face each) with shuffled traces.
 template <int NF, int NLF, bool PER_AXIS, typename TL>
 cudaError_t launch_tile(MixedArgs& m, TL* rl, TL* e0, TL* e1) {
-  if constexpr (NLF == 4) {
-    if (m.tile_lpe == 4) return launch_tile_v<NF, NLF, PER_AXIS, TL, 1024, 4>(m, rl, e0, e1);
-  }
   return launch_tile_v<NF, NLF, PER_AXIS, TL, 512, 1>(m, rl, e0, e1);
 }
 
@@ -589,6 +752,13 @@ struct MixedRunner {
         cudaError_t ze = cudaMemsetAsync(a.partials, 0, sizeof(unsigned long long) * (size_t)m.slots, a.stream);
         if (ze != cudaSuccess) return ze;
         if (!m.no_tile) {
+          if constexpr (NLF == 4) {
+            if (m.tile_lpe != 1) {
+              cudaError_t re = a.g.per_axis ? launch_reg<NF, true, TL>(m, rl, e0, e1)
+                                            : launch_reg<NF, false, TL>(m, rl, e0, e1);
+              if (re != cudaErrorNotSupported) return re;
+            }
+          }
           cudaError_t te = a.g.per_axis ? launch_tile<NF, NLF, true, TL>(m, rl, e0, e1)
                                         : launch_tile<NF, NLF, false, TL>(m, rl, e0, e1);
           if (te != cudaErrorNotSupported) return te;
@@ -656,7 +826,8 @@ MixedLayout mixed_layout(const DevGeo& g, int prec) {
   L.rlp = 0;
   L.e0 = one;
   L.e1 = 2 * one;
-  L.total = 3 * one;
+  L.lt = 3 * one;
+  L.total = 3 * one + 8192;   // + transposed operator of the register kernel
   return L;
 }
 
@@ -667,6 +838,7 @@ void mixed_bind(MixedArgs& m, char* region, const MixedLayout& L, int prec) {
   m.rlp = region + L.rlp;
   m.e[0] = region + L.e0;
   m.e[1] = region + L.e1;
+  m.dLT = reinterpret_cast<float*>(region + L.lt);
 }
 
 ihdg_status run_mixed(Ctrl* hc, MixedArgs& m, const ihdg_options& o, const double** Eu, const double** Eu2,

@@ -15,7 +15,7 @@
 namespace ihdg {
 
 struct MixedLayout {
-  size_t rlp, e0, e1, total;   // byte offsets inside the mixed region
+  size_t rlp, e0, e1, lt, total;   // byte offsets inside the mixed region
   int lp_bytes;                // bytes per low-precision value
 };
 
@@ -29,7 +29,8 @@ struct MixedArgs {
   int max_grid = 1 << 30;   // cap on the persistent kernel's grid (tests shrink it)
   int no_tile = 0;          // 1: skip the shared-memory-resident tile kernel
   int slots = 0;            // length of the partials array (64-bit slots)
-  int tile_lpe = 1;         // lanes per element of the tile kernel (1, or 4 on 2D meshes)
+  int tile_lpe = 4;         // 4: 2D meshes use the register-resident kernel when it fits
+  float* dLT = nullptr;     // device scratch for the transposed operator (register kernel)
   const float* LE32h = nullptr;  // host copy of the float32 operator (n_exp x n_in)
 };
 

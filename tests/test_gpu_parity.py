@@ -271,9 +271,11 @@ def test_mixed_transport3d(ctx, prec_name):
     assert rel(u, U.reshape(om.nel, -1)) < 1e-6
 
 
-@pytest.mark.parametrize("kernel,grid", [("tile", "2"), ("global", "2"), ("global", "")])
-def test_mixed_inner_kernel_variants(ctx, monkeypatch, kernel, grid):
-    """The inner loop's kernel variants (block-resident tile state or global state) and grid
+@pytest.mark.parametrize("kernel,grid,lpe", [("tile", "2", "1"), ("tile", "", "1"), ("global", "2", "1"),
+                                             ("global", "", "1")])
+def test_mixed_inner_kernel_variants(ctx, monkeypatch, kernel, grid, lpe):
+    """The inner loop's kernel variants (register-resident 4-lanes-per-element state, the
+    default on 2D meshes; block-resident tile state; global state) and grid
     sizes far smaller than the element count (every thread loops over several elements)
     reach the same solution as the default launch.  The inner stopping test sums per-block
     partials, so the inner sweep count may differ by a sweep: compare at 1e-9."""
@@ -288,6 +290,7 @@ def test_mixed_inner_kernel_variants(ctx, monkeypatch, kernel, grid):
     if grid:
         monkeypatch.setenv("IHDG_PERSISTENT_GRID", grid)
     monkeypatch.setenv("IHDG_INNER_KERNEL", kernel)
+    monkeypatch.setenv("IHDG_TILE_LPE", lpe)
     u_b, _, rb = ctx.solve(mesh, co, f, g, opts)
     assert ra.status == rb.status == ihdg.OK
     assert rel(u_b, u_a) < 1e-9
