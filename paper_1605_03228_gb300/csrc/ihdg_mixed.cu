@@ -546,18 +546,19 @@ cudaError_t launch_tile_v(MixedArgs& m, TL* rl, TL* e0, TL* e1) {
   return cudaErrorNotSupported;
 }
 
-// Persistent inner loop for 2D meshes with register-resident state: four lanes per element,
-// lane l owns face l.  Each lane keeps in registers the exports of its face (per-face
-// layout) or of its axis when the face is the axis' outflow face (per-axis layout), and the
-// matching residual values; it gathers its face's traces (own registers + the neighbour's
-// exports from global memory), broadcasts them to the element's other lanes by shuffles, and
-// accumulates its rows as the traces arrive.  The operator sits in shared memory transposed
-// and padded, LT[k][rowblock * RW + r], so one 128-bit load gives a lane the coefficients of
-// trace k for 4 of its rows.  Every thread owns one (element, face) pair for the whole launch.
-template <int NF, bool PER_AXIS, typename TL>
-__global__ void __launch_bounds__(1024) k_inner_reg(const DevGeo g, const TL* __restrict__ rlp, TL* e0, TL* e1,
-                                                    Ctrl* ctrl, double* partials, const float* __restrict__ LTg) {
-  constexpr int NT = 1024, LPE = 4, NIN = 4 * NF;
+// Persistent inner loop for 2D meshes with register-resident state: LPE lanes per element
+// (2 or 4); lane l owns the faces f = l, l + LPE.  For each of its faces a lane keeps in
+// registers the exports of that face (per-face layout) or of the face's axis when the face is
+// the axis' outflow face (per-axis layout), and the matching residual values; it gathers its
+// faces' traces (own registers + the neighbour's exports from global memory), broadcasts them
+// to the element's other lanes by shuffles, and accumulates its rows as the traces arrive.
+// The operator sits in shared memory transposed and padded, LT[k][rowblock * RW + r], so one
+// 128-bit load gives a lane the coefficients of trace k for 4 rows of one block.  Every thread
+// owns one (element, lane) pair for the whole launch.
+template <int NF, bool PER_AXIS, typename TL, int LPE>
+__global__ void __launch_bounds__(512, 2) k_inner_reg(const DevGeo g, const TL* __restrict__ rlp, TL* e0, TL* e1,
+                                                      Ctrl* ctrl, double* partials, const float* __restrict__ LTg) {
+  constexpr int NT = 512, NIN = 4 * NF, FPL = 4 / LPE;
   constexpr int RW = (NF + 3) & ~3;          // padded row-block width
   constexpr int NRB = 4;                     // row blocks stored (faces; axes use the first 2)
   __shared__ __align__(16) float LT[NIN * NRB * RW];
@@ -569,85 +570,99 @@ __global__ void __launch_bounds__(1024) k_inner_reg(const DevGeo g, const TL* __
   const int max_iters = ctrl->max_iters, inner_max = ctrl->inner_max;
   const double lim = ctrl->inner_rtol * ctrl->rnorm;
   for (int i = threadIdx.x; i < NIN * NRB * RW; i += NT) LT[i] = LTg[i];
-  const int lane = threadIdx.x & 3;                  // face of this thread
-  const int gbase = (threadIdx.x & 31) & ~3;
-  const int K = blockIdx.x * (NT / LPE) + (threadIdx.x >> 2);
+  const int lane = threadIdx.x % LPE;
+  const int gbase = (threadIdx.x & 31) - lane;
+  const int K = blockIdx.x * (NT / LPE) + threadIdx.x / LPE;
   const bool valid = K < (int)g.nel;
   const int ld = (int)g.ld;
-  const int f = lane, a = f >> 1;
-  const int kind = g.kind[f];
-  // rows owned by this lane: face f (per-face) or axis a when f is its outflow face (per-axis)
-  const bool has_rows = valid && (PER_AXIS ? kind == FK_OWN_D : (kind == FK_SUM_D || kind == FK_OWN_D));
-  const int rb = PER_AXIS ? a : f;
-  const int row0 = rb * NF;
-  const bool rows_live = ((g.live >> row0) & 1ull) != 0;
   int c[3] = {0, 0, 0};
   if (valid) coords(g, K, c);
-  const bool bnd = valid && on_bnd(g, c, f);
-  const int Kn = K + ((f & 1) ? (int)g.stride[a] : -(int)g.stride[a]);
-  const int os = row0;                                  // own slot of this face
-  const int ns = PER_AXIS ? a * NF : (f ^ 1) * NF;      // neighbour's slot across it
-  float ev[NF], rv[NF];
+  int kind[FPL], Kn[FPL], ns[FPL], row0[FPL];
+  bool bnd[FPL], rows[FPL];
+#pragma unroll
+  for (int i = 0; i < FPL; ++i) {
+    const int f = lane + LPE * i, a = f >> 1;
+    kind[i] = g.kind[f];
+    bnd[i] = valid && on_bnd(g, c, f);
+    Kn[i] = K + ((f & 1) ? (int)g.stride[a] : -(int)g.stride[a]);
+    ns[i] = PER_AXIS ? a * NF : (f ^ 1) * NF;
+    row0[i] = PER_AXIS ? a * NF : f * NF;
+    const bool owns = PER_AXIS ? kind[i] == FK_OWN_D : (kind[i] == FK_SUM_D || kind[i] == FK_OWN_D);
+    rows[i] = valid && owns && ((g.live >> row0[i]) & 1ull);
+  }
+  float ev[FPL][NF], rv[FPL][NF];
   {
     const TL* ec = (j & 1) ? e1 : e0;
 #pragma unroll
-    for (int r = 0; r < NF; ++r) {
-      ev[r] = (has_rows && rows_live) ? to_f(ec[(row0 + r) * ld + K]) : 0.f;
-      rv[r] = (has_rows && rows_live) ? to_f(rlp[(row0 + r) * ld + K]) : 0.f;
-    }
+    for (int i = 0; i < FPL; ++i)
+#pragma unroll
+      for (int r = 0; r < NF; ++r) {
+        ev[i][r] = rows[i] ? to_f(ec[(row0[i] + r) * ld + K]) : 0.f;
+        rv[i][r] = rows[i] ? to_f(rlp[(row0[i] + r) * ld + K]) : 0.f;
+      }
   }
-  // per-axis inflow lanes need the own value only for OWN faces (none); per-face lanes own
-  // exactly their face's slots, so the gather's own part is ev[] of the same lane
   __syncthreads();
   unsigned* count = &ctrl->bar_count;
   for (int s = 0;; ++s) {
     const TL* __restrict__ ec = (j & 1) ? e1 : e0;
     TL* __restrict__ en = (j & 1) ? e0 : e1;
-    float lt[NF];
+    float lt[FPL][NF];
 #pragma unroll
-    for (int q = 0; q < NF; ++q) {
-      float v = 0.f;
-      if (valid) {
-        if (kind == FK_OWN_D) {
-          v = ev[q];
-        } else if (kind == FK_NBR_D) {
-          if (!bnd) v = to_f(ec[(ns + q) * ld + Kn]);
-        } else if (kind == FK_SUM_D) {
-          if (!bnd) v = ev[q] + to_f(ec[(ns + q) * ld + Kn]);
-          else if (g.bc_mirror) v = ev[q] + ev[q];
-        }
-      }
-      lt[q] = v;
-    }
-    float acc[RW];
-#pragma unroll
-    for (int r = 0; r < RW; ++r) acc[r] = r < NF ? rv[r] : 0.f;
-#pragma unroll
-    for (int src = 0; src < LPE; ++src) {
+    for (int i = 0; i < FPL; ++i)
 #pragma unroll
       for (int q = 0; q < NF; ++q) {
-        const float x = __shfl_sync(0xffffffffu, lt[q], gbase + src);
-        const float* col = LT + ((src * NF + q) * NRB + rb) * RW;
-#pragma unroll
-        for (int r4 = 0; r4 < RW; r4 += 4) {
-          const float4 cf = *reinterpret_cast<const float4*>(col + r4);
-          acc[r4 + 0] = fmaf(cf.x, x, acc[r4 + 0]);
-          acc[r4 + 1] = fmaf(cf.y, x, acc[r4 + 1]);
-          acc[r4 + 2] = fmaf(cf.z, x, acc[r4 + 2]);
-          acc[r4 + 3] = fmaf(cf.w, x, acc[r4 + 3]);
+        float v = 0.f;
+        if (valid) {
+          if (kind[i] == FK_OWN_D) {
+            v = ev[i][q];
+          } else if (kind[i] == FK_NBR_D) {
+            if (!bnd[i]) v = to_f(ec[(ns[i] + q) * ld + Kn[i]]);
+          } else if (kind[i] == FK_SUM_D) {
+            if (!bnd[i]) v = ev[i][q] + to_f(ec[(ns[i] + q) * ld + Kn[i]]);
+            else if (g.bc_mirror) v = ev[i][q] + ev[i][q];
+          }
         }
+        lt[i][q] = v;
       }
-    }
+    float acc[FPL][RW];
+#pragma unroll
+    for (int i = 0; i < FPL; ++i)
+#pragma unroll
+      for (int r = 0; r < RW; ++r) acc[i][r] = r < NF ? rv[i][r] : 0.f;
+#pragma unroll
+    for (int src = 0; src < LPE; ++src)
+#pragma unroll
+      for (int is = 0; is < FPL; ++is)
+#pragma unroll
+        for (int q = 0; q < NF; ++q) {
+          const float x = __shfl_sync(0xffffffffu, lt[is][q], gbase + src);
+          const int k = (src + LPE * is) * NF + q;        // trace index: face src + LPE*is, node q
+#pragma unroll
+          for (int i = 0; i < FPL; ++i) {
+            const int rbi = row0[i] / NF;
+            const float* col = LT + (k * NRB + rbi) * RW;
+#pragma unroll
+            for (int r4 = 0; r4 < RW; r4 += 4) {
+              const float4 cf = *reinterpret_cast<const float4*>(col + r4);
+              acc[i][r4 + 0] = fmaf(cf.x, x, acc[i][r4 + 0]);
+              acc[i][r4 + 1] = fmaf(cf.y, x, acc[i][r4 + 1]);
+              acc[i][r4 + 2] = fmaf(cf.z, x, acc[i][r4 + 2]);
+              acc[i][r4 + 3] = fmaf(cf.w, x, acc[i][r4 + 3]);
+            }
+          }
+        }
     float st = 0.f;
-    if (has_rows && rows_live) {
+#pragma unroll
+    for (int i = 0; i < FPL; ++i) {
+      if (!rows[i]) continue;
 #pragma unroll
       for (int r = 0; r < NF; ++r) {
-        const TL nv = from_f<TL>(acc[r]);
+        const TL nv = from_f<TL>(acc[i][r]);
         const float nvf = to_f(nv);
-        const float d = nvf - ev[r];
+        const float d = nvf - ev[i][r];
         st = fmaf(d, d, st);
-        ev[r] = nvf;
-        en[(row0 + r) * ld + K] = nv;
+        ev[i][r] = nvf;
+        en[(row0[i] + r) * ld + K] = nv;
       }
     }
     const int it = iter0 + s + 1;
@@ -675,21 +690,21 @@ __global__ void __launch_bounds__(1024) k_inner_reg(const DevGeo g, const TL* __
   }
 }
 
-// Launch k_inner_reg when every (element, face) pair can be a resident thread.
-template <int NF, bool PER_AXIS, typename TL>
-cudaError_t launch_reg(MixedArgs& m, TL* rl, TL* e0, TL* e1) {
+// Launch k_inner_reg with the most lanes per element whose grid is co-resident.
+template <int NF, bool PER_AXIS, typename TL, int LPE>
+cudaError_t launch_reg_v(MixedArgs& m, TL* rl, TL* e0, TL* e1) {
   constexpr int NIN = 4 * NF, RW = (NF + 3) & ~3, NRB = 4;
   const LaunchArgs& a = m.base;
-  if (a.g.dim != 2 || !m.LE32h || (long long)a.g.ld * a.g.n_exp >= (1LL << 31)) return cudaErrorNotSupported;
-  auto k = k_inner_reg<NF, PER_AXIS, TL>;
+  if (a.g.dim != 2 || !m.LE32h || !m.dLT || (long long)a.g.ld * a.g.n_exp >= (1LL << 31)) return cudaErrorNotSupported;
+  auto k = k_inner_reg<NF, PER_AXIS, TL, LPE>;
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, 1024, 0);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, 512, 0);
   if (e != cudaSuccess) return e;
-  const long long grid = (a.g.nel + 255) / 256;
+  const long long epb = 512 / LPE;
+  const long long grid = (a.g.nel + epb - 1) / epb;
   if (grid > (long long)per * sms || grid > m.max_grid || grid > m.slots / 2) return cudaErrorNotSupported;
-  if (m.dLT == nullptr) return cudaErrorNotSupported;
   // transposed, padded operator: LT[k][rb * RW + r] = L_E[rb * NF + r][k]
   std::vector<float> lt((size_t)NIN * NRB * RW, 0.f);
   const int nrb = a.g.n_exp / NF;
@@ -706,9 +721,16 @@ cudaError_t launch_reg(MixedArgs& m, TL* rl, TL* e0, TL* e1) {
   double* pp = a.partials;
   const float* ltp = m.dLT;
   void* args[] = {&gg, &rlc, &e0, &e1, &ct, &pp, &ltp};
-  e = cudaLaunchCooperativeKernel((const void*)k, dim3((unsigned)grid), dim3(1024), args, 0, a.stream);
+  e = cudaLaunchCooperativeKernel((const void*)k, dim3((unsigned)grid), dim3(512), args, 0, a.stream);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
+}
+
+template <int NF, bool PER_AXIS, typename TL>
+cudaError_t launch_reg(MixedArgs& m, TL* rl, TL* e0, TL* e1) {
+  cudaError_t e = launch_reg_v<NF, PER_AXIS, TL, 4>(m, rl, e0, e1);
+  if (e != cudaErrorNotSupported) return e;
+  return launch_reg_v<NF, PER_AXIS, TL, 2>(m, rl, e0, e1);
 }
 
 // Tile kernel shape: one element per thread (default) or, with IHDG_TILE_LPE=4 on 2D
