@@ -33,13 +33,16 @@ struct Ctrl {
   int max_iters;
   int inner_max;
   int timeout;            // a bounded device wait ran out (the loop stops, status ERR_TIMEOUT)
-  unsigned int bar_count; // grid barrier of the persistent kernels: arrivals
-  unsigned int bar_gen;   //   and generation
+  unsigned int bar_gen;   // (unused)
   double tol, diverge_factor, inner_rtol;
   double res;             // last float64 stopping residual
   double res_min;
   double rnorm;           // mixed: export-space norm of the current r (low precision check)
   double inner_step;      // mixed: last inner step norm
+  // arrival counter of the persistent kernels' grid barrier, alone on its cache line: every
+  // block polls it, so no other field may share the line
+  alignas(128) unsigned int bar_count;
+  unsigned int pad_[31];
 };
 
 enum { FK_NONE_D = 0, FK_OWN_D = 1, FK_NBR_D = 2, FK_SUM_D = 3 };

@@ -180,45 +180,43 @@ __global__ void __launch_bounds__(BS) k_inner_first(DevGeo g, OpsDev op, const d
   }
 }
 
-// Flag-slot barrier with reduction, for cooperative launches.  Slot b (64 bits) holds the
-// float partial sum of block b in its low half and a tag in its high half; tags are the
-// solve's sweep numbers, so a slot written in sweep s is recognised without resetting it
-// (the slots are cleared before every launch).  Thread 0 publishes the block's slot with a
-// release store after the block's writes (bar.sync orders them before it); every block then
-// acquire-polls all slots until they carry the tag and sums the partials in slot order, so
-// all blocks obtain the same total.  Each poll is bounded by ~1 s of SM clock; on expiry
-// the block sets ctrl->timeout and every block stops at its next check.
-__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
-  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 
+// Grid barrier plus sum of one double per block, for cooperative launches.  The arrival
+// counter only grows (cleared before the launch): barrier number b completes when it
+// reaches (b+1) * gridDim.x.  Thread 0 publishes the block's partial, arrives with a
+// release add and polls with acquire loads (bounded by ~1 s of SM clock, then
+// ctrl->timeout); warp 0 then sums the partials in block order with a fixed shuffle tree,
+// so every block obtains the same total.
 template <int NT>
-__device__ double flag_reduce(unsigned long long* slots, double block_partial, unsigned tag, Ctrl* ctrl,
-                              double* ws, double* s_out) {
+__device__ double barrier_sum(double* part, unsigned* count, unsigned nb, double mine, Ctrl* ctrl, double* s_out,
+                              int* s_flag) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    const unsigned long long pk =
-        ((unsigned long long)tag << 32) | (unsigned long long)__float_as_uint((float)block_partial);
-    st_release_u64(slots + blockIdx.x, pk);
-  }
-  double v = 0.0;
-  for (int i = threadIdx.x; i < (int)gridDim.x; i += NT) {
+    part[blockIdx.x] = mine;
+    red_release_add(count, 1u);
+    const unsigned target = nb * gridDim.x;
     const long long t0 = clock64();
-    unsigned long long x;
-    for (;;) {
-      x = ld_acquire_u64(slots + i);
-      if ((unsigned)(x >> 32) == tag) break;
+    while (ld_acquire_u32(count) < target) {
       if (clock64() - t0 > 2000000000LL) { atomicExch(&ctrl->timeout, 1); break; }
     }
-    v += (double)__uint_as_float((unsigned)(x & 0xffffffffull));
+    *s_flag = *(volatile int*)&ctrl->timeout;
   }
-  const double tot = block_sum(v, ws);
-  if (threadIdx.x == 0) *s_out = tot;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += 32) v += __ldcg(part + i);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) *s_out = v;
+  }
   __syncthreads();
   return *s_out;
 }
@@ -234,6 +232,7 @@ __global__ void __launch_bounds__(PBS) k_inner_persist(DevGeo g, OpsDev op, cons
   constexpr int NIN = NF * NLF;
   __shared__ double ws[PBS / 32];
   __shared__ double s_tot;
+  __shared__ int s_to;
   extern __shared__ float sf[];
   if (ctrl_done(ctrl) || *(volatile const int*)&ctrl->inner_done) return;
   int j = *(volatile const int*)&ctrl->inner_iter;
@@ -284,8 +283,9 @@ __global__ void __launch_bounds__(PBS) k_inner_persist(DevGeo g, OpsDev op, cons
     }
     const int it = iter0 + s + 1;
     const double bs = block_sum((double)acc, ws);
-    const double tot = flag_reduce<PBS>(reinterpret_cast<unsigned long long*>(partials), bs, (unsigned)it, ctrl, ws, &s_tot);
-    if (*(volatile int*)&ctrl->timeout) break;
+    const double tot = barrier_sum<PBS>(partials + (size_t)(s & 1) * gridDim.x, &ctrl->bar_count, (unsigned)(s + 1), bs,
+                                        ctrl, &s_tot, &s_to);
+    if (s_to) break;
     const double step = sqrt(tot);
     j += 1;
     const bool stop = step <= lim || j >= inner_max || it >= max_iters || !(step == step) || isinf(step);
@@ -309,45 +309,6 @@ struct LTile {
   float L[NEXP][NIN];
 };
 
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
-  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Grid barrier plus sum of one double per block, for cooperative launches.  The arrival
-// counter only grows (cleared before the launch): barrier number b completes when it
-// reaches (b+1) * gridDim.x.  Thread 0 publishes the block's partial, arrives with a
-// release add and polls with acquire loads (bounded by ~1 s of SM clock, then
-// ctrl->timeout); warp 0 then sums the partials in block order with a fixed shuffle tree,
-// so every block obtains the same total.
-template <int NT>
-__device__ double barrier_sum(double* part, unsigned* count, unsigned nb, double mine, Ctrl* ctrl, double* s_out) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    part[blockIdx.x] = mine;
-    red_release_add(count, 1u);
-    const unsigned target = nb * gridDim.x;
-    const long long t0 = clock64();
-    while (ld_acquire_u32(count) < target) {
-      if (clock64() - t0 > 2000000000LL) { atomicExch(&ctrl->timeout, 1); break; }
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double v = 0.0;
-    for (int i = threadIdx.x; i < (int)gridDim.x; i += 32) v += __ldcg(part + i);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (threadIdx.x == 0) *s_out = v;
-  }
-  __syncthreads();
-  return *s_out;
-}
-
 // Persistent inner loop with block-resident state.  Block b owns elements
 // [b*epb, b*epb + epb); their own exports e_j and the residual r stay in shared memory
 // (TL precision: the values the neighbours see), with each element's boundary-face mask.
@@ -368,6 +329,7 @@ __global__ void __launch_bounds__(NT) k_inner_tile(const DevGeo g, const TL* __r
   constexpr int EPP = NT / LPE;                     // elements per pass
   static_assert(NLF % LPE == 0 && 32 % LPE == 0, "lanes per element must divide faces and warps");
   __shared__ double s_tot;
+  __shared__ int s_to;
   extern __shared__ __align__(16) unsigned char smraw[];
   if (ctrl_done(ctrl) || *(volatile const int*)&ctrl->inner_done) return;
   int j = *(volatile const int*)&ctrl->inner_iter;
@@ -481,8 +443,8 @@ __global__ void __launch_bounds__(NT) k_inner_tile(const DevGeo g, const TL* __r
     double blk = 0.0;
     if (threadIdx.x == 0)
       for (int w = 0; w < NT / 32; ++w) blk += wsum[w];
-    const double tot = barrier_sum<NT>(partials + (size_t)(s & 1) * gridDim.x, count, (unsigned)(s + 1), blk, ctrl, &s_tot);
-    if (*(volatile int*)&ctrl->timeout) break;
+    const double tot = barrier_sum<NT>(partials + (size_t)(s & 1) * gridDim.x, count, (unsigned)(s + 1), blk, ctrl, &s_tot, &s_to);
+    if (s_to) break;
     const double step = sqrt(tot);
     j += 1;
     const bool stop = step <= lim || j >= inner_max || it >= max_iters || !(step == step) || isinf(step);
@@ -564,6 +526,7 @@ __global__ void __launch_bounds__(512, 2) k_inner_reg(const DevGeo g, const TL* 
   __shared__ __align__(16) float LT[NIN * NRB * RW];
   __shared__ double wsum[NT / 32];
   __shared__ double s_tot;
+  __shared__ int s_to;
   if (ctrl_done(ctrl) || *(volatile const int*)&ctrl->inner_done) return;
   int j = *(volatile const int*)&ctrl->inner_iter;
   const int iter0 = *(volatile const int*)&ctrl->iter;
@@ -674,8 +637,8 @@ __global__ void __launch_bounds__(512, 2) k_inner_reg(const DevGeo g, const TL* 
     double blk = 0.0;
     if (threadIdx.x == 0)
       for (int w = 0; w < NT / 32; ++w) blk += wsum[w];
-    const double tot = barrier_sum<NT>(partials + (size_t)(s & 1) * gridDim.x, count, (unsigned)(s + 1), blk, ctrl, &s_tot);
-    if (*(volatile int*)&ctrl->timeout) break;
+    const double tot = barrier_sum<NT>(partials + (size_t)(s & 1) * gridDim.x, count, (unsigned)(s + 1), blk, ctrl, &s_tot, &s_to);
+    if (s_to) break;
     const double step = sqrt(tot);
     j += 1;
     const bool stop = step <= lim || j >= inner_max || it >= max_iters || !(step == step) || isinf(step);
@@ -770,9 +733,6 @@ struct MixedRunner {
         }
         k<<<grid_for(a.g.nel), BS, smem, a.stream>>>(a.g, a.op, m.r64, e0, a.ctrl, a.partials, a.res_hist);
       } else {
-        // the flag slots of the persistent kernels start cleared (tags are sweep numbers)
-        cudaError_t ze = cudaMemsetAsync(a.partials, 0, sizeof(unsigned long long) * (size_t)m.slots, a.stream);
-        if (ze != cudaSuccess) return ze;
         if (!m.no_tile) {
           if constexpr (NLF == 4) {
             if (m.tile_lpe != 1) {
@@ -804,6 +764,8 @@ struct MixedRunner {
         Ctrl* ct = a.ctrl;
         double* pp = a.partials;
         void* args[] = {&gg, &oo, &rlc, &e0, &e1, &ct, &pp};
+        e = cudaMemsetAsync(&a.ctrl->bar_count, 0, sizeof(unsigned), a.stream);
+        if (e != cudaSuccess) return e;
         e = cudaLaunchCooperativeKernel((const void*)k, dim3(grid), dim3(PBS), args, smem, a.stream);
         if (e != cudaSuccess) return e;
       }
