@@ -198,6 +198,7 @@ __device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
 template <int NT>
 __device__ double barrier_sum(double* part, unsigned* count, unsigned nb, double mine, Ctrl* ctrl, double* s_out,
                               int* s_flag) {
+  __shared__ double wred[NT / 32];
   __syncthreads();
   if (threadIdx.x == 0) {
     part[blockIdx.x] = mine;
@@ -210,12 +211,17 @@ __device__ double barrier_sum(double* part, unsigned* count, unsigned nb, double
     *s_flag = *(volatile int*)&ctrl->timeout;
   }
   __syncthreads();
-  if (threadIdx.x < 32) {
-    double v = 0.0;
-    for (int i = threadIdx.x; i < (int)gridDim.x; i += 32) v += __ldcg(part + i);
+  // every thread loads its block's partials at once (one round trip), then a fixed tree
+  double v = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += NT) v += __ldcg(part + i);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (threadIdx.x == 0) *s_out = v;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) wred[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < NT / 32; ++w) t += wred[w];
+    *s_out = t;
   }
   __syncthreads();
   return *s_out;
@@ -237,6 +243,7 @@ __global__ void __launch_bounds__(PBS) k_inner_persist(DevGeo g, OpsDev op, cons
   if (ctrl_done(ctrl) || *(volatile const int*)&ctrl->inner_done) return;
   int j = *(volatile const int*)&ctrl->inner_iter;
   const int iter0 = *(volatile const int*)&ctrl->iter;
+  const int lowp0 = *(volatile const int*)&ctrl->lowp_sweeps;
   const int max_iters = ctrl->max_iters, inner_max = ctrl->inner_max;
   const double lim = ctrl->inner_rtol * ctrl->rnorm;
   for (int i = threadIdx.x; i < g.n_exp * NIN; i += PBS) sf[i] = op.LE32[i];
@@ -292,7 +299,7 @@ __global__ void __launch_bounds__(PBS) k_inner_persist(DevGeo g, OpsDev op, cons
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       ctrl->inner_iter = j;
       ctrl->iter = it;
-      ctrl->lowp_sweeps += 1;
+      ctrl->lowp_sweeps = lowp0 + s + 1;
       ctrl->inner_step = step;
       if (stop) ctrl->inner_done = 1;
     }
@@ -334,6 +341,7 @@ __global__ void __launch_bounds__(NT) k_inner_tile(const DevGeo g, const TL* __r
   if (ctrl_done(ctrl) || *(volatile const int*)&ctrl->inner_done) return;
   int j = *(volatile const int*)&ctrl->inner_iter;
   const int iter0 = *(volatile const int*)&ctrl->iter;
+  const int lowp0 = *(volatile const int*)&ctrl->lowp_sweeps;
   const int max_iters = ctrl->max_iters, inner_max = ctrl->inner_max;
   const double lim = ctrl->inner_rtol * ctrl->rnorm;
   TL* ev = reinterpret_cast<TL*>(smraw);        // [NEXP][epb]
@@ -451,7 +459,7 @@ __global__ void __launch_bounds__(NT) k_inner_tile(const DevGeo g, const TL* __r
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       ctrl->inner_iter = j;
       ctrl->iter = it;
-      ctrl->lowp_sweeps += 1;
+      ctrl->lowp_sweeps = lowp0 + s + 1;
       ctrl->inner_step = step;
       if (stop) ctrl->inner_done = 1;
     }
@@ -530,6 +538,7 @@ __global__ void __launch_bounds__(512, 2) k_inner_reg(const DevGeo g, const TL* 
   if (ctrl_done(ctrl) || *(volatile const int*)&ctrl->inner_done) return;
   int j = *(volatile const int*)&ctrl->inner_iter;
   const int iter0 = *(volatile const int*)&ctrl->iter;
+  const int lowp0 = *(volatile const int*)&ctrl->lowp_sweeps;
   const int max_iters = ctrl->max_iters, inner_max = ctrl->inner_max;
   const double lim = ctrl->inner_rtol * ctrl->rnorm;
   for (int i = threadIdx.x; i < NIN * NRB * RW; i += NT) LT[i] = LTg[i];
@@ -645,7 +654,7 @@ __global__ void __launch_bounds__(512, 2) k_inner_reg(const DevGeo g, const TL* 
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       ctrl->inner_iter = j;
       ctrl->iter = it;
-      ctrl->lowp_sweeps += 1;
+      ctrl->lowp_sweeps = lowp0 + s + 1;
       ctrl->inner_step = step;
       if (stop) ctrl->inner_done = 1;
     }
