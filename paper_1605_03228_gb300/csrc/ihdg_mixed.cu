@@ -198,7 +198,9 @@ __device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
 template <int NT>
 __device__ double barrier_sum(double* part, unsigned* count, unsigned nb, double mine, Ctrl* ctrl, double* s_out,
                               int* s_flag) {
-  __shared__ double wred[NT / 32];
+  // GB300's float64 rate is a small fraction of float32: every per-thread step here is
+  // float32, and only thread 0 touches float64 (the published partial and the final sum)
+  __shared__ float wred[NT / 32];
   __syncthreads();
   if (threadIdx.x == 0) {
     part[blockIdx.x] = mine;
@@ -211,16 +213,16 @@ __device__ double barrier_sum(double* part, unsigned* count, unsigned nb, double
     *s_flag = *(volatile int*)&ctrl->timeout;
   }
   __syncthreads();
-  // every thread loads its block's partials at once (one round trip), then a fixed tree
-  double v = 0.0;
-  for (int i = threadIdx.x; i < (int)gridDim.x; i += NT) v += __ldcg(part + i);
+  // every thread loads its share of the partials at once (one round trip), then a fixed tree
+  float v = 0.f;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += NT) v += (float)__ldcg(part + i);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   if ((threadIdx.x & 31) == 0) wred[threadIdx.x >> 5] = v;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
-    for (int w = 0; w < NT / 32; ++w) t += wred[w];
+    for (int w = 0; w < NT / 32; ++w) t += (double)wred[w];
     *s_out = t;
   }
   __syncthreads();
@@ -238,7 +240,8 @@ __global__ void __launch_bounds__(PBS) k_inner_persist(DevGeo g, OpsDev op, cons
   constexpr int NIN = NF * NLF;
   __shared__ double ws[PBS / 32];
   __shared__ double s_tot;
-  __shared__ int s_to;
+  __shared__ int s_to, s_stop;
+  __shared__ float wsum_p[PBS / 32];
   extern __shared__ float sf[];
   if (ctrl_done(ctrl) || *(volatile const int*)&ctrl->inner_done) return;
   int j = *(volatile const int*)&ctrl->inner_iter;
@@ -289,21 +292,32 @@ __global__ void __launch_bounds__(PBS) k_inner_persist(DevGeo g, OpsDev op, cons
       }
     }
     const int it = iter0 + s + 1;
-    const double bs = block_sum((double)acc, ws);
+    float bsf = acc;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bsf += __shfl_down_sync(0xffffffffu, bsf, o);
+    if ((threadIdx.x & 31) == 0) wsum_p[threadIdx.x >> 5] = bsf;
+    __syncthreads();
+    double bs = 0.0;
+    if (threadIdx.x == 0)
+      for (int w = 0; w < PBS / 32; ++w) bs += (double)wsum_p[w];
     const double tot = barrier_sum<PBS>(partials + (size_t)(s & 1) * gridDim.x, &ctrl->bar_count, (unsigned)(s + 1), bs,
                                         ctrl, &s_tot, &s_to);
     if (s_to) break;
-    const double step = sqrt(tot);
     j += 1;
-    const bool stop = step <= lim || j >= inner_max || it >= max_iters || !(step == step) || isinf(step);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      ctrl->inner_iter = j;
-      ctrl->iter = it;
-      ctrl->lowp_sweeps = lowp0 + s + 1;
-      ctrl->inner_step = step;
-      if (stop) ctrl->inner_done = 1;
+    if (threadIdx.x == 0) {
+      const double step = sqrt(tot);
+      const bool stop = step <= lim || j >= inner_max || it >= max_iters || !(step == step) || isinf(step);
+      s_stop = stop ? 1 : 0;
+      if (blockIdx.x == 0) {
+        ctrl->inner_iter = j;
+        ctrl->iter = it;
+        ctrl->lowp_sweeps = lowp0 + s + 1;
+        ctrl->inner_step = step;
+        if (stop) ctrl->inner_done = 1;
+      }
     }
-    if (stop) break;
+    __syncthreads();
+    if (s_stop) break;
   }
 }
 
@@ -336,7 +350,7 @@ __global__ void __launch_bounds__(NT) k_inner_tile(const DevGeo g, const TL* __r
   constexpr int EPP = NT / LPE;                     // elements per pass
   static_assert(NLF % LPE == 0 && 32 % LPE == 0, "lanes per element must divide faces and warps");
   __shared__ double s_tot;
-  __shared__ int s_to;
+  __shared__ int s_to, s_stop;
   extern __shared__ __align__(16) unsigned char smraw[];
   if (ctrl_done(ctrl) || *(volatile const int*)&ctrl->inner_done) return;
   int j = *(volatile const int*)&ctrl->inner_iter;
@@ -442,28 +456,32 @@ __global__ void __launch_bounds__(NT) k_inner_tile(const DevGeo g, const TL* __r
       if constexpr (LPE > 1) __syncwarp();
     }
     const int it = iter0 + s + 1;
-    double bs = (double)acc;
+    float bs = acc;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) bs += __shfl_down_sync(0xffffffffu, bs, o);
-    __shared__ double wsum[NT / 32];
+    __shared__ float wsum[NT / 32];
     if (wl == 0) wsum[threadIdx.x >> 5] = bs;
     __syncthreads();
     double blk = 0.0;
     if (threadIdx.x == 0)
-      for (int w = 0; w < NT / 32; ++w) blk += wsum[w];
+      for (int w = 0; w < NT / 32; ++w) blk += (double)wsum[w];
     const double tot = barrier_sum<NT>(partials + (size_t)(s & 1) * gridDim.x, count, (unsigned)(s + 1), blk, ctrl, &s_tot, &s_to);
     if (s_to) break;
-    const double step = sqrt(tot);
     j += 1;
-    const bool stop = step <= lim || j >= inner_max || it >= max_iters || !(step == step) || isinf(step);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      ctrl->inner_iter = j;
-      ctrl->iter = it;
-      ctrl->lowp_sweeps = lowp0 + s + 1;
-      ctrl->inner_step = step;
-      if (stop) ctrl->inner_done = 1;
+    if (threadIdx.x == 0) {
+      const double step = sqrt(tot);
+      const bool stop = step <= lim || j >= inner_max || it >= max_iters || !(step == step) || isinf(step);
+      s_stop = stop ? 1 : 0;
+      if (blockIdx.x == 0) {
+        ctrl->inner_iter = j;
+        ctrl->iter = it;
+        ctrl->lowp_sweeps = lowp0 + s + 1;
+        ctrl->inner_step = step;
+        if (stop) ctrl->inner_done = 1;
+      }
     }
-    if (stop) break;
+    __syncthreads();
+    if (s_stop) break;
   }
 }
 
@@ -532,9 +550,9 @@ __global__ void __launch_bounds__(512, 2) k_inner_reg(const DevGeo g, const TL* 
   constexpr int RW = (NF + 3) & ~3;          // padded row-block width
   constexpr int NRB = 4;                     // row blocks stored (faces; axes use the first 2)
   __shared__ __align__(16) float LT[NIN * NRB * RW];
-  __shared__ double wsum[NT / 32];
+  __shared__ float wsum[NT / 32];
   __shared__ double s_tot;
-  __shared__ int s_to;
+  __shared__ int s_to, s_stop;
   if (ctrl_done(ctrl) || *(volatile const int*)&ctrl->inner_done) return;
   int j = *(volatile const int*)&ctrl->inner_iter;
   const int iter0 = *(volatile const int*)&ctrl->iter;
@@ -638,27 +656,31 @@ __global__ void __launch_bounds__(512, 2) k_inner_reg(const DevGeo g, const TL* 
       }
     }
     const int it = iter0 + s + 1;
-    double bs = (double)st;
+    float bs = st;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) bs += __shfl_down_sync(0xffffffffu, bs, o);
     if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = bs;
     __syncthreads();
     double blk = 0.0;
     if (threadIdx.x == 0)
-      for (int w = 0; w < NT / 32; ++w) blk += wsum[w];
+      for (int w = 0; w < NT / 32; ++w) blk += (double)wsum[w];
     const double tot = barrier_sum<NT>(partials + (size_t)(s & 1) * gridDim.x, count, (unsigned)(s + 1), blk, ctrl, &s_tot, &s_to);
     if (s_to) break;
-    const double step = sqrt(tot);
     j += 1;
-    const bool stop = step <= lim || j >= inner_max || it >= max_iters || !(step == step) || isinf(step);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      ctrl->inner_iter = j;
-      ctrl->iter = it;
-      ctrl->lowp_sweeps = lowp0 + s + 1;
-      ctrl->inner_step = step;
-      if (stop) ctrl->inner_done = 1;
+    if (threadIdx.x == 0) {
+      const double step = sqrt(tot);
+      const bool stop = step <= lim || j >= inner_max || it >= max_iters || !(step == step) || isinf(step);
+      s_stop = stop ? 1 : 0;
+      if (blockIdx.x == 0) {
+        ctrl->inner_iter = j;
+        ctrl->iter = it;
+        ctrl->lowp_sweeps = lowp0 + s + 1;
+        ctrl->inner_step = step;
+        if (stop) ctrl->inner_done = 1;
+      }
     }
-    if (stop) break;
+    __syncthreads();
+    if (s_stop) break;
   }
 }
 
