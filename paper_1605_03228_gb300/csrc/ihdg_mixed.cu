@@ -24,7 +24,16 @@ template <typename T> __device__ __forceinline__ T from_f(float v);
 template <> __device__ __forceinline__ float from_f<float>(float v) { return v; }
 template <> __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
 
-// gather from a low-precision array, widening to TA
+// Load through L2 (ld.global.cg): values other blocks wrote earlier in the same persistent
+// launch must not come from this SM's L1, which is not coherent with their writes.
+template <typename T> __device__ __forceinline__ float ldcg_f(const T* p);
+template <> __device__ __forceinline__ float ldcg_f<float>(const float* p) { return __ldcg(p); }
+template <> __device__ __forceinline__ float ldcg_f<__nv_bfloat16>(const __nv_bfloat16* p) {
+  const unsigned short b = __ldcg(reinterpret_cast<const unsigned short*>(p));
+  return __uint_as_float((unsigned)b << 16);
+}
+
+// gather from a low-precision array, widening to TA (through L2, see ldcg_f)
 template <int NF, int NLF, typename TL, typename TA, typename Out>
 __device__ __forceinline__ void gather_lp(const DevGeo& g, const TL* __restrict__ E, long long K, const int* c, Out&& put) {
 #pragma unroll
@@ -38,12 +47,12 @@ __device__ __forceinline__ void gather_lp(const DevGeo& g, const TL* __restrict_
     for (int j = 0; j < NF; ++j) {
       TA v = TA(0);
       if (kind == FK_OWN_D) {
-        v = (TA)to_f(own[(long long)j * g.ld]);
+        v = (TA)ldcg_f(own + (long long)j * g.ld);
       } else if (kind == FK_NBR_D) {
-        if (!bnd) v = (TA)to_f(nb[(long long)j * g.ld]);
+        if (!bnd) v = (TA)ldcg_f(nb + (long long)j * g.ld);
       } else if (kind == FK_SUM_D) {
-        const TA o = (TA)to_f(own[(long long)j * g.ld]);
-        if (!bnd) v = o + (TA)to_f(nb[(long long)j * g.ld]);
+        const TA o = (TA)ldcg_f(own + (long long)j * g.ld);
+        if (!bnd) v = o + (TA)ldcg_f(nb + (long long)j * g.ld);
         else if (g.bc_mirror) v = o + o;
       }
       put(f * NF + j, v);
@@ -229,6 +238,40 @@ __device__ double barrier_sum(double* part, unsigned* count, unsigned nb, double
   return *s_out;
 }
 
+// Lagged grid reduction for the register and tile kernels.  After sweep s every block
+// publishes its float partial in partf[(s & 1) * grid + block] and arrives at the barrier
+// (thread 0: release add, bounded acquire poll).  At the top of sweep s+1 every thread loads
+// its share of sweep s's partials together with its trace gathers; sum_partials then folds
+// them with a fixed tree (the same in every block) and thread 0 takes the loop decision.
+// Everything per thread is float32 (GB300's float64 latency would dominate a sweep).
+__device__ __forceinline__ void arrive_wait(float* partf, unsigned* count, unsigned nb, float mine, Ctrl* ctrl,
+                                            int* s_flag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    partf[blockIdx.x] = mine;
+    red_release_add(count, 1u);
+    const unsigned target = nb * gridDim.x;
+    const long long t0 = clock64();
+    while (ld_acquire_u32(count) < target) {
+      if (clock64() - t0 > 2000000000LL) { atomicExch(&ctrl->timeout, 1); break; }
+    }
+    *s_flag = *(volatile int*)&ctrl->timeout;
+  }
+  __syncthreads();
+}
+
+template <int NT>
+__device__ __forceinline__ float sum_partials(float pv, float* wred) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) pv += __shfl_down_sync(0xffffffffu, pv, o);
+  if ((threadIdx.x & 31) == 0) wred[threadIdx.x >> 5] = pv;
+  __syncthreads();
+  float t = 0.f;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < NT / 32; ++w) t += wred[w];
+  return t;   // valid in thread 0
+}
+
 // Persistent inner loop on the correction equation: e_{j+1} = r + L_E t(e_j), until the
 // step norm falls below inner_rtol * ||r||, inner_max sweeps, or the sweep budget.  One
 // cooperative launch runs many sweeps; each sweep ends with a grid barrier after which every
@@ -272,7 +315,7 @@ __global__ void __launch_bounds__(PBS) k_inner_persist(DevGeo g, OpsDev op, cons
           if (e < g.n_exp && row_live(g, e, NF)) {
             const long long at = (long long)e * g.ld + K;
             rv[i] = to_f(rlp[at]);
-            ov[i] = to_f(ec[at]);
+            ov[i] = ldcg_f(ec + at);
           }
         }
 #pragma unroll
@@ -593,9 +636,15 @@ __global__ void __launch_bounds__(512, 2) k_inner_reg(const DevGeo g, const TL* 
   }
   __syncthreads();
   unsigned* count = &ctrl->bar_count;
+  float* partf = reinterpret_cast<float*>(partials);
+  const float limf = (float)lim;
   for (int s = 0;; ++s) {
-    const TL* __restrict__ ec = (j & 1) ? e1 : e0;
-    TL* __restrict__ en = (j & 1) ? e0 : e1;
+    const TL* __restrict__ ec = ((j + s) & 1) ? e1 : e0;
+    TL* __restrict__ en = ((j + s) & 1) ? e0 : e1;
+    // previous sweep's partials (one round trip, together with the trace gathers below)
+    float pv = 0.f;
+    if (s > 0)
+      for (int i = threadIdx.x; i < (int)gridDim.x; i += NT) pv += __ldcg(partf + ((s - 1) & 1) * gridDim.x + i);
     float lt[FPL][NF];
 #pragma unroll
     for (int i = 0; i < FPL; ++i)
@@ -606,14 +655,33 @@ __global__ void __launch_bounds__(512, 2) k_inner_reg(const DevGeo g, const TL* 
           if (kind[i] == FK_OWN_D) {
             v = ev[i][q];
           } else if (kind[i] == FK_NBR_D) {
-            if (!bnd[i]) v = to_f(ec[(ns[i] + q) * ld + Kn[i]]);
+            if (!bnd[i]) v = ldcg_f(ec + (ns[i] + q) * ld + Kn[i]);
           } else if (kind[i] == FK_SUM_D) {
-            if (!bnd[i]) v = ev[i][q] + to_f(ec[(ns[i] + q) * ld + Kn[i]]);
+            if (!bnd[i]) v = ev[i][q] + ldcg_f(ec + (ns[i] + q) * ld + Kn[i]);
             else if (g.bc_mirror) v = ev[i][q] + ev[i][q];
           }
         }
         lt[i][q] = v;
       }
+    // decision on the s sweeps done so far (the last one's step norm when s > 0)
+    {
+      const float tot = sum_partials<NT>(pv, wsum);
+      if (threadIdx.x == 0) {
+        const float step = sqrtf(tot);
+        const bool budget = j + s >= inner_max || iter0 + s >= max_iters;
+        const bool stop = budget || (s > 0 && (step <= limf || !(step == step) || isinf(step)));
+        s_stop = stop ? 1 : 0;
+        if (blockIdx.x == 0) {
+          ctrl->inner_iter = j + s;
+          ctrl->iter = iter0 + s;
+          ctrl->lowp_sweeps = lowp0 + s;
+          if (s > 0) ctrl->inner_step = (double)step;
+          if (stop) ctrl->inner_done = 1;
+        }
+      }
+      __syncthreads();
+      if (s_stop) break;
+    }
     float acc[FPL][RW];
 #pragma unroll
     for (int i = 0; i < FPL; ++i)
@@ -655,32 +723,9 @@ __global__ void __launch_bounds__(512, 2) k_inner_reg(const DevGeo g, const TL* 
         en[(row0[i] + r) * ld + K] = nv;
       }
     }
-    const int it = iter0 + s + 1;
-    float bs = st;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) bs += __shfl_down_sync(0xffffffffu, bs, o);
-    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = bs;
-    __syncthreads();
-    double blk = 0.0;
-    if (threadIdx.x == 0)
-      for (int w = 0; w < NT / 32; ++w) blk += (double)wsum[w];
-    const double tot = barrier_sum<NT>(partials + (size_t)(s & 1) * gridDim.x, count, (unsigned)(s + 1), blk, ctrl, &s_tot, &s_to);
+    const float blk = sum_partials<NT>(st, wsum);
+    arrive_wait(partf + (s & 1) * gridDim.x, count, (unsigned)(s + 1), blk, ctrl, &s_to);
     if (s_to) break;
-    j += 1;
-    if (threadIdx.x == 0) {
-      const double step = sqrt(tot);
-      const bool stop = step <= lim || j >= inner_max || it >= max_iters || !(step == step) || isinf(step);
-      s_stop = stop ? 1 : 0;
-      if (blockIdx.x == 0) {
-        ctrl->inner_iter = j;
-        ctrl->iter = it;
-        ctrl->lowp_sweeps = lowp0 + s + 1;
-        ctrl->inner_step = step;
-        if (stop) ctrl->inner_done = 1;
-      }
-    }
-    __syncthreads();
-    if (s_stop) break;
   }
 }
 
