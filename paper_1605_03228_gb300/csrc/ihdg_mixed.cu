@@ -588,7 +588,8 @@ cudaError_t launch_tile_v(MixedArgs& m, TL* rl, TL* e0, TL* e1) {
 // owns one (element, lane) pair for the whole launch.
 template <int NF, bool PER_AXIS, typename TL, int LPE>
 __global__ void __launch_bounds__(512, 2) k_inner_reg(const DevGeo g, const TL* __restrict__ rlp, TL* e0, TL* e1,
-                                                      Ctrl* ctrl, double* partials, const float* __restrict__ LTg) {
+                                                      Ctrl* ctrl, double* partials, const float* __restrict__ LTg,
+                                                      const int epb) {
   constexpr int NT = 512, NIN = 4 * NF, FPL = 4 / LPE;
   constexpr int RW = (NF + 3) & ~3;          // padded row-block width
   constexpr int NRB = 4;                     // row blocks stored (faces; axes use the first 2)
@@ -605,8 +606,8 @@ __global__ void __launch_bounds__(512, 2) k_inner_reg(const DevGeo g, const TL* 
   for (int i = threadIdx.x; i < NIN * NRB * RW; i += NT) LT[i] = LTg[i];
   const int lane = threadIdx.x % LPE;
   const int gbase = (threadIdx.x & 31) - lane;
-  const int K = blockIdx.x * (NT / LPE) + threadIdx.x / LPE;
-  const bool valid = K < (int)g.nel;
+  const int K = blockIdx.x * epb + threadIdx.x / LPE;   // epb <= NT / LPE elements per block
+  const bool valid = (int)(threadIdx.x / LPE) < epb && K < (int)g.nel;
   const int ld = (int)g.ld;
   int c[3] = {0, 0, 0};
   if (valid) coords(g, K, c);
@@ -741,9 +742,13 @@ cudaError_t launch_reg_v(MixedArgs& m, TL* rl, TL* e0, TL* e1) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, 512, 0);
   if (e != cudaSuccess) return e;
-  const long long epb = 512 / LPE;
-  const long long grid = (a.g.nel + epb - 1) / epb;
-  if (grid > (long long)per * sms || grid > m.max_grid || grid > m.slots / 2) return cudaErrorNotSupported;
+  // the grid is a multiple of the SM count with the elements spread evenly over it
+  long long grid = (long long)per * sms;
+  if (grid > m.max_grid) grid = m.max_grid;
+  const long long epb = (a.g.nel + grid - 1) / grid;
+  if (epb > 512 / LPE) return cudaErrorNotSupported;
+  grid = (a.g.nel + epb - 1) / epb;
+  if (grid > m.slots / 2) return cudaErrorNotSupported;
   // transposed, padded operator: LT[k][rb * RW + r] = L_E[rb * NF + r][k]
   std::vector<float> lt((size_t)NIN * NRB * RW, 0.f);
   const int nrb = a.g.n_exp / NF;
@@ -759,7 +764,8 @@ cudaError_t launch_reg_v(MixedArgs& m, TL* rl, TL* e0, TL* e1) {
   Ctrl* ct = a.ctrl;
   double* pp = a.partials;
   const float* ltp = m.dLT;
-  void* args[] = {&gg, &rlc, &e0, &e1, &ct, &pp, &ltp};
+  int ep = (int)epb;
+  void* args[] = {&gg, &rlc, &e0, &e1, &ct, &pp, &ltp, &ep};
   e = cudaLaunchCooperativeKernel((const void*)k, dim3((unsigned)grid), dim3(512), args, 0, a.stream);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
