@@ -29,6 +29,8 @@ struct Plan {
   ihdg_coeffs co{};
   Ops ops;
   std::vector<float> le32;   // host float32 copy of L_E (kernel parameter of the tile kernel)
+  std::vector<double> img;   // packed float64 operator image
+  std::vector<size_t> off;   // offsets of the operators in img
   DevGeo g{};
   OpsDev op{};
   void* dbuf = nullptr;
@@ -106,24 +108,22 @@ void fill_geo(const ihdg_mesh& m, const Ops& o, DevGeo& g) {
       for (int j = 0; j < o.nf; ++j) g.live |= 1ull << (o.own_off[f] + j);
 }
 
-// Build (or find) the plan of a problem: host float64 operators and their device copies.
-ihdg_status get_plan(ihdg_ctx* ctx, const ihdg_mesh& m, const ihdg_coeffs& co, Plan*& out, double* setup_ms) {
-  for (auto& p : ctx->plans)
-    if (same_problem(p->mesh, m, p->co, co)) { out = p.get(); if (setup_ms) *setup_ms = 0.0; return IHDG_OK; }
-  auto t0 = std::chrono::steady_clock::now();
-  auto pl = std::make_unique<Plan>();
-  pl->mesh = m;
-  pl->co = co;
+// Host part of a plan: float64 operators, device geometry, and the packed operator image
+// (float64 block followed by the float32 copy of L_E) ready for one upload.
+ihdg_status prepare_plan(ihdg_ctx* ctx, const ihdg_mesh& m, const ihdg_coeffs& co, Plan& pl) {
+  pl.mesh = m;
+  pl.co = co;
   std::string err;
-  ihdg_status st = build_ops(m, co, pl->ops, err);
+  ihdg_status st = build_ops(m, co, pl.ops, err);
   if (st != IHDG_OK) return fail(ctx, st, err);
-  const Ops& o = pl->ops;
+  const Ops& o = pl.ops;
   if (!shape_supported(m.dim, o.nf))
     return fail(ctx, IHDG_ERR_UNSUPPORTED, "this (dim, p) has no compiled sweep kernel (built: 2D p=1..4, 3D p=1..2)");
-  fill_geo(m, o, pl->g);
-  // pack all operators into one host image, then one upload
-  std::vector<double> img;
-  std::vector<size_t> off;
+  fill_geo(m, o, pl.g);
+  std::vector<double>& img = pl.img;
+  std::vector<size_t>& off = pl.off;
+  img.clear();
+  off.clear();
   auto put = [&](const std::vector<double>& v) { off.push_back(img.size()); img.insert(img.end(), v.begin(), v.end()); size_t pad = (32 - img.size() % 32) % 32; img.insert(img.end(), pad, 0.0); };
   std::vector<double> Qp;
   for (int i = 0; i < o.n_in; ++i)
@@ -137,27 +137,50 @@ ihdg_status get_plan(ihdg_ctx* ctx, const ihdg_mesh& m, const ihdg_coeffs& co, P
   put(o.PqF.empty() ? empty : o.PqF); put(o.PqV.empty() ? empty : o.PqV);
   put(o.facevol);
   put(o.Mb);
-  size_t nd = img.size();
-  pl->le32.assign(o.LE.begin(), o.LE.end());
-  const std::vector<float>& le32 = pl->le32;
-  size_t bytes = align256(nd * sizeof(double)) + align256(le32.size() * sizeof(float));
-  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-  CK(cudaMalloc(&pl->dbuf, bytes), "cudaMalloc(operators)");
-  pl->dbytes = bytes;
-  CK(cudaMemcpy(pl->dbuf, img.data(), nd * sizeof(double), cudaMemcpyHostToDevice), "upload operators");
-  float* d32 = reinterpret_cast<float*>(static_cast<char*>(pl->dbuf) + align256(nd * sizeof(double)));
-  CK(cudaMemcpy(d32, le32.data(), le32.size() * sizeof(float), cudaMemcpyHostToDevice), "upload operators");
-  const double* b = static_cast<const double*>(pl->dbuf);
+  pl.le32.assign(o.LE.begin(), o.LE.end());
+  pl.dbytes = align256(img.size() * sizeof(double)) + align256(pl.le32.size() * sizeof(float));
+  return IHDG_OK;
+}
+
+// Copy the operator image to device memory at `base` (pl.dbytes bytes) on `stream` and point
+// the plan's device operators into it.
+ihdg_status upload_plan(ihdg_ctx* ctx, Plan& pl, void* base, cudaStream_t stream) {
+  const size_t nd = pl.img.size();
+  CK(cudaMemcpyAsync(base, pl.img.data(), nd * sizeof(double), cudaMemcpyHostToDevice, stream), "upload operators");
+  float* d32 = reinterpret_cast<float*>(static_cast<char*>(base) + align256(nd * sizeof(double)));
+  CK(cudaMemcpyAsync(d32, pl.le32.data(), pl.le32.size() * sizeof(float), cudaMemcpyHostToDevice, stream), "upload operators");
+  CK(cudaStreamSynchronize(stream), "upload operators");
+  const double* b = static_cast<const double*>(base);
+  const std::vector<size_t>& off = pl.off;
   size_t k = 0;
-  OpsDev& op = pl->op;
+  OpsDev& op = pl.op;
   op.LE = b + off[k++]; op.Qp = b + off[k++]; op.Lvol = b + off[k++]; op.R = b + off[k++]; op.Mn = b + off[k++];
   op.PF = b + off[k++]; op.PV = b + off[k++];
   for (int f = 0; f < 6; ++f) op.PFb[f] = b + off[k++];
   for (int f = 0; f < 6; ++f) op.PVb[f] = b + off[k++];
   op.Pg = b + off[k++]; op.PqF = b + off[k++]; op.PqV = b + off[k++]; op.facevol = b + off[k++];
   op.Mb = b + off[k++];
-  for (int c = 0; c < 4; ++c) op.wcomp[c] = o.wcomp[c];
+  for (int c = 0; c < 4; ++c) op.wcomp[c] = pl.ops.wcomp[c];
   op.LE32 = d32;
+  return IHDG_OK;
+}
+
+// Build (or find) the plan of a problem: host float64 operators and their device copies
+// (cudaMalloc'd, cached in the context).
+ihdg_status get_plan(ihdg_ctx* ctx, const ihdg_mesh& m, const ihdg_coeffs& co, Plan*& out, double* setup_ms) {
+  for (auto& p : ctx->plans)
+    if (same_problem(p->mesh, m, p->co, co)) { out = p.get(); if (setup_ms) *setup_ms = 0.0; return IHDG_OK; }
+  auto t0 = std::chrono::steady_clock::now();
+  auto pl = std::make_unique<Plan>();
+  ihdg_status st = prepare_plan(ctx, m, co, *pl);
+  if (st != IHDG_OK) return st;
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  CK(cudaMalloc(&pl->dbuf, pl->dbytes), "cudaMalloc(operators)");
+  st = upload_plan(ctx, *pl, pl->dbuf, nullptr);
+  if (st != IHDG_OK) {
+    cudaFree(pl->dbuf);
+    return st;
+  }
   if (ctx->plans.size() >= 16) {
     cudaFree(ctx->plans.front()->dbuf);
     ctx->plans.erase(ctx->plans.begin());
