@@ -176,6 +176,24 @@ ihdg_status ihdg_solve_device(ihdg_ctx* ctx, const ihdg_mesh* mesh, const ihdg_c
                               void* d_workspace, size_t workspace_bytes, void* stream,
                               ihdg_result* res);
 
+/* As ihdg_solve_device, for callers that cannot allocate device memory: code embedded in
+ * a host application whose allocator owns all of the GPU's memory, or in a pipeline where a
+ * cudaMalloc/cudaFree (which synchronise the device) is not allowed.  The paper has no
+ * counterpart: this is a deployment variant of the same solve.  It allocates nothing: the
+ * operator image and the whole solve workspace live in one file-scope device array of
+ * IHDG_STATIC_SCRATCH_BYTES that every GPU which loads the library holds until exit.  The
+ * caller passes inputs and outputs (device memory, as for ihdg_solve_device).  Problems
+ * whose scratch exceeds the array fail with IHDG_ERR_NOMEM and a message giving the size.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  All calls share the array and it keeps
+ * the last call's contents: calls whose GPU work overlaps (other streams or host threads)
+ * race, so serialise them. */
+#define IHDG_STATIC_SCRATCH_BYTES (64u * 1024u * 1024u)
+ihdg_status ihdg_solve_device_static(ihdg_ctx* ctx, const ihdg_mesh* mesh, const ihdg_coeffs* coeffs,
+                                     const double* d_f_qp, const double* d_g_qp,
+                                     const ihdg_options* opts, double* d_u_out, double* d_trace_out,
+                                     void* stream, ihdg_result* res);
+
 /* Linearized shallow water (Section 3, Eq. localSolverDD), walls on the whole boundary:
  * advance q (in/out, [n_el][3][(p+1)^2] volume layout (phi, u, v), host) by nsteps
  * backward-Euler steps of coeffs->dt; each step runs the iHDG iteration warm-started from

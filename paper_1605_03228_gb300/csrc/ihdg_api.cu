@@ -10,6 +10,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <sstream>
 #include <string>
 #include <vector>
@@ -512,6 +513,68 @@ ihdg_status ihdg_solve(ihdg_ctx* ctx, const ihdg_mesh* mesh, const ihdg_coeffs* 
   if (st != IHDG_OK) return st;
   CK(cudaMemcpy(u_out, d_u, sizeof(double) * sz.n_el * sz.nvol, cudaMemcpyDeviceToHost), "copy u");
   if (trace_out) CK(cudaMemcpy(trace_out, d_t, sizeof(double) * sz.n_face * sz.nface_nodes, cudaMemcpyDeviceToHost), "copy trace");
+  return IHDG_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Solve that allocates no device memory.  Its scratch (operator image and the whole solve
+// workspace) is this file-scope array, which every GPU that loads the library holds until
+// the process exits.  Host code cannot use the array's name as a device address: the first
+// call on each device resolves the address with cudaGetSymbolAddress (with that device
+// current) and every call passes that pointer on.  All calls share the array, so calls whose
+// work overlaps on the GPU (other streams, other host threads) race; each call writes every
+// scratch value before reading it (the loop state is initialised by its first kernel).
+static __device__ __align__(256) unsigned char g_ihdg_static_scratch[IHDG_STATIC_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_static_mu;
+void* g_static_addr[256] = {nullptr};   // device address of g_ihdg_static_scratch, per device
+
+ihdg_status static_scratch(ihdg_ctx* ctx, void** out) {
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (ctx->device < 0 || ctx->device >= 256) return fail(ctx, IHDG_ERR_INVALID, "device index out of range");
+  if (!g_static_addr[ctx->device]) {
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    void* p = nullptr;
+    CK(cudaGetSymbolAddress(&p, g_ihdg_static_scratch), "cudaGetSymbolAddress(static scratch)");
+    g_static_addr[ctx->device] = p;
+  }
+  *out = g_static_addr[ctx->device];
+  return IHDG_OK;
+}
+}  // namespace
+
+extern "C" ihdg_status ihdg_solve_device_static(ihdg_ctx* ctx, const ihdg_mesh* mesh, const ihdg_coeffs* co,
+                                                const double* d_f, const double* d_g, const ihdg_options* opts,
+                                                double* d_u, double* d_tr, void* stream, ihdg_result* res) {
+  if (!ctx) return IHDG_ERR_INVALID;
+  if (!mesh || !co || !d_f || !d_g || !d_u) return fail(ctx, IHDG_ERR_INVALID, "null argument");
+  if (co->pde == IHDG_SWE) return fail(ctx, IHDG_ERR_INVALID, "shallow water is solved by ihdg_swe_steps*");
+  ihdg_options o = defaults(opts);
+  ihdg_status st = check_opts(ctx, o);
+  if (st != IHDG_OK) return st;
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  Plan pl;
+  st = prepare_plan(ctx, *mesh, *co, pl);
+  if (st != IHDG_OK) return st;
+  const Layout L = layout_for(pl.g, o, false);
+  const size_t need = align256(pl.dbytes) + L.total;
+  if (need > (size_t)IHDG_STATIC_SCRATCH_BYTES) {
+    std::ostringstream os;
+    os << "problem needs " << need << " bytes of scratch; ihdg_solve_device_static holds at most "
+       << (size_t)IHDG_STATIC_SCRATCH_BYTES << " (use ihdg_solve_device with a caller workspace)";
+    return fail(ctx, IHDG_ERR_NOMEM, os.str());
+  }
+  void* base = nullptr;
+  st = static_scratch(ctx, &base);
+  if (st != IHDG_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = upload_plan(ctx, pl, base, s);
+  if (st != IHDG_OK) return st;
+  SrcDev src{d_f, d_g, nullptr};
+  st = device_iterate(ctx, &pl, o, src, o.u0, d_u, d_tr, static_cast<char*>(base) + align256(pl.dbytes), L, s, res);
+  if (st != IHDG_OK) return st;
+  ctx->err.clear();
   return IHDG_OK;
 }
 

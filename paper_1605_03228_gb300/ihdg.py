@@ -54,7 +54,8 @@ class Sizes(ctypes.Structure):
 
 EXPORTED = ["ihdg_create", "ihdg_destroy", "ihdg_last_error", "ihdg_problem_sizes", "ihdg_quadrature_points",
             "ihdg_node_points", "ihdg_solve", "ihdg_workspace_bytes", "ihdg_solve_device", "ihdg_swe_steps",
-            "ihdg_swe_steps_device", "ihdg_host_operator"]
+            "ihdg_swe_steps_device", "ihdg_host_operator", "ihdg_solve_device_static"]
+STATIC_SCRATCH_BYTES = 64 * 1024 * 1024
 
 _lib = None
 
@@ -89,6 +90,7 @@ def load(build_if_missing=True):
     L.ihdg_swe_steps.argtypes = [VP, P(Mesh), P(Coeffs), dp, I, P(Options), P(I), P(Result)]
     L.ihdg_swe_steps_device.argtypes = [VP, P(Mesh), P(Coeffs), VP, I, P(Options), P(I), VP, SZ, VP, P(Result)]
     L.ihdg_host_operator.argtypes = [P(Mesh), P(Coeffs), I, P(I), P(I), dp]
+    L.ihdg_solve_device_static.argtypes = [VP, P(Mesh), P(Coeffs), VP, VP, P(Options), VP, VP, VP, P(Result)]
     for name in EXPORTED:
         f = getattr(L, name)
         if name not in ("ihdg_destroy", "ihdg_last_error"):
@@ -240,6 +242,17 @@ class Context:
                                       ctypes.c_void_p(d_tr) if d_tr else None, ctypes.c_void_p(d_ws),
                                       ctypes.c_size_t(ws_bytes), ctypes.c_void_p(stream), ctypes.byref(res))
         self._check(st, "ihdg_solve_device")
+        return res
+
+    def solve_device_static(self, mesh, coeffs, d_f, d_g, opts, d_u, d_tr, stream=0):
+        """Device-pointer solve that allocates nothing (scratch in the library's static
+        device array, see ihdg_solve_device_static).  Returns Result."""
+        res = Result()
+        st = self.L.ihdg_solve_device_static(self.h, ctypes.byref(mesh), ctypes.byref(coeffs), ctypes.c_void_p(d_f),
+                                             ctypes.c_void_p(d_g), ctypes.byref(opts), ctypes.c_void_p(d_u),
+                                             ctypes.c_void_p(d_tr) if d_tr else None, ctypes.c_void_p(stream),
+                                             ctypes.byref(res))
+        self._check(st, "ihdg_solve_device_static")
         return res
 
     def swe_steps(self, mesh, coeffs, q, nsteps, opts):
