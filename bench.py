@@ -57,6 +57,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=0, help="override the elements per side (profiling cases)")
     ap.add_argument("--no-extras", action="store_true", help="skip the as-listed and float64 comparison solves")
+    ap.add_argument("--prec", default="", choices=["", "FP64", "MIXED_FP32", "MIXED_BF16"],
+                    help="override the workload's precision (profiling cases)")
+    ap.add_argument("--inner-max", type=int, default=0, help="mixed: inner sweeps per outer step (profiling cases)")
+    ap.add_argument("--inner-rtol", type=float, default=0.0, help="mixed: inner stopping ratio (profiling cases)")
     return ap.parse_args()
 
 
@@ -240,6 +244,9 @@ def main():
     if args.n:
         spec["n"] = (args.n,) * spec["dim"]
         spec["desc"] = f"[{args.n} per side] " + spec["desc"]
+    if args.prec:
+        spec["prec"] = args.prec
+        spec["desc"] = f"[{args.prec}] " + spec["desc"]
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -268,7 +275,7 @@ def main():
     prec = getattr(ih, spec["prec"])
     a, b = inputs(ih, spec, mesh, co)
     swe = spec["pde"] == "swe"
-    opts = ih.make_options(spec["tol"], max_iters=4000, prec=prec)
+    opts = ih.make_options(spec["tol"], max_iters=4000, prec=prec, inner_max=args.inner_max, inner_rtol=args.inner_rtol)
     nws = ih.workspace_bytes(mesh, co, opts)
     ws = torch.empty(nws + 256, dtype=torch.uint8, device=dev)
     wsp = (ws.data_ptr() + 255) // 256 * 256
@@ -322,7 +329,8 @@ def main():
     status = ih.STATUS_NAMES[r.status]
 
     # roofline of the dominant kernel: one profiled solve (events around every sweep launch)
-    rp = step(ih.make_options(spec["tol"], max_iters=4000, prec=prec, profile=1))
+    rp = step(ih.make_options(spec["tol"], max_iters=4000, prec=prec, profile=1, inner_max=args.inner_max,
+                              inner_rtol=args.inner_rtol))
     lp_bytes = 2 if prec == ih.MIXED_BF16 else 4
     if prec == ih.FP64:
         kern, kms = "k_sweep64", rp.fp64_sweep_ms
