@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="convdiff2d",
-                    choices=["convdiff2d", "transport2d", "transport3d", "swe"])
+                    choices=["convdiff2d", "transport2d", "transport3d", "swe", "serving"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=0, help="override the elements per side (profiling cases)")
     ap.add_argument("--no-extras", action="store_true", help="skip the as-listed and float64 comparison solves")
@@ -61,6 +61,9 @@ def parse():
                     help="override the workload's precision (profiling cases)")
     ap.add_argument("--inner-max", type=int, default=0, help="mixed: inner sweeps per outer step (profiling cases)")
     ap.add_argument("--inner-rtol", type=float, default=0.0, help="mixed: inner stopping ratio (profiling cases)")
+    ap.add_argument("--requests", type=int, default=400, help="serving: number of requests (the listed stream is 10000)")
+    ap.add_argument("--load", type=float, default=0.8, help="serving: offered load as a fraction of measured capacity")
+    ap.add_argument("--slots", type=int, default=8, help="serving: concurrent solves")
     return ap.parse_args()
 
 
@@ -78,6 +81,11 @@ def workload_spec(name):
         b = 1 / math.sqrt(3)
         return dict(name="transport3d", dim=3, n=(64, 64, 64), p=2, pde="transport", beta=(b, b, b), tol=1e-8,
                     prec="MIXED_BF16", desc="3D transport 64^3 p=2 beta=(1,1,1)/sqrt3 u=sin sin sin tol 1e-8 bf16+f64")
+    if name == "serving":
+        return dict(name="serving", dim=2, n=(0, 0), p=0, pde="convdiff", tol=1e-8, prec="MIXED_FP32",
+                    desc="serving stream: 2D conv-diff requests, side log-uniform in [16,256], p in 1..4, "
+                         "kappa log-uniform in [1e-4,1], beta angle uniform, seeded manufactured solutions, "
+                         "Poisson arrivals, admitted by HBM footprint, mixed precision, tol 1e-8")
     if name == "swe":
         return dict(name="swe", dim=2, n=(512, 512), p=2, pde="swe", Phi=1.0, dt=1.0 / (512 * 12), listed_dt=1e-3,
                     nsteps=100, tol=1e-8, prec="MIXED_FP32",
@@ -237,6 +245,87 @@ def cpu_baseline(spec, budget_s=15.0):
             "sample": f"{n} sweeps (Algorithm 1, float64 numpy, BLAS threads) on the full {spec['n']} mesh"}
 
 
+# ----------------------------------------------------------------------------- serving
+def serving_request(ih, rq):
+    mesh = ih.make_mesh(2, (rq["side"], rq["side"]), rq["p"])
+    co = ih.make_coeffs(ih.CONVDIFF, beta=rq["beta"], kappa=rq["kappa"])
+    vol, bnd = ih.quadrature_points(mesh, co)
+    f = W.convdiff_forcing(vol, rq["kappa"], rq["beta"], 0.0, rq["a"], rq["b"])
+    g = W.convdiff_exact(bnd, rq["a"], rq["b"])
+    opts = ih.make_options(1e-8, max_iters=2000, prec=ih.MIXED_FP32)
+    s = ih.problem_sizes(mesh, co)
+    return mesh, co, f, g, opts, s.n_el * s.nvol
+
+
+def run_serving(args, ih, ctx, world, rank):
+    """Closed-loop capacity on a sample, then an open-loop Poisson stream at the offered load."""
+    reqs, gaps = W.serving_requests(max(args.requests, 64), seed=12345)
+    budget = 16 * 1024 ** 3
+    ctx.server_start(budget, args.slots)
+    try:
+        def drain(pending, done):
+            for t in list(pending):
+                r = ctx.poll(t)
+                if r is not None:
+                    mesh, co, dofs = pending.pop(t)
+                    ctx.fetch(t, mesh, co, want_trace=False)
+                    done.append((r, dofs))
+
+        # capacity: the first 64 requests submitted at once
+        sample = [serving_request(ih, rq) for rq in reqs[:64]]
+        pending, done = {}, []
+        t0 = time.perf_counter()
+        for (m, c, f, g, o, d) in sample:
+            pending[ctx.submit(m, c, f, g, o)] = (m, c, d)
+        while pending:
+            drain(pending, done)
+            time.sleep(0.0005)
+        cap = len(sample) / (time.perf_counter() - t0)
+        # open loop: Poisson arrivals at load * capacity
+        rate = args.load * cap
+        arrivals = np.cumsum(gaps[:args.requests] / rate)
+        pending, done = {}, []
+        clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+        clocks.start()
+        t0 = time.perf_counter()
+        for i in range(args.requests):
+            m, c, f, g, o, d = serving_request(ih, reqs[i])
+            while time.perf_counter() - t0 < arrivals[i]:
+                drain(pending, done)
+                time.sleep(0.0002)
+            pending[ctx.submit(m, c, f, g, o)] = (m, c, d)
+            drain(pending, done)
+        while pending:
+            drain(pending, done)
+            time.sleep(0.0005)
+        wall = time.perf_counter() - t0
+        clk = clocks.stop()
+    finally:
+        ctx.server_stop()
+    lat = np.array([r.latency_ms for r, _ in done])
+    updates = sum(d * r.iterations for r, d in done)
+    status = {}
+    for r, _ in done:
+        k = ih.STATUS_NAMES[r.status]
+        status[k] = status.get(k, 0) + 1
+    value = world * updates / wall
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.requests, "warmup": 64,
+            "ms_per_step": wall * 1e3 / args.requests, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": workload_spec("serving")["desc"], "requests": args.requests, "slots": args.slots,
+                       "hbm_budget_bytes": budget, "offered_load": args.load, "capacity_req_per_s": cap,
+                       "status_counts": status, "l2": "not flushed: requests stream through the server"},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "mean": float(lat.mean())},
+            "requests_per_s": args.requests / wall,
+            "e2e": {"value": value, "unit": UNIT, "note": "host buffers in and out through ihdg_submit/ihdg_fetch",
+                    "h2d_bytes_per_step": None, "d2h_bytes_per_step": None},
+            "gpu_launches": int(sum(r.kernel_launches for r, _ in done)), "clocks": clk, "roofline": None,
+            "cpu_baseline": None}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 # ----------------------------------------------------------------------------- our arm
 def main():
     args = parse()
@@ -268,6 +357,12 @@ def main():
     dev = torch.device(f"cuda:{local}")
     torch.cuda.set_device(dev)
     ctx = ih.Context(local)
+    if spec["name"] == "serving":
+        run_serving(args, ih, ctx, world, rank)
+        ctx.close()
+        if dist is not None:
+            dist.destroy_process_group()
+        return
     stream = torch.cuda.current_stream(dev)
     sp = stream.cuda_stream
     mesh, co = make_problem(ih, spec)

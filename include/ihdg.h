@@ -116,6 +116,8 @@ typedef struct {
   int lowp_launches;       /* profile: low-precision sweep launches timed */
   int kernel_launches;     /* CUDA kernels this call launched (including sweeps that found
                               the loop already stopped and returned at once) */
+  double latency_ms;       /* serving: submit -> results on the host */
+  double queue_ms;         /* serving: submit -> admitted to a slot */
 } ihdg_result;
 
 typedef struct {
@@ -217,6 +219,30 @@ ihdg_status ihdg_swe_steps_device(ihdg_ctx* ctx, const ihdg_mesh* mesh,
  * (nvol x nqv).  Row-major into data (may be NULL to query rows/cols only). */
 ihdg_status ihdg_host_operator(const ihdg_mesh* mesh, const ihdg_coeffs* coeffs, int which,
                                int* rows, int* cols, double* data);
+
+/* Serving: continuous batching of independent steady solves (transport or
+ * convection-diffusion) on one GPU.  ihdg_server_start allocates one device arena of
+ * hbm_budget_bytes and starts `slots` worker threads, each with its own CUDA stream.
+ * ihdg_submit copies the request's inputs (host arrays as for ihdg_solve), prepares its
+ * operators on the calling thread, and queues it; it fails with IHDG_ERR_NOMEM when the
+ * request's footprint (operators, workspace, inputs, outputs) exceeds the whole budget.  A
+ * free slot admits the first queued request whose footprint fits in the arena's free space,
+ * so requests arriving while others run start as soon as a slot and memory free up, and the
+ * slots' GPU work overlaps.  Traces and all solve state stay on the device until the slot
+ * copies u and the trace back.  ihdg_poll returns IHDG_ERR_BUSY until the request is done,
+ * then its result (status, sweeps, latency_ms from submit to completion, queue_ms);
+ * ihdg_fetch copies u (and the trace unless NULL) and releases the ticket.  A request's
+ * launch configuration depends only on its own size, so its result is the same alone and in
+ * any mix.  The paper solves one problem at a time; this is a deployment interface around
+ * the same solve.  ihdg_server_stop waits for running requests and frees the arena. */
+typedef long long ihdg_ticket;
+ihdg_status ihdg_server_start(ihdg_ctx* ctx, size_t hbm_budget_bytes, int slots);
+ihdg_status ihdg_server_stop(ihdg_ctx* ctx);
+ihdg_status ihdg_submit(ihdg_ctx* ctx, const ihdg_mesh* mesh, const ihdg_coeffs* coeffs,
+                        const double* f_qp, const double* g_qp, const ihdg_options* opts,
+                        ihdg_ticket* out);
+ihdg_status ihdg_poll(ihdg_ctx* ctx, ihdg_ticket ticket, ihdg_result* res);
+ihdg_status ihdg_fetch(ihdg_ctx* ctx, ihdg_ticket ticket, double* u_out, double* trace_out);
 
 #ifdef __cplusplus
 }

@@ -9,8 +9,12 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <condition_variable>
+#include <deque>
 #include <memory>
 #include <mutex>
+#include <thread>
+#include <unordered_map>
 #include <sstream>
 #include <string>
 #include <vector>
@@ -46,9 +50,12 @@ bool same_problem(const ihdg_mesh& a, const ihdg_mesh& b, const ihdg_coeffs& ca,
 
 }  // namespace
 
+namespace { struct Server; }
+
 struct ihdg_ctx {
   int device = 0;
   std::string err;
+  Server* server = nullptr;   // serving state (ihdg_server_start .. ihdg_server_stop)
   std::vector<std::unique_ptr<Plan>> plans;
   // device scratch of the host-pointer calls (inputs, outputs, workspace)
   void* scratch = nullptr;
@@ -388,6 +395,7 @@ ihdg_status ihdg_create(ihdg_ctx** out, int device) {
 
 void ihdg_destroy(ihdg_ctx* ctx) {
   if (!ctx) return;
+  if (ctx->server) ihdg_server_stop(ctx);
   cudaSetDevice(ctx->device);
   for (auto& p : ctx->plans) cudaFree(p->dbuf);
   if (ctx->scratch) cudaFree(ctx->scratch);
@@ -575,6 +583,276 @@ extern "C" ihdg_status ihdg_solve_device_static(ihdg_ctx* ctx, const ihdg_mesh* 
   st = device_iterate(ctx, &pl, o, src, o.u0, d_u, d_tr, static_cast<char*>(base) + align256(pl.dbytes), L, s, res);
   if (st != IHDG_OK) return st;
   ctx->err.clear();
+  return IHDG_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Serving: continuous batching of independent solve requests.
+//
+// The server owns one device arena of the HBM budget.  ihdg_submit validates and copies a
+// request, prepares its operators on the caller's thread, and queues it.  Each of the
+// server's slots is a host thread with its own context (pinned loop-state readback), its own
+// CUDA stream and one request at a time: it takes the first queued request whose footprint
+// (operator image + workspace + inputs + outputs) fits in the arena's free space, runs the
+// solve on its stream, copies the results back and frees its space, then takes the next.
+// Requests that arrive while others run are admitted as soon as a slot and memory free up,
+// and the slots' kernels overlap on the device.  A request's launch configuration depends
+// only on its own size, so its result is the same alone and in any mix.
+namespace {
+
+double now_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+struct Request {
+  long long id = 0;
+  Plan plan;
+  ihdg_options opts{};
+  std::vector<double> f, g, u, tr;
+  size_t fbytes = 0, gbytes = 0, ubytes = 0, tbytes = 0, footprint = 0, arena_off = 0;
+  Layout L{};
+  ihdg_result res{};
+  ihdg_status st = IHDG_OK;
+  std::string err;
+  int state = 0;   // 0 queued, 1 running, 2 done
+  double t_submit = 0, t_start = 0, t_end = 0;
+};
+
+struct Server {
+  int device = 0;
+  char* arena = nullptr;
+  size_t budget = 0;
+  std::vector<std::pair<size_t, size_t>> free_list;   // (offset, size), sorted by offset
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<Request*> queue;
+  std::unordered_map<long long, std::unique_ptr<Request>> all;
+  std::vector<std::thread> workers;
+  std::vector<ihdg_ctx*> slot_ctx;
+  std::vector<cudaStream_t> streams;
+  bool stop = false;
+  long long next_id = 1;
+
+  bool alloc(size_t bytes, size_t* off) {   // first fit; caller holds mu
+    for (size_t i = 0; i < free_list.size(); ++i) {
+      if (free_list[i].second >= bytes) {
+        *off = free_list[i].first;
+        free_list[i].first += bytes;
+        free_list[i].second -= bytes;
+        if (free_list[i].second == 0) free_list.erase(free_list.begin() + i);
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(size_t off, size_t bytes) {   // caller holds mu; coalesce neighbours
+    auto it = free_list.begin();
+    while (it != free_list.end() && it->first < off) ++it;
+    it = free_list.insert(it, {off, bytes});
+    if (it + 1 != free_list.end() && it->first + it->second == (it + 1)->first) {
+      it->second += (it + 1)->second;
+      free_list.erase(it + 1);
+    }
+    if (it != free_list.begin() && (it - 1)->first + (it - 1)->second == it->first) {
+      (it - 1)->second += it->second;
+      free_list.erase(it);
+    }
+  }
+};
+
+void serve_one(ihdg_ctx* sctx, cudaStream_t stream, Server* sv, Request* r) {
+  char* base = sv->arena + r->arena_off;
+  double* d_f = reinterpret_cast<double*>(base);
+  double* d_g = reinterpret_cast<double*>(base + r->fbytes);
+  double* d_u = reinterpret_cast<double*>(base + r->fbytes + r->gbytes);
+  double* d_t = reinterpret_cast<double*>(base + r->fbytes + r->gbytes + r->ubytes);
+  char* img = base + r->fbytes + r->gbytes + r->ubytes + r->tbytes;
+  char* ws = img + align256(r->plan.dbytes);
+  ihdg_status st = IHDG_OK;
+  cudaError_t e = cudaMemcpyAsync(d_f, r->f.data(), r->f.size() * sizeof(double), cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_g, r->g.data(), r->g.size() * sizeof(double), cudaMemcpyHostToDevice, stream);
+  if (e != cudaSuccess) { st = IHDG_ERR_CUDA; sctx->err = cudaGetErrorString(e); }
+  if (st == IHDG_OK) st = upload_plan(sctx, r->plan, img, stream);
+  if (st == IHDG_OK) {
+    SrcDev src{d_f, d_g, nullptr};
+    st = device_iterate(sctx, &r->plan, r->opts, src, nullptr, d_u, d_t, ws, r->L, stream, &r->res);
+  }
+  if (st == IHDG_OK) {
+    e = cudaMemcpyAsync(r->u.data(), d_u, r->u.size() * sizeof(double), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(r->tr.data(), d_t, r->tr.size() * sizeof(double), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) { st = IHDG_ERR_CUDA; sctx->err = cudaGetErrorString(e); }
+  }
+  r->st = st;
+  if (st != IHDG_OK) r->err = sctx->err;
+}
+
+void slot_loop(Server* sv, int slot) {
+  cudaSetDevice(sv->device);
+  ihdg_ctx* sctx = sv->slot_ctx[slot];
+  cudaStream_t stream = sv->streams[slot];
+  for (;;) {
+    Request* r = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(sv->mu);
+      for (;;) {
+        if (sv->stop) return;
+        for (auto it = sv->queue.begin(); it != sv->queue.end(); ++it) {
+          size_t off = 0;
+          if (sv->alloc((*it)->footprint, &off)) {
+            r = *it;
+            r->arena_off = off;
+            r->state = 1;
+            r->t_start = now_ms();
+            sv->queue.erase(it);
+            break;
+          }
+        }
+        if (r) break;
+        sv->cv.wait(lk);
+      }
+    }
+    serve_one(sctx, stream, sv, r);
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      sv->release(r->arena_off, r->footprint);
+      r->t_end = now_ms();
+      r->res.latency_ms = r->t_end - r->t_submit;
+      r->res.queue_ms = r->t_start - r->t_submit;
+      r->state = 2;
+    }
+    sv->cv.notify_all();
+  }
+}
+
+}  // namespace
+
+extern "C" ihdg_status ihdg_server_start(ihdg_ctx* ctx, size_t hbm_budget_bytes, int slots) {
+  if (!ctx) return IHDG_ERR_INVALID;
+  if (ctx->server) return fail(ctx, IHDG_ERR_INVALID, "the server is already running");
+  if (slots < 1 || slots > 64) return fail(ctx, IHDG_ERR_INVALID, "slots must be in 1..64");
+  if (hbm_budget_bytes < (1u << 20)) return fail(ctx, IHDG_ERR_INVALID, "hbm_budget_bytes must be at least 1 MiB");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  auto sv = std::make_unique<Server>();
+  sv->device = ctx->device;
+  sv->budget = hbm_budget_bytes & ~size_t(255);
+  cudaError_t e = cudaMalloc(&sv->arena, sv->budget);
+  if (e != cudaSuccess) return fail(ctx, IHDG_ERR_NOMEM, std::string("server arena: ") + cudaGetErrorString(e));
+  sv->free_list.push_back({0, sv->budget});
+  for (int i = 0; i < slots; ++i) {
+    ihdg_ctx* c = nullptr;
+    cudaStream_t s = nullptr;
+    if (ihdg_create(&c, ctx->device) != IHDG_OK || cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+      for (auto* x : sv->slot_ctx) ihdg_destroy(x);
+      for (auto x : sv->streams) cudaStreamDestroy(x);
+      if (c) ihdg_destroy(c);
+      cudaFree(sv->arena);
+      return fail(ctx, IHDG_ERR_CUDA, "server slot set-up failed");
+    }
+    sv->slot_ctx.push_back(c);
+    sv->streams.push_back(s);
+  }
+  Server* raw = sv.release();
+  for (int i = 0; i < slots; ++i) raw->workers.emplace_back(slot_loop, raw, i);
+  ctx->server = raw;
+  ctx->err.clear();
+  return IHDG_OK;
+}
+
+extern "C" ihdg_status ihdg_server_stop(ihdg_ctx* ctx) {
+  if (!ctx) return IHDG_ERR_INVALID;
+  Server* sv = ctx->server;
+  if (!sv) return IHDG_OK;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->stop = true;
+  }
+  sv->cv.notify_all();
+  for (auto& t : sv->workers) t.join();   // a running request finishes first
+  cudaSetDevice(sv->device);
+  for (auto* c : sv->slot_ctx) ihdg_destroy(c);
+  for (auto s : sv->streams) cudaStreamDestroy(s);
+  cudaFree(sv->arena);
+  delete sv;
+  ctx->server = nullptr;
+  return IHDG_OK;
+}
+
+extern "C" ihdg_status ihdg_submit(ihdg_ctx* ctx, const ihdg_mesh* mesh, const ihdg_coeffs* co, const double* f_qp,
+                                   const double* g_qp, const ihdg_options* opts, ihdg_ticket* out) {
+  if (!ctx) return IHDG_ERR_INVALID;
+  Server* sv = ctx->server;
+  if (!sv) return fail(ctx, IHDG_ERR_INVALID, "no server: call ihdg_server_start first");
+  if (!mesh || !co || !f_qp || !g_qp || !out) return fail(ctx, IHDG_ERR_INVALID, "null argument");
+  if (co->pde == IHDG_SWE) return fail(ctx, IHDG_ERR_INVALID, "shallow water is solved by ihdg_swe_steps*");
+  auto r = std::make_unique<Request>();
+  r->t_submit = now_ms();
+  r->opts = defaults(opts);
+  r->opts.u0 = nullptr;
+  r->opts.profile = 0;
+  ihdg_status st = check_opts(ctx, r->opts);
+  if (st != IHDG_OK) return st;
+  st = prepare_plan(ctx, *mesh, *co, r->plan);
+  if (st != IHDG_OK) return st;
+  ihdg_sizes sz;
+  ihdg_problem_sizes(mesh, co, &sz);
+  r->f.assign(f_qp, f_qp + (size_t)sz.n_el * sz.nqv);
+  r->g.assign(g_qp, g_qp + (size_t)sz.n_bface * sz.nqf);
+  r->u.resize((size_t)sz.n_el * sz.nvol);
+  r->tr.resize((size_t)sz.n_face * sz.nface_nodes);
+  r->fbytes = align256(r->f.size() * sizeof(double));
+  r->gbytes = align256(r->g.size() * sizeof(double));
+  r->ubytes = align256(r->u.size() * sizeof(double));
+  r->tbytes = align256(r->tr.size() * sizeof(double));
+  r->L = layout_for(r->plan.g, r->opts, false);
+  r->footprint = r->fbytes + r->gbytes + r->ubytes + r->tbytes + align256(r->plan.dbytes) + r->L.total;
+  if (r->footprint > sv->budget) {
+    std::ostringstream os;
+    os << "request needs " << r->footprint << " bytes of HBM, the server budget is " << sv->budget;
+    return fail(ctx, IHDG_ERR_NOMEM, os.str());
+  }
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    r->id = sv->next_id++;
+    *out = r->id;
+    sv->queue.push_back(r.get());
+    sv->all.emplace(r->id, std::move(r));
+  }
+  sv->cv.notify_all();
+  ctx->err.clear();
+  return IHDG_OK;
+}
+
+extern "C" ihdg_status ihdg_poll(ihdg_ctx* ctx, ihdg_ticket t, ihdg_result* res) {
+  if (!ctx) return IHDG_ERR_INVALID;
+  Server* sv = ctx->server;
+  if (!sv) return fail(ctx, IHDG_ERR_INVALID, "no server");
+  std::lock_guard<std::mutex> lk(sv->mu);
+  auto it = sv->all.find(t);
+  if (it == sv->all.end()) return fail(ctx, IHDG_ERR_INVALID, "unknown ticket");
+  Request* r = it->second.get();
+  if (r->state != 2) return IHDG_ERR_BUSY;
+  if (r->st != IHDG_OK) return fail(ctx, r->st, r->err);
+  if (res) *res = r->res;
+  return IHDG_OK;
+}
+
+extern "C" ihdg_status ihdg_fetch(ihdg_ctx* ctx, ihdg_ticket t, double* u_out, double* trace_out) {
+  if (!ctx) return IHDG_ERR_INVALID;
+  Server* sv = ctx->server;
+  if (!sv) return fail(ctx, IHDG_ERR_INVALID, "no server");
+  std::unique_ptr<Request> r;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->all.find(t);
+    if (it == sv->all.end()) return fail(ctx, IHDG_ERR_INVALID, "unknown ticket");
+    if (it->second->state != 2) return IHDG_ERR_BUSY;
+    r = std::move(it->second);
+    sv->all.erase(it);
+  }
+  if (r->st != IHDG_OK) return fail(ctx, r->st, r->err);
+  if (u_out) std::memcpy(u_out, r->u.data(), r->u.size() * sizeof(double));
+  if (trace_out) std::memcpy(trace_out, r->tr.data(), r->tr.size() * sizeof(double));
   return IHDG_OK;
 }
 

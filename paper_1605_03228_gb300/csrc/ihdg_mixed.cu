@@ -744,6 +744,8 @@ cudaError_t launch_reg_v(MixedArgs& m, TL* rl, TL* e0, TL* e1) {
   if (e != cudaSuccess) return e;
   // the grid is a multiple of the SM count with the elements spread evenly over it
   long long grid = (long long)per * sms;
+  const long long small = (a.g.nel + 127) / 128;   // small problems keep >= 128 elements per block
+  if (grid > small) grid = small;
   if (grid > m.max_grid) grid = m.max_grid;
   const long long epb = (a.g.nel + grid - 1) / grid;
   if (epb > 512 / LPE) return cudaErrorNotSupported;

@@ -40,7 +40,8 @@ class Result(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("fp64_sweeps", ctypes.c_int), ("lowp_sweeps", ctypes.c_int),
                 ("residual", ctypes.c_double), ("status", ctypes.c_int), ("setup_ms", ctypes.c_double),
                 ("solve_ms", ctypes.c_double), ("fp64_sweep_ms", ctypes.c_double), ("lowp_sweep_ms", ctypes.c_double),
-                ("fp64_launches", ctypes.c_int), ("lowp_launches", ctypes.c_int), ("kernel_launches", ctypes.c_int)]
+                ("fp64_launches", ctypes.c_int), ("lowp_launches", ctypes.c_int), ("kernel_launches", ctypes.c_int),
+                ("latency_ms", ctypes.c_double), ("queue_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -54,7 +55,8 @@ class Sizes(ctypes.Structure):
 
 EXPORTED = ["ihdg_create", "ihdg_destroy", "ihdg_last_error", "ihdg_problem_sizes", "ihdg_quadrature_points",
             "ihdg_node_points", "ihdg_solve", "ihdg_workspace_bytes", "ihdg_solve_device", "ihdg_swe_steps",
-            "ihdg_swe_steps_device", "ihdg_host_operator", "ihdg_solve_device_static"]
+            "ihdg_swe_steps_device", "ihdg_host_operator", "ihdg_solve_device_static", "ihdg_server_start",
+            "ihdg_server_stop", "ihdg_submit", "ihdg_poll", "ihdg_fetch"]
 STATIC_SCRATCH_BYTES = 64 * 1024 * 1024
 
 _lib = None
@@ -91,6 +93,11 @@ def load(build_if_missing=True):
     L.ihdg_swe_steps_device.argtypes = [VP, P(Mesh), P(Coeffs), VP, I, P(Options), P(I), VP, SZ, VP, P(Result)]
     L.ihdg_host_operator.argtypes = [P(Mesh), P(Coeffs), I, P(I), P(I), dp]
     L.ihdg_solve_device_static.argtypes = [VP, P(Mesh), P(Coeffs), VP, VP, P(Options), VP, VP, VP, P(Result)]
+    L.ihdg_server_start.argtypes = [VP, SZ, I]
+    L.ihdg_server_stop.argtypes = [VP]
+    L.ihdg_submit.argtypes = [VP, P(Mesh), P(Coeffs), dp, dp, P(Options), P(ctypes.c_longlong)]
+    L.ihdg_poll.argtypes = [VP, ctypes.c_longlong, P(Result)]
+    L.ihdg_fetch.argtypes = [VP, ctypes.c_longlong, dp, dp]
     for name in EXPORTED:
         f = getattr(L, name)
         if name not in ("ihdg_destroy", "ihdg_last_error"):
@@ -254,6 +261,39 @@ class Context:
                                              ctypes.byref(res))
         self._check(st, "ihdg_solve_device_static")
         return res
+
+    # ---------------------------------------------------------------- serving
+    def server_start(self, hbm_budget_bytes, slots):
+        self._check(self.L.ihdg_server_start(self.h, ctypes.c_size_t(hbm_budget_bytes), slots), "ihdg_server_start")
+
+    def server_stop(self):
+        self._check(self.L.ihdg_server_stop(self.h), "ihdg_server_stop")
+
+    def submit(self, mesh, coeffs, f_qp, g_qp, opts):
+        f = np.ascontiguousarray(f_qp, dtype=np.float64)
+        g = np.ascontiguousarray(g_qp, dtype=np.float64)
+        t = ctypes.c_longlong()
+        st = self.L.ihdg_submit(self.h, ctypes.byref(mesh), ctypes.byref(coeffs), _dptr(f), _dptr(g),
+                                ctypes.byref(opts), ctypes.byref(t))
+        self._check(st, "ihdg_submit")
+        return t.value
+
+    def poll(self, ticket):
+        """Result when done, None while busy."""
+        res = Result()
+        st = self.L.ihdg_poll(self.h, ctypes.c_longlong(ticket), ctypes.byref(res))
+        if st == ERR_BUSY:
+            return None
+        self._check(st, "ihdg_poll")
+        return res
+
+    def fetch(self, ticket, mesh, coeffs, want_trace=True):
+        s = problem_sizes(mesh, coeffs)
+        u = np.zeros((s.n_el, s.nvol))
+        tr = np.zeros((s.n_face, s.nface_nodes)) if want_trace else None
+        st = self.L.ihdg_fetch(self.h, ctypes.c_longlong(ticket), _dptr(u), _dptr(tr))
+        self._check(st, "ihdg_fetch")
+        return u, tr
 
     def swe_steps(self, mesh, coeffs, q, nsteps, opts):
         """Host-buffer shallow-water stepping; q is updated in place.  Returns (iters, Result)."""
