@@ -281,15 +281,16 @@ def run_serving(args, ih, ctx, world, rank):
             drain(pending, done)
             time.sleep(0.0005)
         cap = len(sample) / (time.perf_counter() - t0)
-        # open loop: Poisson arrivals at load * capacity
+        # open loop: Poisson arrivals at load * capacity (inputs generated beforehand)
         rate = args.load * cap
         arrivals = np.cumsum(gaps[:args.requests] / rate)
+        stream = [serving_request(ih, rq) for rq in reqs[:args.requests]]
         pending, done = {}, []
         clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
         clocks.start()
         t0 = time.perf_counter()
         for i in range(args.requests):
-            m, c, f, g, o, d = serving_request(ih, reqs[i])
+            m, c, f, g, o, d = stream[i]
             while time.perf_counter() - t0 < arrivals[i]:
                 drain(pending, done)
                 time.sleep(0.0002)
