@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
+#include <type_traits>
 #include <vector>
 
 #include "ihdg_common.cuh"
@@ -730,6 +732,293 @@ __global__ void __launch_bounds__(512, 2) k_inner_reg(const DevGeo g, const TL* 
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Tensor-core local apply (tcgen05): persistent inner loop with bf16 operands and a float32
+// accumulator in tensor memory.  Per tile of 128 elements the GEMM
+//     D[128 x NP] = A[128 x KP] . B[NP x KP]^T,   A = gathered traces t, B = L_E (rows = exports)
+// runs as KP/16 tcgen05.mma.kind::f16 (M128 N NP K16) issued by one thread; operands sit in
+// shared memory in the K-major, no-swizzle core-matrix layout (8 rows x 16 bytes per core
+// matrix; cores adjacent along K are 128 B apart, 8-row groups are KP*16 B apart).  The
+// accumulator occupies TC_COLS columns of tensor memory allocated per block for the whole
+// launch; each warp reads its 32 lanes back (tcgen05.ld 32x32b) for the epilogue
+// e_{j+1} = r + D.  Every wait (mbarrier, grid barrier) is bounded; on expiry the kernel sets
+// ctrl->timeout, waits (bounded) for its MMAs, frees its tensor memory and returns.
+namespace tc {
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);   // version 1, no swizzle
+}
+// kind::f16 instruction descriptor: D f32, A and B bf16, both K-major, N and M encoded
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+               "selp.u32 %0, 1, 0, p;\n\t}\n" : "=r"(ok) : "r"(mbar), "r"(parity) : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {   // bounded (~1 s)
+  const long long t0 = clock64();
+  while (!mbar_try(mbar, parity))
+    if (clock64() - t0 > 2000000000LL) return false;
+  return true;
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void ld32(uint32_t taddr, float* d) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) d[i] = __uint_as_float(r[i]);
+}
+}  // namespace tc
+
+constexpr int TC_COLS = 32;   // tensor-memory columns per block (NP <= 32)
+
+template <int NF, int NLF, bool PER_AXIS>
+__global__ void __launch_bounds__(128) k_inner_tc(const DevGeo g, const __nv_bfloat16* __restrict__ rlp,
+                                                  __nv_bfloat16* e0, __nv_bfloat16* e1, Ctrl* ctrl,
+                                                  double* partials, const __nv_bfloat16* __restrict__ Bg) {
+  using TL = __nv_bfloat16;
+  constexpr int NIN = NF * NLF;
+  constexpr int NEXP = PER_AXIS ? NF * (NLF / 2) : NF * NLF;
+  constexpr int KP = (NIN + 15) / 16 * 16;
+  constexpr int NP = (NEXP + 15) / 16 * 16;
+  static_assert(NP <= TC_COLS && KP <= 64, "tile shape");
+  constexpr int ROWB = KP * 16;                 // bytes per 8-row group (KP/8 core matrices)
+  __shared__ __align__(1024) unsigned char sB[NP / 8 * ROWB];    // B first: A follows it
+  __shared__ __align__(1024) unsigned char sA[128 / 8 * ROWB];
+  __shared__ __align__(8) unsigned long long s_mbar;
+  __shared__ uint32_t s_tmem;
+  __shared__ float wsum[4];
+  __shared__ int s_to, s_stop;
+  if (ctrl_done(ctrl) || *(volatile const int*)&ctrl->inner_done) return;
+  const int jj0 = *(volatile const int*)&ctrl->inner_iter;
+  const int iter0 = *(volatile const int*)&ctrl->iter;
+  const int lowp0 = *(volatile const int*)&ctrl->lowp_sweeps;
+  const int max_iters = ctrl->max_iters, inner_max = ctrl->inner_max;
+  const float limf = (float)(ctrl->inner_rtol * ctrl->rnorm);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  // set-up: tensor memory, mbarrier, operator B
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(&s_tmem)),
+                 "r"(TC_COLS) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&s_mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(Bg);
+    uint4* dst = reinterpret_cast<uint4*>(sB);
+    for (int i = tid; i < NP / 8 * ROWB / 16; i += 128) dst[i] = src[i];
+  }
+  tc::fence_proxy_async();
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t taddr = s_tmem;
+  const uint32_t mbar = tc::smem_u32(&s_mbar);
+  const uint32_t aaddr = tc::smem_u32(sA), baddr = tc::smem_u32(sB);
+  constexpr uint32_t IDESC = tc::idesc_bf16(128, NP);
+  uint32_t phase = 0;
+  const int ld = (int)g.ld;
+  const int ntiles = (int)((g.nel + 127) / 128);
+  unsigned* count = &ctrl->bar_count;
+  float* partf = reinterpret_cast<float*>(partials);
+  int failed = 0;
+  for (int s = 0;; ++s) {
+    const TL* __restrict__ ec = ((jj0 + s) & 1) ? e1 : e0;
+    TL* __restrict__ en = ((jj0 + s) & 1) ? e0 : e1;
+    // lagged loop decision (see k_inner_reg)
+    float pv = 0.f;
+    if (s > 0)
+      for (int i = tid; i < (int)gridDim.x; i += 128) pv += __ldcg(partf + ((s - 1) & 1) * gridDim.x + i);
+    {
+      const float tot = sum_partials<128>(pv, wsum);
+      if (tid == 0) {
+        const float step = sqrtf(tot);
+        const bool budget = jj0 + s >= inner_max || iter0 + s >= max_iters;
+        const bool stop = budget || (s > 0 && (step <= limf || !(step == step) || isinf(step)));
+        s_stop = stop ? 1 : 0;
+        if (blockIdx.x == 0) {
+          ctrl->inner_iter = jj0 + s;
+          ctrl->iter = iter0 + s;
+          ctrl->lowp_sweeps = lowp0 + s;
+          if (s > 0) ctrl->inner_step = (double)step;
+          if (stop) ctrl->inner_done = 1;
+        }
+      }
+      __syncthreads();
+      if (s_stop) break;
+    }
+    float acc = 0.f;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+      const int K = tile * 128 + tid;
+      const bool valid = K < (int)g.nel;
+      int c[3] = {0, 0, 0};
+      if (valid) coords(g, K, c);
+      // a1: gather this element's traces into row `tid` of A (bf16, core-matrix layout)
+      float t[KP];
+#pragma unroll
+      for (int k = NIN; k < KP; ++k) t[k] = 0.f;
+#pragma unroll
+      for (int f = 0; f < NLF; ++f) {
+        const int kind = g.kind[f];
+        const int a = f >> 1;
+        const bool bnd = valid && on_bnd(g, c, f);
+        const int os = PER_AXIS ? a * NF : f * NF;
+        const int ns = PER_AXIS ? a * NF : (f ^ 1) * NF;
+        const int Kn = K + ((f & 1) ? (int)g.stride[a] : -(int)g.stride[a]);
+#pragma unroll
+        for (int q = 0; q < NF; ++q) {
+          float v = 0.f;
+          if (valid) {
+            if (kind == FK_OWN_D) {
+              v = ldcg_f(ec + (os + q) * ld + K);
+            } else if (kind == FK_NBR_D) {
+              if (!bnd) v = ldcg_f(ec + (ns + q) * ld + Kn);
+            } else if (kind == FK_SUM_D) {
+              const float o = ldcg_f(ec + (os + q) * ld + K);
+              if (!bnd) v = o + ldcg_f(ec + (ns + q) * ld + Kn);
+              else if (g.bc_mirror) v = o + o;
+            }
+          }
+          t[f * NF + q] = v;
+        }
+      }
+#pragma unroll
+      for (int kc = 0; kc < KP / 8; ++kc) {
+        __align__(16) __nv_bfloat16 h[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) h[u] = __float2bfloat16_rn(t[kc * 8 + u]);
+        *reinterpret_cast<uint4*>(sA + (tid >> 3) * ROWB + kc * 128 + (tid & 7) * 16) = *reinterpret_cast<uint4*>(h);
+      }
+      tc::fence_proxy_async();
+      tc::fence_before();
+      __syncthreads();
+      tc::fence_after();
+      // a3: D = A . B^T on the tensor cores
+      if (tid == 0) {
+#pragma unroll
+        for (int kk = 0; kk < KP / 16; ++kk)
+          tc::mma_bf16(taddr, tc::sdesc(aaddr + kk * 256, 128, ROWB), tc::sdesc(baddr + kk * 256, 128, ROWB), IDESC,
+                       kk > 0 ? 1u : 0u);
+        tc::commit(mbar);
+      }
+      __syncwarp();
+      // the block agrees on the outcome of the (bounded) wait, so all threads take the same path
+      const int ok = tc::mbar_wait(mbar, phase) ? 1 : 0;
+      failed = __syncthreads_or(!ok);
+      phase ^= 1u;
+      if (failed) break;
+      tc::fence_after();
+      // a4: epilogue from this warp's 32 accumulator lanes
+      float d[32];
+      tc::ld32(taddr + ((uint32_t)(warp * 32) << 16), d);
+      if (valid) {
+#pragma unroll
+        for (int e = 0; e < NEXP; ++e) {
+          if ((g.live >> e) & 1ull) {
+            const float v = to_f(rlp[e * ld + K]) + d[e];
+            const TL nv = from_f<TL>(v);
+            const float dl = to_f(nv) - ldcg_f(ec + e * ld + K);
+            acc = fmaf(dl, dl, acc);
+            en[e * ld + K] = nv;
+          }
+        }
+      }
+      tc::fence_before();
+      __syncthreads();
+    }
+    if (failed) {
+      if (tid == 0) atomicExch(&ctrl->timeout, 1);
+      break;
+    }
+    const float blk = sum_partials<128>(acc, wsum);
+    arrive_wait(partf + (s & 1) * gridDim.x, count, (unsigned)(s + 1), blk, ctrl, &s_to);
+    if (s_to) break;
+  }
+  // release tensor memory on every path (a failed MMA wait gets one more bounded wait)
+  if (failed) tc::mbar_wait(mbar, phase ^ 1u);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(TC_COLS) : "memory");
+}
+
+// Launch the tensor-core inner kernel (bf16 storage).  B = L_E in the core-matrix layout is
+// built on the host and copied to the workspace.
+template <int NF, int NLF, bool PER_AXIS>
+cudaError_t launch_tc(MixedArgs& m, __nv_bfloat16* rl, __nv_bfloat16* e0, __nv_bfloat16* e1) {
+  constexpr int NIN = NF * NLF;
+  constexpr int NEXP = PER_AXIS ? NF * (NLF / 2) : NF * NLF;
+  constexpr int KP = (NIN + 15) / 16 * 16, NP = (NEXP + 15) / 16 * 16;
+  if constexpr (NP > TC_COLS || KP > 64) {
+    return cudaErrorNotSupported;
+  } else {
+    const LaunchArgs& a = m.base;
+    if (!m.LE32h || !m.dLT || a.g.n_exp != NEXP || (long long)a.g.ld * NEXP >= (1LL << 31)) return cudaErrorNotSupported;
+    auto k = k_inner_tc<NF, NLF, PER_AXIS>;
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, 128, 0);
+    if (e != cudaSuccess) return e;
+    if (per > 8) per = 8;                          // 8 x 32 tensor-memory columns per SM at most
+    if (per < 1) return cudaErrorNotSupported;
+    long long grid = (long long)per * sms;
+    const long long ntiles = (a.g.nel + 127) / 128;
+    if (grid > ntiles) grid = ntiles;
+    if (grid > m.max_grid) grid = m.max_grid;
+    if (grid > m.slots / 2) return cudaErrorNotSupported;
+    // B[n][k] = L_E[n][k] (bf16), core-matrix layout: (n/8)*KP*16 + (k/8)*128 + (n%8)*16 + (k%8)*2 bytes
+    std::vector<__nv_bfloat16> hb((size_t)NP * KP, __float2bfloat16_rn(0.f));
+    for (int n = 0; n < NEXP; ++n)
+      for (int kk = 0; kk < NIN; ++kk) {
+        const size_t off = (size_t)(n / 8) * KP * 8 + (kk / 8) * 64 + (n % 8) * 8 + (kk % 8);
+        hb[off] = __float2bfloat16_rn(m.LE32h[n * NIN + kk]);
+      }
+    e = cudaMemcpyAsync(m.dLT, hb.data(), hb.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice, a.stream);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(&a.ctrl->bar_count, 0, sizeof(unsigned), a.stream);
+    if (e != cudaSuccess) return e;
+    DevGeo gg = a.g;
+    const __nv_bfloat16* rlc = rl;
+    Ctrl* ct = a.ctrl;
+    double* pp = a.partials;
+    const __nv_bfloat16* bp = reinterpret_cast<const __nv_bfloat16*>(m.dLT);
+    void* args[] = {&gg, &rlc, &e0, &e1, &ct, &pp, &bp};
+    e = cudaLaunchCooperativeKernel((const void*)k, dim3((unsigned)grid), dim3(128), args, 0, a.stream);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+  }
+}
+
 // Launch k_inner_reg with the most lanes per element whose grid is co-resident.
 template <int NF, bool PER_AXIS, typename TL, int LPE>
 cudaError_t launch_reg_v(MixedArgs& m, TL* rl, TL* e0, TL* e1) {
@@ -817,6 +1106,12 @@ struct MixedRunner {
         }
         k<<<grid_for(a.g.nel), BS, smem, a.stream>>>(a.g, a.op, m.r64, e0, a.ctrl, a.partials, a.res_hist);
       } else {
+        if constexpr (std::is_same<TL, __nv_bfloat16>::value) {
+          if (m.use_tc) {
+            cudaError_t ce = a.g.per_axis ? launch_tc<NF, NLF, true>(m, rl, e0, e1) : launch_tc<NF, NLF, false>(m, rl, e0, e1);
+            if (ce != cudaErrorNotSupported) return ce;
+          }
+        }
         if (!m.no_tile) {
           if constexpr (NLF == 4) {
             if (m.tile_lpe != 1) {

@@ -31,6 +31,7 @@ struct MixedArgs {
   int slots = 0;            // length of the partials array (64-bit slots)
   int tile_lpe = 4;         // 4: 2D meshes use the register-resident kernel when it fits
   float* dLT = nullptr;     // device scratch for the transposed operator (register kernel)
+  int use_tc = 0;           // bf16: local apply on the tensor cores (tcgen05)
   const float* LE32h = nullptr;  // host copy of the float32 operator (n_exp x n_in)
 };
 

@@ -296,6 +296,48 @@ def test_mixed_inner_kernel_variants(ctx, monkeypatch, kernel, grid, lpe):
     assert rel(u_b, u_a) < 1e-9
 
 
+@pytest.mark.parametrize("case,grid", [("t3d_p1", ""), ("t3d_p2", ""), ("cd2d_p3", ""), ("t2d_p2", "3")])
+def test_mixed_bf16_tensor_core_inner(ctx, monkeypatch, case, grid):
+    """bf16 inner sweeps with the local apply on the tensor cores (IHDG_INNER_KERNEL=tc:
+    tcgen05 MMA over tiles of 128 elements, operands bf16, accumulation float32) reach the
+    oracle's float64 solution at the mixed bar.  The meshes leave a ragged last tile
+    (element counts not multiples of 128), and a grid of 3 blocks makes every block loop
+    over several tiles per sweep."""
+    ihdg = ih()
+    if case.startswith("t3d"):
+        n, p = ((9, 7, 11), 1) if case == "t3d_p1" else ((6, 5, 7), 2)
+        beta = tuple(np.ones(3) / np.sqrt(3))
+        mesh = ihdg.make_mesh(3, n, p)
+        co = ihdg.make_coeffs(ihdg.TRANSPORT, beta=beta)
+        vol, bnd = ihdg.quadrature_points(mesh, co)
+        f, g = W.transport3d_forcing(vol, beta), W.transport3d_exact(bnd)
+        pr = Transport(Discretisation(BoxMesh(3, n), p), np.array(beta))
+    elif case == "cd2d_p3":
+        n, p, kappa = (13, 11), 3, 1e-4
+        mesh = ihdg.make_mesh(2, n, p)
+        co = ihdg.make_coeffs(ihdg.CONVDIFF, beta=(1.0, 1.0), kappa=kappa)
+        vol, bnd = ihdg.quadrature_points(mesh, co)
+        f, g = W.convdiff_forcing(vol, kappa), W.convdiff_exact(bnd)
+        pr = ConvDiff(Discretisation(BoxMesh(2, n), p), np.array([1.0, 1.0]), kappa)
+    else:
+        n, p, beta = (29, 23), 2, (0.8, 1.0)
+        mesh = ihdg.make_mesh(2, n, p)
+        co = ihdg.make_coeffs(ihdg.TRANSPORT, beta=beta)
+        vol, bnd = ihdg.quadrature_points(mesh, co)
+        f, g = W.transport2d_forcing(vol, beta), W.transport2d_exact(bnd)
+        pr = Transport(Discretisation(BoxMesh(2, n), p), np.array(beta))
+    tol = 1e-9
+    U, T, K, r, st = pr.iterate(f, g, tol, max_iters=20000)
+    assert st == STATUS_OK
+    monkeypatch.setenv("IHDG_INNER_KERNEL", "tc")
+    if grid:
+        monkeypatch.setenv("IHDG_PERSISTENT_GRID", grid)
+    u, tr, res = ctx.solve(mesh, co, f, g, ihdg.make_options(tol, prec=ihdg.MIXED_BF16, max_iters=20000))
+    assert res.status == ihdg.OK, res.as_dict()
+    assert res.lowp_sweeps > 0
+    assert rel(u, U.reshape(pr.mesh.nel, -1)) < 1e-6
+
+
 def test_mixed_convdiff(ctx):
     ihdg = ih()
     n, p, kappa = (12, 10), 3, 1e-4
