@@ -317,12 +317,13 @@ ihdg_status device_iterate(ihdg_ctx* ctx, Plan* pl, const ihdg_options& o, const
       int v = std::atoi(cap);
       if (v > 0) m.max_grid = v;
     }
-    // IHDG_INNER_KERNEL=global selects the global-memory persistent kernel over the tile one
-    // IHDG_INNER_KERNEL: "tc" runs bf16 inner sweeps' local apply on the tensor cores
-    // (tcgen05); "global" selects the global-state CUDA-core kernel
+    // bf16 inner sweeps run their local apply on the tensor cores (tcgen05) by default.
+    // IHDG_INNER_KERNEL selects a CUDA-core kernel instead: "tile" (register- or shared-
+    // memory-resident state) or "global" (global-memory state); "tc" keeps the default.
+    m.use_tc = o.prec == IHDG_MIXED_BF16 ? 1 : 0;
     if (const char* ker = std::getenv("IHDG_INNER_KERNEL")) {
       m.no_tile = std::strcmp(ker, "global") == 0;
-      m.use_tc = (std::strcmp(ker, "tc") == 0 && o.prec == IHDG_MIXED_BF16) ? 1 : 0;
+      if (std::strcmp(ker, "tc") != 0) m.use_tc = 0;
     }
     // IHDG_TILE_LPE=1 skips the register-resident 2D kernel (one element per thread instead)
     if (const char* lpe = std::getenv("IHDG_TILE_LPE")) m.tile_lpe = std::atoi(lpe) == 1 ? 1 : 4;

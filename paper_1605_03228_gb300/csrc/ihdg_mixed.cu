@@ -441,33 +441,38 @@ __global__ void __launch_bounds__(NT) k_inner_tile(const DevGeo g, const TL* __r
       const bool valid = le < cnt;
       const int K = K0 + le;
       const unsigned m = valid ? bm[le] : 0u;
-      // a1: this lane's faces
+      // a1: this lane's faces.  The neighbours' exports are read with unconditional loads
+      // (an in-bounds index where nothing is needed), so all of them are in flight at once.
       float lt[FPL][NF];
+      int nbi[FPL];
+      bool nbm[FPL];
+      float wo[FPL];
 #pragma unroll
       for (int i = 0; i < FPL; ++i) {
         const int f = i * LPE + lane;                 // runtime face of this lane
         const int kind = g.kind[f];
         const bool bnd = (m >> f) & 1u;
         const int a = f >> 1;
-        const int os = PER_AXIS ? a * NF : f * NF;
         const int ns = PER_AXIS ? a * NF : (f ^ 1) * NF;
         const int Kn = K + ((f & 1) ? (int)g.stride[a] : -(int)g.stride[a]);
+        nbm[i] = valid && !bnd && (kind == FK_NBR_D || kind == FK_SUM_D);
+        nbi[i] = nbm[i] ? ns * ld + Kn : ns * ld + K0;
+        wo[i] = !valid ? 0.f
+                : kind == FK_OWN_D ? 1.f
+                : kind == FK_SUM_D ? (!bnd ? 1.f : (g.bc_mirror ? 2.f : 0.f)) : 0.f;
+      }
 #pragma unroll
-        for (int q = 0; q < NF; ++q) {
-          float v = 0.f;
-          if (valid) {
-            if (kind == FK_OWN_D) {
-              v = to_f(ev[(os + q) * epb + le]);
-            } else if (kind == FK_NBR_D) {
-              if (!bnd) v = to_f(ec[(ns + q) * ld + Kn]);
-            } else if (kind == FK_SUM_D) {
-              const float o = to_f(ev[(os + q) * epb + le]);
-              if (!bnd) v = o + to_f(ec[(ns + q) * ld + Kn]);
-              else if (g.bc_mirror) v = o + o;
-            }
-          }
-          lt[i][q] = v;
-        }
+      for (int i = 0; i < FPL; ++i)
+#pragma unroll
+        for (int q = 0; q < NF; ++q) lt[i][q] = to_f(ec[nbi[i] + q * ld]);
+      const int lc = valid ? le : 0;
+#pragma unroll
+      for (int i = 0; i < FPL; ++i) {
+        const int f = i * LPE + lane;
+        const int os = PER_AXIS ? (f >> 1) * NF : f * NF;
+#pragma unroll
+        for (int q = 0; q < NF; ++q)
+          lt[i][q] = wo[i] * to_f(ev[(os + q) * epb + lc]) + (nbm[i] ? lt[i][q] : 0.f);
       }
       // exchange: every lane of the element obtains all NIN traces
       float t[NIN];
@@ -613,18 +618,28 @@ __global__ void __launch_bounds__(512, 2) k_inner_reg(const DevGeo g, const TL* 
   const int ld = (int)g.ld;
   int c[3] = {0, 0, 0};
   if (valid) coords(g, K, c);
-  int kind[FPL], Kn[FPL], ns[FPL], row0[FPL];
-  bool bnd[FPL], rows[FPL];
+  // per face of this lane: where the neighbour's exports sit (nbi, an in-bounds index also
+  // where nothing is read, so that every sweep's gathers are unconditional loads) and how
+  // the trace combines own (wo) and neighbour (wn) values
+  int kind[FPL], nbi[FPL], row0[FPL];
+  bool rows[FPL], nbm[FPL];
+  float wo[FPL];
 #pragma unroll
   for (int i = 0; i < FPL; ++i) {
     const int f = lane + LPE * i, a = f >> 1;
     kind[i] = g.kind[f];
-    bnd[i] = valid && on_bnd(g, c, f);
-    Kn[i] = K + ((f & 1) ? (int)g.stride[a] : -(int)g.stride[a]);
-    ns[i] = PER_AXIS ? a * NF : (f ^ 1) * NF;
+    const bool bnd = valid && on_bnd(g, c, f);
+    const int Kn = K + ((f & 1) ? (int)g.stride[a] : -(int)g.stride[a]);
+    const int ns = PER_AXIS ? a * NF : (f ^ 1) * NF;
     row0[i] = PER_AXIS ? a * NF : f * NF;
     const bool owns = PER_AXIS ? kind[i] == FK_OWN_D : (kind[i] == FK_SUM_D || kind[i] == FK_OWN_D);
     rows[i] = valid && owns && ((g.live >> row0[i]) & 1ull);
+    const bool nb = valid && !bnd && (kind[i] == FK_NBR_D || kind[i] == FK_SUM_D);
+    nbi[i] = nb ? ns * ld + Kn : ns * ld + (valid ? K : 0);
+    nbm[i] = nb;
+    wo[i] = !valid ? 0.f
+            : kind[i] == FK_OWN_D ? 1.f
+            : kind[i] == FK_SUM_D ? (!bnd ? 1.f : (g.bc_mirror ? 2.f : 0.f)) : 0.f;
   }
   float ev[FPL][NF], rv[FPL][NF];
   {
@@ -652,20 +667,11 @@ __global__ void __launch_bounds__(512, 2) k_inner_reg(const DevGeo g, const TL* 
 #pragma unroll
     for (int i = 0; i < FPL; ++i)
 #pragma unroll
-      for (int q = 0; q < NF; ++q) {
-        float v = 0.f;
-        if (valid) {
-          if (kind[i] == FK_OWN_D) {
-            v = ev[i][q];
-          } else if (kind[i] == FK_NBR_D) {
-            if (!bnd[i]) v = ldcg_f(ec + (ns[i] + q) * ld + Kn[i]);
-          } else if (kind[i] == FK_SUM_D) {
-            if (!bnd[i]) v = ev[i][q] + ldcg_f(ec + (ns[i] + q) * ld + Kn[i]);
-            else if (g.bc_mirror) v = ev[i][q] + ev[i][q];
-          }
-        }
-        lt[i][q] = v;
-      }
+      for (int q = 0; q < NF; ++q) lt[i][q] = ldcg_f(ec + nbi[i] + q * ld);
+#pragma unroll
+    for (int i = 0; i < FPL; ++i)
+#pragma unroll
+      for (int q = 0; q < NF; ++q) lt[i][q] = wo[i] * ev[i][q] + (nbm[i] ? lt[i][q] : 0.f);   // never 0 * (unread)
     // decision on the s sweeps done so far (the last one's step norm when s > 0)
     {
       const float tot = sum_partials<NT>(pv, wsum);
@@ -739,8 +745,8 @@ __global__ void __launch_bounds__(512, 2) k_inner_reg(const DevGeo g, const TL* 
 // runs as KP/16 tcgen05.mma.kind::f16 (M128 N NP K16) issued by one thread; operands sit in
 // shared memory in the K-major, no-swizzle core-matrix layout (8 rows x 16 bytes per core
 // matrix; cores adjacent along K are 128 B apart, 8-row groups are KP*16 B apart).  The
-// accumulator occupies TC_COLS columns of tensor memory allocated per block for the whole
-// launch; each warp reads its 32 lanes back (tcgen05.ld 32x32b) for the epilogue
+// accumulator of each of the block's TC_G tiles occupies 32 columns of tensor memory allocated
+// for the whole launch; each warp reads its 32 lanes back (tcgen05.ld 32x32b) for the epilogue
 // e_{j+1} = r + D.  Every wait (mbarrier, grid barrier) is bounded; on expiry the kernel sets
 // ctrl->timeout, waits (bounded) for its MMAs, frees its tensor memory and returns.
 namespace tc {
@@ -793,26 +799,51 @@ __device__ __forceinline__ void ld32(uint32_t taddr, float* d) {
 #pragma unroll
   for (int i = 0; i < 32; ++i) d[i] = __uint_as_float(r[i]);
 }
+__device__ __forceinline__ void group_bar(int id) { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
+// OR of v over the 128 threads of named barrier `id` (also a barrier)
+__device__ __forceinline__ int group_or(int id, int v) {
+  int r;
+  asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.s32 p, %1, 0;\n\tbar.red.or.pred q, %2, 128, p;\n\t"
+               "selp.s32 %0, 1, 0, q;\n\t}\n" : "=r"(r) : "r"(v), "r"(id) : "memory");
+  return r;
+}
 }  // namespace tc
 
-constexpr int TC_COLS = 32;   // tensor-memory columns per block (NP <= 32)
+constexpr int TC_G = 4;   // tiles in flight per block: one per 128-thread group
 
+// Shared memory of k_inner_tc: B, then one A tile per group (core-matrix layouts).
 template <int NF, int NLF, bool PER_AXIS>
-__global__ void __launch_bounds__(128) k_inner_tc(const DevGeo g, const __nv_bfloat16* __restrict__ rlp,
-                                                  __nv_bfloat16* e0, __nv_bfloat16* e1, Ctrl* ctrl,
-                                                  double* partials, const __nv_bfloat16* __restrict__ Bg) {
+struct TcShape {
+  static constexpr int NIN = NF * NLF;
+  static constexpr int NEXP = PER_AXIS ? NF * (NLF / 2) : NF * NLF;
+  static constexpr int KP = (NIN + 15) / 16 * 16;    // K padded to the MMA's K step
+  static constexpr int NP = (NEXP + 15) / 16 * 16;   // N padded to a multiple of 16
+  static constexpr int ROWB = KP * 16;               // bytes per 8-row group (KP/8 core matrices)
+  static constexpr int BBYTES = NP / 8 * ROWB;
+  static constexpr int ABYTES = 128 / 8 * ROWB;
+  static constexpr int SMEM = BBYTES + TC_G * ABYTES;
+  static constexpr uint32_t TCOLS = TC_G * 32 <= 32 ? 32 : TC_G * 32 <= 64 ? 64 : TC_G * 32 <= 128 ? 128 : 256;
+  static constexpr bool OK = NP <= 32 && KP <= 64;
+};
+
+// Group gr of the block handles tiles blockIdx.x * TC_G + gr, + gridDim.x * TC_G, ...; the
+// assignment is the same in every sweep, so each thread always owns the same elements.  A
+// group gathers its tile's traces into its A buffer, one thread issues the MMAs into the
+// group's 32 tensor-memory columns, and while they run the group loads the residual and the
+// current corrections its epilogue needs.  Groups synchronise among themselves with named
+// barriers only, so the four tiles of a block overlap their latencies.
+template <int NF, int NLF, bool PER_AXIS>
+__global__ void __launch_bounds__(128 * TC_G, 1) k_inner_tc(const DevGeo g, const __nv_bfloat16* __restrict__ rlp,
+                                                           __nv_bfloat16* e0, __nv_bfloat16* e1, Ctrl* ctrl,
+                                                           double* partials, const __nv_bfloat16* __restrict__ Bg) {
   using TL = __nv_bfloat16;
-  constexpr int NIN = NF * NLF;
-  constexpr int NEXP = PER_AXIS ? NF * (NLF / 2) : NF * NLF;
-  constexpr int KP = (NIN + 15) / 16 * 16;
-  constexpr int NP = (NEXP + 15) / 16 * 16;
-  static_assert(NP <= TC_COLS && KP <= 64, "tile shape");
-  constexpr int ROWB = KP * 16;                 // bytes per 8-row group (KP/8 core matrices)
-  __shared__ __align__(1024) unsigned char sB[NP / 8 * ROWB];    // B first: A follows it
-  __shared__ __align__(1024) unsigned char sA[128 / 8 * ROWB];
-  __shared__ __align__(8) unsigned long long s_mbar;
+  using S = TcShape<NF, NLF, PER_AXIS>;
+  constexpr int NT = 128 * TC_G, NIN = S::NIN, NEXP = S::NEXP, KP = S::KP, NP = S::NP, ROWB = S::ROWB;
+  static_assert(S::OK, "tile shape");
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  __shared__ __align__(8) unsigned long long s_mbar[TC_G];
   __shared__ uint32_t s_tmem;
-  __shared__ float wsum[4];
+  __shared__ float wsum[NT / 32];
   __shared__ int s_to, s_stop;
   if (ctrl_done(ctrl) || *(volatile const int*)&ctrl->inner_done) return;
   const int jj0 = *(volatile const int*)&ctrl->inner_iter;
@@ -820,45 +851,126 @@ __global__ void __launch_bounds__(128) k_inner_tc(const DevGeo g, const __nv_bfl
   const int lowp0 = *(volatile const int*)&ctrl->lowp_sweeps;
   const int max_iters = ctrl->max_iters, inner_max = ctrl->inner_max;
   const float limf = (float)(ctrl->inner_rtol * ctrl->rnorm);
-  const int tid = threadIdx.x, warp = tid >> 5;
-  // set-up: tensor memory, mbarrier, operator B
-  if (warp == 0) {
+  const int tid = threadIdx.x, gr = tid >> 7, gt = tid & 127, wq = (tid >> 5) & 3;
+  unsigned char* sB = tc_smem;
+  unsigned char* sA = tc_smem + S::BBYTES + gr * S::ABYTES;
+  // set-up: tensor memory, one mbarrier per group, operator B
+  if (tid < 32) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(&s_tmem)),
-                 "r"(TC_COLS) : "memory");
+                 "r"(S::TCOLS) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&s_mbar)) : "memory");
+  if (tid < TC_G) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&s_mbar[tid])) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   {
     const uint4* src = reinterpret_cast<const uint4*>(Bg);
     uint4* dst = reinterpret_cast<uint4*>(sB);
-    for (int i = tid; i < NP / 8 * ROWB / 16; i += 128) dst[i] = src[i];
+    for (int i = tid; i < S::BBYTES / 16; i += NT) dst[i] = src[i];
   }
   tc::fence_proxy_async();
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
-  const uint32_t taddr = s_tmem;
-  const uint32_t mbar = tc::smem_u32(&s_mbar);
+  const uint32_t tmem0 = s_tmem;
+  const uint32_t tcol = tmem0 + (uint32_t)(gr * 32);                 // this group's accumulator
+  const uint32_t tld = tcol + ((uint32_t)(wq * 32) << 16);            // this warp's 32 lanes of it
+  const uint32_t mbar = tc::smem_u32(&s_mbar[gr]);
   const uint32_t aaddr = tc::smem_u32(sA), baddr = tc::smem_u32(sB);
   constexpr uint32_t IDESC = tc::idesc_bf16(128, NP);
+  const int bar_id = 1 + gr;
   uint32_t phase = 0;
-  const int ld = (int)g.ld;
-  const int ntiles = (int)((g.nel + 127) / 128);
+  const int ld = (int)g.ld, nel = (int)g.nel;
+  const int ntiles = (nel + 127) / 128;
+  const int tile0 = blockIdx.x * TC_G + gr, tstride = gridDim.x * TC_G;
   unsigned* count = &ctrl->bar_count;
   float* partf = reinterpret_cast<float*>(partials);
   int failed = 0;
+  // a1: gather element (tile*128 + gt)'s traces into row gt of this group's A (bf16).  Every
+  // load is unconditional (rows past the mesh and faces on the boundary read a safe address
+  // and are masked afterwards), so all of them are in flight at once.  own[] keeps the
+  // element's current exports for the epilogue's step norm.
+  float own[NEXP];
+  auto gather_pack = [&](int tile, const TL* __restrict__ ec) {
+    const int K = tile * 128 + gt;
+    const bool valid = K < nel;
+    const int Kc = valid ? K : 0;
+    int c[3] = {0, 0, 0};
+    if (valid) coords(g, K, c);
+    const unsigned short* eb = reinterpret_cast<const unsigned short*>(ec);
+    int o1[NLF], o2[NLF];
+    bool u1[NLF], u2[NLF], z[NLF];
+#pragma unroll
+    for (int f = 0; f < NLF; ++f) {
+      const int kind = g.kind[f], a = f >> 1;
+      const bool bnd = valid && on_bnd(g, c, f);
+      const int os = PER_AXIS ? a * NF : f * NF;
+      const int ns = PER_AXIS ? a * NF : (f ^ 1) * NF;
+      const int Kn = Kc + ((f & 1) ? (int)g.stride[a] : -(int)g.stride[a]);
+      const bool nbr = valid && !bnd && (kind == FK_NBR_D || kind == FK_SUM_D);
+      if (PER_AXIS) {   // one source per face: own (outflow) or the neighbour's (inflow)
+        u1[f] = valid && (kind == FK_OWN_D || (kind == FK_NBR_D && !bnd));
+        o1[f] = (kind == FK_NBR_D && nbr) ? ns * ld + Kn : os * ld + Kc;
+        u2[f] = false;
+        o2[f] = 0;
+        z[f] = kind != FK_OWN_D;    // not an own row
+      } else {          // own + neighbour; on the boundary mirror (2 own) or zero
+        u1[f] = valid && (kind == FK_OWN_D || (kind == FK_SUM_D && (!bnd || g.bc_mirror)));
+        o1[f] = os * ld + Kc;
+        u2[f] = nbr || (valid && kind == FK_SUM_D && bnd && g.bc_mirror);
+        o2[f] = nbr ? ns * ld + Kn : os * ld + Kc;
+        z[f] = !(kind == FK_OWN_D || kind == FK_SUM_D);
+      }
+    }
+    unsigned short r1[NIN], r2[PER_AXIS ? 1 : NIN];
+#pragma unroll
+    for (int f = 0; f < NLF; ++f)
+#pragma unroll
+      for (int q = 0; q < NF; ++q) r1[f * NF + q] = __ldcg(eb + o1[f] + q * ld);
+    if constexpr (!PER_AXIS) {
+#pragma unroll
+      for (int f = 0; f < NLF; ++f)
+#pragma unroll
+        for (int q = 0; q < NF; ++q) r2[f * NF + q] = __ldcg(eb + o2[f] + q * ld);
+    }
+    float t[KP];
+#pragma unroll
+    for (int k = NIN; k < KP; ++k) t[k] = 0.f;
+#pragma unroll
+    for (int f = 0; f < NLF; ++f) {
+      const int os = PER_AXIS ? (f >> 1) * NF : f * NF;
+#pragma unroll
+      for (int q = 0; q < NF; ++q) {
+        const float x = u1[f] ? __uint_as_float((unsigned)r1[f * NF + q] << 16) : 0.f;
+        float v = x;
+        if constexpr (!PER_AXIS) v += u2[f] ? __uint_as_float((unsigned)r2[f * NF + q] << 16) : 0.f;
+        t[f * NF + q] = v;
+        // the own export row: read in full (also on the boundary) for the step norm
+        const float xo = __uint_as_float((unsigned)r1[f * NF + q] << 16);
+        if (PER_AXIS) { if (!z[f]) own[os + q] = valid ? xo : 0.f; }
+        else own[os + q] = (valid && !z[f]) ? xo : 0.f;
+      }
+    }
+#pragma unroll
+    for (int kc = 0; kc < KP / 8; ++kc) {
+      __align__(16) __nv_bfloat16 h[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) h[u] = __float2bfloat16_rn(t[kc * 8 + u]);
+      *reinterpret_cast<uint4*>(sA + (gt >> 3) * ROWB + kc * 128 + (gt & 7) * 16) = *reinterpret_cast<uint4*>(h);
+    }
+  };
   for (int s = 0;; ++s) {
     const TL* __restrict__ ec = ((jj0 + s) & 1) ? e1 : e0;
     TL* __restrict__ en = ((jj0 + s) & 1) ? e0 : e1;
-    // lagged loop decision (see k_inner_reg)
+    // previous sweep's partials, in flight together with the first tile's gathers
     float pv = 0.f;
     if (s > 0)
-      for (int i = tid; i < (int)gridDim.x; i += 128) pv += __ldcg(partf + ((s - 1) & 1) * gridDim.x + i);
+      for (int i = tid; i < (int)gridDim.x; i += NT) pv += __ldcg(partf + ((s - 1) & 1) * gridDim.x + i);
+    if (tile0 < ntiles) gather_pack(tile0, ec);
+    // lagged loop decision (as in k_inner_reg)
     {
-      const float tot = sum_partials<128>(pv, wsum);
+      const float tot = sum_partials<NT>(pv, wsum);
       if (tid == 0) {
         const float step = sqrtf(tot);
         const bool budget = jj0 + s >= inner_max || iter0 + s >= max_iters;
@@ -876,135 +988,106 @@ __global__ void __launch_bounds__(128) k_inner_tc(const DevGeo g, const __nv_bfl
       if (s_stop) break;
     }
     float acc = 0.f;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-      const int K = tile * 128 + tid;
-      const bool valid = K < (int)g.nel;
-      int c[3] = {0, 0, 0};
-      if (valid) coords(g, K, c);
-      // a1: gather this element's traces into row `tid` of A (bf16, core-matrix layout)
-      float t[KP];
-#pragma unroll
-      for (int k = NIN; k < KP; ++k) t[k] = 0.f;
-#pragma unroll
-      for (int f = 0; f < NLF; ++f) {
-        const int kind = g.kind[f];
-        const int a = f >> 1;
-        const bool bnd = valid && on_bnd(g, c, f);
-        const int os = PER_AXIS ? a * NF : f * NF;
-        const int ns = PER_AXIS ? a * NF : (f ^ 1) * NF;
-        const int Kn = K + ((f & 1) ? (int)g.stride[a] : -(int)g.stride[a]);
-#pragma unroll
-        for (int q = 0; q < NF; ++q) {
-          float v = 0.f;
-          if (valid) {
-            if (kind == FK_OWN_D) {
-              v = ldcg_f(ec + (os + q) * ld + K);
-            } else if (kind == FK_NBR_D) {
-              if (!bnd) v = ldcg_f(ec + (ns + q) * ld + Kn);
-            } else if (kind == FK_SUM_D) {
-              const float o = ldcg_f(ec + (os + q) * ld + K);
-              if (!bnd) v = o + ldcg_f(ec + (ns + q) * ld + Kn);
-              else if (g.bc_mirror) v = o + o;
-            }
-          }
-          t[f * NF + q] = v;
-        }
-      }
-#pragma unroll
-      for (int kc = 0; kc < KP / 8; ++kc) {
-        __align__(16) __nv_bfloat16 h[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) h[u] = __float2bfloat16_rn(t[kc * 8 + u]);
-        *reinterpret_cast<uint4*>(sA + (tid >> 3) * ROWB + kc * 128 + (tid & 7) * 16) = *reinterpret_cast<uint4*>(h);
-      }
+    for (int tile = tile0; tile < ntiles; tile += tstride) {
+      if (tile != tile0) gather_pack(tile, ec);
       tc::fence_proxy_async();
       tc::fence_before();
-      __syncthreads();
+      tc::group_bar(bar_id);
       tc::fence_after();
       // a3: D = A . B^T on the tensor cores
-      if (tid == 0) {
+      if (gt == 0) {
 #pragma unroll
         for (int kk = 0; kk < KP / 16; ++kk)
-          tc::mma_bf16(taddr, tc::sdesc(aaddr + kk * 256, 128, ROWB), tc::sdesc(baddr + kk * 256, 128, ROWB), IDESC,
+          tc::mma_bf16(tcol, tc::sdesc(aaddr + kk * 256, 128, ROWB), tc::sdesc(baddr + kk * 256, 128, ROWB), IDESC,
                        kk > 0 ? 1u : 0u);
         tc::commit(mbar);
       }
       __syncwarp();
-      // the block agrees on the outcome of the (bounded) wait, so all threads take the same path
+      // the epilogue's operands load while the MMAs run
+      const int K = tile * 128 + gt;
+      const bool valid = K < nel;
+      unsigned short rr[NEXP];
+      const unsigned short* rb = reinterpret_cast<const unsigned short*>(rlp);
+#pragma unroll
+      for (int e = 0; e < NEXP; ++e) rr[e] = rb[e * ld + (valid ? K : 0)];
+      // the group agrees on the outcome of the (bounded) wait, so all its threads take one path
       const int ok = tc::mbar_wait(mbar, phase) ? 1 : 0;
-      failed = __syncthreads_or(!ok);
+      const int bad = tc::group_or(bar_id, !ok);
       phase ^= 1u;
-      if (failed) break;
+      if (bad) { failed = 1; break; }
       tc::fence_after();
-      // a4: epilogue from this warp's 32 accumulator lanes
+      // a4: e_{j+1} = r + D from this warp's 32 accumulator lanes
       float d[32];
-      tc::ld32(taddr + ((uint32_t)(warp * 32) << 16), d);
+      tc::ld32(tld, d);
       if (valid) {
 #pragma unroll
         for (int e = 0; e < NEXP; ++e) {
           if ((g.live >> e) & 1ull) {
-            const float v = to_f(rlp[e * ld + K]) + d[e];
-            const TL nv = from_f<TL>(v);
-            const float dl = to_f(nv) - ldcg_f(ec + e * ld + K);
+            const TL nv = from_f<TL>(__uint_as_float((unsigned)rr[e] << 16) + d[e]);
+            const float dl = to_f(nv) - own[e];
             acc = fmaf(dl, dl, acc);
             en[e * ld + K] = nv;
           }
         }
       }
-      tc::fence_before();
-      __syncthreads();
     }
-    if (failed) {
+    if (__syncthreads_or(failed)) {
       if (tid == 0) atomicExch(&ctrl->timeout, 1);
       break;
     }
-    const float blk = sum_partials<128>(acc, wsum);
+    const float blk = sum_partials<NT>(acc, wsum);
     arrive_wait(partf + (s & 1) * gridDim.x, count, (unsigned)(s + 1), blk, ctrl, &s_to);
     if (s_to) break;
   }
-  // release tensor memory on every path (a failed MMA wait gets one more bounded wait)
+  // release tensor memory on every path (a group whose MMA wait expired waits once more)
   if (failed) tc::mbar_wait(mbar, phase ^ 1u);
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(TC_COLS) : "memory");
+  if (tid < 32)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem0), "r"(S::TCOLS) : "memory");
 }
 
 // Launch the tensor-core inner kernel (bf16 storage).  B = L_E in the core-matrix layout is
-// built on the host and copied to the workspace.
+// built on the host and copied to the workspace once per solve.
 template <int NF, int NLF, bool PER_AXIS>
 cudaError_t launch_tc(MixedArgs& m, __nv_bfloat16* rl, __nv_bfloat16* e0, __nv_bfloat16* e1) {
-  constexpr int NIN = NF * NLF;
-  constexpr int NEXP = PER_AXIS ? NF * (NLF / 2) : NF * NLF;
-  constexpr int KP = (NIN + 15) / 16 * 16, NP = (NEXP + 15) / 16 * 16;
-  if constexpr (NP > TC_COLS || KP > 64) {
+  using S = TcShape<NF, NLF, PER_AXIS>;
+  if constexpr (!S::OK) {
     return cudaErrorNotSupported;
   } else {
+    constexpr int NIN = S::NIN, NEXP = S::NEXP, KP = S::KP, NP = S::NP;
     const LaunchArgs& a = m.base;
     if (!m.LE32h || !m.dLT || a.g.n_exp != NEXP || (long long)a.g.ld * NEXP >= (1LL << 31)) return cudaErrorNotSupported;
+    static_assert((size_t)NP * KP * 2 <= 8192, "operator scratch");
     auto k = k_inner_tc<NF, NLF, PER_AXIS>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
+    if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, 128, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, 128 * TC_G, S::SMEM);
     if (e != cudaSuccess) return e;
-    if (per > 8) per = 8;                          // 8 x 32 tensor-memory columns per SM at most
+    if (per > (int)(512 / S::TCOLS)) per = (int)(512 / S::TCOLS);   // 512 tensor-memory columns per SM
     if (per < 1) return cudaErrorNotSupported;
     long long grid = (long long)per * sms;
     const long long ntiles = (a.g.nel + 127) / 128;
-    if (grid > ntiles) grid = ntiles;
+    const long long need = (ntiles + TC_G - 1) / TC_G;
+    if (grid > need) grid = need;
     if (grid > m.max_grid) grid = m.max_grid;
     if (grid > m.slots / 2) return cudaErrorNotSupported;
-    // B[n][k] = L_E[n][k] (bf16), core-matrix layout: (n/8)*KP*16 + (k/8)*128 + (n%8)*16 + (k%8)*2 bytes
-    std::vector<__nv_bfloat16> hb((size_t)NP * KP, __float2bfloat16_rn(0.f));
-    for (int n = 0; n < NEXP; ++n)
-      for (int kk = 0; kk < NIN; ++kk) {
-        const size_t off = (size_t)(n / 8) * KP * 8 + (kk / 8) * 64 + (n % 8) * 8 + (kk % 8);
-        hb[off] = __float2bfloat16_rn(m.LE32h[n * NIN + kk]);
-      }
-    e = cudaMemcpyAsync(m.dLT, hb.data(), hb.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice, a.stream);
-    if (e != cudaSuccess) return e;
+    if (m.lt_kind != 2) {
+      // B[n][k] = L_E[n][k] (bf16): byte (n/8)*KP*16 + (k/8)*128 + (n%8)*16 + (k%8)*2
+      std::vector<__nv_bfloat16> hb((size_t)NP * KP, __float2bfloat16_rn(0.f));
+      for (int n = 0; n < NEXP; ++n)
+        for (int kk = 0; kk < NIN; ++kk) {
+          const size_t off = (size_t)(n / 8) * KP * 8 + (kk / 8) * 64 + (n % 8) * 8 + (kk % 8);
+          hb[off] = __float2bfloat16_rn(m.LE32h[n * NIN + kk]);
+        }
+      e = cudaMemcpyAsync(m.dLT, hb.data(), hb.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice, a.stream);
+      if (e != cudaSuccess) return e;
+      m.lt_kind = 2;
+    }
     e = cudaMemsetAsync(&a.ctrl->bar_count, 0, sizeof(unsigned), a.stream);
     if (e != cudaSuccess) return e;
     DevGeo gg = a.g;
@@ -1013,7 +1096,7 @@ cudaError_t launch_tc(MixedArgs& m, __nv_bfloat16* rl, __nv_bfloat16* e0, __nv_b
     double* pp = a.partials;
     const __nv_bfloat16* bp = reinterpret_cast<const __nv_bfloat16*>(m.dLT);
     void* args[] = {&gg, &rlc, &e0, &e1, &ct, &pp, &bp};
-    e = cudaLaunchCooperativeKernel((const void*)k, dim3((unsigned)grid), dim3(128), args, 0, a.stream);
+    e = cudaLaunchCooperativeKernel((const void*)k, dim3((unsigned)grid), dim3(128 * TC_G), args, S::SMEM, a.stream);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
   }
@@ -1046,8 +1129,11 @@ cudaError_t launch_reg_v(MixedArgs& m, TL* rl, TL* e0, TL* e1) {
   for (int kk = 0; kk < NIN; ++kk)
     for (int b = 0; b < nrb; ++b)
       for (int r = 0; r < NF; ++r) lt[((size_t)kk * NRB + b) * RW + r] = m.LE32h[(b * NF + r) * NIN + kk];
-  e = cudaMemcpyAsync(m.dLT, lt.data(), lt.size() * sizeof(float), cudaMemcpyHostToDevice, a.stream);
-  if (e != cudaSuccess) return e;
+  if (m.lt_kind != 1) {
+    e = cudaMemcpyAsync(m.dLT, lt.data(), lt.size() * sizeof(float), cudaMemcpyHostToDevice, a.stream);
+    if (e != cudaSuccess) return e;
+    m.lt_kind = 1;
+  }
   e = cudaMemsetAsync(&a.ctrl->bar_count, 0, sizeof(unsigned), a.stream);
   if (e != cudaSuccess) return e;
   DevGeo gg = a.g;

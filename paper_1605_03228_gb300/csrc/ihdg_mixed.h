@@ -32,6 +32,7 @@ struct MixedArgs {
   int tile_lpe = 4;         // 4: 2D meshes use the register-resident kernel when it fits
   float* dLT = nullptr;     // device scratch for the transposed operator (register kernel)
   int use_tc = 0;           // bf16: local apply on the tensor cores (tcgen05)
+  int lt_kind = 0;          // operator layout now in dLT: 0 none, 1 register kernel, 2 tensor-core B
   const float* LE32h = nullptr;  // host copy of the float32 operator (n_exp x n_in)
 };
 

@@ -296,13 +296,15 @@ def test_mixed_inner_kernel_variants(ctx, monkeypatch, kernel, grid, lpe):
     assert rel(u_b, u_a) < 1e-9
 
 
-@pytest.mark.parametrize("case,grid", [("t3d_p1", ""), ("t3d_p2", ""), ("cd2d_p3", ""), ("t2d_p2", "3")])
-def test_mixed_bf16_tensor_core_inner(ctx, monkeypatch, case, grid):
-    """bf16 inner sweeps with the local apply on the tensor cores (IHDG_INNER_KERNEL=tc:
+@pytest.mark.parametrize("case,grid,kernel", [("t3d_p1", "", "tc"), ("t3d_p2", "", "tc"), ("cd2d_p3", "", "tc"),
+                                              ("t2d_p2", "1", "tc"), ("t3d_p1", "", "tile"), ("cd2d_p3", "", "tile")])
+def test_mixed_bf16_tensor_core_inner(ctx, monkeypatch, case, grid, kernel):
+    """bf16 inner sweeps with the local apply on the tensor cores (the default, kernel "tc":
     tcgen05 MMA over tiles of 128 elements, operands bf16, accumulation float32) reach the
-    oracle's float64 solution at the mixed bar.  The meshes leave a ragged last tile
-    (element counts not multiples of 128), and a grid of 3 blocks makes every block loop
-    over several tiles per sweep."""
+    oracle's float64 solution at the mixed bar, and so do bf16 sweeps on the CUDA cores
+    (kernel "tile").  The meshes leave a ragged last tile
+    (element counts not multiples of 128) and some of a block's four tile groups without a
+    tile; a grid of one block makes its groups loop over several tiles per sweep."""
     ihdg = ih()
     if case.startswith("t3d"):
         n, p = ((9, 7, 11), 1) if case == "t3d_p1" else ((6, 5, 7), 2)
@@ -329,7 +331,7 @@ def test_mixed_bf16_tensor_core_inner(ctx, monkeypatch, case, grid):
     tol = 1e-9
     U, T, K, r, st = pr.iterate(f, g, tol, max_iters=20000)
     assert st == STATUS_OK
-    monkeypatch.setenv("IHDG_INNER_KERNEL", "tc")
+    monkeypatch.setenv("IHDG_INNER_KERNEL", kernel)
     if grid:
         monkeypatch.setenv("IHDG_PERSISTENT_GRID", grid)
     u, tr, res = ctx.solve(mesh, co, f, g, ihdg.make_options(tol, prec=ihdg.MIXED_BF16, max_iters=20000))
