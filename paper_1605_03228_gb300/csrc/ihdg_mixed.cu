@@ -601,9 +601,8 @@ __global__ void __launch_bounds__(512, 2) k_inner_reg(const DevGeo g, const TL* 
   constexpr int RW = (NF + 3) & ~3;          // padded row-block width
   constexpr int NRB = 4;                     // row blocks stored (faces; axes use the first 2)
   __shared__ __align__(16) float LT[NIN * NRB * RW];
-  __shared__ float wsum[NT / 32];
-  __shared__ double s_tot;
-  __shared__ int s_to, s_stop;
+  __shared__ float wsum[NT / 32], wdec[NT / 32];
+  __shared__ int s_to;
   if (ctrl_done(ctrl) || *(volatile const int*)&ctrl->inner_done) return;
   int j = *(volatile const int*)&ctrl->inner_iter;
   const int iter0 = *(volatile const int*)&ctrl->iter;
@@ -672,25 +671,6 @@ __global__ void __launch_bounds__(512, 2) k_inner_reg(const DevGeo g, const TL* 
     for (int i = 0; i < FPL; ++i)
 #pragma unroll
       for (int q = 0; q < NF; ++q) lt[i][q] = wo[i] * ev[i][q] + (nbm[i] ? lt[i][q] : 0.f);   // never 0 * (unread)
-    // decision on the s sweeps done so far (the last one's step norm when s > 0)
-    {
-      const float tot = sum_partials<NT>(pv, wsum);
-      if (threadIdx.x == 0) {
-        const float step = sqrtf(tot);
-        const bool budget = j + s >= inner_max || iter0 + s >= max_iters;
-        const bool stop = budget || (s > 0 && (step <= limf || !(step == step) || isinf(step)));
-        s_stop = stop ? 1 : 0;
-        if (blockIdx.x == 0) {
-          ctrl->inner_iter = j + s;
-          ctrl->iter = iter0 + s;
-          ctrl->lowp_sweeps = lowp0 + s;
-          if (s > 0) ctrl->inner_step = (double)step;
-          if (stop) ctrl->inner_done = 1;
-        }
-      }
-      __syncthreads();
-      if (s_stop) break;
-    }
     float acc[FPL][RW];
 #pragma unroll
     for (int i = 0; i < FPL; ++i)
@@ -718,6 +698,29 @@ __global__ void __launch_bounds__(512, 2) k_inner_reg(const DevGeo g, const TL* 
             }
           }
         }
+    // decision on the s sweeps done so far (the last one's step norm when s > 0), taken
+    // after the local apply so that the partial sums have arrived.  Every thread folds the
+    // warp sums in the same order: all threads of all blocks take the same decision.
+    {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) pv += __shfl_xor_sync(0xffffffffu, pv, o);
+      if ((threadIdx.x & 31) == 0) wdec[threadIdx.x >> 5] = pv;
+      __syncthreads();
+      float tot = 0.f;
+#pragma unroll
+      for (int w = 0; w < NT / 32; ++w) tot += wdec[w];
+      const float step = sqrtf(tot);
+      const bool budget = j + s >= inner_max || iter0 + s >= max_iters;
+      const bool stop = budget || (s > 0 && (step <= limf || !(step == step) || isinf(step)));
+      if (threadIdx.x == 0 && blockIdx.x == 0) {
+        ctrl->inner_iter = j + s;
+        ctrl->iter = iter0 + s;
+        ctrl->lowp_sweeps = lowp0 + s;
+        if (s > 0) ctrl->inner_step = (double)step;
+        if (stop) ctrl->inner_done = 1;
+      }
+      if (stop) break;
+    }
     float st = 0.f;
 #pragma unroll
     for (int i = 0; i < FPL; ++i) {
