@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the as-listed and float64 comparison solves")
     ap.add_argument("--prec", default="", choices=["", "FP64", "MIXED_FP32", "MIXED_BF16"],
                     help="override the workload's precision (profiling cases)")
+    ap.add_argument("--flux", default="upwind", choices=["upwind", "npc"],
+                    help="transport workloads: numerical flux (npc: Eq. Ntaub, finite termination)")
     ap.add_argument("--inner-max", type=int, default=0, help="mixed: inner sweeps per outer step (profiling cases)")
     ap.add_argument("--inner-rtol", type=float, default=0.0, help="mixed: inner stopping ratio (profiling cases)")
     ap.add_argument("--requests", type=int, default=400, help="serving: number of requests (the listed stream is 10000)")
@@ -99,7 +101,8 @@ def make_problem(ih, spec, kappa=None):
     if spec["pde"] == "convdiff":
         co = ih.make_coeffs(ih.CONVDIFF, beta=spec["beta"], kappa=spec["kappa"] if kappa is None else kappa)
     elif spec["pde"] == "transport":
-        co = ih.make_coeffs(ih.TRANSPORT, beta=spec["beta"])
+        co = ih.make_coeffs(ih.TRANSPORT, beta=spec["beta"],
+                            flux=ih.FLUX_NPC if spec.get("flux") == "npc" else ih.FLUX_UPWIND)
     else:
         co = ih.make_coeffs(ih.SWE, Phi=spec["Phi"], dt=spec["dt"])
     return mesh, co
@@ -183,7 +186,7 @@ def run_reference(args, spec, rank):
         f, g = W.convdiff_forcing(X, spec["kappa"], spec["beta"]), W.convdiff_exact(B)
         prev = None
     elif spec["pde"] == "transport":
-        pr = Transport(disc, np.array(spec["beta"]))
+        pr = Transport(disc, np.array(spec["beta"]), flux=spec.get("flux", "upwind"))
         X, B = disc.volume_points(), disc.boundary_points()
         if spec["dim"] == 2:
             f, g = W.transport2d_forcing(X, spec["beta"]), W.transport2d_exact(B)
@@ -337,6 +340,11 @@ def main():
     if args.prec:
         spec["prec"] = args.prec
         spec["desc"] = f"[{args.prec}] " + spec["desc"]
+    if args.flux != "upwind":
+        if spec["pde"] != "transport":
+            raise SystemExit("--flux npc applies to the transport workloads only")
+        spec["flux"] = args.flux
+        spec["desc"] = f"[{args.flux} flux] " + spec["desc"]
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

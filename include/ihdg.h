@@ -58,6 +58,15 @@ typedef enum {
 
 typedef enum { IHDG_TRANSPORT = 0, IHDG_CONVDIFF = 1, IHDG_SWE = 2 } ihdg_pde;
 
+/* Numerical flux of the transport equation (Section 3).  IHDG_FLUX_UPWIND: the upwind HDG
+ * flux, tau = |beta.n| with the weighted trace of Eq. transportLocale.  IHDG_FLUX_NPC: the
+ * flux of Eq. Ntaub, tau = |beta.n|(1 + sgn(beta.n))/2 - beta.n (0 on outflow faces), no
+ * weight on the trace; the iteration then terminates after as many sweeps as there are
+ * element layers along the flow (Theorem iHDG-NPC).  Both make the trace the upwind value and
+ * have the same fixed point.  Convection-diffusion and shallow water take only the upwind
+ * flux (the paper gives NPC's tau for transport only). */
+typedef enum { IHDG_FLUX_UPWIND = 0, IHDG_FLUX_NPC = 1 } ihdg_flux;
+
 /* Arithmetic of the sweep.  FP64: every step in float64.  MIXED_*: defect correction --
  * float64 outer sweeps form the residual r = S(E) - E and its float64 norm; inner sweeps on
  * the correction equation e = r + G(e) run in float32 (CUDA cores), TF32 or BF16 (tcgen05
@@ -86,6 +95,8 @@ typedef struct {
   double coriolis_f;    /* shallow water Coriolis parameter (constant) */
   double friction;      /* shallow water bottom friction gamma >= 0 */
   double dt;            /* shallow water backward-Euler step, > 0 */
+  ihdg_flux flux;       /* transport: IHDG_FLUX_UPWIND (0, the default) or IHDG_FLUX_NPC;
+                           other PDEs: must be IHDG_FLUX_UPWIND (else IHDG_ERR_UNSUPPORTED) */
 } ihdg_coeffs;
 
 typedef struct {

@@ -11,7 +11,8 @@ What is computed, following the paper:
   then solves every element's local equation for u^{k+1} ("element by element"), then
   measures ||u^{k+1} - u^k||_{L2(Omega)} (the stopping test of Section 6.1,
   Eq. (tolerancecriteriarelerror)).
-* Section 3, Eqs. (transportLocalk1)/(transportLocale): scalar transport.
+* Section 3, Eqs. (transportLocalk1)/(transportLocale): scalar transport; and the NPC flux
+  of Section 3 (Eq. Ntaub and the trace formula after it) as the alternative.
 * Section 3, Eq. (localSolverDD) and the trace formula below it: linearized shallow water,
   backward Euler in time.
 * Section 4.1, Eqs. (ErrorDDMCD1)/(ErrorDDMCD2) and the flux (general_flux_convdiff):
@@ -36,6 +37,10 @@ Readings of points the paper leaves open (each is also listed in the design note
   R6 Convection-diffusion: tau^+- = (alpha - beta.n^+-)/2 with alpha = sqrt((beta.n)^2+4)
      (gamma = 1), so tau^+ + tau^- = alpha.
   R7 Shallow water walls: the mirror state, phi_hat = phi^- + sqrt(Phi) vel^-.n^-.
+  R8 NPC flux (transport): the local equation is the HDG one with stabilisation
+     tau = |beta.n| (1 + sgn(beta.n))/2 - beta.n and no weight on the trace; the trace
+     ({{tau u}} + {{beta.n u}})/{{tau}} reduces to the upwind value, and g on the inflow
+     boundary.
 """
 import numpy as np
 
@@ -274,28 +279,47 @@ class Problem:
 class Transport(Problem):
     """Steady scalar transport beta.grad u = f, constant beta (Section 3).
 
-    Local equation (transportLocalk1):
-        -(u, div(beta v))_K + <beta.n u + |beta.n|(u - u_hat^k), v>_dK = (f, v)_K
-    Weighted trace (transportLocale): |beta.n| u_hat = {{beta.n u}} + |beta.n| {{u}},
-    i.e. the upwind value; g on the inflow boundary.
+    Upwind HDG flux (flux="upwind"):
+      Local equation (transportLocalk1):
+          -(u, div(beta v))_K + <beta.n u + |beta.n|(u - u_hat^k), v>_dK = (f, v)_K
+      Weighted trace (transportLocale): |beta.n| u_hat = {{beta.n u}} + |beta.n| {{u}},
+      i.e. the upwind value; g on the inflow boundary.
+    NPC flux (flux="npc", Section 3, Eq. Ntaub):
+      Local equation -(u, div(beta v))_K + <beta.n u + tau (u - u_hat^k), v>_dK = (f, v)_K
+      with tau = |beta.n| (1 + sgn(beta.n))/2 - beta.n: 0 on outflow faces, |beta.n| on
+      inflow faces.  Trace ({{tau u}} + {{beta.n u}})/{{tau}}: on a face where the flow goes
+      from K^- to K^+ (beta.n^- = b > 0) tau^- = 0 and tau^+ = b, so the trace is u^-, the
+      upwind value again; the outflow faces no longer feed back into their own element.
     """
 
     nc = 1
 
-    def __init__(self, disc, beta):
+    def __init__(self, disc, beta, flux="upwind"):
         self.beta = np.asarray(beta, dtype=np.float64)[: disc.d]
+        if flux not in ("upwind", "npc"):
+            raise ValueError("flux must be 'upwind' or 'npc'")
+        self.flux = flux
         super().__init__(disc)
 
     def bn(self, f):
         return float(self.disc.normal[f] @ self.beta)
+
+    @staticmethod
+    def tau_npc(bn):
+        """Eq. Ntaub: tau = |beta.n| (1 + sgn(beta.n))/2 - beta.n."""
+        return abs(bn) * (1.0 + np.sign(bn)) / 2.0 - bn
+
+    def tau(self, f):
+        """Stabilisation on face f: |beta.n| (upwind) or Eq. Ntaub (NPC)."""
+        bn = self.bn(f)
+        return abs(bn) if self.flux == "upwind" else self.tau_npc(bn)
 
     def local_matrix(self):
         disc = self.disc
         # -(u, beta.grad v) (constant beta, so div(beta v) = beta.grad v)
         A = -sum(self.beta[a] * disc.K[a] for a in range(disc.d))
         for f in range(2 * disc.d):
-            bn = self.bn(f)
-            A = A + (bn + abs(bn)) * disc.Mf[f]
+            A = A + (self.bn(f) + self.tau(f)) * disc.Mf[f]
         return A
 
     def volume_rhs(self, f_qp, U_prev=None):
@@ -316,7 +340,7 @@ class Transport(Problem):
 
     def trace_coupling(self):
         disc = self.disc
-        return [abs(self.bn(f)) * disc.Ff[f] for f in range(2 * disc.d)]
+        return [self.tau(f) * disc.Ff[f] for f in range(2 * disc.d)]
 
     def trace_rhs(self, T):
         Te = self.elem_traces(T)
@@ -327,7 +351,7 @@ class Transport(Problem):
         return self.disc.mass_norm2(dU[:, 0, :])
 
     def face_equations(self, vals, T, g):
-        """Conservation (transportGlobal) on interior faces: [[beta.n u + |beta.n|(u - u_hat)]]
+        """Conservation (transportGlobal) on interior faces: [[beta.n u + tau (u - u_hat)]]
         = 0; inflow boundary u_hat = g; outflow boundary u_hat = u^-; beta.n = 0: u_hat = {{u}}."""
         m = self.mesh
         L, R = (np.nan_to_num(v) for v in vals[0])
@@ -336,7 +360,12 @@ class Transport(Problem):
         hasR = (m.face_right >= 0)[:, None]
         gfull = np.zeros_like(T)
         gfull[m.bface_ids] = g
-        interior = np.where(b != 0, b * L - b * R + np.abs(b) * (L + R - 2 * T), 0.5 * (L + R) - T)
+        if self.flux == "upwind":
+            tL = tR = np.abs(b)
+        else:   # the left element's normal is +axis (beta.n = b), the right one's -axis
+            tL = self.tau_npc(b)
+            tR = self.tau_npc(-b)
+        interior = np.where(b != 0, b * L - b * R + tL * (L - T) + tR * (R - T), 0.5 * (L + R) - T)
         own = np.where(hasL, L, R)
         inflow = ((b > 0) & ~hasL) | ((b < 0) & ~hasR)
         boundary = np.where(inflow, gfull - T, own - T)

@@ -212,6 +212,8 @@ ihdg_status validate(const ihdg_mesh& m, const ihdg_coeffs* co, std::string& err
   if (co->pde != IHDG_TRANSPORT && co->pde != IHDG_CONVDIFF && co->pde != IHDG_SWE) { err = "coeffs.pde is not a known PDE"; return IHDG_ERR_INVALID; }
   for (int a = 0; a < m.dim; ++a)
     if (!std::isfinite(co->beta[a])) { err = "coeffs.beta must be finite"; return IHDG_ERR_INVALID; }
+  if (co->flux != IHDG_FLUX_UPWIND && co->flux != IHDG_FLUX_NPC) { err = "coeffs.flux is not a known flux"; return IHDG_ERR_INVALID; }
+  if (co->flux == IHDG_FLUX_NPC && co->pde != IHDG_TRANSPORT) { err = "the NPC flux is defined for transport only"; return IHDG_ERR_UNSUPPORTED; }
   if (co->pde == IHDG_CONVDIFF) {
     if (!(co->kappa > 0) || !std::isfinite(co->kappa)) { err = "coeffs.kappa must be > 0"; return IHDG_ERR_INVALID; }
     if (!(co->nu >= 0) || !std::isfinite(co->nu)) { err = "coeffs.nu must be >= 0"; return IHDG_ERR_INVALID; }
@@ -495,8 +497,12 @@ ihdg_status build_ops(const ihdg_mesh& m, const ihdg_coeffs& co, Ops& o, std::st
     for (int a = 0; a < d; ++a) add_vol(K[a], 0, 0, -co.beta[a]);       // -(u, beta.grad v)
     for (int f = 0; f < nlf; ++f) {
       double bn = nsign(f) * co.beta[f / 2];
-      add_face_mass(f, 0, 0, bn + std::fabs(bn));                        // <(beta.n + |beta.n|) u, v>
-      if (bn != 0) add_G(f, 0, std::fabs(bn), bn < 0, 1.0);               // <|beta.n| u_hat, v>
+      // stabilisation: upwind |beta.n|; NPC (Eq. Ntaub) |beta.n|(1 + sgn(beta.n))/2 - beta.n,
+      // which is 0 on outflow faces (no trace coupling there) and |beta.n| on inflow faces
+      const double sg = bn > 0 ? 1.0 : (bn < 0 ? -1.0 : 0.0);
+      const double tau = co.flux == IHDG_FLUX_NPC ? std::fabs(bn) * (1.0 + sg) / 2.0 - bn : std::fabs(bn);
+      add_face_mass(f, 0, 0, bn + tau);                                  // <(beta.n + tau) u, v>
+      if (tau != 0) add_G(f, 0, tau, bn < 0, 1.0);                       // <tau u_hat, v>
     }
     R.assign((size_t)o.n_exp * nvol, 0.0);
     for (int f = 0; f < nlf; ++f)

@@ -16,6 +16,7 @@ OK, ERR_INVALID, ERR_NOMEM, ERR_CUDA, NOT_CONVERGED, DIVERGED, ERR_BUSY, ERR_TIM
 STATUS_NAMES = {0: "OK", 1: "ERR_INVALID", 2: "ERR_NOMEM", 3: "ERR_CUDA", 4: "NOT_CONVERGED", 5: "DIVERGED",
                 6: "ERR_BUSY", 7: "ERR_TIMEOUT", 8: "ERR_UNSUPPORTED"}
 TRANSPORT, CONVDIFF, SWE = 0, 1, 2
+FLUX_UPWIND, FLUX_NPC = 0, 1
 FP64, MIXED_FP32, MIXED_TF32, MIXED_BF16 = 0, 1, 2, 3
 
 
@@ -27,7 +28,7 @@ class Mesh(ctypes.Structure):
 class Coeffs(ctypes.Structure):
     _fields_ = [("pde", ctypes.c_int), ("beta", ctypes.c_double * 3), ("kappa", ctypes.c_double),
                 ("nu", ctypes.c_double), ("Phi", ctypes.c_double), ("coriolis_f", ctypes.c_double),
-                ("friction", ctypes.c_double), ("dt", ctypes.c_double)]
+                ("friction", ctypes.c_double), ("dt", ctypes.c_double), ("flux", ctypes.c_int)]
 
 
 class Options(ctypes.Structure):
@@ -117,9 +118,11 @@ def make_mesh(dim, n, p, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0)):
     return m
 
 
-def make_coeffs(pde, beta=(0.0, 0.0, 0.0), kappa=0.0, nu=0.0, Phi=0.0, coriolis_f=0.0, friction=0.0, dt=0.0):
+def make_coeffs(pde, beta=(0.0, 0.0, 0.0), kappa=0.0, nu=0.0, Phi=0.0, coriolis_f=0.0, friction=0.0, dt=0.0,
+                flux=0):
     c = Coeffs()
     c.pde = pde
+    c.flux = flux
     for a in range(3):
         c.beta[a] = float(beta[a]) if a < len(beta) else 0.0
     c.kappa, c.nu, c.Phi, c.coriolis_f, c.friction, c.dt = kappa, nu, Phi, coriolis_f, friction, dt

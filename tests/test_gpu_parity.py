@@ -101,6 +101,49 @@ def test_transport3d_fp64(ctx, n, p, beta):
     assert rel(tr, oracle_trace_at_nodes(disc, T)) < 1e-10
 
 
+@pytest.mark.parametrize("d,n,p,beta", [(2, (8, 8), 2, (1.0, 0.5)), (2, (9, 6), 3, (-0.6, 1.0)),
+                                        (2, (5, 7), 4, (0.8, -0.3)), (3, (4, 3, 5), 2, (1.0, 1.0, 1.0)),
+                                        (3, (3, 4, 3), 1, (0.5, -0.8, 0.3))])
+def test_transport_npc_fp64(ctx, d, n, p, beta):
+    """NPC flux (Eq. Ntaub) on the float64 path: the oracle's iteration count, which is the
+    number of element layers along the flow plus one (finite termination), and its solution."""
+    ihdg = ih()
+    b = np.array(beta) / np.linalg.norm(beta)
+    mesh = ihdg.make_mesh(d, n, p)
+    co = ihdg.make_coeffs(ihdg.TRANSPORT, beta=tuple(b), flux=ihdg.FLUX_NPC)
+    vol, bnd = ihdg.quadrature_points(mesh, co)
+    if d == 2:
+        f, g = W.transport2d_forcing(vol, tuple(b)), W.transport2d_exact(bnd)
+    else:
+        f, g = W.transport3d_forcing(vol, tuple(b)), W.transport3d_exact(bnd)
+    tol = 1e-10
+    u, tr, res = ctx.solve(mesh, co, f, g, ihdg.make_options(tol))
+    om = BoxMesh(d, n)
+    disc = Discretisation(om, p)
+    U, T, K, r, st, hist = Transport(disc, b, flux="npc").iterate(f, g, tol, history=True)
+    assert res.status == ihdg.OK and st == STATUS_OK
+    check_iteration_count(res.iterations, K, hist, tol)
+    assert K == sum(x - 1 for x in n) + 2
+    assert rel(u, U.reshape(om.nel, -1)) < 1e-10
+    assert rel(tr, oracle_trace_at_nodes(disc, T)) < 1e-10
+
+
+@pytest.mark.parametrize("prec_name", ["MIXED_FP32", "MIXED_BF16"])
+def test_transport_npc_mixed(ctx, prec_name):
+    """NPC flux through the mixed-precision path (outer float64, inner low precision)."""
+    ihdg = ih()
+    n, p, beta = (20, 17), 2, (1.0, 0.5)
+    mesh = ihdg.make_mesh(2, n, p)
+    co = ihdg.make_coeffs(ihdg.TRANSPORT, beta=beta, flux=ihdg.FLUX_NPC)
+    vol, bnd = ihdg.quadrature_points(mesh, co)
+    f, g = W.transport2d_forcing(vol, beta), W.transport2d_exact(bnd)
+    u, tr, res = ctx.solve(mesh, co, f, g, ihdg.make_options(1e-10, prec=getattr(ihdg, prec_name)))
+    om = BoxMesh(2, n)
+    U, T, K, r, st = Transport(Discretisation(om, p), np.array(beta), flux="npc").iterate(f, g, 1e-10)
+    assert res.status == ihdg.OK, res.as_dict()
+    assert rel(u, U.reshape(om.nel, -1)) < 1e-6
+
+
 def test_transport_beta_axis_aligned(ctx):
     """beta . n = 0 on the y faces: zero-weight faces, trace reported as {{u}}."""
     ihdg = ih()

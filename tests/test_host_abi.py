@@ -79,6 +79,11 @@ def test_invalid_arguments_rejected():
     m3 = ihdg.make_mesh(3, (2, 2, 2), 2)
     c3 = ihdg.make_coeffs(ihdg.SWE, Phi=1.0, dt=0.1)
     assert L.ihdg_problem_sizes(ctypes.byref(m3), ctypes.byref(c3), ctypes.byref(s)) == ihdg.ERR_UNSUPPORTED
+    bad_flux = ihdg.make_coeffs(ihdg.TRANSPORT, beta=(1, 1), flux=7)
+    m2 = ihdg.make_mesh(2, (2, 2), 2)
+    assert L.ihdg_problem_sizes(ctypes.byref(m2), ctypes.byref(bad_flux), ctypes.byref(s)) == ihdg.ERR_INVALID
+    npc_cd = ihdg.make_coeffs(ihdg.CONVDIFF, beta=(1, 1), kappa=0.1, flux=ihdg.FLUX_NPC)
+    assert L.ihdg_problem_sizes(ctypes.byref(m2), ctypes.byref(npc_cd), ctypes.byref(s)) == ihdg.ERR_UNSUPPORTED
     m = ihdg.make_mesh(2, (2, 2), 5)
     c = ihdg.make_coeffs(ihdg.TRANSPORT, beta=(1, 1))
     assert L.ihdg_problem_sizes(ctypes.byref(m), ctypes.byref(c), ctypes.byref(s)) == ihdg.ERR_UNSUPPORTED
@@ -131,13 +136,13 @@ def check_one_sweep(mesh, co, problem, kinds, own_off, nbr_off, mirror, U_prev=N
     assert abs(np.einsum("ki,ij,kj->", dt, Q, dt) - problem.norm2(du)) < 1e-10 * problem.norm2(du)
 
 
-@pytest.mark.parametrize("p", [1, 3])
-def test_export_form_matches_oracle_transport(p):
+@pytest.mark.parametrize("p,flux", [(1, "upwind"), (3, "upwind"), (2, "npc"), (3, "npc")])
+def test_export_form_matches_oracle_transport(p, flux):
     beta = (1.0, 0.5)
     mesh = ihdg.make_mesh(2, (3, 3), p)
-    co = ihdg.make_coeffs(ihdg.TRANSPORT, beta=beta)
+    co = ihdg.make_coeffs(ihdg.TRANSPORT, beta=beta, flux=ihdg.FLUX_NPC if flux == "npc" else ihdg.FLUX_UPWIND)
     om = BoxMesh(2, (3, 3))
-    pr = Transport(Discretisation(om, p), np.array(beta))
+    pr = Transport(Discretisation(om, p), np.array(beta), flux=flux)
     nf = p + 1
     kinds = ["nbr", "own", "nbr", "own"]          # beta > 0: -x, -y inflow; +x, +y outflow
     own_off = [(f // 2) * nf for f in range(4)]   # export slot = axis * nf + node

@@ -237,3 +237,78 @@ def test_iterations_nearly_independent_of_p():
     """Table 1: the upwind iteration count barely changes with p at a fixed mesh."""
     ks = [mms_transport_2d(8, p)[1] for p in (1, 2, 3, 4)]
     assert max(ks) <= 1.15 * min(ks), ks
+
+
+# ------------------------------------------------------------------------------ NPC flux
+def npc_case(d, n, p, beta, flux="npc"):
+    """Manufactured problem of the 2D/3D transport workloads with the given flux."""
+    import workloads as W
+    m = BoxMesh(d, (n,) * d)
+    disc = Discretisation(m, p)
+    pr = Transport(disc, np.asarray(beta, dtype=float), flux=flux)
+    X, G = disc.volume_points(), disc.boundary_points()
+    if d == 2:
+        f, g = W.transport2d_forcing(X, beta), W.transport2d_exact(G)
+    else:
+        f, g = W.transport3d_forcing(X, beta), W.transport3d_exact(G)
+    return pr, f, g
+
+
+def test_npc_tau_is_zero_on_outflow_and_abs_on_inflow():
+    """Eq. Ntaub: tau = |b|(1+sgn b)/2 - b is 0 for b > 0, |b| for b < 0, 0 for b = 0."""
+    for b in (0.3, 2.0):
+        assert Transport.tau_npc(b) == 0.0
+        assert Transport.tau_npc(-b) == b
+    assert Transport.tau_npc(0.0) == 0.0
+
+
+@pytest.mark.parametrize("d,n,p,beta", [(2, 4, 1, (1.0, 0.5)), (2, 5, 2, (0.3, 1.0)), (2, 3, 3, (-1.0, 0.7)),
+                                        (3, 3, 1, (0.6, 0.8, 0.5)), (3, 2, 2, (1.0, -0.4, 0.9))])
+def test_npc_finite_termination(d, n, p, beta):
+    """Theorem (iHDG-NPC): with the NPC flux the iteration terminates.  On an n^d box with no
+    zero component of beta an element's value depends only on its upwind neighbours, so the
+    element at upwind graph distance m from the inflow corner is exact after m+1 sweeps: the
+    iterate equals the direct solution after d(n-1)+1 sweeps and not one sweep earlier, and
+    the stopping test first holds one sweep later.  (Table 1 lists 2n+1 for the 2D meshes,
+    one more than the 2n here; the paper does not state its count convention.)"""
+    pr, f, g = npc_case(d, n, p, beta)
+    Ud, _ = pr.direct_solve(f, g)
+    layers = d * (n - 1) + 1
+    U_last = pr.iterate(f, g, 0.0, max_iters=layers)[0]
+    U_prev = pr.iterate(f, g, 0.0, max_iters=layers - 1)[0]
+    scale = np.abs(Ud).max()
+    assert np.abs(U_last - Ud).max() < 1e-12 * scale
+    assert np.abs(U_prev - Ud).max() > 1e-6 * scale
+    U, T, K, res, st = pr.iterate(f, g, 1e-12, max_iters=1000)
+    assert st == STATUS_OK and K == layers + 1
+
+
+@pytest.mark.parametrize("d,p,beta", [(2, 2, (1.0, 0.5)), (2, 3, (-0.6, 1.0)), (3, 1, (0.6, -0.8, 0.5))])
+def test_npc_and_upwind_share_the_fixed_point(d, p, beta):
+    """Both fluxes make the trace the upwind value, so both HDG discretisations are upwind DG:
+    the NPC direct solve, the NPC iterate and the upwind direct solve coincide."""
+    pr_n, f, g = npc_case(d, 3, p, beta, "npc")
+    pr_u, _, _ = npc_case(d, 3, p, beta, "upwind")
+    Un, Tn = pr_n.direct_solve(f, g)
+    Uu, Tu = pr_u.direct_solve(f, g)
+    Ui, Ti, K, res, st = pr_n.iterate(f, g, 1e-13, max_iters=1000)
+    assert st == STATUS_OK
+    assert np.abs(Un - Uu).max() < 1e-11 and np.abs(Tn - Tu).max() < 1e-11
+    assert np.abs(Ui - Un).max() < 1e-11
+
+
+def test_npc_local_matrix_differs_from_upwind_only_on_outflow_faces():
+    """A_npc = A_upwind - sum over outflow faces of |beta.n| M_f, and the trace coupling of
+    an outflow face vanishes (a plain check of where Eq. Ntaub enters)."""
+    disc = Discretisation(BoxMesh(2, (2, 2)), 2)
+    beta = np.array([0.8, -0.5])
+    pu, pn = Transport(disc, beta), Transport(disc, beta, flux="npc")
+    D = pu.A - pn.A
+    E = sum(max(pu.bn(f), 0.0) * disc.Mf[f] for f in range(4))
+    assert np.abs(D - E).max() < 1e-14
+    Wn = pn.trace_coupling()
+    for f in range(4):
+        if pu.bn(f) > 0:
+            assert np.abs(Wn[f]).max() == 0.0
+        else:
+            assert np.abs(Wn[f] - pu.trace_coupling()[f]).max() < 1e-15
