@@ -106,7 +106,8 @@ typedef struct {
   double diverge_factor;   /* DIVERGED when residual > factor * its running minimum;
                               <= 0 disables the check (default 1e6 when == 0) */
   int inner_max;           /* mixed: inner sweeps per outer step cap (0 = automatic) */
-  double inner_rtol;       /* mixed: inner stop when step norm <= inner_rtol * ||r|| (0 = auto) */
+  double inner_rtol;       /* mixed: inner stop when step norm <= inner_rtol * ||r||
+                              (0 = auto: 2e-3 for float32, 0.2 for bf16) */
   const double* u0;        /* optional initial guess, volume layout (host for ihdg_solve,
                               device for ihdg_solve_device); NULL = zero */
   int profile;             /* 1: time every sweep launch with CUDA events (one launch per
