@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=0, help="override the elements per side (profiling cases)")
     ap.add_argument("--no-extras", action="store_true", help="skip the as-listed and float64 comparison solves")
-    ap.add_argument("--prec", default="", choices=["", "FP64", "MIXED_FP32", "MIXED_BF16"],
+    ap.add_argument("--prec", default="", choices=["", "FP64", "MIXED_FP32", "MIXED_TF32", "MIXED_BF16"],
                     help="override the workload's precision (profiling cases)")
     ap.add_argument("--flux", default="upwind", choices=["upwind", "npc"],
                     help="transport workloads: numerical flux (npc: Eq. Ntaub, finite termination)")

@@ -321,13 +321,14 @@ ihdg_status device_iterate(ihdg_ctx* ctx, Plan* pl, const ihdg_options& o, const
       int v = std::atoi(cap);
       if (v > 0) m.max_grid = v;
     }
-    // bf16 inner sweeps run their local apply on the tensor cores (tcgen05) by default.
-    // IHDG_INNER_KERNEL selects a CUDA-core kernel instead: "tile" (register- or shared-
-    // memory-resident state) or "global" (global-memory state); "tc" keeps the default.
-    m.use_tc = o.prec == IHDG_MIXED_BF16 ? 1 : 0;
+    // Inner sweeps run their local apply on the tensor cores (tcgen05) by default for bf16,
+    // tf32, and float32 on 3D meshes (split tf32, three passes); float32 on 2D meshes uses the
+    // register kernel.  IHDG_INNER_KERNEL overrides: "tc" (tensor cores wherever the shape
+    // fits), "tile" (register- or shared-memory-resident CUDA-core kernels) or "global".
+    m.use_tc = (o.prec == IHDG_MIXED_BF16 || o.prec == IHDG_MIXED_TF32 || (o.prec == IHDG_MIXED_FP32 && pl->g.dim == 3)) ? 1 : 0;
     if (const char* ker = std::getenv("IHDG_INNER_KERNEL")) {
       m.no_tile = std::strcmp(ker, "global") == 0;
-      if (std::strcmp(ker, "tc") != 0) m.use_tc = 0;
+      m.use_tc = std::strcmp(ker, "tc") == 0 ? 1 : 0;
     }
     // IHDG_TILE_LPE=1 skips the register-resident 2D kernel (one element per thread instead)
     if (const char* lpe = std::getenv("IHDG_TILE_LPE")) m.tile_lpe = std::atoi(lpe) == 1 ? 1 : 4;

@@ -8,32 +8,19 @@
 #include <cmath>
 #include <cstdint>
 #include <type_traits>
+#include <cstring>
 #include <vector>
 
 #include "ihdg_common.cuh"
 #include "ihdg_dev.h"
 #include "ihdg_kernels.h"
 #include "ihdg_mixed.h"
+#include "ihdg_persist.cuh"
+#include "ihdg_tc.h"
 
 namespace ihdg {
 
 namespace {
-
-template <typename T> __device__ __forceinline__ float to_f(T v);
-template <> __device__ __forceinline__ float to_f<float>(float v) { return v; }
-template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
-template <typename T> __device__ __forceinline__ T from_f(float v);
-template <> __device__ __forceinline__ float from_f<float>(float v) { return v; }
-template <> __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
-
-// Load through L2 (ld.global.cg): values other blocks wrote earlier in the same persistent
-// launch must not come from this SM's L1, which is not coherent with their writes.
-template <typename T> __device__ __forceinline__ float ldcg_f(const T* p);
-template <> __device__ __forceinline__ float ldcg_f<float>(const float* p) { return __ldcg(p); }
-template <> __device__ __forceinline__ float ldcg_f<__nv_bfloat16>(const __nv_bfloat16* p) {
-  const unsigned short b = __ldcg(reinterpret_cast<const unsigned short*>(p));
-  return __uint_as_float((unsigned)b << 16);
-}
 
 // gather from a low-precision array, widening to TA (through L2, see ldcg_f)
 template <int NF, int NLF, typename TL, typename TA, typename Out>
@@ -191,15 +178,6 @@ __global__ void __launch_bounds__(BS) k_inner_first(DevGeo g, OpsDev op, const d
   }
 }
 
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
-  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
 // Grid barrier plus sum of one double per block, for cooperative launches.  The arrival
 // counter only grows (cleared before the launch): barrier number b completes when it
 // reaches (b+1) * gridDim.x.  Thread 0 publishes the block's partial, arrives with a
@@ -240,39 +218,6 @@ __device__ double barrier_sum(double* part, unsigned* count, unsigned nb, double
   return *s_out;
 }
 
-// Lagged grid reduction for the register and tile kernels.  After sweep s every block
-// publishes its float partial in partf[(s & 1) * grid + block] and arrives at the barrier
-// (thread 0: release add, bounded acquire poll).  At the top of sweep s+1 every thread loads
-// its share of sweep s's partials together with its trace gathers; sum_partials then folds
-// them with a fixed tree (the same in every block) and thread 0 takes the loop decision.
-// Everything per thread is float32 (GB300's float64 latency would dominate a sweep).
-__device__ __forceinline__ void arrive_wait(float* partf, unsigned* count, unsigned nb, float mine, Ctrl* ctrl,
-                                            int* s_flag) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    partf[blockIdx.x] = mine;
-    red_release_add(count, 1u);
-    const unsigned target = nb * gridDim.x;
-    const long long t0 = clock64();
-    while (ld_acquire_u32(count) < target) {
-      if (clock64() - t0 > 2000000000LL) { atomicExch(&ctrl->timeout, 1); break; }
-    }
-    *s_flag = *(volatile int*)&ctrl->timeout;
-  }
-  __syncthreads();
-}
-
-template <int NT>
-__device__ __forceinline__ float sum_partials(float pv, float* wred) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) pv += __shfl_down_sync(0xffffffffu, pv, o);
-  if ((threadIdx.x & 31) == 0) wred[threadIdx.x >> 5] = pv;
-  __syncthreads();
-  float t = 0.f;
-  if (threadIdx.x == 0)
-    for (int w = 0; w < NT / 32; ++w) t += wred[w];
-  return t;   // valid in thread 0
-}
 
 // Persistent inner loop on the correction equation: e_{j+1} = r + L_E t(e_j), until the
 // step norm falls below inner_rtol * ||r||, inner_max sweeps, or the sweep budget.  One
@@ -741,370 +686,6 @@ __global__ void __launch_bounds__(512, 2) k_inner_reg(const DevGeo g, const TL* 
   }
 }
 
-// ---------------------------------------------------------------------------------------
-// Tensor-core local apply (tcgen05): persistent inner loop with bf16 operands and a float32
-// accumulator in tensor memory.  Per tile of 128 elements the GEMM
-//     D[128 x NP] = A[128 x KP] . B[NP x KP]^T,   A = gathered traces t, B = L_E (rows = exports)
-// runs as KP/16 tcgen05.mma.kind::f16 (M128 N NP K16) issued by one thread; operands sit in
-// shared memory in the K-major, no-swizzle core-matrix layout (8 rows x 16 bytes per core
-// matrix; cores adjacent along K are 128 B apart, 8-row groups are KP*16 B apart).  The
-// accumulator of each of the block's TC_G tiles occupies 32 columns of tensor memory allocated
-// for the whole launch; each warp reads its 32 lanes back (tcgen05.ld 32x32b) for the epilogue
-// e_{j+1} = r + D.  Every wait (mbarrier, grid barrier) is bounded; on expiry the kernel sets
-// ctrl->timeout, waits (bounded) for its MMAs, frees its tensor memory and returns.
-namespace tc {
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);   // version 1, no swizzle
-}
-// kind::f16 instruction descriptor: D f32, A and B bf16, both K-major, N and M encoded
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
-      "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-}
-__device__ __forceinline__ void commit(uint32_t mbar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-               "selp.u32 %0, 1, 0, p;\n\t}\n" : "=r"(ok) : "r"(mbar), "r"(parity) : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {   // bounded (~1 s)
-  const long long t0 = clock64();
-  while (!mbar_try(mbar, parity))
-    if (clock64() - t0 > 2000000000LL) return false;
-  return true;
-}
-__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void ld32(uint32_t taddr, float* d) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) d[i] = __uint_as_float(r[i]);
-}
-__device__ __forceinline__ void group_bar(int id) { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
-// OR of v over the 128 threads of named barrier `id` (also a barrier)
-__device__ __forceinline__ int group_or(int id, int v) {
-  int r;
-  asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.s32 p, %1, 0;\n\tbar.red.or.pred q, %2, 128, p;\n\t"
-               "selp.s32 %0, 1, 0, q;\n\t}\n" : "=r"(r) : "r"(v), "r"(id) : "memory");
-  return r;
-}
-}  // namespace tc
-
-constexpr int TC_G = 4;   // tiles in flight per block: one per 128-thread group
-
-// Shared memory of k_inner_tc: B, then one A tile per group (core-matrix layouts).
-template <int NF, int NLF, bool PER_AXIS>
-struct TcShape {
-  static constexpr int NIN = NF * NLF;
-  static constexpr int NEXP = PER_AXIS ? NF * (NLF / 2) : NF * NLF;
-  static constexpr int KP = (NIN + 15) / 16 * 16;    // K padded to the MMA's K step
-  static constexpr int NP = (NEXP + 15) / 16 * 16;   // N padded to a multiple of 16
-  static constexpr int ROWB = KP * 16;               // bytes per 8-row group (KP/8 core matrices)
-  static constexpr int BBYTES = NP / 8 * ROWB;
-  static constexpr int ABYTES = 128 / 8 * ROWB;
-  static constexpr int SMEM = BBYTES + TC_G * ABYTES;
-  static constexpr uint32_t TCOLS = TC_G * 32 <= 32 ? 32 : TC_G * 32 <= 64 ? 64 : TC_G * 32 <= 128 ? 128 : 256;
-  static constexpr bool OK = NP <= 32 && KP <= 64;
-};
-
-// Group gr of the block handles tiles blockIdx.x * TC_G + gr, + gridDim.x * TC_G, ...; the
-// assignment is the same in every sweep, so each thread always owns the same elements.  A
-// group gathers its tile's traces into its A buffer, one thread issues the MMAs into the
-// group's 32 tensor-memory columns, and while they run the group loads the residual and the
-// current corrections its epilogue needs.  Groups synchronise among themselves with named
-// barriers only, so the four tiles of a block overlap their latencies.
-template <int NF, int NLF, bool PER_AXIS>
-__global__ void __launch_bounds__(128 * TC_G, 1) k_inner_tc(const DevGeo g, const __nv_bfloat16* __restrict__ rlp,
-                                                           __nv_bfloat16* e0, __nv_bfloat16* e1, Ctrl* ctrl,
-                                                           double* partials, const __nv_bfloat16* __restrict__ Bg) {
-  using TL = __nv_bfloat16;
-  using S = TcShape<NF, NLF, PER_AXIS>;
-  constexpr int NT = 128 * TC_G, NIN = S::NIN, NEXP = S::NEXP, KP = S::KP, NP = S::NP, ROWB = S::ROWB;
-  static_assert(S::OK, "tile shape");
-  extern __shared__ __align__(1024) unsigned char tc_smem[];
-  __shared__ __align__(8) unsigned long long s_mbar[TC_G];
-  __shared__ uint32_t s_tmem;
-  __shared__ float wsum[NT / 32];
-  __shared__ int s_to, s_stop;
-  if (ctrl_done(ctrl) || *(volatile const int*)&ctrl->inner_done) return;
-  const int jj0 = *(volatile const int*)&ctrl->inner_iter;
-  const int iter0 = *(volatile const int*)&ctrl->iter;
-  const int lowp0 = *(volatile const int*)&ctrl->lowp_sweeps;
-  const int max_iters = ctrl->max_iters, inner_max = ctrl->inner_max;
-  const float limf = (float)(ctrl->inner_rtol * ctrl->rnorm);
-  const int tid = threadIdx.x, gr = tid >> 7, gt = tid & 127, wq = (tid >> 5) & 3;
-  unsigned char* sB = tc_smem;
-  unsigned char* sA = tc_smem + S::BBYTES + gr * S::ABYTES;
-  // set-up: tensor memory, one mbarrier per group, operator B
-  if (tid < 32) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(&s_tmem)),
-                 "r"(S::TCOLS) : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  if (tid < TC_G) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&s_mbar[tid])) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  {
-    const uint4* src = reinterpret_cast<const uint4*>(Bg);
-    uint4* dst = reinterpret_cast<uint4*>(sB);
-    for (int i = tid; i < S::BBYTES / 16; i += NT) dst[i] = src[i];
-  }
-  tc::fence_proxy_async();
-  tc::fence_before();
-  __syncthreads();
-  tc::fence_after();
-  const uint32_t tmem0 = s_tmem;
-  const uint32_t tcol = tmem0 + (uint32_t)(gr * 32);                 // this group's accumulator
-  const uint32_t tld = tcol + ((uint32_t)(wq * 32) << 16);            // this warp's 32 lanes of it
-  const uint32_t mbar = tc::smem_u32(&s_mbar[gr]);
-  const uint32_t aaddr = tc::smem_u32(sA), baddr = tc::smem_u32(sB);
-  constexpr uint32_t IDESC = tc::idesc_bf16(128, NP);
-  const int bar_id = 1 + gr;
-  uint32_t phase = 0;
-  const int ld = (int)g.ld, nel = (int)g.nel;
-  const int ntiles = (nel + 127) / 128;
-  const int tile0 = blockIdx.x * TC_G + gr, tstride = gridDim.x * TC_G;
-  unsigned* count = &ctrl->bar_count;
-  float* partf = reinterpret_cast<float*>(partials);
-  int failed = 0;
-  // a1: gather element (tile*128 + gt)'s traces into row gt of this group's A (bf16).  Every
-  // load is unconditional (rows past the mesh and faces on the boundary read a safe address
-  // and are masked afterwards), so all of them are in flight at once.  own[] keeps the
-  // element's current exports for the epilogue's step norm.
-  float own[NEXP];
-  auto gather_pack = [&](int tile, const TL* __restrict__ ec) {
-    const int K = tile * 128 + gt;
-    const bool valid = K < nel;
-    const int Kc = valid ? K : 0;
-    int c[3] = {0, 0, 0};
-    if (valid) coords(g, K, c);
-    const unsigned short* eb = reinterpret_cast<const unsigned short*>(ec);
-    int o1[NLF], o2[NLF];
-    bool u1[NLF], u2[NLF], z[NLF];
-#pragma unroll
-    for (int f = 0; f < NLF; ++f) {
-      const int kind = g.kind[f], a = f >> 1;
-      const bool bnd = valid && on_bnd(g, c, f);
-      const int os = PER_AXIS ? a * NF : f * NF;
-      const int ns = PER_AXIS ? a * NF : (f ^ 1) * NF;
-      const int Kn = Kc + ((f & 1) ? (int)g.stride[a] : -(int)g.stride[a]);
-      const bool nbr = valid && !bnd && (kind == FK_NBR_D || kind == FK_SUM_D);
-      if (PER_AXIS) {   // one source per face: own (outflow) or the neighbour's (inflow)
-        u1[f] = valid && (kind == FK_OWN_D || (kind == FK_NBR_D && !bnd));
-        o1[f] = (kind == FK_NBR_D && nbr) ? ns * ld + Kn : os * ld + Kc;
-        u2[f] = false;
-        o2[f] = 0;
-        z[f] = kind != FK_OWN_D;    // not an own row
-      } else {          // own + neighbour; on the boundary mirror (2 own) or zero
-        u1[f] = valid && (kind == FK_OWN_D || (kind == FK_SUM_D && (!bnd || g.bc_mirror)));
-        o1[f] = os * ld + Kc;
-        u2[f] = nbr || (valid && kind == FK_SUM_D && bnd && g.bc_mirror);
-        o2[f] = nbr ? ns * ld + Kn : os * ld + Kc;
-        z[f] = !(kind == FK_OWN_D || kind == FK_SUM_D);
-      }
-    }
-    unsigned short r1[NIN], r2[PER_AXIS ? 1 : NIN];
-#pragma unroll
-    for (int f = 0; f < NLF; ++f)
-#pragma unroll
-      for (int q = 0; q < NF; ++q) r1[f * NF + q] = __ldcg(eb + o1[f] + q * ld);
-    if constexpr (!PER_AXIS) {
-#pragma unroll
-      for (int f = 0; f < NLF; ++f)
-#pragma unroll
-        for (int q = 0; q < NF; ++q) r2[f * NF + q] = __ldcg(eb + o2[f] + q * ld);
-    }
-    float t[KP];
-#pragma unroll
-    for (int k = NIN; k < KP; ++k) t[k] = 0.f;
-#pragma unroll
-    for (int f = 0; f < NLF; ++f) {
-      const int os = PER_AXIS ? (f >> 1) * NF : f * NF;
-#pragma unroll
-      for (int q = 0; q < NF; ++q) {
-        const float x = u1[f] ? __uint_as_float((unsigned)r1[f * NF + q] << 16) : 0.f;
-        float v = x;
-        if constexpr (!PER_AXIS) v += u2[f] ? __uint_as_float((unsigned)r2[f * NF + q] << 16) : 0.f;
-        t[f * NF + q] = v;
-        // the own export row: read in full (also on the boundary) for the step norm
-        const float xo = __uint_as_float((unsigned)r1[f * NF + q] << 16);
-        if (PER_AXIS) { if (!z[f]) own[os + q] = valid ? xo : 0.f; }
-        else own[os + q] = (valid && !z[f]) ? xo : 0.f;
-      }
-    }
-#pragma unroll
-    for (int kc = 0; kc < KP / 8; ++kc) {
-      __align__(16) __nv_bfloat16 h[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) h[u] = __float2bfloat16_rn(t[kc * 8 + u]);
-      *reinterpret_cast<uint4*>(sA + (gt >> 3) * ROWB + kc * 128 + (gt & 7) * 16) = *reinterpret_cast<uint4*>(h);
-    }
-  };
-  for (int s = 0;; ++s) {
-    const TL* __restrict__ ec = ((jj0 + s) & 1) ? e1 : e0;
-    TL* __restrict__ en = ((jj0 + s) & 1) ? e0 : e1;
-    // previous sweep's partials, in flight together with the first tile's gathers
-    float pv = 0.f;
-    if (s > 0)
-      for (int i = tid; i < (int)gridDim.x; i += NT) pv += __ldcg(partf + ((s - 1) & 1) * gridDim.x + i);
-    if (tile0 < ntiles) gather_pack(tile0, ec);
-    // lagged loop decision (as in k_inner_reg)
-    {
-      const float tot = sum_partials<NT>(pv, wsum);
-      if (tid == 0) {
-        const float step = sqrtf(tot);
-        const bool budget = jj0 + s >= inner_max || iter0 + s >= max_iters;
-        const bool stop = budget || (s > 0 && (step <= limf || !(step == step) || isinf(step)));
-        s_stop = stop ? 1 : 0;
-        if (blockIdx.x == 0) {
-          ctrl->inner_iter = jj0 + s;
-          ctrl->iter = iter0 + s;
-          ctrl->lowp_sweeps = lowp0 + s;
-          if (s > 0) ctrl->inner_step = (double)step;
-          if (stop) ctrl->inner_done = 1;
-        }
-      }
-      __syncthreads();
-      if (s_stop) break;
-    }
-    float acc = 0.f;
-    for (int tile = tile0; tile < ntiles; tile += tstride) {
-      if (tile != tile0) gather_pack(tile, ec);
-      tc::fence_proxy_async();
-      tc::fence_before();
-      tc::group_bar(bar_id);
-      tc::fence_after();
-      // a3: D = A . B^T on the tensor cores
-      if (gt == 0) {
-#pragma unroll
-        for (int kk = 0; kk < KP / 16; ++kk)
-          tc::mma_bf16(tcol, tc::sdesc(aaddr + kk * 256, 128, ROWB), tc::sdesc(baddr + kk * 256, 128, ROWB), IDESC,
-                       kk > 0 ? 1u : 0u);
-        tc::commit(mbar);
-      }
-      __syncwarp();
-      // the epilogue's operands load while the MMAs run
-      const int K = tile * 128 + gt;
-      const bool valid = K < nel;
-      unsigned short rr[NEXP];
-      const unsigned short* rb = reinterpret_cast<const unsigned short*>(rlp);
-#pragma unroll
-      for (int e = 0; e < NEXP; ++e) rr[e] = rb[e * ld + (valid ? K : 0)];
-      // the group agrees on the outcome of the (bounded) wait, so all its threads take one path
-      const int ok = tc::mbar_wait(mbar, phase) ? 1 : 0;
-      const int bad = tc::group_or(bar_id, !ok);
-      phase ^= 1u;
-      if (bad) { failed = 1; break; }
-      tc::fence_after();
-      // a4: e_{j+1} = r + D from this warp's 32 accumulator lanes
-      float d[32];
-      tc::ld32(tld, d);
-      if (valid) {
-#pragma unroll
-        for (int e = 0; e < NEXP; ++e) {
-          if ((g.live >> e) & 1ull) {
-            const TL nv = from_f<TL>(__uint_as_float((unsigned)rr[e] << 16) + d[e]);
-            const float dl = to_f(nv) - own[e];
-            acc = fmaf(dl, dl, acc);
-            en[e * ld + K] = nv;
-          }
-        }
-      }
-    }
-    if (__syncthreads_or(failed)) {
-      if (tid == 0) atomicExch(&ctrl->timeout, 1);
-      break;
-    }
-    const float blk = sum_partials<NT>(acc, wsum);
-    arrive_wait(partf + (s & 1) * gridDim.x, count, (unsigned)(s + 1), blk, ctrl, &s_to);
-    if (s_to) break;
-  }
-  // release tensor memory on every path (a group whose MMA wait expired waits once more)
-  if (failed) tc::mbar_wait(mbar, phase ^ 1u);
-  tc::fence_before();
-  __syncthreads();
-  tc::fence_after();
-  if (tid < 32)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem0), "r"(S::TCOLS) : "memory");
-}
-
-// Launch the tensor-core inner kernel (bf16 storage).  B = L_E in the core-matrix layout is
-// built on the host and copied to the workspace once per solve.
-template <int NF, int NLF, bool PER_AXIS>
-cudaError_t launch_tc(MixedArgs& m, __nv_bfloat16* rl, __nv_bfloat16* e0, __nv_bfloat16* e1) {
-  using S = TcShape<NF, NLF, PER_AXIS>;
-  if constexpr (!S::OK) {
-    return cudaErrorNotSupported;
-  } else {
-    constexpr int NIN = S::NIN, NEXP = S::NEXP, KP = S::KP, NP = S::NP;
-    const LaunchArgs& a = m.base;
-    if (!m.LE32h || !m.dLT || a.g.n_exp != NEXP || (long long)a.g.ld * NEXP >= (1LL << 31)) return cudaErrorNotSupported;
-    static_assert((size_t)NP * KP * 2 <= 8192, "operator scratch");
-    auto k = k_inner_tc<NF, NLF, PER_AXIS>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, 128 * TC_G, S::SMEM);
-    if (e != cudaSuccess) return e;
-    if (per > (int)(512 / S::TCOLS)) per = (int)(512 / S::TCOLS);   // 512 tensor-memory columns per SM
-    if (per < 1) return cudaErrorNotSupported;
-    long long grid = (long long)per * sms;
-    const long long ntiles = (a.g.nel + 127) / 128;
-    const long long need = (ntiles + TC_G - 1) / TC_G;
-    if (grid > need) grid = need;
-    if (grid > m.max_grid) grid = m.max_grid;
-    if (grid > m.slots / 2) return cudaErrorNotSupported;
-    if (m.lt_kind != 2) {
-      // B[n][k] = L_E[n][k] (bf16): byte (n/8)*KP*16 + (k/8)*128 + (n%8)*16 + (k%8)*2
-      std::vector<__nv_bfloat16> hb((size_t)NP * KP, __float2bfloat16_rn(0.f));
-      for (int n = 0; n < NEXP; ++n)
-        for (int kk = 0; kk < NIN; ++kk) {
-          const size_t off = (size_t)(n / 8) * KP * 8 + (kk / 8) * 64 + (n % 8) * 8 + (kk % 8);
-          hb[off] = __float2bfloat16_rn(m.LE32h[n * NIN + kk]);
-        }
-      e = cudaMemcpyAsync(m.dLT, hb.data(), hb.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice, a.stream);
-      if (e != cudaSuccess) return e;
-      m.lt_kind = 2;
-    }
-    e = cudaMemsetAsync(&a.ctrl->bar_count, 0, sizeof(unsigned), a.stream);
-    if (e != cudaSuccess) return e;
-    DevGeo gg = a.g;
-    const __nv_bfloat16* rlc = rl;
-    Ctrl* ct = a.ctrl;
-    double* pp = a.partials;
-    const __nv_bfloat16* bp = reinterpret_cast<const __nv_bfloat16*>(m.dLT);
-    void* args[] = {&gg, &rlc, &e0, &e1, &ct, &pp, &bp};
-    e = cudaLaunchCooperativeKernel((const void*)k, dim3((unsigned)grid), dim3(128 * TC_G), args, S::SMEM, a.stream);
-    if (e != cudaSuccess) return e;
-    return cudaGetLastError();
-  }
-}
-
 // Launch k_inner_reg with the most lanes per element whose grid is co-resident.
 template <int NF, bool PER_AXIS, typename TL, int LPE>
 cudaError_t launch_reg_v(MixedArgs& m, TL* rl, TL* e0, TL* e1) {
@@ -1195,11 +776,21 @@ struct MixedRunner {
         }
         k<<<grid_for(a.g.nel), BS, smem, a.stream>>>(a.g, a.op, m.r64, e0, a.ctrl, a.partials, a.res_hist);
       } else {
-        if constexpr (std::is_same<TL, __nv_bfloat16>::value) {
-          if (m.use_tc) {
-            cudaError_t ce = a.g.per_axis ? launch_tc<NF, NLF, true>(m, rl, e0, e1) : launch_tc<NF, NLF, false>(m, rl, e0, e1);
-            if (ce != cudaErrorNotSupported) return ce;
+        if (m.use_tc) {
+          cudaError_t ce;
+          if constexpr (std::is_same<TL, __nv_bfloat16>::value) {
+            ce = a.g.per_axis ? launch_tc<NF, NLF, true, TC_BF16>(m, rl, e0, e1)
+                              : launch_tc<NF, NLF, false, TC_BF16>(m, rl, e0, e1);
+          } else if (m.prec == IHDG_MIXED_TF32) {
+            ce = a.g.per_axis ? launch_tc<NF, NLF, true, TC_TF32>(m, rl, e0, e1)
+                              : launch_tc<NF, NLF, false, TC_TF32>(m, rl, e0, e1);
+          } else {
+            ce = a.g.per_axis ? launch_tc<NF, NLF, true, TC_TF32X4>(m, rl, e0, e1)
+                              : launch_tc<NF, NLF, false, TC_TF32X4>(m, rl, e0, e1);
           }
+          if (ce != cudaErrorNotSupported) return ce;
+          // shapes the tensor-core kernel does not take (n_in > 64 or n_exp > 32) fall through
+          // to the CUDA-core kernels in full float32
         }
         if (!m.no_tile) {
           if constexpr (NLF == 4) {
@@ -1279,7 +870,7 @@ MixedLayout mixed_layout(const DevGeo& g, int prec) {
   L.e0 = one;
   L.e1 = 2 * one;
   L.lt = 3 * one;
-  L.total = 3 * one + 8192;   // + transposed operator of the register kernel
+  L.total = 3 * one + MIXED_LT_BYTES;   // + the register kernel's or the tensor-core kernel's operator
   return L;
 }
 
@@ -1300,7 +891,6 @@ ihdg_status run_mixed(Ctrl* hc, MixedArgs& m, const ihdg_options& o, const doubl
     if (e != cudaSuccess) { err = std::string(where) + ": " + cudaGetErrorString(e); return false; }
     return true;
   };
-  if (o.prec == IHDG_MIXED_TF32) { err = "TF32 inner sweeps need the tensor-core kernel, not built in this library"; return IHDG_ERR_UNSUPPORTED; }
   if (!ck(cudaMemcpyAsync(hc, a.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, a.stream), "ctrl readback") ||
       !ck(cudaStreamSynchronize(a.stream), "first sweep"))
     return IHDG_ERR_CUDA;

@@ -14,6 +14,8 @@
 
 namespace ihdg {
 
+constexpr size_t MIXED_LT_BYTES = 16384;   // operator scratch in the mixed workspace
+
 struct MixedLayout {
   size_t rlp, e0, e1, lt, total;   // byte offsets inside the mixed region
   int lp_bytes;                // bytes per low-precision value

@@ -339,13 +339,19 @@ def test_mixed_inner_kernel_variants(ctx, monkeypatch, kernel, grid, lpe):
     assert rel(u_b, u_a) < 1e-9
 
 
-@pytest.mark.parametrize("case,grid,kernel", [("t3d_p1", "", "tc"), ("t3d_p2", "", "tc"), ("cd2d_p3", "", "tc"),
-                                              ("t2d_p2", "1", "tc"), ("t3d_p1", "", "tile"), ("cd2d_p3", "", "tile")])
-def test_mixed_bf16_tensor_core_inner(ctx, monkeypatch, case, grid, kernel):
-    """bf16 inner sweeps with the local apply on the tensor cores (the default, kernel "tc":
-    tcgen05 MMA over tiles of 128 elements, operands bf16, accumulation float32) reach the
-    oracle's float64 solution at the mixed bar, and so do bf16 sweeps on the CUDA cores
-    (kernel "tile").  The meshes leave a ragged last tile
+TC_CASES = [("t3d_p1", "", "tc", "MIXED_BF16"), ("t3d_p2", "", "tc", "MIXED_BF16"), ("cd2d_p3", "", "tc", "MIXED_BF16"),
+            ("t2d_p2", "1", "tc", "MIXED_BF16"), ("t3d_p1", "", "tile", "MIXED_BF16"), ("cd2d_p3", "", "tile", "MIXED_BF16"),
+            ("t3d_p1", "", "tc", "MIXED_FP32"), ("t3d_p2", "", "tc", "MIXED_FP32"), ("cd2d_p3", "", "tc", "MIXED_FP32"),
+            ("t2d_p2", "1", "tc", "MIXED_FP32"), ("t3d_p2", "", "tc", "MIXED_TF32"), ("cd2d_p3", "", "tc", "MIXED_TF32")]
+
+
+@pytest.mark.parametrize("case,grid,kernel,prec_name", TC_CASES)
+def test_mixed_tensor_core_inner(ctx, monkeypatch, case, grid, kernel, prec_name):
+    """Inner sweeps with the local apply on the tensor cores (kernel "tc": tcgen05 MMA over
+    tiles of 128 elements with a float32 accumulator in tensor memory) reach the oracle's
+    float64 solution at the mixed bar, for every operand mode: bf16 (kind::f16), float32 as
+    four tf32 passes on hi/lo splits, and one tf32 pass; and so do bf16 sweeps on the CUDA
+    cores (kernel "tile").  The meshes leave a ragged last tile
     (element counts not multiples of 128) and some of a block's four tile groups without a
     tile; a grid of one block makes its groups loop over several tiles per sweep."""
     ihdg = ih()
@@ -377,7 +383,7 @@ def test_mixed_bf16_tensor_core_inner(ctx, monkeypatch, case, grid, kernel):
     monkeypatch.setenv("IHDG_INNER_KERNEL", kernel)
     if grid:
         monkeypatch.setenv("IHDG_PERSISTENT_GRID", grid)
-    u, tr, res = ctx.solve(mesh, co, f, g, ihdg.make_options(tol, prec=ihdg.MIXED_BF16, max_iters=20000))
+    u, tr, res = ctx.solve(mesh, co, f, g, ihdg.make_options(tol, prec=getattr(ihdg, prec_name), max_iters=20000))
     assert res.status == ihdg.OK, res.as_dict()
     assert res.lowp_sweeps > 0
     assert rel(u, U.reshape(pr.mesh.nel, -1)) < 1e-6
