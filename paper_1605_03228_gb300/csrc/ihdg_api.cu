@@ -201,7 +201,7 @@ ihdg_status get_plan(ihdg_ctx* ctx, const ihdg_mesh& m, const ihdg_coeffs& co, P
 
 // Workspace layout of one solve (offsets in bytes from the workspace base).
 struct Layout {
-  size_t ctrl, partials, res_hist, F, ring, qnext, mixed, total;
+  size_t ctrl, partials, res_hist, F, V, ring, qnext, mixed, total;
   MixedLayout mx;
 };
 
@@ -214,6 +214,7 @@ Layout layout_for(const DevGeo& g, const ihdg_options& o, bool swe) {
   L.partials = take(sizeof(double) * (size_t)partials_needed(g.nel));
   L.res_hist = take(sizeof(double) * (size_t)(maxit + 2));
   L.F = take(sizeof(double) * (size_t)g.n_exp * g.ld);
+  L.V = take(sizeof(double) * (size_t)g.nvol * g.ld);
   L.ring = take(3 * sizeof(double) * (size_t)g.n_exp * g.ld);
   L.qnext = swe ? take(sizeof(double) * (size_t)g.nvol * g.nel) : 0;
   if (o.prec != IHDG_FP64) {
@@ -257,6 +258,7 @@ ihdg_status device_iterate(ihdg_ctx* ctx, Plan* pl, const ihdg_options& o, const
   a.src = src;
   a.u0 = u0;
   a.F = reinterpret_cast<double*>(ws + L.F);
+  a.V = reinterpret_cast<double*>(ws + L.V);
   a.ring = reinterpret_cast<double*>(ws + L.ring);
   a.ring_stride = (long long)pl->g.n_exp * pl->g.ld;
   a.ctrl = reinterpret_cast<Ctrl*>(ws + L.ctrl);

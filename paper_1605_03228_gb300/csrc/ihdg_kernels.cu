@@ -56,11 +56,14 @@ __device__ __forceinline__ void volume_source(const DevGeo& g, const OpsDev& op,
 
 // ---------------------------------------------------------------------------------------
 // a2 (once per solve / per time step): export forcing F = R A^{-1} b.
-__global__ void __launch_bounds__(BS) k_forcing(DevGeo g, OpsDev op, SrcDev src, double* __restrict__ F) {
+__global__ void __launch_bounds__(BS) k_forcing(DevGeo g, OpsDev op, SrcDev src, double* __restrict__ F,
+                                                double* __restrict__ V) {
   const long long K = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (K >= g.nel) return;
   int c[3];
   coords(g, K, c);
+  // the volume source A^{-1} b, kept for the first sweep's residual and the reconstruction
+  volume_source(g, op, src, K, c, [&](int i, double v) { V[(long long)i * g.ld + K] = v; });
   for (int e = 0; e < g.n_exp; ++e) {
     if (!row_live(g, e, g.nf)) continue;
     double v = 0.0;
@@ -102,9 +105,10 @@ __global__ void __launch_bounds__(BS) k_export0(DevGeo g, OpsDev op, const doubl
 // First sweep (k = 0 -> 1): E^1 = F + L_E t(E^0), and the residual ||u^1 - u^0|| on the
 // full volume state (u^0 is the initial guess, not a previous local solve).
 template <int NF, int NLF>
-__global__ void __launch_bounds__(BS) k_first(DevGeo g, OpsDev op, SrcDev src, const double* __restrict__ u0,
-                                              const double* __restrict__ F, double* ring, long long ring_stride,
-                                              Ctrl* ctrl, double* partials, double* res_hist) {
+__global__ void __launch_bounds__(BS) k_first(DevGeo g, OpsDev op, const double* __restrict__ V,
+                                              const double* __restrict__ u0, const double* __restrict__ F,
+                                              double* ring, long long ring_stride, Ctrl* ctrl, double* partials,
+                                              double* res_hist) {
   constexpr int NIN = NF * NLF;
   __shared__ double ws[BS / 32];
   extern __shared__ double sdyn[];
@@ -112,27 +116,32 @@ __global__ void __launch_bounds__(BS) k_first(DevGeo g, OpsDev op, SrcDev src, c
   const long long K = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   double acc = 0.0;
   if (K < g.nel) {
-    int c[3];
-    coords(g, K, c);
-    double t[NIN];
-    gather<NF, NLF, double, double>(g, ring, K, c, [&](int s, double v) { t[s] = v; });
     double* E1 = ring + ring_stride;
-    for (int e = 0; e < g.n_exp; ++e) {
-      if (!row_live(g, e, NF)) continue;
-      double v = F[(long long)e * g.ld + K];
-      const double* row = op.LE + (long long)e * NIN;
+    if (u0) {
+      int c[3];
+      coords(g, K, c);
+      double t[NIN];
+      gather<NF, NLF, double, double>(g, ring, K, c, [&](int s, double v) { t[s] = v; });
+      for (int e = 0; e < g.n_exp; ++e) {
+        if (!row_live(g, e, NF)) continue;
+        double v = F[(long long)e * g.ld + K];
+        const double* row = op.LE + (long long)e * NIN;
 #pragma unroll
-      for (int s = 0; s < NIN; ++s) v += row[s] * t[s];
-      E1[(long long)e * g.ld + K] = v;
-    }
-    volume_source(g, op, src, K, c, [&](int i, double v) { du[i * BS] = v; });
-    for (int i = 0; i < g.nvol; ++i) {
-      double v = du[i * BS];
-      const double* row = op.Lvol + (long long)i * NIN;
+        for (int s = 0; s < NIN; ++s) v += row[s] * t[s];
+        E1[(long long)e * g.ld + K] = v;
+      }
+      for (int i = 0; i < g.nvol; ++i) {
+        double v = V[(long long)i * g.ld + K];
+        const double* row = op.Lvol + (long long)i * NIN;
 #pragma unroll
-      for (int s = 0; s < NIN; ++s) v += row[s] * t[s];
-      if (u0) v -= u0[K * g.nvol + i];
-      du[i * BS] = v;
+        for (int s = 0; s < NIN; ++s) v += row[s] * t[s];
+        du[i * BS] = v - u0[K * g.nvol + i];
+      }
+    } else {
+      // u^0 = 0: E^0 = 0, so t(E^0) = 0, E^1 = F and u^1 - u^0 = A^{-1} b
+      for (int e = 0; e < g.n_exp; ++e)
+        if (row_live(g, e, NF)) E1[(long long)e * g.ld + K] = F[(long long)e * g.ld + K];
+      for (int i = 0; i < g.nvol; ++i) du[i * BS] = V[(long long)i * g.ld + K];
     }
     // ||du||^2 in the stopping norm: sum over components c of w_c du_c^T M du_c
     for (int comp = 0; comp < g.nvol / g.nb; ++comp) {
@@ -220,8 +229,9 @@ __global__ void __launch_bounds__(BS) k_sweep64(DevGeo g, OpsDev op, const doubl
 
 // Volume reconstruction u = A^{-1} b + L_vol t(E) (+ L_vol t(E2) when E2 is given).
 template <int NF, int NLF>
-__global__ void __launch_bounds__(BS) k_reconstruct(DevGeo g, OpsDev op, SrcDev src, const double* __restrict__ E,
-                                                    const double* __restrict__ E2, double* __restrict__ u) {
+__global__ void __launch_bounds__(BS) k_reconstruct(DevGeo g, OpsDev op, const double* __restrict__ V,
+                                                    const double* __restrict__ E, const double* __restrict__ E2,
+                                                    double* __restrict__ u) {
   constexpr int NIN = NF * NLF;
   const long long K = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (K >= g.nel) return;
@@ -230,12 +240,13 @@ __global__ void __launch_bounds__(BS) k_reconstruct(DevGeo g, OpsDev op, SrcDev 
   double t[NIN];
   gather<NF, NLF, double, double>(g, E, K, c, [&](int s, double v) { t[s] = v; });
   if (E2) gather<NF, NLF, double, double>(g, E2, K, c, [&](int s, double v) { t[s] += v; });
-  volume_source(g, op, src, K, c, [&](int i, double v) {
+  for (int i = 0; i < g.nvol; ++i) {
+    double v = V[(long long)i * g.ld + K];
     const double* row = op.Lvol + (long long)i * NIN;
 #pragma unroll
     for (int s = 0; s < NIN; ++s) v += row[s] * t[s];
     u[K * g.nvol + i] = v;
-  });
+  }
 }
 
 // Trace output on every face node (Algorithm 1 step 3 applied to the final iterate):
@@ -345,7 +356,7 @@ cudaError_t run_first_t(const LaunchArgs& a) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  kern<<<grid_for(a.g.nel), BS, smem, a.stream>>>(a.g, a.op, a.src, a.u0, a.F, a.ring, a.ring_stride, a.ctrl, a.partials, a.res_hist);
+  kern<<<grid_for(a.g.nel), BS, smem, a.stream>>>(a.g, a.op, a.V, a.u0, a.F, a.ring, a.ring_stride, a.ctrl, a.partials, a.res_hist);
   return cudaGetLastError();
 }
 
@@ -365,7 +376,7 @@ cudaError_t run_sweep64_t(const LaunchArgs& a, int count) {
 
 template <int NF, int NLF>
 cudaError_t run_reconstruct_t(const LaunchArgs& a, const double* E, const double* E2, double* u) {
-  k_reconstruct<NF, NLF><<<grid_for(a.g.nel), BS, 0, a.stream>>>(a.g, a.op, a.src, E, E2, u);
+  k_reconstruct<NF, NLF><<<grid_for(a.g.nel), BS, 0, a.stream>>>(a.g, a.op, a.V, E, E2, u);
   return cudaGetLastError();
 }
 
@@ -405,7 +416,7 @@ cudaError_t launch_ctrl_init(const LaunchArgs& a, double tol, double div, int ma
   return cudaGetLastError();
 }
 cudaError_t launch_forcing(const LaunchArgs& a) {
-  k_forcing<<<grid_for(a.g.nel), BS, 0, a.stream>>>(a.g, a.op, a.src, a.F);
+  k_forcing<<<grid_for(a.g.nel), BS, 0, a.stream>>>(a.g, a.op, a.src, a.F, a.V);
   return cudaGetLastError();
 }
 cudaError_t launch_export0(const LaunchArgs& a, const double* u0, double* E0) {

@@ -39,6 +39,7 @@ struct LaunchArgs {
   SrcDev src;
   const double* u0;       // initial guess (volume layout) or nullptr
   double* F;              // export forcing, n_exp x ld
+  double* V;              // volume source A^{-1} b, nvol x ld (computed once with F)
   double* ring;           // three export slots of n_exp x ld
   long long ring_stride;  // = n_exp * ld
   Ctrl* ctrl;
