@@ -332,6 +332,9 @@ ihdg_status device_iterate(ihdg_ctx* ctx, Plan* pl, const ihdg_options& o, const
       m.no_tile = std::strcmp(ker, "global") == 0;
       m.use_tc = std::strcmp(ker, "tc") == 0 ? 1 : 0;
     }
+    // IHDG_REG_NT=512: register kernel with two 512-thread blocks per SM instead of one
+    // 1024-thread block (twice the grid-barrier arrivals; 1.4% slower on the headline mesh)
+    if (const char* nt = std::getenv("IHDG_REG_NT")) m.reg_nt = std::atoi(nt) == 512 ? 512 : 1024;
     // IHDG_TILE_LPE=1 skips the register-resident 2D kernel (one element per thread instead)
     if (const char* lpe = std::getenv("IHDG_TILE_LPE")) m.tile_lpe = std::atoi(lpe) == 1 ? 1 : 4;
     m.LE32h = pl->le32.data();

@@ -538,11 +538,11 @@ cudaError_t launch_tile_v(MixedArgs& m, TL* rl, TL* e0, TL* e1) {
 // The operator sits in shared memory transposed and padded, LT[k][rowblock * RW + r], so one
 // 128-bit load gives a lane the coefficients of trace k for 4 rows of one block.  Every thread
 // owns one (element, lane) pair for the whole launch.
-template <int NF, bool PER_AXIS, typename TL, int LPE>
-__global__ void __launch_bounds__(512, 2) k_inner_reg(const DevGeo g, const TL* __restrict__ rlp, TL* e0, TL* e1,
-                                                      Ctrl* ctrl, double* partials, const float* __restrict__ LTg,
-                                                      const int epb) {
-  constexpr int NT = 512, NIN = 4 * NF, FPL = 4 / LPE;
+template <int NF, bool PER_AXIS, typename TL, int LPE, int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT) k_inner_reg(const DevGeo g, const TL* __restrict__ rlp, TL* e0,
+                                                             TL* e1, Ctrl* ctrl, double* partials,
+                                                             const float* __restrict__ LTg, const int epb) {
+  constexpr int NIN = 4 * NF, FPL = 4 / LPE;
   constexpr int RW = (NF + 3) & ~3;          // padded row-block width
   constexpr int NRB = 4;                     // row blocks stored (faces; axes use the first 2)
   __shared__ __align__(16) float LT[NIN * NRB * RW];
@@ -686,17 +686,18 @@ __global__ void __launch_bounds__(512, 2) k_inner_reg(const DevGeo g, const TL* 
   }
 }
 
-// Launch k_inner_reg with the most lanes per element whose grid is co-resident.
-template <int NF, bool PER_AXIS, typename TL, int LPE>
+// Launch k_inner_reg with the most lanes per element whose grid is co-resident (NT threads
+// per block: 512, two blocks per SM, or 1024, one block per SM and half the barrier arrivals).
+template <int NF, bool PER_AXIS, typename TL, int LPE, int NT>
 cudaError_t launch_reg_v(MixedArgs& m, TL* rl, TL* e0, TL* e1) {
   constexpr int NIN = 4 * NF, RW = (NF + 3) & ~3, NRB = 4;
   const LaunchArgs& a = m.base;
   if (a.g.dim != 2 || !m.LE32h || !m.dLT || (long long)a.g.ld * a.g.n_exp >= (1LL << 31)) return cudaErrorNotSupported;
-  auto k = k_inner_reg<NF, PER_AXIS, TL, LPE>;
+  auto k = k_inner_reg<NF, PER_AXIS, TL, LPE, NT>;
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, 512, 0);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, NT, 0);
   if (e != cudaSuccess) return e;
   // the grid is a multiple of the SM count with the elements spread evenly over it
   long long grid = (long long)per * sms;
@@ -704,7 +705,7 @@ cudaError_t launch_reg_v(MixedArgs& m, TL* rl, TL* e0, TL* e1) {
   if (grid > small) grid = small;
   if (grid > m.max_grid) grid = m.max_grid;
   const long long epb = (a.g.nel + grid - 1) / grid;
-  if (epb > 512 / LPE) return cudaErrorNotSupported;
+  if (epb > NT / LPE) return cudaErrorNotSupported;
   grid = (a.g.nel + epb - 1) / epb;
   if (grid > m.slots / 2) return cudaErrorNotSupported;
   // transposed, padded operator: LT[k][rb * RW + r] = L_E[rb * NF + r][k]
@@ -727,16 +728,21 @@ cudaError_t launch_reg_v(MixedArgs& m, TL* rl, TL* e0, TL* e1) {
   const float* ltp = m.dLT;
   int ep = (int)epb;
   void* args[] = {&gg, &rlc, &e0, &e1, &ct, &pp, &ltp, &ep};
-  e = cudaLaunchCooperativeKernel((const void*)k, dim3((unsigned)grid), dim3(512), args, 0, a.stream);
+  e = cudaLaunchCooperativeKernel((const void*)k, dim3((unsigned)grid), dim3(NT), args, 0, a.stream);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
 template <int NF, bool PER_AXIS, typename TL>
 cudaError_t launch_reg(MixedArgs& m, TL* rl, TL* e0, TL* e1) {
-  cudaError_t e = launch_reg_v<NF, PER_AXIS, TL, 4>(m, rl, e0, e1);
+  cudaError_t e;
+  if (m.reg_nt == 1024) {
+    e = launch_reg_v<NF, PER_AXIS, TL, 2, 1024>(m, rl, e0, e1);
+    if (e != cudaErrorNotSupported) return e;
+  }
+  e = launch_reg_v<NF, PER_AXIS, TL, 4, 512>(m, rl, e0, e1);
   if (e != cudaErrorNotSupported) return e;
-  return launch_reg_v<NF, PER_AXIS, TL, 2>(m, rl, e0, e1);
+  return launch_reg_v<NF, PER_AXIS, TL, 2, 512>(m, rl, e0, e1);
 }
 
 // Tile kernel shape: one element per thread (default) or, with IHDG_TILE_LPE=4 on 2D

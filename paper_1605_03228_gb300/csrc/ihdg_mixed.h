@@ -33,6 +33,7 @@ struct MixedArgs {
   int slots = 0;            // length of the partials array (64-bit slots)
   int tile_lpe = 4;         // 4: 2D meshes use the register-resident kernel when it fits
   float* dLT = nullptr;     // device scratch for the transposed operator (register kernel)
+  int reg_nt = 1024;        // register kernel block size (1024: one block per SM; or 512)
   int use_tc = 0;           // bf16: local apply on the tensor cores (tcgen05)
   int lt_kind = 0;          // operator layout now in dLT: 0 none, 1 register kernel, 2 tensor-core B
   const float* LE32h = nullptr;  // host copy of the float32 operator (n_exp x n_in)

@@ -315,7 +315,7 @@ def test_mixed_transport3d(ctx, prec_name):
 
 
 @pytest.mark.parametrize("kernel,grid,lpe", [("tile", "2", "1"), ("tile", "", "1"), ("global", "2", "1"),
-                                             ("global", "", "1")])
+                                             ("global", "", "1"), ("tile", "", "4")])
 def test_mixed_inner_kernel_variants(ctx, monkeypatch, kernel, grid, lpe):
     """The inner loop's kernel variants (register-resident 4-lanes-per-element state, the
     default on 2D meshes; block-resident tile state; global state) and grid
@@ -334,6 +334,8 @@ def test_mixed_inner_kernel_variants(ctx, monkeypatch, kernel, grid, lpe):
         monkeypatch.setenv("IHDG_PERSISTENT_GRID", grid)
     monkeypatch.setenv("IHDG_INNER_KERNEL", kernel)
     monkeypatch.setenv("IHDG_TILE_LPE", lpe)
+    if lpe == "4":
+        monkeypatch.setenv("IHDG_REG_NT", "512")      # the register kernel's two-blocks-per-SM shape
     u_b, _, rb = ctx.solve(mesh, co, f, g, opts)
     assert ra.status == rb.status == ihdg.OK
     assert rel(u_b, u_a) < 1e-9
