@@ -61,6 +61,8 @@ def parse():
                     help="override the workload's precision (profiling cases)")
     ap.add_argument("--flux", default="upwind", choices=["upwind", "npc"],
                     help="transport workloads: numerical flux (npc: Eq. Ntaub, finite termination)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="mixed: skip ihdg_autotune (inner kernel and stopping ratio by the automatic rules)")
     ap.add_argument("--inner-max", type=int, default=0, help="mixed: inner sweeps per outer step (profiling cases)")
     ap.add_argument("--inner-rtol", type=float, default=0.0, help="mixed: inner stopping ratio (profiling cases)")
     ap.add_argument("--requests", type=int, default=400, help="serving: number of requests (the listed stream is 10000)")
@@ -94,6 +96,10 @@ def workload_spec(name):
                     desc="2D linearized shallow water 512x512 p=2 Phi=1 walls, Gaussian bump + 1% seeded noise, "
                          "backward Euler 100 steps at dt=h/((p+1)(p+2)) (listed dt=1e-3 diverges, rho~6)")
     raise ValueError(name)
+
+
+def swe_spec(spec):
+    return spec["pde"] == "swe"
 
 
 def make_problem(ih, spec, kappa=None):
@@ -380,6 +386,17 @@ def main():
     a, b = inputs(ih, spec, mesh, co)
     swe = spec["pde"] == "swe"
     opts = ih.make_options(spec["tol"], max_iters=4000, prec=prec, inner_max=args.inner_max, inner_rtol=args.inner_rtol)
+    # mixed precision: the library's autotuner picks the inner kernel and stopping ratio by
+    # timing complete solves (outside the timed region; the choice is cached in the context)
+    tune = None
+    if (prec != ih.FP64 and not swe_spec(spec) and not args.no_autotune and args.inner_rtol == 0.0
+            and not os.environ.get("IHDG_INNER_KERNEL")):
+        tuned, tune_ms = ctx.autotune(mesh, co, *inputs(ih, spec, mesh, co), opts)
+        opts = tuned
+        names = {ih.KERNEL_TENSOR_CORES: "tensor cores (tcgen05)", ih.KERNEL_CUDA_CORES: "CUDA cores",
+                 ih.KERNEL_GLOBAL: "CUDA cores, global state"}
+        tune = {"by": "ihdg_autotune", "inner_kernel": names.get(tuned.inner_kernel, "auto"),
+                "inner_rtol": tuned.inner_rtol, "best_solve_ms": tune_ms}
     nws = ih.workspace_bytes(mesh, co, opts)
     ws = torch.empty(nws + 256, dtype=torch.uint8, device=dev)
     wsp = (ws.data_ptr() + 255) // 256 * 256
@@ -534,7 +551,8 @@ def main():
             "vs_baseline": None, "dtype": dtype, "data": "synthetic",
             "config": {"workload": spec["desc"], "n_el": sz.n_el, "nvol": sz.nvol, "sweeps_per_step": float(np.mean(sweeps)),
                        "status": status, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                       "l2": "flushed between steps (512 MB write, outside the timed events)"},
+                       "l2": "flushed between steps (512 MB write, outside the timed events)",
+                       "inner": tune if tune else "automatic rules"},
             "e2e": e2e, "gpu_launches": int(np.sum(launches)), "roofline": roof, "clocks": clk,
             "cpu_baseline": base}
     line.update(extras)

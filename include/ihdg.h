@@ -78,6 +78,18 @@ typedef enum {
   IHDG_MIXED_BF16 = 3
 } ihdg_precision;
 
+/* Inner-sweep kernel of the mixed path.  AUTO: tensor cores for bf16, tf32 and 3D float32,
+ * the register-resident CUDA-core kernel for 2D float32 (or what ihdg_autotune chose for the
+ * problem on this context).  TENSOR_CORES: tcgen05 local apply wherever the element shape
+ * fits (n_in <= 64, n_exp <= 32), else the CUDA-core kernels.  CUDA_CORES: register- or
+ * shared-memory-resident state.  GLOBAL: global-memory state (any size). */
+typedef enum {
+  IHDG_KERNEL_AUTO = 0,
+  IHDG_KERNEL_TENSOR_CORES = 1,
+  IHDG_KERNEL_CUDA_CORES = 2,
+  IHDG_KERNEL_GLOBAL = 3
+} ihdg_inner_kernel;
+
 /* Uniform box mesh of n[0] x n[1] (x n[2]) congruent elements on [lo, hi], order p. */
 typedef struct {
   int dim;          /* 2 or 3 (shallow water: 2) */
@@ -107,11 +119,12 @@ typedef struct {
                               <= 0 disables the check (default 1e6 when == 0) */
   int inner_max;           /* mixed: inner sweeps per outer step cap (0 = automatic) */
   double inner_rtol;       /* mixed: inner stop when step norm <= inner_rtol * ||r||
-                              (0 = auto: 2e-3 for float32, 0.2 for bf16) */
+                              (0 = auto: 2e-3 float32, 1e-2 tf32, 0.2 bf16, or the autotuned value) */
   const double* u0;        /* optional initial guess, volume layout (host for ihdg_solve,
                               device for ihdg_solve_device); NULL = zero */
   int profile;             /* 1: time every sweep launch with CUDA events (one launch per
                               host check, so slower overall) and report the averages below */
+  ihdg_inner_kernel inner_kernel;   /* mixed: inner-sweep kernel (AUTO = 0) */
 } ihdg_options;
 
 typedef struct {
@@ -207,6 +220,19 @@ ihdg_status ihdg_solve_device_static(ihdg_ctx* ctx, const ihdg_mesh* mesh, const
                                      const double* d_f_qp, const double* d_g_qp,
                                      const ihdg_options* opts, double* d_u_out, double* d_trace_out,
                                      void* stream, ihdg_result* res);
+
+/* Autotuner of the mixed path: times complete solves of the caller's problem (host inputs as
+ * for ihdg_solve) for every inner-kernel choice and a ladder of inner stopping ratios
+ * (float32/tf32: 5e-4 .. 1e-2; bf16: 2e-2 .. 0.3), keeps the fastest that converges, and
+ * returns it in *tuned (a copy of *opts with inner_kernel and inner_rtol set) with its device
+ * time in *best_ms.  The choice is also cached in the context for this problem shape (pde,
+ * flux, dim, n, p, precision): later solves on the context whose inner_kernel is AUTO and
+ * inner_rtol 0 use it.  Serving slots do not (their results must not depend on timing).
+ * FP64 options have nothing to tune: *tuned = *opts.  Errors as for ihdg_solve; a problem
+ * that converges under no candidate returns IHDG_NOT_CONVERGED. */
+ihdg_status ihdg_autotune(ihdg_ctx* ctx, const ihdg_mesh* mesh, const ihdg_coeffs* coeffs,
+                          const double* f_qp, const double* g_qp, const ihdg_options* opts,
+                          ihdg_options* tuned, double* best_ms);
 
 /* Linearized shallow water (Section 3, Eq. localSolverDD), walls on the whole boundary:
  * advance q (in/out, [n_el][3][(p+1)^2] volume layout (phi, u, v), host) by nsteps

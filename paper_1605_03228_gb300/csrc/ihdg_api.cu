@@ -12,6 +12,7 @@
 #include <condition_variable>
 #include <deque>
 #include <memory>
+#include <map>
 #include <mutex>
 #include <thread>
 #include <unordered_map>
@@ -61,6 +62,8 @@ struct ihdg_ctx {
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
   Ctrl* h_ctrl = nullptr;   // pinned readback of the loop state
+  // ihdg_autotune's choices: problem shape -> (inner kernel, inner stopping ratio)
+  std::map<std::string, std::pair<int, double>> tuned;
 };
 
 namespace {
@@ -235,7 +238,7 @@ ihdg_options defaults(const ihdg_options* o) {
   // floor spends sweeps without progress, while the float64 outer step that follows restores
   // full accuracy.  Measured on the conv.-diff., 3D transport and shallow-water workloads
   // (total sweeps to tol fell by 20-75% against 1e-4 / 1e-2).
-  if (r.inner_rtol <= 0.0) r.inner_rtol = r.prec == IHDG_MIXED_BF16 ? 0.2 : (r.prec == IHDG_MIXED_TF32 ? 1e-2 : 2e-3);
+  if (r.inner_rtol < 0.0) r.inner_rtol = 0.0;   // 0: automatic, resolved with the inner kernel
   return r;
 }
 
@@ -243,7 +246,17 @@ ihdg_status check_opts(ihdg_ctx* ctx, const ihdg_options& o) {
   if (!(o.tol >= 0.0) || !std::isfinite(o.tol)) return fail(ctx, IHDG_ERR_INVALID, "opts.tol must be finite and >= 0");
   if (o.prec < IHDG_FP64 || o.prec > IHDG_MIXED_BF16) return fail(ctx, IHDG_ERR_INVALID, "opts.prec is not a known precision");
   if (o.max_iters > 100000000) return fail(ctx, IHDG_ERR_INVALID, "opts.max_iters too large");
+  if (o.inner_kernel < IHDG_KERNEL_AUTO || o.inner_kernel > IHDG_KERNEL_GLOBAL)
+    return fail(ctx, IHDG_ERR_INVALID, "opts.inner_kernel is not a known kernel");
   return IHDG_OK;
+}
+
+// Key of ihdg_autotune's cache: the problem shape and precision.
+std::string tune_key(const ihdg_mesh& m, const ihdg_coeffs& c, int prec) {
+  std::ostringstream os;
+  os << c.pde << '/' << c.flux << '/' << m.dim << '/' << m.n[0] << 'x' << m.n[1] << 'x' << (m.dim == 3 ? m.n[2] : 1)
+     << "/p" << m.p << "/prec" << prec;
+  return os.str();
 }
 
 // One solve of the iteration on the device: forcing, first sweep, sweep loop (float64 or
@@ -275,7 +288,22 @@ ihdg_status device_iterate(ihdg_ctx* ctx, Plan* pl, const ihdg_options& o, const
     CK(cudaEventCreate(&tm.a), "cudaEventCreate");
     CK(cudaEventCreate(&tm.b), "cudaEventCreate");
   }
-  CK(launch_ctrl_init(a, o.tol, o.diverge_factor, o.max_iters, o.inner_max, o.inner_rtol), "ctrl init");
+  // inner kernel and stopping ratio of the mixed path: the caller's, else the autotuned ones
+  // for this problem shape, else the automatic rules
+  int inner_kernel = o.inner_kernel;
+  double inner_rtol = o.inner_rtol;
+  if (o.prec != IHDG_FP64 && inner_kernel == IHDG_KERNEL_AUTO && inner_rtol <= 0.0) {
+    auto it = ctx->tuned.find(tune_key(pl->mesh, pl->co, o.prec));
+    if (it != ctx->tuned.end()) {
+      inner_kernel = it->second.first;
+      inner_rtol = it->second.second;
+    }
+  }
+  // Inner stop well above the low-precision rounding floor: an inner loop pushed towards its
+  // floor spends sweeps without progress, while the float64 outer step that follows restores
+  // full accuracy (measured on the conv.-diff., 3D transport and shallow-water workloads).
+  if (inner_rtol <= 0.0) inner_rtol = o.prec == IHDG_MIXED_BF16 ? 0.2 : (o.prec == IHDG_MIXED_TF32 ? 1e-2 : 2e-3);
+  CK(launch_ctrl_init(a, o.tol, o.diverge_factor, o.max_iters, o.inner_max, inner_rtol), "ctrl init");
   CK(launch_forcing(a), "forcing kernel");
   CK(launch_export0(a, u0, a.ring), "initial export kernel");
   CK(launch_first(a), "first sweep kernel");
@@ -328,7 +356,10 @@ ihdg_status device_iterate(ihdg_ctx* ctx, Plan* pl, const ihdg_options& o, const
     // register kernel.  IHDG_INNER_KERNEL overrides: "tc" (tensor cores wherever the shape
     // fits), "tile" (register- or shared-memory-resident CUDA-core kernels) or "global".
     m.use_tc = (o.prec == IHDG_MIXED_BF16 || o.prec == IHDG_MIXED_TF32 || (o.prec == IHDG_MIXED_FP32 && pl->g.dim == 3)) ? 1 : 0;
-    if (const char* ker = std::getenv("IHDG_INNER_KERNEL")) {
+    if (inner_kernel != IHDG_KERNEL_AUTO) {
+      m.use_tc = inner_kernel == IHDG_KERNEL_TENSOR_CORES ? 1 : 0;
+      m.no_tile = inner_kernel == IHDG_KERNEL_GLOBAL ? 1 : 0;
+    } else if (const char* ker = std::getenv("IHDG_INNER_KERNEL")) {
       m.no_tile = std::strcmp(ker, "global") == 0;
       m.use_tc = std::strcmp(ker, "tc") == 0 ? 1 : 0;
     }
@@ -537,6 +568,75 @@ ihdg_status ihdg_solve(ihdg_ctx* ctx, const ihdg_mesh* mesh, const ihdg_coeffs* 
   if (st != IHDG_OK) return st;
   CK(cudaMemcpy(u_out, d_u, sizeof(double) * sz.n_el * sz.nvol, cudaMemcpyDeviceToHost), "copy u");
   if (trace_out) CK(cudaMemcpy(trace_out, d_t, sizeof(double) * sz.n_face * sz.nface_nodes, cudaMemcpyDeviceToHost), "copy trace");
+  return IHDG_OK;
+}
+
+ihdg_status ihdg_autotune(ihdg_ctx* ctx, const ihdg_mesh* mesh, const ihdg_coeffs* co, const double* f_qp,
+                          const double* g_qp, const ihdg_options* opts, ihdg_options* tuned, double* best_ms) {
+  if (!ctx) return IHDG_ERR_INVALID;
+  if (!mesh || !co || !f_qp || !g_qp || !tuned) return fail(ctx, IHDG_ERR_INVALID, "null argument");
+  if (co->pde == IHDG_SWE) return fail(ctx, IHDG_ERR_INVALID, "shallow water is solved by ihdg_swe_steps*");
+  ihdg_sizes sz;
+  ihdg_status st = ihdg_problem_sizes(mesh, co, &sz);
+  if (st != IHDG_OK) {
+    std::string err;
+    validate(*mesh, co, err);
+    return fail(ctx, st, err.empty() ? "invalid problem" : err);
+  }
+  ihdg_options o = defaults(opts);
+  st = check_opts(ctx, o);
+  if (st != IHDG_OK) return st;
+  *tuned = opts ? *opts : o;
+  if (best_ms) *best_ms = 0.0;
+  if (o.prec == IHDG_FP64) return IHDG_OK;
+  size_t ws = 0;
+  ihdg_workspace_bytes(mesh, co, &o, &ws);
+  size_t bf = align256(sizeof(double) * sz.n_el * sz.nqv), bg = align256(sizeof(double) * sz.n_bface * sz.nqf);
+  size_t bu = align256(sizeof(double) * sz.n_el * sz.nvol);
+  size_t bu0 = o.u0 ? bu : 0;
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  st = ensure_scratch(ctx, bf + bg + bu + bu0 + ws);
+  if (st != IHDG_OK) return st;
+  char* s = static_cast<char*>(ctx->scratch);
+  double* d_f = reinterpret_cast<double*>(s);
+  double* d_g = reinterpret_cast<double*>(s + bf);
+  double* d_u = reinterpret_cast<double*>(s + bf + bg);
+  double* d_u0 = o.u0 ? reinterpret_cast<double*>(s + bf + bg + bu) : nullptr;
+  char* d_ws = s + bf + bg + bu + bu0;
+  CK(cudaMemcpy(d_f, f_qp, sizeof(double) * sz.n_el * sz.nqv, cudaMemcpyHostToDevice), "copy f");
+  CK(cudaMemcpy(d_g, g_qp, sizeof(double) * sz.n_bface * sz.nqf, cudaMemcpyHostToDevice), "copy g");
+  if (o.u0) CK(cudaMemcpy(d_u0, o.u0, sizeof(double) * sz.n_el * sz.nvol, cudaMemcpyHostToDevice), "copy u0");
+  static const double ladder32[] = {5e-4, 1e-3, 2e-3, 5e-3, 1e-2};
+  static const double ladder16[] = {2e-2, 5e-2, 0.1, 0.2, 0.3};
+  const double* ladder = o.prec == IHDG_MIXED_BF16 ? ladder16 : ladder32;
+  const int kernels[] = {IHDG_KERNEL_TENSOR_CORES, IHDG_KERNEL_CUDA_CORES};
+  double best = 1e300;
+  int best_k = IHDG_KERNEL_AUTO;
+  double best_r = 0.0;
+  for (int pass = 0; pass < 2; ++pass)          // pass 0 warms every kernel up (module loads)
+    for (int k : kernels)
+      for (int i = 0; i < (pass == 0 ? 1 : 5); ++i) {
+        ihdg_options oc = o;
+        oc.u0 = d_u0;
+        oc.inner_kernel = static_cast<ihdg_inner_kernel>(k);
+        oc.inner_rtol = ladder[pass == 0 ? 2 : i];
+        oc.profile = 0;
+        ihdg_result r{};
+        st = ihdg_solve_device(ctx, mesh, co, d_f, d_g, &oc, d_u, nullptr, d_ws, ws, nullptr, &r);
+        if (st == IHDG_ERR_CUDA || st == IHDG_ERR_TIMEOUT || st == IHDG_ERR_NOMEM) return st;
+        if (pass == 0 || st != IHDG_OK || r.status != IHDG_OK) continue;
+        if (r.solve_ms < best) {
+          best = r.solve_ms;
+          best_k = k;
+          best_r = oc.inner_rtol;
+        }
+      }
+  if (best_k == IHDG_KERNEL_AUTO) return fail(ctx, IHDG_NOT_CONVERGED, "no candidate converged");
+  ctx->tuned[tune_key(*mesh, *co, o.prec)] = {best_k, best_r};
+  tuned->inner_kernel = static_cast<ihdg_inner_kernel>(best_k);
+  tuned->inner_rtol = best_r;
+  if (best_ms) *best_ms = best;
+  ctx->err.clear();
   return IHDG_OK;
 }
 

@@ -17,6 +17,7 @@ STATUS_NAMES = {0: "OK", 1: "ERR_INVALID", 2: "ERR_NOMEM", 3: "ERR_CUDA", 4: "NO
                 6: "ERR_BUSY", 7: "ERR_TIMEOUT", 8: "ERR_UNSUPPORTED"}
 TRANSPORT, CONVDIFF, SWE = 0, 1, 2
 FLUX_UPWIND, FLUX_NPC = 0, 1
+KERNEL_AUTO, KERNEL_TENSOR_CORES, KERNEL_CUDA_CORES, KERNEL_GLOBAL = 0, 1, 2, 3
 FP64, MIXED_FP32, MIXED_TF32, MIXED_BF16 = 0, 1, 2, 3
 
 
@@ -34,7 +35,8 @@ class Coeffs(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iters", ctypes.c_int), ("prec", ctypes.c_int),
                 ("diverge_factor", ctypes.c_double), ("inner_max", ctypes.c_int),
-                ("inner_rtol", ctypes.c_double), ("u0", ctypes.c_void_p), ("profile", ctypes.c_int)]
+                ("inner_rtol", ctypes.c_double), ("u0", ctypes.c_void_p), ("profile", ctypes.c_int),
+                ("inner_kernel", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
@@ -94,6 +96,7 @@ def load(build_if_missing=True):
     L.ihdg_swe_steps_device.argtypes = [VP, P(Mesh), P(Coeffs), VP, I, P(Options), P(I), VP, SZ, VP, P(Result)]
     L.ihdg_host_operator.argtypes = [P(Mesh), P(Coeffs), I, P(I), P(I), dp]
     L.ihdg_solve_device_static.argtypes = [VP, P(Mesh), P(Coeffs), VP, VP, P(Options), VP, VP, VP, P(Result)]
+    L.ihdg_autotune.argtypes = [VP, P(Mesh), P(Coeffs), dp, dp, P(Options), P(Options), dp]
     L.ihdg_server_start.argtypes = [VP, SZ, I]
     L.ihdg_server_stop.argtypes = [VP]
     L.ihdg_submit.argtypes = [VP, P(Mesh), P(Coeffs), dp, dp, P(Options), P(ctypes.c_longlong)]
@@ -130,8 +133,9 @@ def make_coeffs(pde, beta=(0.0, 0.0, 0.0), kappa=0.0, nu=0.0, Phi=0.0, coriolis_
 
 
 def make_options(tol, max_iters=2000, prec=FP64, diverge_factor=0.0, inner_max=0, inner_rtol=0.0, u0=None,
-                 profile=0):
+                 profile=0, inner_kernel=0):
     o = Options()
+    o.inner_kernel = inner_kernel
     o.tol, o.max_iters, o.prec, o.diverge_factor = tol, max_iters, prec, diverge_factor
     o.inner_max, o.inner_rtol = inner_max, inner_rtol
     o.u0 = u0
@@ -243,6 +247,17 @@ class Context:
                                ctypes.byref(opts), _dptr(u), _dptr(tr), ctypes.byref(res))
         self._check(st, "ihdg_solve")
         return u, tr, res
+
+    def autotune(self, mesh, coeffs, f_qp, g_qp, opts):
+        """ihdg_autotune: returns (tuned Options, device time of the fastest solve in ms)."""
+        f = np.ascontiguousarray(f_qp, dtype=np.float64)
+        g = np.ascontiguousarray(g_qp, dtype=np.float64)
+        tuned = Options()
+        best = ctypes.c_double(0.0)
+        st = self.L.ihdg_autotune(self.h, ctypes.byref(mesh), ctypes.byref(coeffs), _dptr(f), _dptr(g),
+                                  ctypes.byref(opts), ctypes.byref(tuned), ctypes.byref(best))
+        self._check(st, "ihdg_autotune")
+        return tuned, best.value
 
     def solve_device(self, mesh, coeffs, d_f, d_g, opts, d_u, d_tr, d_ws, ws_bytes, stream=0):
         """Device-pointer solve (integer pointers).  Returns Result."""

@@ -487,3 +487,31 @@ def test_full_size_transport3d_sampled(ctx):
                               lambda X: W.transport3d_forcing(X, b), W.transport3d_exact)
     got = np.array([u[c[0] + 64 * (c[1] + 64 * c[2])] for c in centers])
     assert rel(got, ref) < 1e-10
+
+
+# ------------------------------------------------------------------------------ autotuner
+def test_autotune_choice_converges_and_is_cached(ctx):
+    """ihdg_autotune times complete solves over the inner-kernel choices and a ladder of inner
+    stopping ratios and returns the fastest.  Its options reach the oracle's solution at the
+    mixed bar, and a later solve with automatic options on the same context uses the cached
+    choice (bitwise the same result as passing the tuned options).  FP64 has nothing to tune."""
+    ihdg = ih()
+    n, p, kappa = (40, 36), 3, 1e-4
+    mesh = ihdg.make_mesh(2, n, p)
+    co = ihdg.make_coeffs(ihdg.CONVDIFF, beta=(1.0, 1.0), kappa=kappa)
+    vol, bnd = ihdg.quadrature_points(mesh, co)
+    f, g = W.convdiff_forcing(vol, kappa), W.convdiff_exact(bnd)
+    opts = ihdg.make_options(1e-8, prec=ihdg.MIXED_FP32, max_iters=20000)
+    tuned, best_ms = ctx.autotune(mesh, co, f, g, opts)
+    assert tuned.inner_kernel in (ihdg.KERNEL_TENSOR_CORES, ihdg.KERNEL_CUDA_CORES)
+    assert tuned.inner_rtol > 0 and best_ms > 0
+    assert tuned.prec == ihdg.MIXED_FP32 and tuned.tol == opts.tol
+    u_t, _, r_t = ctx.solve(mesh, co, f, g, tuned)
+    u_a, _, r_a = ctx.solve(mesh, co, f, g, opts)
+    assert r_t.status == r_a.status == ihdg.OK
+    assert r_a.iterations == r_t.iterations and np.array_equal(u_a, u_t)
+    om = BoxMesh(2, n)
+    U, T, K, r, st = ConvDiff(Discretisation(om, p), np.array([1.0, 1.0]), kappa).iterate(f, g, 1e-8, max_iters=20000)
+    assert rel(u_t, U.reshape(om.nel, -1)) < 1e-6
+    t64, ms64 = ctx.autotune(mesh, co, f, g, ihdg.make_options(1e-8))
+    assert t64.prec == ihdg.FP64 and t64.inner_kernel == ihdg.KERNEL_AUTO and ms64 == 0.0
