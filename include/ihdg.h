@@ -135,8 +135,10 @@ typedef struct {
   ihdg_status status;
   double setup_ms;         /* host operator build + uploads (0 when cached) */
   double solve_ms;         /* device time of the sweep loop and reconstruction */
-  double fp64_sweep_ms;    /* profile: mean device time of one float64 sweep launch */
-  double lowp_sweep_ms;    /* profile: mean device time of one low-precision sweep launch */
+  double fp64_sweep_ms;    /* profile: mean device time of one float64 launch (plain sweep;
+                              mixed: outer sweep or residual check) */
+  double lowp_sweep_ms;    /* profile: device time of the persistent low-precision inner
+                              loop per sweep it ran */
   int fp64_launches;       /* profile: float64 sweep launches timed */
   int lowp_launches;       /* profile: low-precision sweep launches timed */
   int kernel_launches;     /* CUDA kernels this call launched (including sweeps that found

@@ -928,7 +928,9 @@ ihdg_status run_mixed(Ctrl* hc, MixedArgs& m, const ihdg_options& o, const doubl
     return true;
   };
   for (int outer = 0; outer < 1000000; ++outer) {
-    if (!launch(0, has_e, true) || !launch(1, 0, false)) return IHDG_ERR_CUDA;
+    // the residual kernel (float64 norm of t(r), plus one low-precision sweep) is timed with
+    // the float64 launches, so the low-precision figure is the persistent inner loop's alone
+    if (!launch(0, has_e, true) || !launch(1, 0, true)) return IHDG_ERR_CUDA;
     has_e = 1;
     // the persistent inner kernel runs until the inner loop stops (it returns at once when
     // the residual check above already ended the solve)
