@@ -98,6 +98,20 @@ def workload_spec(name):
     raise ValueError(name)
 
 
+def aggregate(ms, units, dist, device):
+    """Whole-job figures of a replicas run (one process per GPU, no data exchange): the
+    slowest rank's time per step (MAX over ranks) and the units all ranks processed per step
+    (SUM).  Without a process group they are this process's own."""
+    if dist is None:
+        return ms, units
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def swe_spec(spec):
     return spec["pde"] == "swe"
 
@@ -440,13 +454,8 @@ def main():
         launches.append(r.kernel_launches)
     barrier()
     clk = clocks.stop()
-    ms = float(np.mean(times))
-    if dist is not None:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    per_step_updates = sz.n_el * sz.nvol * float(np.mean(sweeps))
-    value = world * per_step_updates / (ms * 1e-3)
+    ms, job_updates = aggregate(float(np.mean(times)), sz.n_el * sz.nvol * float(np.mean(sweeps)), dist, dev)
+    value = job_updates / (ms * 1e-3)
     status = ih.STATUS_NAMES[r.status]
 
     # roofline of the dominant kernel: one profiled solve (events around every sweep launch)
