@@ -228,7 +228,6 @@ template <int NF, int NLF, typename TL>
 __global__ void __launch_bounds__(PBS) k_inner_persist(DevGeo g, OpsDev op, const TL* __restrict__ rlp, TL* e0,
                                                        TL* e1, Ctrl* ctrl, double* partials) {
   constexpr int NIN = NF * NLF;
-  __shared__ double ws[PBS / 32];
   __shared__ double s_tot;
   __shared__ int s_to, s_stop;
   __shared__ float wsum_p[PBS / 32];

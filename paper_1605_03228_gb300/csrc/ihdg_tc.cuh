@@ -29,7 +29,7 @@ namespace {
 // thread; operands sit in shared memory in the K-major, no-swizzle core-matrix layout (8 rows
 // x 16 bytes per core matrix; cores adjacent along K are 128 B apart, 8-row groups are
 // KP/(16/element size) x 128 B apart).  The
-// accumulator of each of the block's TC_G tiles occupies 32 columns of tensor memory allocated
+// accumulator of each of the block's G tiles occupies 32 columns of tensor memory allocated
 // for the whole launch; each warp reads its 32 lanes back (tcgen05.ld 32x32b) for the epilogue
 // e_{j+1} = r + D.  Every wait (mbarrier, grid barrier) is bounded; on expiry the kernel sets
 // ctrl->timeout, waits (bounded) for its MMAs, frees its tensor memory and returns.
@@ -410,7 +410,7 @@ cudaError_t launch_tc(MixedArgs& m, void* rlv, void* e0v, void* e1v) {
   if constexpr (!S::OK) {
     return cudaErrorNotSupported;
   } else {
-    constexpr int NIN = S::NIN, NEXP = S::NEXP, KP = S::KP, NP = S::NP, EPC = S::EPC, G = S::G;
+    constexpr int NIN = S::NIN, NEXP = S::NEXP, EPC = S::EPC, G = S::G;
     const LaunchArgs& a = m.base;
     if (!m.LE32h || !m.dLT || a.g.n_exp != NEXP || (long long)a.g.ld * NEXP >= (1LL << 31)) return cudaErrorNotSupported;
     static_assert((size_t)S::NSPLIT * S::BBYTES <= MIXED_LT_BYTES, "operator scratch");
