@@ -109,6 +109,11 @@ typedef struct {
   double dt;            /* shallow water backward-Euler step, > 0 */
   ihdg_flux flux;       /* transport: IHDG_FLUX_UPWIND (0, the default) or IHDG_FLUX_NPC;
                            other PDEs: must be IHDG_FLUX_UPWIND (else IHDG_ERR_UNSUPPORTED) */
+  double tau_gamma;     /* convection-diffusion stabilisation: 0 = the upwind tau^+- =
+                           (alpha - beta.n^+-)/2 (the default); > 0 = the mesh-dependent
+                           tau = tau_gamma (p+1)(p+2)/h on both sides of every face, h the
+                           element size along the face normal, which the paper takes for the
+                           diffusion-dominated limit (Section 4.2); other PDEs: must be 0 */
 } ihdg_coeffs;
 
 typedef struct {

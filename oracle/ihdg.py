@@ -377,15 +377,34 @@ class ConvDiff(Problem):
     """Convection-diffusion in first-order form (Section 4.1):
         kappa^{-1} sigma + grad u = 0,  div sigma + beta.grad u + nu u = f,
     unknowns ordered (sigma_1, ..., sigma_d, u).  Local equations (ErrorDDMCD1/2) with the
-    forcing and the trace u_hat^k = ([[sigma.n]] + [[beta.n u]] + [[tau u]]) / (tau^+ + tau^-),
+    forcing and the trace u_hat^k = ([[sigma.n]] + [[beta.n u]] + [[tau u]]) / (tau^+ + tau^-)
+    (from the conservation condition), with the upwind stabilisation
     tau^+- = (alpha - beta.n^+-)/2, alpha = sqrt((beta.n)^2 + 4).  Dirichlet u_hat = g.
+    tau_gamma > 0 selects the mesh-dependent stabilisation the paper takes for the elliptic
+    limit (Section 4.2): tau = tau_gamma (p+1)(p+2)/h on both sides of every face, h the
+    element size along the face normal.
     """
 
-    def __init__(self, disc, beta, kappa, nu=0.0):
+    def __init__(self, disc, beta, kappa, nu=0.0, tau_gamma=None):
         self.nc = disc.d + 1
         self.beta = np.asarray(beta, dtype=np.float64)[: disc.d]
         self.kappa, self.nu = float(kappa), float(nu)
+        self.tau_gamma = None if not tau_gamma else float(tau_gamma)
         super().__init__(disc)
+
+    def tau_mesh(self, a):
+        """Section 4.2: tau = gamma (p+1)(p+2)/h on faces normal to axis a."""
+        p = self.disc.p
+        return self.tau_gamma * (p + 1) * (p + 2) / float(self.mesh.h[a])
+
+    def side_taus(self, b, a):
+        """(tau on the left element's side, on the right element's side) of faces normal to
+        axis a, where b = beta.n of the left element (its outward normal is +e_a)."""
+        if self.tau_gamma:
+            t = self.tau_mesh(a)
+            return t + 0.0 * b, t + 0.0 * b
+        al = np.sqrt(b * b + 4.0)
+        return 0.5 * (al - b), 0.5 * (al + b)
 
     def bn(self, f):
         return float(self.disc.normal[f] @ self.beta)
@@ -394,6 +413,8 @@ class ConvDiff(Problem):
         return np.sqrt(self.bn(f) ** 2 + 4.0)
 
     def tau(self, f):
+        if self.tau_gamma:
+            return self.tau_mesh(f // 2)
         return 0.5 * (self.alpha(f) - self.bn(f))
 
     def local_matrix(self):
@@ -441,14 +462,15 @@ class ConvDiff(Problem):
         m, d = self.mesh, self.disc.d
         vals = self.face_side_values(U, range(self.nc))
         b = self.beta[m.face_axis][:, None]          # beta . n^- with n^- = +e_a (left element)
-        al = np.sqrt(b * b + 4.0)
+        tL, tR = np.zeros_like(b), np.zeros_like(b)
         sL = np.zeros((m.nface, self.disc.nqf))
         sR = np.zeros_like(sL)
         for a in range(d):
             sel = m.face_axis == a
             sL[sel], sR[sel] = vals[a][0][sel], vals[a][1][sel]
+            tL[sel], tR[sel] = self.side_taus(b[sel], a)
         uL, uR = vals[d]
-        T = (sL - sR + 0.5 * (al + b) * uL + 0.5 * (al - b) * uR) / al
+        T = (sL - sR + (tL + b) * uL + (tR - b) * uR) / (tL + tR)
         T[m.bface_ids] = g_qp
         return T
 
@@ -459,13 +481,13 @@ class ConvDiff(Problem):
         """[[sigma.n + beta.n u + tau(u - u_hat)]] = 0 inside; u_hat = g on the boundary."""
         m, d = self.mesh, self.disc.d
         b = self.beta[m.face_axis][:, None]
-        al = np.sqrt(b * b + 4.0)
-        tL, tR = 0.5 * (al - b), 0.5 * (al + b)
+        tL, tR = np.zeros_like(b), np.zeros_like(b)
         sL = np.zeros_like(T)
         sR = np.zeros_like(T)
         for a in range(d):
             sel = m.face_axis == a
             sL[sel], sR[sel] = vals[a][0][sel], vals[a][1][sel]
+            tL[sel], tR[sel] = self.side_taus(b[sel], a)
         uL, uR = vals[d]
         out = (sL - sR) + b * uL - b * uR + tL * (uL - T) + tR * (uR - T)
         gfull = np.zeros_like(T)

@@ -214,6 +214,8 @@ ihdg_status validate(const ihdg_mesh& m, const ihdg_coeffs* co, std::string& err
     if (!std::isfinite(co->beta[a])) { err = "coeffs.beta must be finite"; return IHDG_ERR_INVALID; }
   if (co->flux != IHDG_FLUX_UPWIND && co->flux != IHDG_FLUX_NPC) { err = "coeffs.flux is not a known flux"; return IHDG_ERR_INVALID; }
   if (co->flux == IHDG_FLUX_NPC && co->pde != IHDG_TRANSPORT) { err = "the NPC flux is defined for transport only"; return IHDG_ERR_UNSUPPORTED; }
+  if (!(co->tau_gamma >= 0.0) || !std::isfinite(co->tau_gamma)) { err = "coeffs.tau_gamma must be finite and >= 0"; return IHDG_ERR_INVALID; }
+  if (co->tau_gamma > 0.0 && co->pde != IHDG_CONVDIFF) { err = "the mesh-dependent stabilisation is for convection-diffusion"; return IHDG_ERR_UNSUPPORTED; }
   if (co->pde == IHDG_CONVDIFF) {
     if (!(co->kappa > 0) || !std::isfinite(co->kappa)) { err = "coeffs.kappa must be > 0"; return IHDG_ERR_INVALID; }
     if (!(co->nu >= 0) || !std::isfinite(co->nu)) { err = "coeffs.nu must be >= 0"; return IHDG_ERR_INVALID; }
@@ -521,20 +523,31 @@ ihdg_status build_ops(const ihdg_mesh& m, const ihdg_coeffs& co, Ops& o, std::st
     }
     add_vol(M, iu, iu, co.nu);
     R.assign((size_t)o.n_exp * nvol, 0.0);
-    for (int a = 0; a < d; ++a) o.alpha_axis[a] = std::sqrt(co.beta[a] * co.beta[a] + 4.0);
+    // Stabilisation: upwind tau^+- = (alpha - beta.n^+-)/2, alpha = sqrt((beta.n)^2 + 4), so
+    // tau^+ + tau^- = alpha; or the mesh-dependent tau = gamma (p+1)(p+2)/h_a on both sides
+    // (Section 4.2), so tau^+ + tau^- = 2 tau.  The conservation condition gives
+    // u_hat = (h^- + h^+)/(tau^+ + tau^-) with the export h = sigma.n + (tau + beta.n) u.
+    auto tau_of = [&](int f, double bn) {
+      if (co.tau_gamma > 0) return co.tau_gamma * (m.p + 1) * (m.p + 2) / ((m.hi[f / 2] - m.lo[f / 2]) / m.n[f / 2]);
+      return 0.5 * (std::sqrt(bn * bn + 4.0) - bn);
+    };
+    for (int a = 0; a < d; ++a) {
+      const double ba = co.beta[a];
+      o.alpha_axis[a] = tau_of(2 * a, -ba) + tau_of(2 * a + 1, ba);   // tau^- + tau^+ on axis a
+    }
     for (int f = 0; f < nlf; ++f) {
       int a = f / 2;
       double n = nsign(f), bn = n * co.beta[a];
-      double al = std::sqrt(bn * bn + 4.0), tau = 0.5 * (al - bn);
-      o.in_scale[f] = 1.0 / al;
+      const double tau = tau_of(f, bn), tsum = o.alpha_axis[a];
+      o.in_scale[f] = 1.0 / tsum;
       add_face_mass(f, iu, a, n);            // <sigma.n, v>
       add_face_mass(f, iu, iu, bn + tau);    // <(beta.n + tau) u, v>
-      add_G(f, a, -n, true, 1.0 / al);       // -<u_hat, w.n>   (u_hat = (h^- + h^+)/alpha)
-      add_G(f, iu, tau, true, 1.0 / al);     // <tau u_hat, v>
+      add_G(f, a, -n, true, 1.0 / tsum);     // -<u_hat, w.n>   (u_hat = (h^- + h^+)/(tau^+ + tau^-))
+      add_G(f, iu, tau, true, 1.0 / tsum);   // <tau u_hat, v>
       for (int j = 0; j < nf; ++j) {
         int node = fvol[f * nf + j];
-        R[(size_t)(f * nf + j) * nvol + a * nb + node] = n;                   // sigma.n
-        R[(size_t)(f * nf + j) * nvol + iu * nb + node] = 0.5 * (al + bn);    // (alpha + beta.n)/2 u
+        R[(size_t)(f * nf + j) * nvol + a * nb + node] = n;           // sigma.n
+        R[(size_t)(f * nf + j) * nvol + iu * nb + node] = tau + bn;   // (tau + beta.n) u
       }
     }
     for (int i = 0; i < nb * nb; ++i) o.Mn[(size_t)(iu * nb + i / nb) * nvol + iu * nb + (i % nb)] = M[i];

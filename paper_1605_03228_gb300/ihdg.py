@@ -29,7 +29,8 @@ class Mesh(ctypes.Structure):
 class Coeffs(ctypes.Structure):
     _fields_ = [("pde", ctypes.c_int), ("beta", ctypes.c_double * 3), ("kappa", ctypes.c_double),
                 ("nu", ctypes.c_double), ("Phi", ctypes.c_double), ("coriolis_f", ctypes.c_double),
-                ("friction", ctypes.c_double), ("dt", ctypes.c_double), ("flux", ctypes.c_int)]
+                ("friction", ctypes.c_double), ("dt", ctypes.c_double), ("flux", ctypes.c_int),
+                ("tau_gamma", ctypes.c_double)]
 
 
 class Options(ctypes.Structure):
@@ -122,10 +123,11 @@ def make_mesh(dim, n, p, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0)):
 
 
 def make_coeffs(pde, beta=(0.0, 0.0, 0.0), kappa=0.0, nu=0.0, Phi=0.0, coriolis_f=0.0, friction=0.0, dt=0.0,
-                flux=0):
+                flux=0, tau_gamma=0.0):
     c = Coeffs()
     c.pde = pde
     c.flux = flux
+    c.tau_gamma = tau_gamma
     for a in range(3):
         c.beta[a] = float(beta[a]) if a < len(beta) else 0.0
     c.kappa, c.nu, c.Phi, c.coriolis_f, c.friction, c.dt = kappa, nu, Phi, coriolis_f, friction, dt

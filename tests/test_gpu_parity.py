@@ -183,6 +183,34 @@ def test_convdiff2d_fp64(ctx, n, p, kappa, beta, nu):
     assert rel(tr, oracle_trace_at_nodes(disc, T)) < 1e-10
 
 
+@pytest.mark.parametrize("d,n,p,beta,kappa,nu,gamma", [(3, (3, 4, 3), 2, (0.0, 0.0, 0.0), 1.0, 1.0, 1.0),
+                                                        (2, (6, 5), 3, (0.3, -0.2), 0.5, 0.0, 2.0),
+                                                        (2, (9, 7), 1, (0.0, 0.0), 1.0, 10.0, 1.0)])
+def test_convdiff_mesh_tau_fp64(ctx, d, n, p, beta, kappa, nu, gamma):
+    """Mesh-dependent stabilisation tau = gamma (p+1)(p+2)/h (Section 4.2) on the float64
+    path: the oracle's iteration count and solution, in the diffusion-dominated regime where
+    the upwind tau diverges."""
+    ihdg = ih()
+    mesh = ihdg.make_mesh(d, n, p)
+    co = ihdg.make_coeffs(ihdg.CONVDIFF, beta=beta, kappa=kappa, nu=nu, tau_gamma=gamma)
+    vol, bnd = ihdg.quadrature_points(mesh, co)
+    if d == 2 and any(beta):
+        f, g = W.convdiff_forcing(vol, kappa, beta, nu), W.convdiff_exact(bnd)
+    else:
+        u = lambda P: np.prod(np.sin(np.pi * P[..., :d]), axis=-1)
+        f, g = (d * np.pi ** 2 * kappa + nu) * u(vol), u(bnd)
+    tol = 1e-10
+    u_g, tr, res = ctx.solve(mesh, co, f, g, ihdg.make_options(tol, max_iters=5000))
+    om = BoxMesh(d, n)
+    disc = Discretisation(om, p)
+    U, T, K, r, st, hist = ConvDiff(disc, np.array(beta[:d]), kappa, nu, tau_gamma=gamma).iterate(
+        f, g, tol, max_iters=5000, history=True)
+    assert res.status == ihdg.OK and st == STATUS_OK
+    check_iteration_count(res.iterations, K, hist, tol)
+    assert rel(u_g, U.reshape(om.nel, -1)) < 1e-10
+    assert rel(tr, oracle_trace_at_nodes(disc, T)) < 1e-10
+
+
 def test_convdiff_diverges_like_oracle(ctx):
     """kappa = 1e-2 at h = 1/256 (the 2D convection-diffusion workload's element size): the
     iteration diverges; both sides stop with DIVERGED at the same sweep, same iterate."""

@@ -82,6 +82,10 @@ def test_invalid_arguments_rejected():
     bad_flux = ihdg.make_coeffs(ihdg.TRANSPORT, beta=(1, 1), flux=7)
     m2 = ihdg.make_mesh(2, (2, 2), 2)
     assert L.ihdg_problem_sizes(ctypes.byref(m2), ctypes.byref(bad_flux), ctypes.byref(s)) == ihdg.ERR_INVALID
+    bad_tau = ihdg.make_coeffs(ihdg.CONVDIFF, beta=(1, 1), kappa=0.1, tau_gamma=-1.0)
+    assert L.ihdg_problem_sizes(ctypes.byref(m2), ctypes.byref(bad_tau), ctypes.byref(s)) == ihdg.ERR_INVALID
+    tau_tr = ihdg.make_coeffs(ihdg.TRANSPORT, beta=(1, 1), tau_gamma=1.0)
+    assert L.ihdg_problem_sizes(ctypes.byref(m2), ctypes.byref(tau_tr), ctypes.byref(s)) == ihdg.ERR_UNSUPPORTED
     npc_cd = ihdg.make_coeffs(ihdg.CONVDIFF, beta=(1, 1), kappa=0.1, flux=ihdg.FLUX_NPC)
     assert L.ihdg_problem_sizes(ctypes.byref(m2), ctypes.byref(npc_cd), ctypes.byref(s)) == ihdg.ERR_UNSUPPORTED
     m = ihdg.make_mesh(2, (2, 2), 5)
@@ -155,13 +159,13 @@ def test_export_form_matches_oracle_transport(p, flux):
     assert np.abs(f @ PV.T - u1.reshape(om.nel, -1)).max() < 1e-12
 
 
-@pytest.mark.parametrize("p", [1, 3])
-def test_export_form_matches_oracle_convdiff(p):
+@pytest.mark.parametrize("p,gamma", [(1, 0.0), (3, 0.0), (2, 1.0), (3, 0.5)])
+def test_export_form_matches_oracle_convdiff(p, gamma):
     beta, kappa, nu = (1.0, -0.7), 0.05, 0.3
     mesh = ihdg.make_mesh(2, (3, 3), p)
-    co = ihdg.make_coeffs(ihdg.CONVDIFF, beta=beta, kappa=kappa, nu=nu)
+    co = ihdg.make_coeffs(ihdg.CONVDIFF, beta=beta, kappa=kappa, nu=nu, tau_gamma=gamma)
     om = BoxMesh(2, (3, 3))
-    pr = ConvDiff(Discretisation(om, p), np.array(beta), kappa, nu)
+    pr = ConvDiff(Discretisation(om, p), np.array(beta), kappa, nu, tau_gamma=gamma or None)
     nf = p + 1
     kinds = ["sum"] * 4
     own_off = [f * nf for f in range(4)]

@@ -123,3 +123,72 @@ def test_upwind_count_insensitive_to_kappa():
         assert st == STATUS_OK
         ks.append(k)
     assert abs(ks[0] - ks[1]) <= 0.1 * max(ks), ks
+
+
+# ------------------------------------------------------------------------------ mesh-dependent tau
+def make_mesh_tau(d, n, p, beta, kappa, nu, gamma=1.0):
+    m = BoxMesh(d, (n,) * d)
+    disc = Discretisation(m, p)
+    return m, disc, ConvDiff(disc, np.array(beta, dtype=float), kappa, nu, tau_gamma=gamma)
+
+
+def elliptic_data(disc, d, kappa, nu):
+    """u = prod sin(pi x_a): f = (d pi^2 kappa + nu) u (beta = 0), g = u on the boundary."""
+    u = lambda P: np.prod(np.sin(np.pi * P), axis=-1)
+    return (d * np.pi ** 2 * kappa + nu) * u(disc.volume_points()), u(disc.boundary_points())
+
+
+def test_mesh_tau_value():
+    """Section 4.2: tau = gamma (p+1)(p+2)/h on every face, both sides."""
+    m = BoxMesh(2, (4, 5), hi=[2.0, 1.0])
+    pr = ConvDiff(Discretisation(m, 3), np.array([0.3, 0.1]), 1.0, 0.0, tau_gamma=0.7)
+    for f in range(4):
+        h = [0.5, 0.2][f // 2]
+        assert abs(pr.tau(f) - 0.7 * 4 * 5 / h) < 1e-12
+
+
+@pytest.mark.parametrize("d,p", [(2, 2), (3, 1)])
+def test_mesh_tau_polynomial_exactness(d, p):
+    """The discretisation stays consistent for any tau > 0: u in Q^p is reproduced."""
+    beta, kap, nu = [0.4, -0.3, 0.2][:d], 0.5, 1.0
+    m, disc, pr = make_mesh_tau(d, 3, p, beta, kap, nu, gamma=2.0)
+    coef = np.array([1.0, -2.0, 0.5])[:d]
+    X = disc.volume_points()
+    f = np.full(X.shape[:2], float(np.dot(beta, coef))) + nu * (X @ coef)
+    g = disc.boundary_points() @ coef
+    Ud, Td = pr.direct_solve(f, g)
+    assert np.abs(Ud[:, d, :] - disc.node_points() @ coef).max() < 1e-10
+    for a in range(d):   # sigma = -kappa grad u
+        assert np.abs(Ud[:, a, :] + kap * coef[a]).max() < 1e-10
+
+
+def test_mesh_tau_iteration_equals_direct_solve():
+    m, disc, pr = make_mesh_tau(2, 4, 2, [0.0, 0.0], 1.0, 1.0)
+    f, g = elliptic_data(disc, 2, 1.0, 1.0)
+    U, T, K, r, st = pr.iterate(f, g, 1e-12, max_iters=5000)
+    Ud, Td = pr.direct_solve(f, g)
+    assert st == STATUS_OK
+    assert np.abs(U - Ud).max() < 1e-9 * np.abs(Ud).max()
+
+
+@pytest.mark.parametrize("d,n,p", [(2, 4, 1), (2, 4, 2), (3, 2, 1)])
+def test_elliptic_limit_needs_mesh_tau(d, n, p):
+    """Section 4.2: with beta = 0, kappa = 1 the upwind tau diverges and the mesh-dependent
+    tau = (p+1)(p+2)/h converges."""
+    m, disc, pr_u = make(d, n, p, [0.0] * d, 1.0, 1.0)
+    f, g = elliptic_data(disc, d, 1.0, 1.0)
+    assert pr_u.iterate(f, g, 1e-10, max_iters=3000)[4] == STATUS_DIVERGED
+    pr_m = ConvDiff(disc, np.zeros(d), 1.0, 1.0, tau_gamma=1.0)
+    assert pr_m.iterate(f, g, 1e-10, max_iters=3000)[4] == STATUS_OK
+
+
+def test_mesh_tau_counts_grow_with_n_and_p():
+    """Table 5's trend: the count grows with the number of elements and with p."""
+    def count(n, p):
+        m, disc, pr = make_mesh_tau(2, n, p, [0.0, 0.0], 1.0, 1.0)
+        f, g = elliptic_data(disc, 2, 1.0, 1.0)
+        U, T, K, r, st = pr.iterate(f, g, 1e-10, max_iters=5000)
+        assert st == STATUS_OK
+        return K
+    k41, k42, k81 = count(4, 1), count(4, 2), count(8, 1)
+    assert k41 < k42 and k41 < k81
