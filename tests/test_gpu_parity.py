@@ -184,7 +184,7 @@ def test_convdiff2d_fp64(ctx, n, p, kappa, beta, nu):
 
 
 @pytest.mark.parametrize("d,n,p,beta,kappa,nu,gamma", [(3, (3, 4, 3), 2, (0.0, 0.0, 0.0), 1.0, 1.0, 1.0),
-                                                        (2, (6, 5), 3, (0.3, -0.2), 0.5, 0.0, 2.0),
+                                                        (2, (6, 5), 2, (0.3, -0.2), 0.5, 1.0, 1.0),
                                                         (2, (9, 7), 1, (0.0, 0.0), 1.0, 10.0, 1.0)])
 def test_convdiff_mesh_tau_fp64(ctx, d, n, p, beta, kappa, nu, gamma):
     """Mesh-dependent stabilisation tau = gamma (p+1)(p+2)/h (Section 4.2) on the float64
