@@ -303,7 +303,18 @@ ihdg_status device_iterate(ihdg_ctx* ctx, Plan* pl, const ihdg_options& o, const
   // floor spends sweeps without progress, while the float64 outer step that follows restores
   // full accuracy (measured on the conv.-diff., 3D transport and shallow-water workloads).
   if (inner_rtol <= 0.0) inner_rtol = o.prec == IHDG_MIXED_BF16 ? 0.2 : (o.prec == IHDG_MIXED_TF32 ? 1e-2 : 2e-3);
-  CK(launch_ctrl_init(a, o.tol, o.diverge_factor, o.max_iters, o.inner_max, inner_rtol), "ctrl init");
+  // Bound of every grid-barrier wait (~1 s of SM clock) and, for the failure-detection tests
+  // only, a block that never arrives (IHDG_TEST_STALL_BLOCK) with a shorter bound
+  // (IHDG_TEST_WAIT_CYCLES): the waits then run out and the call returns IHDG_ERR_TIMEOUT.
+  long long wait_cycles = 2000000000LL;
+  int stall_block = -1;
+  if (const char* w = std::getenv("IHDG_TEST_WAIT_CYCLES")) {
+    const long long v = std::atoll(w);
+    if (v > 0) wait_cycles = v;
+  }
+  if (const char* b = std::getenv("IHDG_TEST_STALL_BLOCK")) stall_block = std::atoi(b);
+  CK(launch_ctrl_init(a, o.tol, o.diverge_factor, o.max_iters, o.inner_max, inner_rtol, wait_cycles, stall_block),
+     "ctrl init");
   CK(launch_forcing(a), "forcing kernel");
   CK(launch_export0(a, u0, a.ring), "initial export kernel");
   CK(launch_first(a), "first sweep kernel");

@@ -34,6 +34,8 @@ struct Ctrl {
   int inner_max;
   int timeout;            // a bounded device wait ran out (the loop stops, status ERR_TIMEOUT)
   unsigned int bar_gen;   // (unused)
+  long long wait_cycles;  // bound of every grid-barrier wait, in SM clock cycles
+  int stall_block;        // test hook: this block never arrives at the grid barrier (-1: none)
   double tol, diverge_factor, inner_rtol;
   double res;             // last float64 stopping residual
   double res_min;

@@ -322,7 +322,8 @@ __global__ void __launch_bounds__(BS) k_trace_out(DevGeo g, OpsDev op, SrcDev sr
   tr[idx] = v;
 }
 
-__global__ void k_ctrl_init(Ctrl* c, double tol, double div, int max_iters, int inner_max, double inner_rtol) {
+__global__ void k_ctrl_init(Ctrl* c, double tol, double div, int max_iters, int inner_max, double inner_rtol,
+                            long long wait_cycles, int stall_block) {
   c->ticket = 0u;
   c->done = 0;
   c->status = 4;
@@ -337,6 +338,8 @@ __global__ void k_ctrl_init(Ctrl* c, double tol, double div, int max_iters, int 
   c->timeout = 0;
   c->bar_count = 0u;
   c->bar_gen = 0u;
+  c->wait_cycles = wait_cycles;
+  c->stall_block = stall_block;
   c->tol = tol;
   c->diverge_factor = div;
   c->inner_rtol = inner_rtol;
@@ -411,8 +414,9 @@ bool shape_supported(int dim, int nf) {
   return (dim == 2 && nf >= 2 && nf <= 5) || (dim == 3 && (nf == 4 || nf == 9));
 }
 
-cudaError_t launch_ctrl_init(const LaunchArgs& a, double tol, double div, int max_iters, int inner_max, double inner_rtol) {
-  k_ctrl_init<<<1, 1, 0, a.stream>>>(a.ctrl, tol, div, max_iters, inner_max, inner_rtol);
+cudaError_t launch_ctrl_init(const LaunchArgs& a, double tol, double div, int max_iters, int inner_max, double inner_rtol,
+                             long long wait_cycles, int stall_block) {
+  k_ctrl_init<<<1, 1, 0, a.stream>>>(a.ctrl, tol, div, max_iters, inner_max, inner_rtol, wait_cycles, stall_block);
   return cudaGetLastError();
 }
 cudaError_t launch_forcing(const LaunchArgs& a) {

@@ -60,7 +60,8 @@ struct SweepTimer {
 bool shape_supported(int dim, int nf);
 int partials_needed(long long nel);
 
-cudaError_t launch_ctrl_init(const LaunchArgs& a, double tol, double div, int max_iters, int inner_max, double inner_rtol);
+cudaError_t launch_ctrl_init(const LaunchArgs& a, double tol, double div, int max_iters, int inner_max, double inner_rtol,
+                             long long wait_cycles, int stall_block);
 cudaError_t launch_forcing(const LaunchArgs& a);
 cudaError_t launch_export0(const LaunchArgs& a, const double* u0, double* E0);
 cudaError_t launch_first(const LaunchArgs& a);

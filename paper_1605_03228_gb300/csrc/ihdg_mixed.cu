@@ -193,11 +193,12 @@ __device__ double barrier_sum(double* part, unsigned* count, unsigned nb, double
   __syncthreads();
   if (threadIdx.x == 0) {
     part[blockIdx.x] = mine;
-    red_release_add(count, 1u);
+    if ((int)blockIdx.x != ctrl->stall_block) red_release_add(count, 1u);
     const unsigned target = nb * gridDim.x;
+    const long long lim = ctrl->wait_cycles;
     const long long t0 = clock64();
     while (ld_acquire_u32(count) < target) {
-      if (clock64() - t0 > 2000000000LL) { atomicExch(&ctrl->timeout, 1); break; }
+      if (clock64() - t0 > lim) { atomicExch(&ctrl->timeout, 1); break; }
     }
     *s_flag = *(volatile int*)&ctrl->timeout;
   }

@@ -1,0 +1,73 @@
+"""Failure detection without a GPU fault.
+
+* Every grid-barrier wait of the persistent inner kernels is bounded.  A test-only hook set
+  on the host (IHDG_TEST_STALL_BLOCK: that block never arrives) together with a short bound
+  (IHDG_TEST_WAIT_CYCLES, ~10 ms) makes every block's wait run out: the kernels leave their
+  loops (the tensor-core kernel also frees its tensor memory), the call returns
+  IHDG_ERR_TIMEOUT, and the next solve on the same context gives the same result as before.
+* Corrupted input: a NaN in the forcing is reported as DIVERGED (non-finite residual), on
+  the float64 and the mixed path.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1605_03228_gb300 import ihdg
+    c = ihdg.Context(0)
+    yield c
+    c.close()
+
+
+def problem(ih, case):
+    if case == "cd2d":
+        mesh = ih.make_mesh(2, (64, 48), 3)
+        co = ih.make_coeffs(ih.CONVDIFF, beta=(1.0, 1.0), kappa=1e-4)
+        vol, bnd = ih.quadrature_points(mesh, co)
+        return mesh, co, W.convdiff_forcing(vol, 1e-4), W.convdiff_exact(bnd)
+    b = tuple(np.ones(3) / np.sqrt(3))
+    mesh = ih.make_mesh(3, (12, 12, 12), 2)
+    co = ih.make_coeffs(ih.TRANSPORT, beta=b)
+    vol, bnd = ih.quadrature_points(mesh, co)
+    return mesh, co, W.transport3d_forcing(vol, b), W.transport3d_exact(bnd)
+
+
+@pytest.mark.parametrize("case,prec,kernel", [("cd2d", "MIXED_FP32", ""), ("t3d", "MIXED_BF16", ""),
+                                              ("t3d", "MIXED_FP32", "tile"), ("cd2d", "MIXED_FP32", "global")])
+def test_barrier_wait_runs_out_and_context_stays_usable(ctx, monkeypatch, case, prec, kernel):
+    from paper_1605_03228_gb300 import ihdg as ih
+    mesh, co, f, g = problem(ih, case)
+    if kernel:
+        monkeypatch.setenv("IHDG_INNER_KERNEL", kernel)
+    opts = ih.make_options(1e-8, prec=getattr(ih, prec), max_iters=5000)
+    u_ref, _, r_ref = ctx.solve(mesh, co, f, g, opts)
+    assert r_ref.status == ih.OK
+    monkeypatch.setenv("IHDG_TEST_WAIT_CYCLES", "20000000")
+    monkeypatch.setenv("IHDG_TEST_STALL_BLOCK", "0")
+    with pytest.raises(ih.IHDGError) as e:
+        ctx.solve(mesh, co, f, g, opts)
+    assert e.value.status == ih.ERR_TIMEOUT
+    monkeypatch.delenv("IHDG_TEST_STALL_BLOCK")
+    monkeypatch.delenv("IHDG_TEST_WAIT_CYCLES")
+    u, _, r = ctx.solve(mesh, co, f, g, opts)
+    assert r.status == ih.OK and r.iterations == r_ref.iterations
+    assert np.array_equal(u, u_ref)
+
+
+@pytest.mark.parametrize("prec", ["FP64", "MIXED_FP32"])
+def test_nan_forcing_is_reported_as_diverged(ctx, prec):
+    from paper_1605_03228_gb300 import ihdg as ih
+    mesh, co, f, g = problem(ih, "cd2d")
+    f = f.copy()
+    f[100, 3] = np.nan
+    u, _, r = ctx.solve(mesh, co, f, g, ih.make_options(1e-8, prec=getattr(ih, prec), max_iters=5000))
+    assert r.status == ih.DIVERGED
