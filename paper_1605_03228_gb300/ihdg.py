@@ -237,13 +237,17 @@ class Context:
         if st != OK:
             raise IHDGError(st, f"{name}: {self.last_error()}")
 
-    def solve(self, mesh, coeffs, f_qp, g_qp, opts, want_trace=True):
-        """Host-buffer solve.  Returns (u [n_el, nvol], trace or None, Result)."""
+    def solve(self, mesh, coeffs, f_qp, g_qp, opts, want_trace=True, u_out=None, trace_out=None):
+        """Host-buffer solve.  Returns (u [n_el, nvol], trace or None, Result).  u_out and
+        trace_out, when given, are C-contiguous float64 host arrays of those shapes (e.g.
+        views of pinned memory) that receive the results."""
         s = problem_sizes(mesh, coeffs)
         f = np.ascontiguousarray(f_qp, dtype=np.float64)
         g = np.ascontiguousarray(g_qp, dtype=np.float64)
-        u = np.zeros((s.n_el, s.nvol))
-        tr = np.zeros((s.n_face, s.nface_nodes)) if want_trace else None
+        u = u_out if u_out is not None else np.zeros((s.n_el, s.nvol))
+        tr = trace_out if trace_out is not None else (np.zeros((s.n_face, s.nface_nodes)) if want_trace else None)
+        assert u.shape == (s.n_el, s.nvol) and u.dtype == np.float64 and u.flags.c_contiguous
+        assert tr is None or (tr.shape == (s.n_face, s.nface_nodes) and tr.dtype == np.float64 and tr.flags.c_contiguous)
         res = Result()
         st = self.L.ihdg_solve(self.h, ctypes.byref(mesh), ctypes.byref(coeffs), _dptr(f), _dptr(g),
                                ctypes.byref(opts), _dptr(u), _dptr(tr), ctypes.byref(res))
