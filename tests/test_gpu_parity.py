@@ -306,6 +306,31 @@ def test_swe_steps_fp64(ctx, n, p, ratio, fc, gam):
     assert rel(q, U.reshape(om.nel, -1)) < 1e-10
 
 
+@pytest.mark.parametrize("prec_name", ["FP64", "MIXED_FP32"])
+def test_swe_restart_from_state_is_exact(ctx, prec_name):
+    """Checkpoint/resume: the volume state q^m is the whole restart state of the time
+    stepping (each step warm-starts from R q^m), so 10 steps equal 5 steps followed by 5 more
+    from the returned state, bit for bit, with the same per-step iteration counts."""
+    ihdg = ih()
+    n, p = (20, 16), 2
+    dt = 0.5 * (1.0 / n[0]) / ((p + 1) * (p + 2))
+    mesh = ihdg.make_mesh(2, n, p)
+    co = ihdg.make_coeffs(ihdg.SWE, Phi=1.0, dt=dt, coriolis_f=0.2, friction=0.05)
+    nodes = ihdg.node_points(mesh, co)
+    q0 = W.swe_bump(nodes, seed=3, width=0.15)
+    opts = ihdg.make_options(1e-10, prec=getattr(ihdg, prec_name))
+    q_all = q0.reshape(q0.shape[0], -1).copy()
+    its_all, r_all = ctx.swe_steps(mesh, co, q_all, 10, opts)
+    q_half = q0.reshape(q0.shape[0], -1).copy()
+    its_a, _ = ctx.swe_steps(mesh, co, q_half, 5, opts)
+    checkpoint = q_half.copy()                         # what a caller would save
+    q_res = checkpoint.copy()
+    its_b, r_b = ctx.swe_steps(mesh, co, q_res, 5, opts)
+    assert r_all.status == r_b.status == ihdg.OK
+    assert its_a + its_b == its_all
+    assert np.array_equal(q_res, q_all)
+
+
 # ------------------------------------------------------------------------------ mixed precision
 @pytest.mark.parametrize("prec_name", ["MIXED_FP32", "MIXED_BF16"])
 def test_mixed_transport2d(ctx, prec_name):
