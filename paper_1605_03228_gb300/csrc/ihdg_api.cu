@@ -265,6 +265,7 @@ std::string tune_key(const ihdg_mesh& m, const ihdg_coeffs& c, int prec) {
 ihdg_status device_iterate(ihdg_ctx* ctx, Plan* pl, const ihdg_options& o, const SrcDev& src, const double* u0,
                            double* d_u, double* d_tr, char* ws, const Layout& L, cudaStream_t stream,
                            ihdg_result* res) {
+  NvtxRange nv_solve(o.prec == IHDG_FP64 ? "ihdg solve (float64)" : "ihdg solve (mixed)");
   LaunchArgs a{};
   a.g = pl->g;
   a.op = pl->op;
@@ -584,6 +585,7 @@ ihdg_status ihdg_solve(ihdg_ctx* ctx, const ihdg_mesh* mesh, const ihdg_coeffs* 
 
 ihdg_status ihdg_autotune(ihdg_ctx* ctx, const ihdg_mesh* mesh, const ihdg_coeffs* co, const double* f_qp,
                           const double* g_qp, const ihdg_options* opts, ihdg_options* tuned, double* best_ms) {
+  NvtxRange nv_tune("ihdg autotune");
   if (!ctx) return IHDG_ERR_INVALID;
   if (!mesh || !co || !f_qp || !g_qp || !tuned) return fail(ctx, IHDG_ERR_INVALID, "null argument");
   if (co->pde == IHDG_SWE) return fail(ctx, IHDG_ERR_INVALID, "shallow water is solved by ihdg_swe_steps*");

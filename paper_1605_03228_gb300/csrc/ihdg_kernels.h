@@ -1,6 +1,7 @@
 // Kernel launch interface of the iHDG sweep (internal header).
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "ihdg_dev.h"
 
@@ -58,6 +59,14 @@ struct SweepTimer {
 };
 
 bool shape_supported(int dim, int nf);
+// NVTX range for profilers (header-only NVTX 3: nothing happens unless a tool is attached)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 int partials_needed(long long nel);
 
 cudaError_t launch_ctrl_init(const LaunchArgs& a, double tol, double div, int max_iters, int inner_max, double inner_rtol,

@@ -928,6 +928,7 @@ ihdg_status run_mixed(Ctrl* hc, MixedArgs& m, const ihdg_options& o, const doubl
     return true;
   };
   for (int outer = 0; outer < 1000000; ++outer) {
+    NvtxRange nv_outer("ihdg outer step");
     // the residual kernel (float64 norm of t(r), plus one low-precision sweep) is timed with
     // the float64 launches, so the low-precision figure is the persistent inner loop's alone
     if (!launch(0, has_e, true) || !launch(1, 0, true)) return IHDG_ERR_CUDA;
