@@ -327,6 +327,21 @@ ihdg_status device_iterate(ihdg_ctx* ctx, Plan* pl, const ihdg_options& o, const
   const double* Et = nullptr;     // exports of u^K
   const double* Et2 = nullptr;
   if (!mixed) {
+    // the whole loop in one cooperative launch when its grid is co-resident (not in profile
+    // mode, which times every sweep launch); otherwise, or after it, batches of launches
+    if (!tm.on) {
+      cudaError_t pe = launch_sweep64_persist(a);
+      if (pe == cudaSuccess) {
+        tm.launches += 1;
+        CK(cudaMemcpyAsync(hc, a.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, stream), "ctrl readback");
+        CK(cudaStreamSynchronize(stream), "persistent sweep loop");
+        if (hc->timeout) return fail(ctx, IHDG_ERR_TIMEOUT, "persistent float64 sweep: a grid barrier wait ran out");
+      } else if (pe != cudaErrorNotSupported) {
+        return cuda_fail(ctx, pe, "persistent sweep kernel");
+      } else {
+        cudaGetLastError();
+      }
+    }
     int batch = 2;
     for (;;) {
       CK(cudaMemcpyAsync(hc, a.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, stream), "ctrl readback");

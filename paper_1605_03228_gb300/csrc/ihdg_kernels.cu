@@ -23,6 +23,7 @@
 #include "ihdg_dev.h"
 #include "ihdg_kernels.h"
 #include "ihdg_common.cuh"
+#include "ihdg_persist.cuh"
 
 namespace ihdg {
 
@@ -227,6 +228,135 @@ __global__ void __launch_bounds__(BS) k_sweep64(DevGeo g, OpsDev op, const doubl
   if (arrive(ctrl, partials, acc, ws, &tot) && threadIdx.x == 0) decide(ctrl, tot, res_hist, true);
 }
 
+// Grid barrier plus the float64 sum of one value per block, for cooperative launches: the
+// same fixed-order sum as arrive() (thread-strided partial loads, then block_sum), so the
+// residual is bitwise the one of the launch-per-sweep path.  Thread 0 publishes the block's
+// value, arrives with a release add and polls with acquire loads bounded by
+// ctrl->wait_cycles (then ctrl->timeout).  The total is valid in every thread.
+__device__ double barrier_sum64(double* part, unsigned* count, unsigned nb, double mine, Ctrl* ctrl, double* ws,
+                                double* s_out, int* s_flag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = mine;
+    if ((int)blockIdx.x != ctrl->stall_block) red_release_add(count, 1u);
+    const unsigned target = nb * gridDim.x;
+    const long long lim = ctrl->wait_cycles;
+    const long long t0 = clock64();
+    while (ld_acquire_u32(count) < target) {
+      if (clock64() - t0 > lim) { atomicExch(&ctrl->timeout, 1); break; }
+    }
+    *s_flag = *(volatile int*)&ctrl->timeout;
+  }
+  __syncthreads();
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) acc += __ldcg(part + i);
+  const double t = block_sum(acc, ws);
+  if (threadIdx.x == 0) *s_out = t;
+  __syncthreads();
+  return *s_out;
+}
+
+// The float64 sweep loop in one cooperative launch (meshes whose one-element-per-thread grid
+// is co-resident): every sweep is k_sweep64's a1..a4, then a grid barrier with the residual
+// sum, then the loop decision, which every block takes identically from the same total
+// (decide()'s rules); block 0 records it in ctrl.  Per sweep this saves a launch and a host
+// check, which dominate on small meshes.
+template <int NF, int NLF>
+__global__ void __launch_bounds__(BS) k_sweep64_persist(DevGeo g, OpsDev op, const double* __restrict__ F,
+                                                        double* ring, long long ring_stride, Ctrl* ctrl,
+                                                        double* partials, double* res_hist) {
+  constexpr int NIN = NF * NLF;
+  constexpr int NQ = NIN * (NIN + 1) / 2;
+  __shared__ double ws[BS / 32];
+  __shared__ double s_tot;
+  __shared__ int s_to;
+  extern __shared__ double sdyn[];
+  if (ctrl_done(ctrl)) return;
+  int it = ctrl_iter(ctrl);
+  double res_min = ctrl->res_min;
+  const double tol = ctrl->tol, divf = ctrl->diverge_factor;
+  const int max_iters = ctrl->max_iters;
+  double* sLE = sdyn;                       // n_exp * NIN
+  double* sQ = sLE + g.n_exp * NIN;         // NQ
+  double* st = sQ + NQ + threadIdx.x;       // per-thread trace column, stride BS
+  for (int i = threadIdx.x; i < g.n_exp * NIN; i += BS) sLE[i] = op.LE[i];
+  for (int i = threadIdx.x; i < NQ; i += BS) sQ[i] = op.Qp[i];
+  __syncthreads();
+  const long long K = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int c[3] = {0, 0, 0};
+  if (K < g.nel) coords(g, K, c);
+  for (int s = 0;; ++s) {
+    const double* Ecur = ring + (long long)(it % 3) * ring_stride;
+    const double* Eprv = ring + (long long)((it + 2) % 3) * ring_stride;
+    double* Enxt = ring + (long long)((it + 1) % 3) * ring_stride;
+    double acc = 0.0;
+    if (K < g.nel) {
+      double d[NIN];
+      gather<NF, NLF, double, double>(g, Ecur, K, c, [&](int q, double v) { st[q * BS] = v; d[q] = v; });
+      gather<NF, NLF, double, double>(g, Eprv, K, c, [&](int q, double v) { d[q] -= v; });
+      int qq = 0;
+#pragma unroll
+      for (int a = 0; a < NIN; ++a) {
+        double r = 0.0;
+#pragma unroll
+        for (int u = a; u < NIN; ++u) r += sQ[qq + u - a] * d[u];
+        qq += NIN - a;
+        acc += d[a] * r;
+      }
+      constexpr int CH = 8;
+#pragma unroll
+      for (int c0 = 0; c0 < NIN; c0 += CH) {
+        double fv[CH];
+#pragma unroll
+        for (int i = 0; i < CH; ++i) fv[i] = (c0 + i < g.n_exp && row_live(g, c0 + i, NF)) ? F[(long long)(c0 + i) * g.ld + K] : 0.0;
+#pragma unroll
+        for (int i = 0; i < CH; ++i) {
+          const int e = c0 + i;
+          if (e < g.n_exp && row_live(g, e, NF)) {
+            double v = fv[i];
+            const double* row = sLE + e * NIN;
+#pragma unroll
+            for (int q = 0; q < NIN; ++q) v += row[q] * st[q * BS];
+            Enxt[(long long)e * g.ld + K] = v;
+          }
+        }
+      }
+    }
+    const double blk = block_sum(acc, ws);
+    const double tot = barrier_sum64(partials + (size_t)(s & 1) * gridDim.x, &ctrl->bar_count, (unsigned)(s + 1),
+                                     blk, ctrl, ws, &s_tot, &s_to);
+    if (s_to) break;
+    // decide()'s rules, taken identically in every block
+    const double res = sqrt(tot);
+    const int k = it + 1;
+    bool done = false;
+    int status = 4;
+    if (res < tol) {
+      done = true;
+      status = 0;
+    } else if (!(res == res) || isinf(res) || (divf > 0.0 && res > divf * res_min)) {
+      done = true;
+      status = 5;
+    } else {
+      if (res < res_min) res_min = res;
+      if (k >= max_iters) done = true;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      ctrl->iter = k;
+      ctrl->fp64_sweeps += 1;
+      ctrl->res = res;
+      if (res_hist) res_hist[k] = res;
+      ctrl->res_min = res_min;
+      if (done) {
+        ctrl->status = status;
+        ctrl->done = 1;
+      }
+    }
+    it = k;
+    if (done) break;
+  }
+}
+
 // Volume reconstruction u = A^{-1} b + L_vol t(E) (+ L_vol t(E2) when E2 is given).
 template <int NF, int NLF>
 __global__ void __launch_bounds__(BS) k_reconstruct(DevGeo g, OpsDev op, const double* __restrict__ V,
@@ -377,6 +507,40 @@ cudaError_t run_sweep64_t(const LaunchArgs& a, int count) {
   return cudaGetLastError();
 }
 
+// One cooperative launch of the whole float64 loop when the grid is co-resident; returns
+// cudaErrorNotSupported (nothing launched) otherwise.
+template <int NF, int NLF>
+cudaError_t run_sweep64_persist_t(const LaunchArgs& a) {
+  constexpr int NIN = NF * NLF;
+  size_t smem = ((size_t)a.g.n_exp * NIN + NIN * (NIN + 1) / 2 + (size_t)NIN * BS) * sizeof(double);
+  auto kern = k_sweep64_persist<NF, NLF>;
+  if (smem > 32 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, BS, smem);
+  if (e != cudaSuccess) return e;
+  const long long grid = grid_for(a.g.nel);
+  if (per < 1 || grid > (long long)per * sms || grid > partials_needed(a.g.nel) / 2 - 1) return cudaErrorNotSupported;
+  e = cudaMemsetAsync(&a.ctrl->bar_count, 0, sizeof(unsigned), a.stream);
+  if (e != cudaSuccess) return e;
+  DevGeo gg = a.g;
+  OpsDev oo = a.op;
+  const double* ff = a.F;
+  double* rr = a.ring;
+  long long rs = a.ring_stride;
+  Ctrl* ct = a.ctrl;
+  double* pp = a.partials;
+  double* rh = a.res_hist;
+  void* args[] = {&gg, &oo, &ff, &rr, &rs, &ct, &pp, &rh};
+  e = cudaLaunchCooperativeKernel((const void*)kern, dim3((unsigned)grid), dim3(BS), args, smem, a.stream);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
 template <int NF, int NLF>
 cudaError_t run_reconstruct_t(const LaunchArgs& a, const double* E, const double* E2, double* u) {
   k_reconstruct<NF, NLF><<<grid_for(a.g.nel), BS, 0, a.stream>>>(a.g, a.op, a.V, E, E2, u);
@@ -404,6 +568,7 @@ cudaError_t dispatch(const DevGeo& g, Args&&... args) {
 
 template <int NF, int NLF> struct FirstFn { static cudaError_t run(const LaunchArgs& a) { return run_first_t<NF, NLF>(a); } };
 template <int NF, int NLF> struct Sweep64Fn { static cudaError_t run(const LaunchArgs& a, int n) { return run_sweep64_t<NF, NLF>(a, n); } };
+template <int NF, int NLF> struct Sweep64PersistFn { static cudaError_t run(const LaunchArgs& a) { return run_sweep64_persist_t<NF, NLF>(a); } };
 template <int NF, int NLF> struct ReconFn {
   static cudaError_t run(const LaunchArgs& a, const double* E, const double* E2, double* u) { return run_reconstruct_t<NF, NLF>(a, E, E2, u); }
 };
@@ -429,6 +594,7 @@ cudaError_t launch_export0(const LaunchArgs& a, const double* u0, double* E0) {
 }
 cudaError_t launch_first(const LaunchArgs& a) { return dispatch<FirstFn>(a.g, a); }
 cudaError_t launch_sweep64(const LaunchArgs& a, int count) { return dispatch<Sweep64Fn>(a.g, a, count); }
+cudaError_t launch_sweep64_persist(const LaunchArgs& a) { return dispatch<Sweep64PersistFn>(a.g, a); }
 cudaError_t launch_reconstruct(const LaunchArgs& a, const double* E, const double* E2, double* u) {
   return dispatch<ReconFn>(a.g, a, E, E2, u);
 }

@@ -75,6 +75,9 @@ cudaError_t launch_forcing(const LaunchArgs& a);
 cudaError_t launch_export0(const LaunchArgs& a, const double* u0, double* E0);
 cudaError_t launch_first(const LaunchArgs& a);
 cudaError_t launch_sweep64(const LaunchArgs& a, int count);
+// the whole float64 loop in one cooperative launch; cudaErrorNotSupported when the grid is
+// not co-resident (then launch_sweep64 in batches)
+cudaError_t launch_sweep64_persist(const LaunchArgs& a);
 cudaError_t launch_reconstruct(const LaunchArgs& a, const double* E, const double* E2, double* u);
 cudaError_t launch_trace_out(const LaunchArgs& a, const double* E, const double* E2, const double* u, int pde,
                              const double* beta, const double* alpha, long long nface, double* tr);

@@ -1,6 +1,7 @@
 """Failure detection without a GPU fault.
 
-* Every grid-barrier wait of the persistent inner kernels is bounded.  A test-only hook set
+* Every grid-barrier wait of the persistent kernels (the mixed path's inner loops and the
+  float64 loop) is bounded.  A test-only hook set
   on the host (IHDG_TEST_STALL_BLOCK: that block never arrives) together with a short bound
   (IHDG_TEST_WAIT_CYCLES, ~10 ms) makes every block's wait run out: the kernels leave their
   loops (the tensor-core kernel also frees its tensor memory), the call returns
@@ -42,7 +43,8 @@ def problem(ih, case):
 
 
 @pytest.mark.parametrize("case,prec,kernel", [("cd2d", "MIXED_FP32", ""), ("t3d", "MIXED_BF16", ""),
-                                              ("t3d", "MIXED_FP32", "tile"), ("cd2d", "MIXED_FP32", "global")])
+                                              ("t3d", "MIXED_FP32", "tile"), ("cd2d", "MIXED_FP32", "global"),
+                                              ("cd2d", "FP64", "")])
 def test_barrier_wait_runs_out_and_context_stays_usable(ctx, monkeypatch, case, prec, kernel):
     from paper_1605_03228_gb300 import ihdg as ih
     mesh, co, f, g = problem(ih, case)
