@@ -35,7 +35,10 @@ __device__ __forceinline__ long long bface_of(const DevGeo& g, const int* c, int
   return g.nbf_off[2] + (long long)s * g.n[0] * g.n[1] + (long long)c[1] * g.n[0] + c[0];
 }
 
-// a1: the trace values t (n_in = nlf * NF) element K needs, from export array E.
+// a1: the trace values t (n_in = nlf * NF) element K needs, from export array E.  Every load
+// is unconditional: a face that needs no own (or no neighbour) value reads an in-bounds
+// stand-in, and selects combine them (the same arithmetic as reading only what is needed),
+// so all of an element's loads are in flight at once.
 template <int NF, int NLF, typename TE, typename TA, typename Out>
 __device__ __forceinline__ void gather(const DevGeo& g, const TE* __restrict__ E, long long K,
                                        const int* c, Out&& put) {
@@ -43,21 +46,22 @@ __device__ __forceinline__ void gather(const DevGeo& g, const TE* __restrict__ E
   for (int f = 0; f < NLF; ++f) {
     const int kind = g.kind[f];
     const bool bnd = on_bnd(g, c, f);
-    const long long Kn = nbr_of(g, K, f);
-    const TE* own = E + (long long)g.own_off[f] * g.ld + K;
-    const TE* nb = E + (long long)g.nbr_off[f] * g.ld + Kn;
+    const bool need_own = kind == FK_OWN_D || kind == FK_SUM_D;
+    const bool need_nb = (kind == FK_NBR_D || kind == FK_SUM_D) && !bnd;
+    const TE* own = E + (long long)(need_own ? g.own_off[f] : 0) * g.ld + K;
+    const TE* nb = need_nb ? E + (long long)g.nbr_off[f] * g.ld + nbr_of(g, K, f) : own;
+    TA o[NF], n[NF];
+#pragma unroll
+    for (int j = 0; j < NF; ++j) {
+      o[j] = (TA)own[(long long)j * g.ld];
+      n[j] = (TA)nb[(long long)j * g.ld];
+    }
 #pragma unroll
     for (int j = 0; j < NF; ++j) {
       TA v = TA(0);
-      if (kind == FK_OWN_D) {
-        v = (TA)own[(long long)j * g.ld];
-      } else if (kind == FK_NBR_D) {
-        if (!bnd) v = (TA)nb[(long long)j * g.ld];
-      } else if (kind == FK_SUM_D) {
-        const TA o = (TA)own[(long long)j * g.ld];
-        if (!bnd) v = o + (TA)nb[(long long)j * g.ld];
-        else if (g.bc_mirror) v = o + o;
-      }
+      if (kind == FK_OWN_D) v = o[j];
+      else if (kind == FK_NBR_D) v = need_nb ? n[j] : TA(0);
+      else if (kind == FK_SUM_D) v = need_nb ? o[j] + n[j] : (g.bc_mirror ? o[j] + o[j] : TA(0));
       put(f * NF + j, v);
     }
   }

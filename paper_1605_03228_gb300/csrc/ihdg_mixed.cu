@@ -29,21 +29,23 @@ __device__ __forceinline__ void gather_lp(const DevGeo& g, const TL* __restrict_
   for (int f = 0; f < NLF; ++f) {
     const int kind = g.kind[f];
     const bool bnd = on_bnd(g, c, f);
-    const long long Kn = nbr_of(g, K, f);
-    const TL* own = E + (long long)g.own_off[f] * g.ld + K;
-    const TL* nb = E + (long long)g.nbr_off[f] * g.ld + Kn;
+    const bool need_own = kind == FK_OWN_D || kind == FK_SUM_D;
+    const bool need_nb = (kind == FK_NBR_D || kind == FK_SUM_D) && !bnd;
+    // unconditional loads from in-bounds stand-ins, combined by selects (as gather())
+    const TL* own = E + (long long)(need_own ? g.own_off[f] : 0) * g.ld + K;
+    const TL* nb = need_nb ? E + (long long)g.nbr_off[f] * g.ld + nbr_of(g, K, f) : own;
+    TA o[NF], n[NF];
+#pragma unroll
+    for (int j = 0; j < NF; ++j) {
+      o[j] = (TA)ldcg_f(own + (long long)j * g.ld);
+      n[j] = (TA)ldcg_f(nb + (long long)j * g.ld);
+    }
 #pragma unroll
     for (int j = 0; j < NF; ++j) {
       TA v = TA(0);
-      if (kind == FK_OWN_D) {
-        v = (TA)ldcg_f(own + (long long)j * g.ld);
-      } else if (kind == FK_NBR_D) {
-        if (!bnd) v = (TA)ldcg_f(nb + (long long)j * g.ld);
-      } else if (kind == FK_SUM_D) {
-        const TA o = (TA)ldcg_f(own + (long long)j * g.ld);
-        if (!bnd) v = o + (TA)ldcg_f(nb + (long long)j * g.ld);
-        else if (g.bc_mirror) v = o + o;
-      }
+      if (kind == FK_OWN_D) v = o[j];
+      else if (kind == FK_NBR_D) v = need_nb ? n[j] : TA(0);
+      else if (kind == FK_SUM_D) v = need_nb ? o[j] + n[j] : (g.bc_mirror ? o[j] + o[j] : TA(0));
       put(f * NF + j, v);
     }
   }
