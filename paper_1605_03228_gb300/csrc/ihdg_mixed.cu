@@ -5,861 +5,14 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
-#include <cmath>
-#include <cstdint>
-#include <type_traits>
-#include <cstring>
-#include <vector>
+#include <string>
 
-#include "ihdg_common.cuh"
-#include "ihdg_dev.h"
 #include "ihdg_kernels.h"
 #include "ihdg_mixed.h"
-#include "ihdg_persist.cuh"
-#include "ihdg_tc.h"
 
 namespace ihdg {
 
 namespace {
-
-// gather from a low-precision array, widening to TA (through L2, see ldcg_f)
-template <int NF, int NLF, typename TL, typename TA, typename Out>
-__device__ __forceinline__ void gather_lp(const DevGeo& g, const TL* __restrict__ E, long long K, const int* c, Out&& put) {
-#pragma unroll
-  for (int f = 0; f < NLF; ++f) {
-    const int kind = g.kind[f];
-    const bool bnd = on_bnd(g, c, f);
-    const bool need_own = kind == FK_OWN_D || kind == FK_SUM_D;
-    const bool need_nb = (kind == FK_NBR_D || kind == FK_SUM_D) && !bnd;
-    // unconditional loads from in-bounds stand-ins, combined by selects (as gather())
-    const TL* own = E + (long long)(need_own ? g.own_off[f] : 0) * g.ld + K;
-    const TL* nb = need_nb ? E + (long long)g.nbr_off[f] * g.ld + nbr_of(g, K, f) : own;
-    TA o[NF], n[NF];
-#pragma unroll
-    for (int j = 0; j < NF; ++j) {
-      o[j] = (TA)ldcg_f(own + (long long)j * g.ld);
-      n[j] = (TA)ldcg_f(nb + (long long)j * g.ld);
-    }
-#pragma unroll
-    for (int j = 0; j < NF; ++j) {
-      TA v = TA(0);
-      if (kind == FK_OWN_D) v = o[j];
-      else if (kind == FK_NBR_D) v = need_nb ? n[j] : TA(0);
-      else if (kind == FK_SUM_D) v = need_nb ? o[j] + n[j] : (g.bc_mirror ? o[j] + o[j] : TA(0));
-      put(f * NF + j, v);
-    }
-  }
-}
-
-constexpr int CH = 8;   // outputs per chunk: their loads are issued together, then stored
-
-// Outer float64 sweep: E' = E + e (own and gathered), r = F + L_E t(E') - E'.
-template <int NF, int NLF, typename TL>
-__global__ void __launch_bounds__(BS) k_outer64(DevGeo g, OpsDev op, const double* __restrict__ F, double* E64,
-                                                long long es, double* __restrict__ r64, TL* __restrict__ rlp,
-                                                const TL* e0, const TL* e1, int has_e, Ctrl* ctrl, double* partials) {
-  constexpr int NIN = NF * NLF;
-  __shared__ double ws[BS / 32];
-  extern __shared__ double sdyn[];
-  if (ctrl_done(ctrl)) return;
-  const int o = *(volatile const int*)&ctrl->outer;
-  const int j = *(volatile const int*)&ctrl->inner_iter;
-  double* sLE = sdyn;
-  double* st = sLE + g.n_exp * NIN + threadIdx.x;
-  for (int i = threadIdx.x; i < g.n_exp * NIN; i += BS) sLE[i] = op.LE[i];
-  __syncthreads();
-  const double* Ecur = E64 + (long long)(o & 1) * es;
-  double* Enx = E64 + (long long)((o + 1) & 1) * es;
-  const TL* ecur = (j & 1) ? e1 : e0;
-  const long long K = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  double acc = 0.0;
-  if (K < g.nel) {
-    int c[3];
-    coords(g, K, c);
-    gather<NF, NLF, double, double>(g, Ecur, K, c, [&](int s, double v) { st[s * BS] = v; });
-    if (has_e) gather_lp<NF, NLF, TL, double>(g, ecur, K, c, [&](int s, double v) { st[s * BS] += v; });
-#pragma unroll
-    for (int c0 = 0; c0 < NIN; c0 += CH) {
-      double own[CH], fv[CH];
-#pragma unroll
-      for (int i = 0; i < CH; ++i) {
-        const int e = c0 + i;
-        own[i] = 0.0;
-        fv[i] = 0.0;
-        if (e < g.n_exp && row_live(g, e, NF)) {
-          const long long at = (long long)e * g.ld + K;
-          own[i] = Ecur[at] + (has_e ? (double)to_f(ecur[at]) : 0.0);
-          fv[i] = F[at];
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < CH; ++i) {
-        const int e = c0 + i;
-        if (e < g.n_exp && row_live(g, e, NF)) {
-          const long long at = (long long)e * g.ld + K;
-          double v = fv[i];
-          const double* row = sLE + e * NIN;
-#pragma unroll
-          for (int s = 0; s < NIN; ++s) v += row[s] * st[s * BS];
-          const double r = v - own[i];
-          Enx[at] = own[i];
-          r64[at] = r;
-          rlp[at] = from_f<TL>((float)r);
-          acc += r * r;
-        }
-      }
-    }
-  }
-  double tot;
-  if (arrive(ctrl, partials, acc, ws, &tot) && threadIdx.x == 0) {
-    ctrl->rnorm = sqrt(tot);
-    ctrl->outer = o + 1;
-    ctrl->iter += 1;
-    ctrl->fp64_sweeps += 1;
-  }
-}
-
-// Float64 stopping residual of the next exact sweep, sqrt(t(r)^T Q t(r)), fused with the
-// first useful inner sweep e = r + L_E t(r) (low precision).
-template <int NF, int NLF, typename TL>
-__global__ void __launch_bounds__(BS) k_inner_first(DevGeo g, OpsDev op, const double* __restrict__ r64,
-                                                    TL* __restrict__ e0, Ctrl* ctrl, double* partials,
-                                                    double* res_hist) {
-  constexpr int NIN = NF * NLF;
-  constexpr int NQ = NIN * (NIN + 1) / 2;
-  __shared__ double ws[BS / 32];
-  extern __shared__ double sdyn[];
-  if (ctrl_done(ctrl)) return;
-  double* sQ = sdyn;
-  float* sL = reinterpret_cast<float*>(sQ + NQ);
-  for (int i = threadIdx.x; i < NQ; i += BS) sQ[i] = op.Qp[i];
-  for (int i = threadIdx.x; i < g.n_exp * NIN; i += BS) sL[i] = op.LE32[i];
-  __syncthreads();
-  const long long K = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  double acc = 0.0;
-  if (K < g.nel) {
-    int c[3];
-    coords(g, K, c);
-    double d[NIN];
-    gather<NF, NLF, double, double>(g, r64, K, c, [&](int s, double v) { d[s] = v; });
-    int q = 0;
-#pragma unroll
-    for (int s = 0; s < NIN; ++s) {
-      double r = 0.0;
-#pragma unroll
-      for (int u = s; u < NIN; ++u) r += sQ[q + u - s] * d[u];
-      q += NIN - s;
-      acc += d[s] * r;
-    }
-    float df[NIN];
-#pragma unroll
-    for (int s = 0; s < NIN; ++s) df[s] = (float)d[s];
-#pragma unroll
-    for (int c0 = 0; c0 < NIN; c0 += CH) {
-      float rv[CH];
-#pragma unroll
-      for (int i = 0; i < CH; ++i) rv[i] = (c0 + i < g.n_exp && row_live(g, c0 + i, NF)) ? (float)r64[(long long)(c0 + i) * g.ld + K] : 0.f;
-#pragma unroll
-      for (int i = 0; i < CH; ++i) {
-        const int e = c0 + i;
-        if (e < g.n_exp && row_live(g, e, NF)) {
-          float v = rv[i];
-          const float* row = sL + e * NIN;
-#pragma unroll
-          for (int s = 0; s < NIN; ++s) v = fmaf(row[s], df[s], v);
-          e0[(long long)e * g.ld + K] = from_f<TL>(v);
-        }
-      }
-    }
-  }
-  double tot;
-  if (arrive(ctrl, partials, acc, ws, &tot) && threadIdx.x == 0) {
-    decide(ctrl, tot, res_hist, false);
-    ctrl->inner_iter = 0;
-    ctrl->inner_done = 0;
-  }
-}
-
-// Grid barrier plus sum of one double per block, for cooperative launches.  The arrival
-// counter only grows (cleared before the launch): barrier number b completes when it
-// reaches (b+1) * gridDim.x.  Thread 0 publishes the block's partial, arrives with a
-// release add and polls with acquire loads (bounded by ~1 s of SM clock, then
-// ctrl->timeout); warp 0 then sums the partials in block order with a fixed shuffle tree,
-// so every block obtains the same total.
-template <int NT>
-__device__ double barrier_sum(double* part, unsigned* count, unsigned nb, double mine, Ctrl* ctrl, double* s_out,
-                              int* s_flag) {
-  // GB300's float64 rate is a small fraction of float32: every per-thread step here is
-  // float32, and only thread 0 touches float64 (the published partial and the final sum)
-  __shared__ float wred[NT / 32];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    part[blockIdx.x] = mine;
-    if ((int)blockIdx.x != ctrl->stall_block) red_release_add(count, 1u);
-    const unsigned target = nb * gridDim.x;
-    const long long lim = ctrl->wait_cycles;
-    const long long t0 = clock64();
-    while (ld_acquire_u32(count) < target) {
-      if (clock64() - t0 > lim) { atomicExch(&ctrl->timeout, 1); break; }
-    }
-    *s_flag = *(volatile int*)&ctrl->timeout;
-  }
-  __syncthreads();
-  // every thread loads its share of the partials at once (one round trip), then a fixed tree
-  float v = 0.f;
-  for (int i = threadIdx.x; i < (int)gridDim.x; i += NT) v += (float)__ldcg(part + i);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) wred[threadIdx.x >> 5] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < NT / 32; ++w) t += (double)wred[w];
-    *s_out = t;
-  }
-  __syncthreads();
-  return *s_out;
-}
-
-
-// Persistent inner loop on the correction equation: e_{j+1} = r + L_E t(e_j), until the
-// step norm falls below inner_rtol * ||r||, inner_max sweeps, or the sweep budget.  One
-// cooperative launch runs many sweeps; each sweep ends with a grid barrier after which every
-// block sums the per-block partials in the same fixed order, so all blocks take the same
-// decision.  Block 0 records the loop state.
-template <int NF, int NLF, typename TL>
-__global__ void __launch_bounds__(PBS) k_inner_persist(DevGeo g, OpsDev op, const TL* __restrict__ rlp, TL* e0,
-                                                       TL* e1, Ctrl* ctrl, double* partials) {
-  constexpr int NIN = NF * NLF;
-  __shared__ double s_tot;
-  __shared__ int s_to, s_stop;
-  __shared__ float wsum_p[PBS / 32];
-  extern __shared__ float sf[];
-  if (ctrl_done(ctrl) || *(volatile const int*)&ctrl->inner_done) return;
-  int j = *(volatile const int*)&ctrl->inner_iter;
-  const int iter0 = *(volatile const int*)&ctrl->iter;
-  const int lowp0 = *(volatile const int*)&ctrl->lowp_sweeps;
-  const int max_iters = ctrl->max_iters, inner_max = ctrl->inner_max;
-  const double lim = ctrl->inner_rtol * ctrl->rnorm;
-  for (int i = threadIdx.x; i < g.n_exp * NIN; i += PBS) sf[i] = op.LE32[i];
-  __syncthreads();
-  const long long stride = (long long)gridDim.x * PBS;
-  for (int s = 0;; ++s) {
-    const TL* __restrict__ ec = (j & 1) ? e1 : e0;
-    TL* __restrict__ en = (j & 1) ? e0 : e1;
-    float acc = 0.f;
-    for (long long K = (long long)blockIdx.x * PBS + threadIdx.x; K < g.nel; K += stride) {
-      int c[3];
-      coords(g, K, c);
-      float t[NIN];
-      gather_lp<NF, NLF, TL, float>(g, ec, K, c, [&](int q, float v) { t[q] = v; });
-#pragma unroll
-      for (int c0 = 0; c0 < NIN; c0 += CH) {
-        float rv[CH], ov[CH];
-#pragma unroll
-        for (int i = 0; i < CH; ++i) {
-          const int e = c0 + i;
-          rv[i] = 0.f;
-          ov[i] = 0.f;
-          if (e < g.n_exp && row_live(g, e, NF)) {
-            const long long at = (long long)e * g.ld + K;
-            rv[i] = to_f(rlp[at]);
-            ov[i] = ldcg_f(ec + at);
-          }
-        }
-#pragma unroll
-        for (int i = 0; i < CH; ++i) {
-          const int e = c0 + i;
-          if (e < g.n_exp && row_live(g, e, NF)) {
-            float v = rv[i];
-            const float* row = sf + e * NIN;
-#pragma unroll
-            for (int q = 0; q < NIN; ++q) v = fmaf(row[q], t[q], v);
-            const TL nv = from_f<TL>(v);
-            const float dl = to_f(nv) - ov[i];
-            acc = fmaf(dl, dl, acc);
-            en[(long long)e * g.ld + K] = nv;
-          }
-        }
-      }
-    }
-    const int it = iter0 + s + 1;
-    float bsf = acc;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) bsf += __shfl_down_sync(0xffffffffu, bsf, o);
-    if ((threadIdx.x & 31) == 0) wsum_p[threadIdx.x >> 5] = bsf;
-    __syncthreads();
-    double bs = 0.0;
-    if (threadIdx.x == 0)
-      for (int w = 0; w < PBS / 32; ++w) bs += (double)wsum_p[w];
-    const double tot = barrier_sum<PBS>(partials + (size_t)(s & 1) * gridDim.x, &ctrl->bar_count, (unsigned)(s + 1), bs,
-                                        ctrl, &s_tot, &s_to);
-    if (s_to) break;
-    j += 1;
-    if (threadIdx.x == 0) {
-      const double step = sqrt(tot);
-      const bool stop = step <= lim || j >= inner_max || it >= max_iters || !(step == step) || isinf(step);
-      s_stop = stop ? 1 : 0;
-      if (blockIdx.x == 0) {
-        ctrl->inner_iter = j;
-        ctrl->iter = it;
-        ctrl->lowp_sweeps = lowp0 + s + 1;
-        ctrl->inner_step = step;
-        if (stop) ctrl->inner_done = 1;
-      }
-    }
-    __syncthreads();
-    if (s_stop) break;
-  }
-}
-
-// Low-precision operator passed by value: the kernel reads it from the parameter (constant)
-// bank, so every multiply-add takes its matrix entry straight from there.
-template <int NF, int NLF, bool PER_AXIS>
-struct LTile {
-  static constexpr int NIN = NF * NLF;
-  static constexpr int NEXP = PER_AXIS ? NF * (NLF / 2) : NF * NLF;
-  float L[NEXP][NIN];
-};
-
-// Persistent inner loop with block-resident state.  Block b owns elements
-// [b*epb, b*epb + epb); their own exports e_j and the residual r stay in shared memory
-// (TL precision: the values the neighbours see), with each element's boundary-face mask.
-// LPE lanes of a warp share one element: lane l gathers the traces of the faces
-// f = l, l + LPE, ... (own exports from shared memory, the neighbour's from global memory),
-// the lanes exchange them by shuffles, and lane l computes the export rows of its faces
-// (per-face layout) or axes (per-axis layout), reading the operator from the parameter
-// bank.  Per sweep only neighbours' exports cross global memory; the loop decision is the
-// same as k_inner_persist's.
-template <int NF, int NLF, bool PER_AXIS, typename TL, int NT, int LPE>
-__global__ void __launch_bounds__(NT) k_inner_tile(const DevGeo g, const TL* __restrict__ rlp, TL* e0, TL* e1,
-                                                   Ctrl* ctrl, double* partials, const int epb,
-                                                   const LTile<NF, NLF, PER_AXIS> Lp) {
-  constexpr int NIN = NF * NLF;
-  constexpr int NEXP = LTile<NF, NLF, PER_AXIS>::NEXP;
-  constexpr int FPL = NLF / LPE;                    // faces per lane
-  constexpr int NBLK = PER_AXIS ? NLF / 2 : NLF;    // export row blocks (axes or faces)
-  constexpr int EPP = NT / LPE;                     // elements per pass
-  static_assert(NLF % LPE == 0 && 32 % LPE == 0, "lanes per element must divide faces and warps");
-  __shared__ double s_tot;
-  __shared__ int s_to, s_stop;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  if (ctrl_done(ctrl) || *(volatile const int*)&ctrl->inner_done) return;
-  int j = *(volatile const int*)&ctrl->inner_iter;
-  const int iter0 = *(volatile const int*)&ctrl->iter;
-  const int lowp0 = *(volatile const int*)&ctrl->lowp_sweeps;
-  const int max_iters = ctrl->max_iters, inner_max = ctrl->inner_max;
-  const double lim = ctrl->inner_rtol * ctrl->rnorm;
-  TL* ev = reinterpret_cast<TL*>(smraw);        // [NEXP][epb]
-  TL* rv = ev + (size_t)NEXP * epb;             // [NEXP][epb]
-  unsigned char* bm = reinterpret_cast<unsigned char*>(rv + (size_t)NEXP * epb);
-  const int ld = (int)g.ld;
-  const int K0 = blockIdx.x * epb;
-  const int cnt = min(epb, (int)g.nel - K0);
-  unsigned* count = &ctrl->bar_count;
-  {
-    const TL* ec = (j & 1) ? e1 : e0;
-    for (int le = threadIdx.x; le < cnt; le += NT) {
-      const int K = K0 + le;
-      int c[3];
-      coords(g, K, c);
-      unsigned m = 0;
-#pragma unroll
-      for (int f = 0; f < NLF; ++f) m |= (on_bnd(g, c, f) ? 1u : 0u) << f;
-      bm[le] = (unsigned char)m;
-#pragma unroll
-      for (int e = 0; e < NEXP; ++e) {
-        ev[e * epb + le] = ((g.live >> e) & 1ull) ? ec[e * ld + K] : from_f<TL>(0.f);
-        rv[e * epb + le] = ((g.live >> e) & 1ull) ? rlp[e * ld + K] : from_f<TL>(0.f);
-      }
-    }
-  }
-  __syncthreads();
-  const int lane = threadIdx.x & (LPE - 1);
-  const int wl = threadIdx.x & 31;
-  const int gbase = wl & ~(LPE - 1);
-  const int npass = (cnt + EPP - 1) / EPP;
-  for (int s = 0;; ++s) {
-    const TL* __restrict__ ec = (j & 1) ? e1 : e0;
-    TL* __restrict__ en = (j & 1) ? e0 : e1;
-    float acc = 0.f;
-    for (int pass = 0; pass < npass; ++pass) {
-      const int le = pass * EPP + threadIdx.x / LPE;
-      const bool valid = le < cnt;
-      const int K = K0 + le;
-      const unsigned m = valid ? bm[le] : 0u;
-      // a1: this lane's faces.  The neighbours' exports are read with unconditional loads
-      // (an in-bounds index where nothing is needed), so all of them are in flight at once.
-      float lt[FPL][NF];
-      int nbi[FPL];
-      bool nbm[FPL];
-      float wo[FPL];
-#pragma unroll
-      for (int i = 0; i < FPL; ++i) {
-        const int f = i * LPE + lane;                 // runtime face of this lane
-        const int kind = g.kind[f];
-        const bool bnd = (m >> f) & 1u;
-        const int a = f >> 1;
-        const int ns = PER_AXIS ? a * NF : (f ^ 1) * NF;
-        const int Kn = K + ((f & 1) ? (int)g.stride[a] : -(int)g.stride[a]);
-        nbm[i] = valid && !bnd && (kind == FK_NBR_D || kind == FK_SUM_D);
-        nbi[i] = nbm[i] ? ns * ld + Kn : ns * ld + K0;
-        wo[i] = !valid ? 0.f
-                : kind == FK_OWN_D ? 1.f
-                : kind == FK_SUM_D ? (!bnd ? 1.f : (g.bc_mirror ? 2.f : 0.f)) : 0.f;
-      }
-#pragma unroll
-      for (int i = 0; i < FPL; ++i)
-#pragma unroll
-        for (int q = 0; q < NF; ++q) lt[i][q] = to_f(ec[nbi[i] + q * ld]);
-      const int lc = valid ? le : 0;
-#pragma unroll
-      for (int i = 0; i < FPL; ++i) {
-        const int f = i * LPE + lane;
-        const int os = PER_AXIS ? (f >> 1) * NF : f * NF;
-#pragma unroll
-        for (int q = 0; q < NF; ++q)
-          lt[i][q] = wo[i] * to_f(ev[(os + q) * epb + lc]) + (nbm[i] ? lt[i][q] : 0.f);
-      }
-      // exchange: every lane of the element obtains all NIN traces
-      float t[NIN];
-#pragma unroll
-      for (int f = 0; f < NLF; ++f)
-#pragma unroll
-        for (int q = 0; q < NF; ++q) {
-          if constexpr (LPE == 1) t[f * NF + q] = lt[f][q];
-          else t[f * NF + q] = __shfl_sync(0xffffffffu, lt[f / LPE][q], gbase + (f % LPE));
-        }
-      if constexpr (LPE > 1) __syncwarp();
-      // a3/a4: this lane's export rows
-      if (valid) {
-#pragma unroll
-        for (int rb = 0; rb < NBLK; ++rb) {
-          if (LPE > 1 && rb % LPE != lane) continue;
-#pragma unroll
-          for (int q = 0; q < NF; ++q) {
-            const int e = rb * NF + q;
-            float v = to_f(rv[e * epb + le]);
-#pragma unroll
-            for (int k = 0; k < NIN; ++k) v = fmaf(Lp.L[e][k], t[k], v);
-            const TL nv = from_f<TL>(v);
-            const float d = to_f(nv) - to_f(ev[e * epb + le]);
-            acc = fmaf(d, d, acc);
-            ev[e * epb + le] = nv;
-            if ((g.live >> e) & 1ull) en[e * ld + K] = nv;
-          }
-        }
-      }
-      if constexpr (LPE > 1) __syncwarp();
-    }
-    const int it = iter0 + s + 1;
-    float bs = acc;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) bs += __shfl_down_sync(0xffffffffu, bs, o);
-    __shared__ float wsum[NT / 32];
-    if (wl == 0) wsum[threadIdx.x >> 5] = bs;
-    __syncthreads();
-    double blk = 0.0;
-    if (threadIdx.x == 0)
-      for (int w = 0; w < NT / 32; ++w) blk += (double)wsum[w];
-    const double tot = barrier_sum<NT>(partials + (size_t)(s & 1) * gridDim.x, count, (unsigned)(s + 1), blk, ctrl, &s_tot, &s_to);
-    if (s_to) break;
-    j += 1;
-    if (threadIdx.x == 0) {
-      const double step = sqrt(tot);
-      const bool stop = step <= lim || j >= inner_max || it >= max_iters || !(step == step) || isinf(step);
-      s_stop = stop ? 1 : 0;
-      if (blockIdx.x == 0) {
-        ctrl->inner_iter = j;
-        ctrl->iter = it;
-        ctrl->lowp_sweeps = lowp0 + s + 1;
-        ctrl->inner_step = step;
-        if (stop) ctrl->inner_done = 1;
-      }
-    }
-    __syncthreads();
-    if (s_stop) break;
-  }
-}
-
-// Launch the tile kernel when its block state fits in shared memory; returns
-// cudaErrorNotSupported (nothing launched) otherwise.
-template <int NF, int NLF, bool PER_AXIS, typename TL, int NT, int LPE>
-cudaError_t launch_tile_v(MixedArgs& m, TL* rl, TL* e0, TL* e1) {
-  using LT = LTile<NF, NLF, PER_AXIS>;
-  const LaunchArgs& a = m.base;
-  if (!m.LE32h || a.g.n_exp != LT::NEXP || (long long)a.g.ld * LT::NEXP >= (1LL << 31)) return cudaErrorNotSupported;
-  auto k = k_inner_tile<NF, NLF, PER_AXIS, TL, NT, LPE>;
-  int dev = 0, sms = 0, smem_max = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  smem_max -= 1024;   // static shared memory of the kernel
-  const long long nel = a.g.nel;
-  for (int bps = 2; bps >= 1; --bps) {
-    long long grid = (long long)bps * sms;
-    const long long cap = (nel + 63) / 64;          // at least 64 elements per block
-    if (grid > cap) grid = cap;
-    if (grid > m.max_grid) grid = m.max_grid;
-    if (grid < 1) grid = 1;
-    const long long epb = (nel + grid - 1) / grid;
-    grid = (nel + epb - 1) / epb;
-    if (grid > m.slots / 2) continue;
-    const size_t smem = (size_t)epb * (2 * LT::NEXP * sizeof(TL) + 1) + 16;
-    if (smem > (size_t)smem_max) continue;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int per = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, NT, smem);
-    if (e != cudaSuccess) return e;
-    if ((long long)per * sms < grid) continue;
-    LT L;
-    for (int r = 0; r < LT::NEXP; ++r)
-      for (int q = 0; q < LT::NIN; ++q) L.L[r][q] = m.LE32h[r * LT::NIN + q];
-    DevGeo gg = a.g;
-    const TL* rlc = rl;
-    Ctrl* ct = a.ctrl;
-    double* pp = a.partials;
-    int ep = (int)epb;
-    e = cudaMemsetAsync(&a.ctrl->bar_count, 0, sizeof(unsigned), a.stream);
-    if (e != cudaSuccess) return e;
-    void* args[] = {&gg, &rlc, &e0, &e1, &ct, &pp, &ep, &L};
-    e = cudaLaunchCooperativeKernel((const void*)k, dim3((unsigned)grid), dim3(NT), args, smem, a.stream);
-    if (e != cudaSuccess) return e;
-    return cudaGetLastError();
-  }
-  return cudaErrorNotSupported;
-}
-
-// Persistent inner loop for 2D meshes with register-resident state: LPE lanes per element
-// (2 or 4); lane l owns the faces f = l, l + LPE.  For each of its faces a lane keeps in
-// registers the exports of that face (per-face layout) or of the face's axis when the face is
-// the axis' outflow face (per-axis layout), and the matching residual values; it gathers its
-// faces' traces (own registers + the neighbour's exports from global memory), broadcasts them
-// to the element's other lanes by shuffles, and accumulates its rows as the traces arrive.
-// The operator sits in shared memory transposed and padded, LT[k][rowblock * RW + r], so one
-// 128-bit load gives a lane the coefficients of trace k for 4 rows of one block.  Every thread
-// owns one (element, lane) pair for the whole launch.
-template <int NF, bool PER_AXIS, typename TL, int LPE, int NT>
-__global__ void __launch_bounds__(NT, 1024 / NT) k_inner_reg(const DevGeo g, const TL* __restrict__ rlp, TL* e0,
-                                                             TL* e1, Ctrl* ctrl, double* partials,
-                                                             const float* __restrict__ LTg, const int epb) {
-  constexpr int NIN = 4 * NF, FPL = 4 / LPE;
-  constexpr int RW = (NF + 3) & ~3;          // padded row-block width
-  constexpr int NRB = 4;                     // row blocks stored (faces; axes use the first 2)
-  __shared__ __align__(16) float LT[NIN * NRB * RW];
-  __shared__ float wsum[NT / 32], wdec[NT / 32];
-  __shared__ int s_to;
-  if (ctrl_done(ctrl) || *(volatile const int*)&ctrl->inner_done) return;
-  int j = *(volatile const int*)&ctrl->inner_iter;
-  const int iter0 = *(volatile const int*)&ctrl->iter;
-  const int lowp0 = *(volatile const int*)&ctrl->lowp_sweeps;
-  const int max_iters = ctrl->max_iters, inner_max = ctrl->inner_max;
-  const double lim = ctrl->inner_rtol * ctrl->rnorm;
-  for (int i = threadIdx.x; i < NIN * NRB * RW; i += NT) LT[i] = LTg[i];
-  const int lane = threadIdx.x % LPE;
-  const int gbase = (threadIdx.x & 31) - lane;
-  const int K = blockIdx.x * epb + threadIdx.x / LPE;   // epb <= NT / LPE elements per block
-  const bool valid = (int)(threadIdx.x / LPE) < epb && K < (int)g.nel;
-  const int ld = (int)g.ld;
-  int c[3] = {0, 0, 0};
-  if (valid) coords(g, K, c);
-  // per face of this lane: where the neighbour's exports sit (nbi, an in-bounds index also
-  // where nothing is read, so that every sweep's gathers are unconditional loads) and how
-  // the trace combines own (wo) and neighbour (wn) values
-  int kind[FPL], nbi[FPL], row0[FPL];
-  bool rows[FPL], nbm[FPL];
-  float wo[FPL];
-#pragma unroll
-  for (int i = 0; i < FPL; ++i) {
-    const int f = lane + LPE * i, a = f >> 1;
-    kind[i] = g.kind[f];
-    const bool bnd = valid && on_bnd(g, c, f);
-    const int Kn = K + ((f & 1) ? (int)g.stride[a] : -(int)g.stride[a]);
-    const int ns = PER_AXIS ? a * NF : (f ^ 1) * NF;
-    row0[i] = PER_AXIS ? a * NF : f * NF;
-    const bool owns = PER_AXIS ? kind[i] == FK_OWN_D : (kind[i] == FK_SUM_D || kind[i] == FK_OWN_D);
-    rows[i] = valid && owns && ((g.live >> row0[i]) & 1ull);
-    const bool nb = valid && !bnd && (kind[i] == FK_NBR_D || kind[i] == FK_SUM_D);
-    nbi[i] = nb ? ns * ld + Kn : ns * ld + (valid ? K : 0);
-    nbm[i] = nb;
-    wo[i] = !valid ? 0.f
-            : kind[i] == FK_OWN_D ? 1.f
-            : kind[i] == FK_SUM_D ? (!bnd ? 1.f : (g.bc_mirror ? 2.f : 0.f)) : 0.f;
-  }
-  float ev[FPL][NF], rv[FPL][NF];
-  {
-    const TL* ec = (j & 1) ? e1 : e0;
-#pragma unroll
-    for (int i = 0; i < FPL; ++i)
-#pragma unroll
-      for (int r = 0; r < NF; ++r) {
-        ev[i][r] = rows[i] ? to_f(ec[(row0[i] + r) * ld + K]) : 0.f;
-        rv[i][r] = rows[i] ? to_f(rlp[(row0[i] + r) * ld + K]) : 0.f;
-      }
-  }
-  __syncthreads();
-  unsigned* count = &ctrl->bar_count;
-  float* partf = reinterpret_cast<float*>(partials);
-  const float limf = (float)lim;
-  for (int s = 0;; ++s) {
-    const TL* __restrict__ ec = ((j + s) & 1) ? e1 : e0;
-    TL* __restrict__ en = ((j + s) & 1) ? e0 : e1;
-    // previous sweep's partials (one round trip, together with the trace gathers below)
-    float pv = 0.f;
-    if (s > 0)
-      for (int i = threadIdx.x; i < (int)gridDim.x; i += NT) pv += __ldcg(partf + ((s - 1) & 1) * gridDim.x + i);
-    float lt[FPL][NF];
-#pragma unroll
-    for (int i = 0; i < FPL; ++i)
-#pragma unroll
-      for (int q = 0; q < NF; ++q) lt[i][q] = ldcg_f(ec + nbi[i] + q * ld);
-#pragma unroll
-    for (int i = 0; i < FPL; ++i)
-#pragma unroll
-      for (int q = 0; q < NF; ++q) lt[i][q] = wo[i] * ev[i][q] + (nbm[i] ? lt[i][q] : 0.f);   // never 0 * (unread)
-    float acc[FPL][RW];
-#pragma unroll
-    for (int i = 0; i < FPL; ++i)
-#pragma unroll
-      for (int r = 0; r < RW; ++r) acc[i][r] = r < NF ? rv[i][r] : 0.f;
-#pragma unroll
-    for (int src = 0; src < LPE; ++src)
-#pragma unroll
-      for (int is = 0; is < FPL; ++is)
-#pragma unroll
-        for (int q = 0; q < NF; ++q) {
-          const float x = __shfl_sync(0xffffffffu, lt[is][q], gbase + src);
-          const int k = (src + LPE * is) * NF + q;        // trace index: face src + LPE*is, node q
-#pragma unroll
-          for (int i = 0; i < FPL; ++i) {
-            const int rbi = row0[i] / NF;
-            const float* col = LT + (k * NRB + rbi) * RW;
-#pragma unroll
-            for (int r4 = 0; r4 < RW; r4 += 4) {
-              const float4 cf = *reinterpret_cast<const float4*>(col + r4);
-              acc[i][r4 + 0] = fmaf(cf.x, x, acc[i][r4 + 0]);
-              acc[i][r4 + 1] = fmaf(cf.y, x, acc[i][r4 + 1]);
-              acc[i][r4 + 2] = fmaf(cf.z, x, acc[i][r4 + 2]);
-              acc[i][r4 + 3] = fmaf(cf.w, x, acc[i][r4 + 3]);
-            }
-          }
-        }
-    // decision on the s sweeps done so far (the last one's step norm when s > 0), taken
-    // after the local apply so that the partial sums have arrived.  Every thread folds the
-    // warp sums in the same order: all threads of all blocks take the same decision.
-    {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) pv += __shfl_xor_sync(0xffffffffu, pv, o);
-      if ((threadIdx.x & 31) == 0) wdec[threadIdx.x >> 5] = pv;
-      __syncthreads();
-      float tot = 0.f;
-#pragma unroll
-      for (int w = 0; w < NT / 32; ++w) tot += wdec[w];
-      const float step = sqrtf(tot);
-      const bool budget = j + s >= inner_max || iter0 + s >= max_iters;
-      const bool stop = budget || (s > 0 && (step <= limf || !(step == step) || isinf(step)));
-      if (threadIdx.x == 0 && blockIdx.x == 0) {
-        ctrl->inner_iter = j + s;
-        ctrl->iter = iter0 + s;
-        ctrl->lowp_sweeps = lowp0 + s;
-        if (s > 0) ctrl->inner_step = (double)step;
-        if (stop) ctrl->inner_done = 1;
-      }
-      if (stop) break;
-    }
-    float st = 0.f;
-#pragma unroll
-    for (int i = 0; i < FPL; ++i) {
-      if (!rows[i]) continue;
-#pragma unroll
-      for (int r = 0; r < NF; ++r) {
-        const TL nv = from_f<TL>(acc[i][r]);
-        const float nvf = to_f(nv);
-        const float d = nvf - ev[i][r];
-        st = fmaf(d, d, st);
-        ev[i][r] = nvf;
-        en[(row0[i] + r) * ld + K] = nv;
-      }
-    }
-    const float blk = sum_partials<NT>(st, wsum);
-    arrive_wait(partf + (s & 1) * gridDim.x, count, (unsigned)(s + 1), blk, ctrl, &s_to);
-    if (s_to) break;
-  }
-}
-
-// Launch k_inner_reg with the most lanes per element whose grid is co-resident (NT threads
-// per block: 512, two blocks per SM, or 1024, one block per SM and half the barrier arrivals).
-template <int NF, bool PER_AXIS, typename TL, int LPE, int NT>
-cudaError_t launch_reg_v(MixedArgs& m, TL* rl, TL* e0, TL* e1) {
-  constexpr int NIN = 4 * NF, RW = (NF + 3) & ~3, NRB = 4;
-  const LaunchArgs& a = m.base;
-  if (a.g.dim != 2 || !m.LE32h || !m.dLT || (long long)a.g.ld * a.g.n_exp >= (1LL << 31)) return cudaErrorNotSupported;
-  auto k = k_inner_reg<NF, PER_AXIS, TL, LPE, NT>;
-  int dev = 0, sms = 0, per = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, NT, 0);
-  if (e != cudaSuccess) return e;
-  // the grid is a multiple of the SM count with the elements spread evenly over it
-  long long grid = (long long)per * sms;
-  const long long small = (a.g.nel + 127) / 128;   // small problems keep >= 128 elements per block
-  if (grid > small) grid = small;
-  if (grid > m.max_grid) grid = m.max_grid;
-  const long long epb = (a.g.nel + grid - 1) / grid;
-  if (epb > NT / LPE) return cudaErrorNotSupported;
-  grid = (a.g.nel + epb - 1) / epb;
-  if (grid > m.slots / 2) return cudaErrorNotSupported;
-  // transposed, padded operator: LT[k][rb * RW + r] = L_E[rb * NF + r][k]
-  std::vector<float> lt((size_t)NIN * NRB * RW, 0.f);
-  const int nrb = a.g.n_exp / NF;
-  for (int kk = 0; kk < NIN; ++kk)
-    for (int b = 0; b < nrb; ++b)
-      for (int r = 0; r < NF; ++r) lt[((size_t)kk * NRB + b) * RW + r] = m.LE32h[(b * NF + r) * NIN + kk];
-  if (m.lt_kind != 1) {
-    e = cudaMemcpyAsync(m.dLT, lt.data(), lt.size() * sizeof(float), cudaMemcpyHostToDevice, a.stream);
-    if (e != cudaSuccess) return e;
-    m.lt_kind = 1;
-  }
-  e = cudaMemsetAsync(&a.ctrl->bar_count, 0, sizeof(unsigned), a.stream);
-  if (e != cudaSuccess) return e;
-  DevGeo gg = a.g;
-  const TL* rlc = rl;
-  Ctrl* ct = a.ctrl;
-  double* pp = a.partials;
-  const float* ltp = m.dLT;
-  int ep = (int)epb;
-  void* args[] = {&gg, &rlc, &e0, &e1, &ct, &pp, &ltp, &ep};
-  e = cudaLaunchCooperativeKernel((const void*)k, dim3((unsigned)grid), dim3(NT), args, 0, a.stream);
-  if (e != cudaSuccess) return e;
-  return cudaGetLastError();
-}
-
-template <int NF, bool PER_AXIS, typename TL>
-cudaError_t launch_reg(MixedArgs& m, TL* rl, TL* e0, TL* e1) {
-  cudaError_t e;
-  if (m.reg_nt == 1024) {
-    e = launch_reg_v<NF, PER_AXIS, TL, 2, 1024>(m, rl, e0, e1);
-    if (e != cudaErrorNotSupported) return e;
-  }
-  e = launch_reg_v<NF, PER_AXIS, TL, 4, 512>(m, rl, e0, e1);
-  if (e != cudaErrorNotSupported) return e;
-  return launch_reg_v<NF, PER_AXIS, TL, 2, 512>(m, rl, e0, e1);
-}
-
-// Tile kernel shape: one element per thread (default) or, with IHDG_TILE_LPE=4 on 2D
-// meshes, four lanes per element (one face each) with shuffled traces.
-template <int NF, int NLF, bool PER_AXIS, typename TL>
-cudaError_t launch_tile(MixedArgs& m, TL* rl, TL* e0, TL* e1) {
-  return launch_tile_v<NF, NLF, PER_AXIS, TL, 512, 1>(m, rl, e0, e1);
-}
-
-inline unsigned grid_for(long long n) { return (unsigned)((n + BS - 1) / BS); }
-
-template <typename TL>
-struct MixedRunner {
-  template <int NF, int NLF>
-  struct Fn {
-    static cudaError_t run(MixedArgs& m, int which, int has_e, int count) {
-      constexpr int NIN = NF * NLF;
-      const LaunchArgs& a = m.base;
-      TL* e0 = static_cast<TL*>(m.e[0]);
-      TL* e1 = static_cast<TL*>(m.e[1]);
-      TL* rl = static_cast<TL*>(m.rlp);
-      if (which == 0) {
-        size_t smem = ((size_t)a.g.n_exp * NIN + (size_t)NIN * BS) * sizeof(double);
-        auto k = k_outer64<NF, NLF, TL>;
-        if (smem > 32 * 1024) {
-          cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-          if (e != cudaSuccess) return e;
-        }
-        k<<<grid_for(a.g.nel), BS, smem, a.stream>>>(a.g, a.op, a.F, m.E64, a.ring_stride, m.r64, rl, e0, e1, has_e,
-                                                      a.ctrl, a.partials);
-      } else if (which == 1) {
-        size_t smem = (size_t)NIN * (NIN + 1) / 2 * sizeof(double) + (size_t)a.g.n_exp * NIN * sizeof(float);
-        auto k = k_inner_first<NF, NLF, TL>;
-        if (smem > 32 * 1024) {
-          cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-          if (e != cudaSuccess) return e;
-        }
-        k<<<grid_for(a.g.nel), BS, smem, a.stream>>>(a.g, a.op, m.r64, e0, a.ctrl, a.partials, a.res_hist);
-      } else {
-        if (m.use_tc) {
-          cudaError_t ce;
-          if constexpr (std::is_same<TL, __nv_bfloat16>::value) {
-            ce = a.g.per_axis ? launch_tc<NF, NLF, true, TC_BF16>(m, rl, e0, e1)
-                              : launch_tc<NF, NLF, false, TC_BF16>(m, rl, e0, e1);
-          } else if (m.prec == IHDG_MIXED_TF32) {
-            ce = a.g.per_axis ? launch_tc<NF, NLF, true, TC_TF32>(m, rl, e0, e1)
-                              : launch_tc<NF, NLF, false, TC_TF32>(m, rl, e0, e1);
-          } else {
-            ce = a.g.per_axis ? launch_tc<NF, NLF, true, TC_TF32X4>(m, rl, e0, e1)
-                              : launch_tc<NF, NLF, false, TC_TF32X4>(m, rl, e0, e1);
-          }
-          if (ce != cudaErrorNotSupported) return ce;
-          // shapes the tensor-core kernel does not take (n_in > 64 or n_exp > 32) fall through
-          // to the CUDA-core kernels in full float32
-        }
-        if (!m.no_tile) {
-          if constexpr (NLF == 4) {
-            if (m.tile_lpe != 1) {
-              cudaError_t re = a.g.per_axis ? launch_reg<NF, true, TL>(m, rl, e0, e1)
-                                            : launch_reg<NF, false, TL>(m, rl, e0, e1);
-              if (re != cudaErrorNotSupported) return re;
-            }
-          }
-          cudaError_t te = a.g.per_axis ? launch_tile<NF, NLF, true, TL>(m, rl, e0, e1)
-                                        : launch_tile<NF, NLF, false, TL>(m, rl, e0, e1);
-          if (te != cudaErrorNotSupported) return te;
-        }
-        // persistent cooperative launch: as many co-resident blocks as the elements need
-        size_t smem = (size_t)a.g.n_exp * NIN * sizeof(float);
-        auto k = k_inner_persist<NF, NLF, TL>;
-        int dev = 0, sms = 0, per = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, PBS, smem);
-        if (e != cudaSuccess) return e;
-        if (per < 1) return cudaErrorInvalidConfiguration;
-        long long need = (a.g.nel + PBS - 1) / PBS;
-        long long cap = (long long)per * sms;
-        int grid = (int)(need < cap ? need : cap);
-        if (grid > m.max_grid) grid = m.max_grid;
-        DevGeo gg = a.g;
-        OpsDev oo = a.op;
-        const TL* rlc = rl;
-        Ctrl* ct = a.ctrl;
-        double* pp = a.partials;
-        void* args[] = {&gg, &oo, &rlc, &e0, &e1, &ct, &pp};
-        e = cudaMemsetAsync(&a.ctrl->bar_count, 0, sizeof(unsigned), a.stream);
-        if (e != cudaSuccess) return e;
-        e = cudaLaunchCooperativeKernel((const void*)k, dim3(grid), dim3(PBS), args, smem, a.stream);
-        if (e != cudaSuccess) return e;
-      }
-      return cudaGetLastError();
-    }
-  };
-};
-
-template <typename TL>
-cudaError_t mixed_launch(MixedArgs& m, int which, int has_e, int count) {
-  const DevGeo& g = m.base.g;
-  using R = MixedRunner<TL>;
-  if (g.dim == 2) {
-    switch (g.nf) {
-      case 2: return R::template Fn<2, 4>::run(m, which, has_e, count);
-      case 3: return R::template Fn<3, 4>::run(m, which, has_e, count);
-      case 4: return R::template Fn<4, 4>::run(m, which, has_e, count);
-      case 5: return R::template Fn<5, 4>::run(m, which, has_e, count);
-    }
-  } else {
-    switch (g.nf) {
-      case 4: return R::template Fn<4, 6>::run(m, which, has_e, count);
-      case 9: return R::template Fn<9, 6>::run(m, which, has_e, count);
-    }
-  }
-  return cudaErrorNotSupported;
-}
 
 cudaError_t mlaunch(MixedArgs& m, int which, int has_e, int count) {
   if (m.prec == IHDG_MIXED_BF16) return mixed_launch<__nv_bfloat16>(m, which, has_e, count);

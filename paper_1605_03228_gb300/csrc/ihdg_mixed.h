@@ -39,6 +39,12 @@ struct MixedArgs {
   const float* LE32h = nullptr;  // host copy of the float32 operator (n_exp x n_in)
 };
 
+// One launch of the mixed loop's kernel `which` (0 outer float64 sweep, 1 residual check + first
+// inner sweep, 2 persistent inner loop) with TL low-precision storage; defined in
+// ihdg_mixed_kern.cuh and instantiated in ihdg_mixed_f32.cu and ihdg_mixed_bf16.cu.
+template <typename TL>
+cudaError_t mixed_launch(MixedArgs& m, int which, int has_e, int count);
+
 MixedLayout mixed_layout(const DevGeo& g, int prec);
 void mixed_bind(MixedArgs& m, char* region, const MixedLayout& L, int prec);
 // Runs the outer/inner loop after the first float64 sweep.  On return, (Eu, Eu2) are the
