@@ -8,7 +8,7 @@
  *   * Section 2, Eqs. (iHDGlocal), (iHDGtrace), Algorithm 1: the iteration.  Every element
  *     solves its local equation with the weighted trace of iterate k, independently of all
  *     others; the weighted trace of iterate k+1 is then formed face by face; the loop stops
- *     when ||u^{k+1} - u^k||_{L2} < tol (Section 6.1, Eq. (tolerancecriteriarelerror)).
+ *     when ||u^{k+1} - u^k||_{L2} < tol (Section 5.1, Eq. (tolerancecriteriarelerror)).
  *   * Section 3: scalar transport (Eqs. transportLocalk1, transportLocale) and linearized
  *     shallow water with backward Euler (Eq. localSolverDD and the trace formula below it).
  *   * Section 4.1: convection-diffusion in first-order form (Eqs. ErrorDDMCD1, ErrorDDMCD2,
@@ -168,24 +168,33 @@ typedef struct {
 typedef struct ihdg_ctx ihdg_ctx;
 
 /* Create a context bound to CUDA device `device`.  Fails with IHDG_ERR_CUDA when no such
- * device exists or it is not sm_103.  *out receives the context (caller destroys it). */
+ * device exists or it is not sm_103.  *out receives the context (caller destroys it).
+ * No counterpart in the paper: the context holds device state (operator images, scratch,
+ * the pinned loop-state readback) across calls.  ihdg_destroy frees it; NULL is ignored. */
 ihdg_status ihdg_create(ihdg_ctx** out, int device);
 void ihdg_destroy(ihdg_ctx* ctx);
-/* One-line description of the last failure on this context ("" when none).  Never NULL. */
+/* One-line description of the last failure on this context ("" when none).  Never NULL.
+ * No counterpart in the paper (error reporting of this library). */
 const char* ihdg_last_error(const ihdg_ctx* ctx);
 
-/* Sizes of every array for this problem (host-only; validates mesh and coefficients). */
+/* Sizes of every array for this problem (host-only; validates mesh and coefficients).  The
+ * spaces are those of Section 2 (volume space V_h, trace space M_h on the skeleton) with the
+ * Q^p / GLL reading given at the top of this file; n_exp and n_in describe this library's
+ * export-state form of the local solve (Section 2, Eq. iHDGlocal). */
 ihdg_status ihdg_problem_sizes(const ihdg_mesh* mesh, const ihdg_coeffs* coeffs, ihdg_sizes* out);
 
 /* Physical coordinates of the quadrature points where the caller samples f and g
- * (host-only).  vol_xyz: [n_el][nqv][dim]; bnd_xyz: [n_bface][nqf][dim]; either may be
+ * (host-only; the paper does not fix the rule: Gauss-Legendre, p+2 points per direction).  vol_xyz: [n_el][nqv][dim]; bnd_xyz: [n_bface][nqf][dim]; either may be
  * NULL.  The library samples nothing itself: the forcing and boundary data are inputs. */
 ihdg_status ihdg_quadrature_points(const ihdg_mesh* mesh, double* vol_xyz, double* bnd_xyz);
 
-/* Physical coordinates of the GLL nodes, [n_el][(p+1)^dim][dim] (host-only). */
+/* Physical coordinates of the GLL nodes, [n_el][(p+1)^dim][dim] (host-only): where the
+ * volume solution of every solve is reported (the nodal basis of V_h, Section 2). */
 ihdg_status ihdg_node_points(const ihdg_mesh* mesh, double* xyz);
 
-/* Steady solve (transport, convection-diffusion) by the iHDG iteration, host buffers.
+/* Steady solve (transport, convection-diffusion) by the iHDG iteration, host buffers:
+ * Algorithm 1 (Section 2, Eqs. iHDGlocal and iHDGtrace) on the equations of Section 3
+ * (transport) or Section 4.1 (convection-diffusion), stopped by the test of Section 5.1.
  *   f_qp      [n_el][nqv]        forcing f at the quadrature points
  *   g_qp      [n_bface][nqf]     Dirichlet / inflow data g at boundary quadrature points
  *                                (transport reads it on inflow faces only)
@@ -196,11 +205,13 @@ ihdg_status ihdg_solve(ihdg_ctx* ctx, const ihdg_mesh* mesh, const ihdg_coeffs* 
                        const double* f_qp, const double* g_qp, const ihdg_options* opts,
                        double* u_out, double* trace_out, ihdg_result* res);
 
-/* Device workspace the device-pointer calls need for this problem and precision. */
+/* Device workspace the device-pointer calls need for this problem and precision.  No
+ * counterpart in the paper (memory sizing of ihdg_solve_device / ihdg_swe_steps_device). */
 ihdg_status ihdg_workspace_bytes(const ihdg_mesh* mesh, const ihdg_coeffs* coeffs,
                                  const ihdg_options* opts, size_t* bytes);
 
-/* As ihdg_solve, but every array (including opts->u0) is DEVICE memory of the context's
+/* As ihdg_solve (Algorithm 1, same citations), but every array (including opts->u0) is
+ * DEVICE memory of the context's
  * device, workspace is caller-allocated device memory of at least ihdg_workspace_bytes(),
  * 256-byte aligned, and all work is ordered on `stream` (a cudaStream_t; NULL = legacy
  * default stream).  Returns after the solve has finished on the device. */
@@ -228,7 +239,8 @@ ihdg_status ihdg_solve_device_static(ihdg_ctx* ctx, const ihdg_mesh* mesh, const
                                      const ihdg_options* opts, double* d_u_out, double* d_trace_out,
                                      void* stream, ihdg_result* res);
 
-/* Autotuner of the mixed path: times complete solves of the caller's problem (host inputs as
+/* No counterpart in the paper (it has no precision or kernel choice).
+ * Autotuner of the mixed path: times complete solves of the caller's problem (host inputs as
  * for ihdg_solve) for every inner-kernel choice and a ladder of inner stopping ratios
  * (float32/tf32: 5e-4 .. 1e-2; bf16: 2e-2 .. 0.3), keeps the fastest that converges, and
  * returns it in *tuned (a copy of *opts with inner_kernel and inner_rtol set) with its device
@@ -250,8 +262,8 @@ ihdg_status ihdg_swe_steps(ihdg_ctx* ctx, const ihdg_mesh* mesh, const ihdg_coef
                            double* q_inout, int nsteps, const ihdg_options* opts,
                            int* iters_per_step, ihdg_result* res);
 
-/* Device-pointer form of ihdg_swe_steps (q and iters_per_step on the host as above are
- * replaced by device q; iters_per_step stays a host array). */
+/* Device-pointer form of ihdg_swe_steps (Section 3, Eq. localSolverDD; the same steps):
+ * q is device memory; iters_per_step stays a host array. */
 ihdg_status ihdg_swe_steps_device(ihdg_ctx* ctx, const ihdg_mesh* mesh,
                                   const ihdg_coeffs* coeffs, double* d_q_inout, int nsteps,
                                   const ihdg_options* opts, int* iters_per_step,
@@ -259,9 +271,10 @@ ihdg_status ihdg_swe_steps_device(ihdg_ctx* ctx, const ihdg_mesh* mesh,
                                   ihdg_result* res);
 
 /* Host-only inspection of the float64 per-element operators this library builds for a
- * problem (no device needed): which = 0 L_E (n_exp x n_in), 1 Q (n_in x n_in), 2 L_vol
- * (nvol x n_in), 3 R (n_exp x nvol), 4 forcing-to-export (n_exp x nqv), 5 forcing-to-volume
- * (nvol x nqv).  Row-major into data (may be NULL to query rows/cols only). */
+ * problem (no device needed), i.e. the precomputed local solve of Section 2, Eq. iHDGlocal:
+ * which = 0 L_E (n_exp x n_in), 1 Q (n_in x n_in), 2 L_vol (nvol x n_in), 3 R (n_exp x
+ * nvol), 4 forcing-to-export (n_exp x nqv), 5 forcing-to-volume (nvol x nqv).  Row-major
+ * into data (may be NULL to query rows/cols only). */
 ihdg_status ihdg_host_operator(const ihdg_mesh* mesh, const ihdg_coeffs* coeffs, int which,
                                int* rows, int* cols, double* data);
 
@@ -288,6 +301,21 @@ ihdg_status ihdg_submit(ihdg_ctx* ctx, const ihdg_mesh* mesh, const ihdg_coeffs*
                         ihdg_ticket* out);
 ihdg_status ihdg_poll(ihdg_ctx* ctx, ihdg_ticket ticket, ihdg_result* res);
 ihdg_status ihdg_fetch(ihdg_ctx* ctx, ihdg_ticket ticket, double* u_out, double* trace_out);
+
+/* Device peak rates that bound the sweep kernels where neither HBM bandwidth nor the bf16
+ * tensor rate does.  No counterpart in the paper: these are roofline denominators.  Each is
+ * the best of five timed launches of one probe kernel (after a warm-up launch) on `device`:
+ * float64 and float32 FMA rates (8 independent FMA chains per thread, 2 flops per FMA, full
+ * occupancy) and the L2 read bandwidth (ld.global.cg over a 48 MB buffer resident in L2).
+ * Allocates and frees its own device memory (a few MB).  Errors: IHDG_ERR_INVALID (null
+ * out), IHDG_ERR_CUDA (no such device, launch failure), IHDG_ERR_NOMEM. */
+typedef struct {
+  double fp64_fma_tflops;
+  double fp32_fma_tflops;
+  double l2_read_gbs;
+  int sms;
+} ihdg_peaks;
+ihdg_status ihdg_measure_peaks(int device, ihdg_peaks* out);
 
 #ifdef __cplusplus
 }

@@ -9,7 +9,7 @@ What is computed, following the paper:
 * Section 2, Eq. (iHDGlocal)/(iHDGtrace) and Algorithm 1: the iteration.  Each sweep first
   forms the (weighted) trace on every face from the previous iterate u^k ("face by face"),
   then solves every element's local equation for u^{k+1} ("element by element"), then
-  measures ||u^{k+1} - u^k||_{L2(Omega)} (the stopping test of Section 6.1,
+  measures ||u^{k+1} - u^k||_{L2(Omega)} (the stopping test of Section 5.1,
   Eq. (tolerancecriteriarelerror)).
 * Section 3, Eqs. (transportLocalk1)/(transportLocale): scalar transport; and the NPC flux
   of Section 3 (Eq. Ntaub and the trace formula after it) as the alternative.

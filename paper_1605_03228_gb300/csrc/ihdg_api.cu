@@ -279,15 +279,25 @@ ihdg_status device_iterate(ihdg_ctx* ctx, Plan* pl, const ihdg_options& o, const
   a.partials = reinterpret_cast<double*>(ws + L.partials);
   a.res_hist = reinterpret_cast<double*>(ws + L.res_hist);
   a.stream = stream;
-  cudaEvent_t e0, e1;
-  CK(cudaEventCreate(&e0), "cudaEventCreate");
-  CK(cudaEventCreate(&e1), "cudaEventCreate");
+  // every event this call creates is destroyed on every return path (errors included)
+  struct Events {
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    ~Events() {
+      for (cudaEvent_t e : ev)
+        if (e) cudaEventDestroy(e);
+    }
+  } evs;
+  CK(cudaEventCreate(&evs.ev[0]), "cudaEventCreate");
+  CK(cudaEventCreate(&evs.ev[1]), "cudaEventCreate");
+  cudaEvent_t e0 = evs.ev[0], e1 = evs.ev[1];
   CK(cudaEventRecord(e0, stream), "cudaEventRecord");
   SweepTimer tm;
   tm.on = o.profile != 0;
   if (tm.on) {
-    CK(cudaEventCreate(&tm.a), "cudaEventCreate");
-    CK(cudaEventCreate(&tm.b), "cudaEventCreate");
+    CK(cudaEventCreate(&evs.ev[2]), "cudaEventCreate");
+    CK(cudaEventCreate(&evs.ev[3]), "cudaEventCreate");
+    tm.a = evs.ev[2];
+    tm.b = evs.ev[3];
   }
   // inner kernel and stopping ratio of the mixed path: the caller's, else the autotuned ones
   // for this problem shape, else the automatic rules
@@ -412,12 +422,6 @@ ihdg_status device_iterate(ihdg_ctx* ctx, Plan* pl, const ihdg_options& o, const
   CK(cudaStreamSynchronize(stream), "solve");
   float ms = 0.f;
   cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  if (tm.on) {
-    cudaEventDestroy(tm.a);
-    cudaEventDestroy(tm.b);
-  }
   if (res) {
     res->fp64_sweep_ms = tm.fp64_n ? tm.fp64_ms / tm.fp64_n : 0.0;
     res->lowp_sweep_ms = tm.lowp_n ? tm.lowp_ms / tm.lowp_n : 0.0;
@@ -706,6 +710,7 @@ extern "C" ihdg_status ihdg_solve_device_static(ihdg_ctx* ctx, const ihdg_mesh* 
   ihdg_status st = check_opts(ctx, o);
   if (st != IHDG_OK) return st;
   CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  const auto t_setup = std::chrono::steady_clock::now();
   Plan pl;
   st = prepare_plan(ctx, *mesh, *co, pl);
   if (st != IHDG_OK) return st;
@@ -723,9 +728,13 @@ extern "C" ihdg_status ihdg_solve_device_static(ihdg_ctx* ctx, const ihdg_mesh* 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   st = upload_plan(ctx, pl, base, s);
   if (st != IHDG_OK) return st;
+  // this path builds and uploads the operators on every call (nothing is cached)
+  const double setup_ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_setup).count();
   SrcDev src{d_f, d_g, nullptr};
   st = device_iterate(ctx, &pl, o, src, o.u0, d_u, d_tr, static_cast<char*>(base) + align256(pl.dbytes), L, s, res);
   if (st != IHDG_OK) return st;
+  if (res) res->setup_ms = setup_ms;
   ctx->err.clear();
   return IHDG_OK;
 }
@@ -827,6 +836,9 @@ void serve_one(ihdg_ctx* sctx, cudaStream_t stream, Server* sv, Request* r) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) { st = IHDG_ERR_CUDA; sctx->err = cudaGetErrorString(e); }
   }
+  // the request's space goes back to the arena after this returns: drain the stream on
+  // every path (an error may leave kernels or copies queued that still write to it)
+  cudaStreamSynchronize(stream);
   r->st = st;
   if (st != IHDG_OK) r->err = sctx->err;
 }

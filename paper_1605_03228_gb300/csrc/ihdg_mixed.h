@@ -4,7 +4,7 @@
 //   outer (float64):  E' = E + e,  r = S(E') - E'                      (k_outer64)
 //   check (float64):  res = ||u(S(E')) - u(E')|| = sqrt(t(r)^T Q t(r))  (k_inner_first)
 //   inner (low):      e <- r + L_E t(e), from e = r, until the step is small  (k_inner)
-// The float64 residual is the paper's stopping quantity (Section 6.1) evaluated for the
+// The float64 residual is the paper's stopping quantity (Section 5.1) evaluated for the
 // next exact sweep from the current state; the output is u(E') with the trace of S(E').
 #pragma once
 #include <string>

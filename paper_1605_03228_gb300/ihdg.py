@@ -57,10 +57,18 @@ class Sizes(ctypes.Structure):
                 ("nface_nodes", ctypes.c_int), ("n_exp", ctypes.c_int), ("n_in", ctypes.c_int)]
 
 
+class Peaks(ctypes.Structure):
+    _fields_ = [("fp64_fma_tflops", ctypes.c_double), ("fp32_fma_tflops", ctypes.c_double),
+                ("l2_read_gbs", ctypes.c_double), ("sms", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 EXPORTED = ["ihdg_create", "ihdg_destroy", "ihdg_last_error", "ihdg_problem_sizes", "ihdg_quadrature_points",
             "ihdg_node_points", "ihdg_solve", "ihdg_workspace_bytes", "ihdg_solve_device", "ihdg_swe_steps",
             "ihdg_swe_steps_device", "ihdg_host_operator", "ihdg_solve_device_static", "ihdg_server_start",
-            "ihdg_server_stop", "ihdg_submit", "ihdg_poll", "ihdg_fetch"]
+            "ihdg_server_stop", "ihdg_submit", "ihdg_poll", "ihdg_fetch", "ihdg_autotune", "ihdg_measure_peaks"]
 STATIC_SCRATCH_BYTES = 64 * 1024 * 1024
 
 _lib = None
@@ -103,6 +111,7 @@ def load(build_if_missing=True):
     L.ihdg_submit.argtypes = [VP, P(Mesh), P(Coeffs), dp, dp, P(Options), P(ctypes.c_longlong)]
     L.ihdg_poll.argtypes = [VP, ctypes.c_longlong, P(Result)]
     L.ihdg_fetch.argtypes = [VP, ctypes.c_longlong, dp, dp]
+    L.ihdg_measure_peaks.argtypes = [I, P(Peaks)]
     for name in EXPORTED:
         f = getattr(L, name)
         if name not in ("ihdg_destroy", "ihdg_last_error"):
@@ -143,6 +152,16 @@ def make_options(tol, max_iters=2000, prec=FP64, diverge_factor=0.0, inner_max=0
     o.u0 = u0
     o.profile = profile
     return o
+
+
+def measure_peaks(device=0):
+    """ihdg_measure_peaks: float64 / float32 FMA rates (TFLOP/s) and L2 read bandwidth (GB/s)."""
+    L = load()
+    pk = Peaks()
+    st = L.ihdg_measure_peaks(int(device), ctypes.byref(pk))
+    if st != OK:
+        raise IHDGError(st, "ihdg_measure_peaks failed")
+    return pk
 
 
 def _dptr(a):

@@ -331,6 +331,37 @@ def test_swe_restart_from_state_is_exact(ctx, prec_name):
     assert np.array_equal(q_res, q_all)
 
 
+@pytest.mark.parametrize("prec_name,n", [("MIXED_FP32", (20, 16)), ("MIXED_BF16", (20, 16)),
+                                         ("MIXED_FP32", (64, 48))])
+def test_swe_steps_mixed(ctx, prec_name, n):
+    """Mixed precision on the shallow-water path (float32 or bf16 inner sweeps, float64 outer
+    sweeps and stopping norm) against the float64 oracle, step by step: each backward-Euler
+    step of Eq. localSolverDD (Section 3) at dt = h/((p+1)(p+2)), the step the paper runs in
+    Section 5.2, warm-started from the previous step's state on both sides.  Bar: relative
+    L2 difference of the volume state <= 1e-6 after every step."""
+    ihdg = ih()
+    p = 2
+    h = 1.0 / n[0]
+    dt = h / ((p + 1) * (p + 2))
+    mesh = ihdg.make_mesh(2, n, p)
+    co = ihdg.make_coeffs(ihdg.SWE, Phi=1.0, dt=dt, coriolis_f=0.3, friction=0.02)
+    nodes = ihdg.node_points(mesh, co)
+    q0 = W.swe_bump(nodes, seed=1, width=0.15)
+    q = q0.reshape(q0.shape[0], -1).copy()
+    om = BoxMesh(2, n)
+    disc = Discretisation(om, p)
+    pr = ShallowWater(disc, 1.0, dt, 0.3, 0.02)
+    U = q0.copy()
+    opts = ihdg.make_options(1e-10, prec=getattr(ihdg, prec_name), max_iters=20000)
+    for step in range(4):
+        its, res = ctx.swe_steps(mesh, co, q, 1, opts)
+        U, T, K, r, st = pr.step(U, 1e-10)
+        assert res.status == ihdg.OK and st == STATUS_OK, (step, res.as_dict())
+        assert res.lowp_sweeps > 0 or res.iterations <= 2
+        e = rel(q, U.reshape(om.nel, -1))
+        assert e < 1e-6, (step, e)
+
+
 # ------------------------------------------------------------------------------ mixed precision
 @pytest.mark.parametrize("prec_name", ["MIXED_FP32", "MIXED_BF16"])
 def test_mixed_transport2d(ctx, prec_name):
@@ -540,6 +571,37 @@ def test_full_size_transport3d_sampled(ctx):
                               lambda X: W.transport3d_forcing(X, b), W.transport3d_exact)
     got = np.array([u[c[0] + 64 * (c[1] + 64 * c[2])] for c in centers])
     assert rel(got, ref) < 1e-10
+
+
+def test_full_size_convdiff_mixed_converged(ctx):
+    """The headline solve itself: 2D convection-diffusion at 256^2, p = 3, kappa = 1e-4,
+    mixed float32 inner sweeps with float64 outer sweeps, in the launch shape of the bench
+    (the register kernel fills every SM with one 1024-thread block, 152 blocks in its grid
+    barrier), run to tolerance 1e-8 and compared with the float64 oracle's converged
+    solution at 48 sampled elements (corners, edges, centre, seeded interior).  The oracle's
+    values are stored in tests/golden/convdiff2d_256_p3.json, written by the committed script
+    beside it from oracle/ alone.  Bar: the mixed path's 1e-6 relative L2 difference."""
+    import json
+    import os
+    ihdg = ih()
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "convdiff2d_256_p3.json")))
+    n, p, kappa, beta = tuple(gold["n"]), gold["p"], gold["kappa"], tuple(gold["beta"])
+    mesh = ihdg.make_mesh(2, n, p)
+    co = ihdg.make_coeffs(ihdg.CONVDIFF, beta=beta, kappa=kappa)
+    vol, bnd = ihdg.quadrature_points(mesh, co)
+    f, g = W.convdiff_forcing(vol, kappa, beta), W.convdiff_exact(bnd)
+    for kernel in ("KERNEL_AUTO", "KERNEL_TENSOR_CORES"):
+        opts = ihdg.make_options(gold["tol"], prec=ihdg.MIXED_FP32, max_iters=4000,
+                                 inner_kernel=getattr(ihdg, kernel))
+        u, tr, res = ctx.solve(mesh, co, f, g, opts)
+        assert res.status == ihdg.OK, res.as_dict()
+        got = u[np.array(gold["elements"])]
+        ref = np.array(gold["u"])
+        assert rel(got, ref) < 1e-6, (kernel, rel(got, ref))
+    # the float64 path stops at the oracle's sweep count on the same problem
+    u64, _, r64 = ctx.solve(mesh, co, f, g, ihdg.make_options(gold["tol"], max_iters=4000))
+    assert abs(r64.iterations - gold["iterations"]) <= 1
+    assert rel(u64[np.array(gold["elements"])], np.array(gold["u"])) < 1e-10
 
 
 # ------------------------------------------------------------------------------ autotuner

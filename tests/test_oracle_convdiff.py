@@ -1,11 +1,11 @@
-"""Pins for the oracle's convection-diffusion iHDG (Section 4, Theorem 4, Section 6.3).
+"""Pins for the oracle's convection-diffusion iHDG (Section 4, Theorem 4, Section 5.3).
 
 * polynomial exactness of the HDG discretisation (u, sigma = -kappa grad u in Q^p);
 * converged iteration equals the static-condensation direct solve (convergent regime);
 * optimal h-convergence p+1 of the direct solution for the 2D convection-diffusion
   workload's manufactured solution;
 * divergence where the paper predicts it: pure diffusion with the upwind tau for any mesh
-  (Section 4.2) and the kappa = 1e-2 mixed regime on fine meshes (Section 6.3);
+  (Section 4.2) and the kappa = 1e-2 mixed regime on fine meshes (Section 5.3);
 * the upwind count is insensitive to kappa when convection dominates (Table 3).
 """
 import numpy as np
@@ -102,7 +102,7 @@ def test_pure_diffusion_upwind_tau_diverges(n):
 
 def test_mixed_regime_diverges_on_fine_mesh_converges_when_convection_dominated():
     """kappa = 1e-2 with h = 1/256 (element Peclet ~0.55) diverges; kappa = 1e-4 at the
-    same h (Peclet ~55) converges (Section 6.3, Theorem 4 conditions)."""
+    same h (Peclet ~55) converges (Section 5.3, Theorem 4 conditions)."""
     m, disc, pr = make(2, 6, 3, [1.0, 1.0], 1e-2, 0.0, h=1 / 256)
     assert spectral_radius(pr, m, disc) > 5.0
     m, disc, pr = make(2, 6, 3, [1.0, 1.0], 1e-4, 0.0, h=1 / 256)

@@ -1,10 +1,10 @@
-"""Pins for the oracle's linearized shallow-water iHDG (Section 3, Theorem 3, Section 6.2).
+"""Pins for the oracle's linearized shallow-water iHDG (Section 3, Theorem 3, Section 5.2).
 
 * each backward-Euler step's converged iterate equals the direct HDG solve of that step;
 * mass conservation (walls carry zero mass flux; interior fluxes cancel at convergence);
 * the backward-Euler energy ||phi||^2 + Phi ||vel||^2 does not increase;
 * optimal h-convergence p+1 against the standing-wave exact solution (shallowexact);
-* a tiny step needs only a couple of iterations with warm start (Section 6.2 reports 2);
+* a tiny step needs only a couple of iterations with warm start (Section 5.2 reports 2);
 * Theorem 3's step restriction: converges at dt = h/((p+1)(p+2)), diverges at 6x that.
 """
 import numpy as np

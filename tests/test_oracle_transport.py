@@ -1,4 +1,4 @@
-"""Pins for the oracle's transport iHDG (Section 3, Theorem 1, Section 6.1).
+"""Pins for the oracle's transport iHDG (Section 3, Theorem 1, Section 5.1).
 
 * polynomial exactness (consistency of the upwind HDG discretisation);
 * the converged iterate equals the static-condensation direct HDG solve (HDGeqn);
