@@ -130,6 +130,11 @@ typedef struct {
   int profile;             /* 1: time every sweep launch with CUDA events (one launch per
                               host check, so slower overall) and report the averages below */
   ihdg_inner_kernel inner_kernel;   /* mixed: inner-sweep kernel (AUTO = 0) */
+  int sweeps_per_sync;     /* mixed, 2D CUDA-core inner kernel: inner sweeps between two grid
+                              barriers.  1: one barrier per sweep (register-resident kernel);
+                              H >= 2: temporal blocking, every block sweeps its tile plus a halo
+                              of H elements H times in shared memory (the same iterates; halo
+                              work recomputed); 0: automatic (the autotuned value, else 4) */
 } ihdg_options;
 
 typedef struct {
@@ -241,12 +246,13 @@ ihdg_status ihdg_solve_device_static(ihdg_ctx* ctx, const ihdg_mesh* mesh, const
 
 /* No counterpart in the paper (it has no precision or kernel choice).
  * Autotuner of the mixed path: times complete solves of the caller's problem (host inputs as
- * for ihdg_solve) for every inner-kernel choice and a ladder of inner stopping ratios
- * (float32/tf32: 5e-4 .. 1e-2; bf16: 2e-2 .. 0.3), keeps the fastest that converges, and
- * returns it in *tuned (a copy of *opts with inner_kernel and inner_rtol set) with its device
- * time in *best_ms.  The choice is also cached in the context for this problem shape (pde,
- * flux, dim, n, p, precision): later solves on the context whose inner_kernel is AUTO and
- * inner_rtol 0 use it.  Serving slots do not (their results must not depend on timing).
+ * for ihdg_solve) for every inner-kernel choice, a ladder of inner stopping ratios
+ * (float32/tf32: 5e-4 .. 1e-2; bf16: 2e-2 .. 0.3) and, for the CUDA-core kernel on 2D
+ * meshes, 1..4 sweeps per grid barrier; keeps the fastest that converges, and returns it in
+ * *tuned (a copy of *opts with inner_kernel, inner_rtol and sweeps_per_sync set) with its
+ * device time in *best_ms.  The choice is also cached in the context for this problem shape
+ * (pde, flux, dim, n, p, precision): later solves on the context whose inner_kernel is AUTO,
+ * inner_rtol 0 and sweeps_per_sync 0 use it.  Serving slots do not (their results must not depend on timing).
  * FP64 options have nothing to tune: *tuned = *opts.  Errors as for ihdg_solve; a problem
  * that converges under no candidate returns IHDG_NOT_CONVERGED. */
 ihdg_status ihdg_autotune(ihdg_ctx* ctx, const ihdg_mesh* mesh, const ihdg_coeffs* coeffs,

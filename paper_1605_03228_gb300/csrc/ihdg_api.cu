@@ -62,8 +62,14 @@ struct ihdg_ctx {
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
   Ctrl* h_ctrl = nullptr;   // pinned readback of the loop state
-  // ihdg_autotune's choices: problem shape -> (inner kernel, inner stopping ratio)
-  std::map<std::string, std::pair<int, double>> tuned;
+  // ihdg_autotune's choices: problem shape -> inner kernel, inner stopping ratio, sweeps per
+  // grid barrier
+  struct Tuned {
+    int kernel;
+    double rtol;
+    int sps;
+  };
+  std::map<std::string, Tuned> tuned;
 };
 
 namespace {
@@ -246,6 +252,8 @@ ihdg_status check_opts(ihdg_ctx* ctx, const ihdg_options& o) {
   if (!(o.tol >= 0.0) || !std::isfinite(o.tol)) return fail(ctx, IHDG_ERR_INVALID, "opts.tol must be finite and >= 0");
   if (o.prec < IHDG_FP64 || o.prec > IHDG_MIXED_BF16) return fail(ctx, IHDG_ERR_INVALID, "opts.prec is not a known precision");
   if (o.max_iters > 100000000) return fail(ctx, IHDG_ERR_INVALID, "opts.max_iters too large");
+  if (o.sweeps_per_sync < 0 || o.sweeps_per_sync > 8)
+    return fail(ctx, IHDG_ERR_INVALID, "opts.sweeps_per_sync must be in 0..8");
   if (o.inner_kernel < IHDG_KERNEL_AUTO || o.inner_kernel > IHDG_KERNEL_GLOBAL)
     return fail(ctx, IHDG_ERR_INVALID, "opts.inner_kernel is not a known kernel");
   return IHDG_OK;
@@ -303,11 +311,13 @@ ihdg_status device_iterate(ihdg_ctx* ctx, Plan* pl, const ihdg_options& o, const
   // for this problem shape, else the automatic rules
   int inner_kernel = o.inner_kernel;
   double inner_rtol = o.inner_rtol;
-  if (o.prec != IHDG_FP64 && inner_kernel == IHDG_KERNEL_AUTO && inner_rtol <= 0.0) {
+  int sps = o.sweeps_per_sync;
+  if (o.prec != IHDG_FP64 && inner_kernel == IHDG_KERNEL_AUTO && inner_rtol <= 0.0 && sps <= 0) {
     auto it = ctx->tuned.find(tune_key(pl->mesh, pl->co, o.prec));
     if (it != ctx->tuned.end()) {
-      inner_kernel = it->second.first;
-      inner_rtol = it->second.second;
+      inner_kernel = it->second.kernel;
+      inner_rtol = it->second.rtol;
+      sps = it->second.sps;
     }
   }
   // Inner stop well above the low-precision rounding floor: an inner loop pushed towards its
@@ -405,6 +415,13 @@ ihdg_status device_iterate(ihdg_ctx* ctx, Plan* pl, const ihdg_options& o, const
     if (const char* nt = std::getenv("IHDG_REG_NT")) m.reg_nt = std::atoi(nt) == 512 ? 512 : 1024;
     // IHDG_TILE_LPE=1 skips the register-resident 2D kernel (one element per thread instead)
     if (const char* lpe = std::getenv("IHDG_TILE_LPE")) m.tile_lpe = std::atoi(lpe) == 1 ? 1 : 4;
+    // sweeps per grid barrier of the 2D CUDA-core inner kernel (temporal blocking when >= 2);
+    // IHDG_SWEEPS_PER_SYNC overrides the automatic choice, 4 (measured on the 256^2 p=3
+    // conv.-diff. solve: 3.2 us per sweep against 4.8 with one barrier per sweep)
+    if (sps <= 0)
+      if (const char* h = std::getenv("IHDG_SWEEPS_PER_SYNC")) sps = std::atoi(h);
+    if (sps <= 0) sps = 4;
+    m.blk_h = sps >= 2 ? (sps > 8 ? 8 : sps) : 0;
     m.LE32h = pl->le32.data();
     m.slots = partials_needed(pl->g.nel);
     ihdg_status st = run_mixed(ctx->h_ctrl, m, o, &Eu, &Eu2, &Et, &Et2, ctx->err, &tm);
@@ -642,31 +659,42 @@ ihdg_status ihdg_autotune(ihdg_ctx* ctx, const ihdg_mesh* mesh, const ihdg_coeff
   static const double ladder16[] = {2e-2, 5e-2, 0.1, 0.2, 0.3};
   const double* ladder = o.prec == IHDG_MIXED_BF16 ? ladder16 : ladder32;
   const int kernels[] = {IHDG_KERNEL_TENSOR_CORES, IHDG_KERNEL_CUDA_CORES};
+  // sweeps per grid barrier: the temporally blocked CUDA-core kernel exists for 2D meshes
+  const int sps_2d[] = {1, 2, 3, 4};
+  const int sps_1[] = {1};
   double best = 1e300;
-  int best_k = IHDG_KERNEL_AUTO;
+  int best_k = IHDG_KERNEL_AUTO, best_s = 1;
   double best_r = 0.0;
   for (int pass = 0; pass < 2; ++pass)          // pass 0 warms every kernel up (module loads)
-    for (int k : kernels)
-      for (int i = 0; i < (pass == 0 ? 1 : 5); ++i) {
-        ihdg_options oc = o;
-        oc.u0 = d_u0;
-        oc.inner_kernel = static_cast<ihdg_inner_kernel>(k);
-        oc.inner_rtol = ladder[pass == 0 ? 2 : i];
-        oc.profile = 0;
-        ihdg_result r{};
-        st = ihdg_solve_device(ctx, mesh, co, d_f, d_g, &oc, d_u, nullptr, d_ws, ws, nullptr, &r);
-        if (st == IHDG_ERR_CUDA || st == IHDG_ERR_TIMEOUT || st == IHDG_ERR_NOMEM) return st;
-        if (pass == 0 || st != IHDG_OK || r.status != IHDG_OK) continue;
-        if (r.solve_ms < best) {
-          best = r.solve_ms;
-          best_k = k;
-          best_r = oc.inner_rtol;
+    for (int k : kernels) {
+      const bool blk = k == IHDG_KERNEL_CUDA_CORES && mesh->dim == 2;
+      const int* sl = blk ? sps_2d : sps_1;
+      const int ns = blk ? 4 : 1;
+      for (int si = 0; si < ns; ++si)
+        for (int i = 0; i < (pass == 0 ? 1 : 5); ++i) {
+          ihdg_options oc = o;
+          oc.u0 = d_u0;
+          oc.inner_kernel = static_cast<ihdg_inner_kernel>(k);
+          oc.inner_rtol = ladder[pass == 0 ? 2 : i];
+          oc.sweeps_per_sync = sl[si];
+          oc.profile = 0;
+          ihdg_result r{};
+          st = ihdg_solve_device(ctx, mesh, co, d_f, d_g, &oc, d_u, nullptr, d_ws, ws, nullptr, &r);
+          if (st == IHDG_ERR_CUDA || st == IHDG_ERR_TIMEOUT || st == IHDG_ERR_NOMEM) return st;
+          if (pass == 0 || st != IHDG_OK || r.status != IHDG_OK) continue;
+          if (r.solve_ms < best) {
+            best = r.solve_ms;
+            best_k = k;
+            best_r = oc.inner_rtol;
+            best_s = sl[si];
+          }
         }
-      }
+    }
   if (best_k == IHDG_KERNEL_AUTO) return fail(ctx, IHDG_NOT_CONVERGED, "no candidate converged");
-  ctx->tuned[tune_key(*mesh, *co, o.prec)] = {best_k, best_r};
+  ctx->tuned[tune_key(*mesh, *co, o.prec)] = {best_k, best_r, best_s};
   tuned->inner_kernel = static_cast<ihdg_inner_kernel>(best_k);
   tuned->inner_rtol = best_r;
+  tuned->sweeps_per_sync = best_s;
   if (best_ms) *best_ms = best;
   ctx->err.clear();
   return IHDG_OK;

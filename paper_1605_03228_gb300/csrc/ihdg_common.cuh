@@ -10,6 +10,21 @@
 namespace ihdg {
 namespace {
 
+// Allow kernel `kern` the device's largest dynamic shared memory (the opt-in maximum less its
+// static shared memory).  Launches still request their own size; the attribute is only the
+// ceiling.  Setting it to a fixed value, rather than to each launch's size, keeps launches
+// from concurrent host threads (serving slots) from lowering it under one another.
+template <typename K>
+inline cudaError_t allow_dynamic_smem(K kern) {
+  int dev = 0, mx = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa{};
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, (const void*)kern);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, mx - (int)fa.sharedSizeBytes);
+  return e;
+}
+
 constexpr int BS = 128;   // threads per block of the element kernels
 constexpr int PBS = 256;  // threads per block of the persistent kernels
 

@@ -486,7 +486,7 @@ cudaError_t run_first_t(const LaunchArgs& a) {
   size_t smem = (size_t)a.g.nvol * BS * sizeof(double);
   auto kern = k_first<NF, NLF>;
   if (smem > 32 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_dynamic_smem(kern);
     if (e != cudaSuccess) return e;
   }
   kern<<<grid_for(a.g.nel), BS, smem, a.stream>>>(a.g, a.op, a.V, a.u0, a.F, a.ring, a.ring_stride, a.ctrl, a.partials, a.res_hist);
@@ -499,7 +499,7 @@ cudaError_t run_sweep64_t(const LaunchArgs& a, int count) {
   size_t smem = ((size_t)a.g.n_exp * NIN + NIN * (NIN + 1) / 2 + (size_t)NIN * BS) * sizeof(double);
   auto kern = k_sweep64<NF, NLF>;
   if (smem > 32 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_dynamic_smem(kern);
     if (e != cudaSuccess) return e;
   }
   for (int i = 0; i < count; ++i)
@@ -515,7 +515,7 @@ cudaError_t run_sweep64_persist_t(const LaunchArgs& a) {
   size_t smem = ((size_t)a.g.n_exp * NIN + NIN * (NIN + 1) / 2 + (size_t)NIN * BS) * sizeof(double);
   auto kern = k_sweep64_persist<NF, NLF>;
   if (smem > 32 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_dynamic_smem(kern);
     if (e != cudaSuccess) return e;
   }
   int dev = 0, sms = 0, per = 0;

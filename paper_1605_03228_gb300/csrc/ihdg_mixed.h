@@ -36,6 +36,7 @@ struct MixedArgs {
   int reg_nt = 1024;        // register kernel block size (1024: one block per SM; or 512)
   int use_tc = 0;           // bf16: local apply on the tensor cores (tcgen05)
   int lt_kind = 0;          // operator layout now in dLT: 0 none, 1 register kernel, 2 tensor-core B
+  int blk_h = 0;            // >= 2: 2D CUDA-core inner sweeps temporally blocked, this many per barrier
   const float* LE32h = nullptr;  // host copy of the float32 operator (n_exp x n_in)
 };
 

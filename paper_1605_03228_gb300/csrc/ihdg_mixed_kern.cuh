@@ -7,6 +7,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -509,7 +510,7 @@ cudaError_t launch_tile_v(MixedArgs& m, TL* rl, TL* e0, TL* e1) {
     if (grid > m.slots / 2) continue;
     const size_t smem = (size_t)epb * (2 * LT::NEXP * sizeof(TL) + 1) + 16;
     if (smem > (size_t)smem_max) continue;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_dynamic_smem(k);
     if (e != cudaSuccess) return e;
     int per = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, NT, smem);
@@ -749,6 +750,293 @@ cudaError_t launch_reg(MixedArgs& m, TL* rl, TL* e0, TL* e1) {
   return launch_reg_v<NF, PER_AXIS, TL, 2, 512>(m, rl, e0, e1);
 }
 
+// Temporally blocked inner loop for 2D meshes.  The mesh is cut into tiles (one per block,
+// tiles_x across); every block keeps its tile plus a halo of H elements on each side (clipped
+// at the mesh boundary) in shared memory: the current and next correction e (TL values held
+// as float, so every value is exactly what the element-per-sweep kernels store) and the
+// residual r.  One super-step runs h <= H sweeps of e <- r + L_E t(e) without leaving the SM:
+// sweep t updates the tile grown by H - t elements, whose inputs all lie in the area that
+// sweep t-1 updated, so after h sweeps the tile holds exactly the iterate the plain sweep
+// reaches after h sweeps.  The block then stores the elements within H of its tile's edges
+// (its neighbours' halo) into the global buffer of the next super-step and arrives at the
+// grid barrier; at the top of the next super-step it reloads its halo from that buffer.
+// One grid barrier and one L2 round trip thus serve h sweeps, at the price of recomputing
+// the halo (the redundant work grows with H).  The stopping test is the one of the other
+// inner kernels, taken on the step norm of the last sweep of each super-step (tile elements
+// only, so every element counts once), lagged by one super-step; on stopping, each block
+// stores its whole tile into the buffer the outer sweep reads for that sweep count.
+struct BlkShape {
+  int tiles_x, tx, ty, halo, ra_max;   // ra_max: largest (pitch x rows) of a region, shared-memory sizing
+};
+
+// Row pitch (elements) of a region row in shared memory: the smallest value >= width that is
+// 8 or 24 modulo 32, so that the 8 x 4 element patch of a warp (and the patch moved by one
+// element or one row) falls on 32 distinct banks.
+__host__ __device__ __forceinline__ int blk_pitch(int width) {
+  const int r = width & 31;
+  return width + (r <= 8 ? 8 - r : (r <= 24 ? 24 - r : 40 - r));
+}
+
+template <int NF, bool PER_AXIS, typename TL, int NT>
+__global__ void __launch_bounds__(NT, 1) k_inner_blk(const DevGeo g, const TL* __restrict__ rlp, TL* e0, TL* e1,
+                                                     Ctrl* ctrl, double* partials, const BlkShape sh,
+                                                     const LTile<NF, 4, PER_AXIS> Lp) {
+  constexpr int NLF = 4;
+  constexpr int NIN = NF * NLF;
+  constexpr int NEXP = LTile<NF, NLF, PER_AXIS>::NEXP;
+  constexpr int SP = NEXP | 1;   // odd word stride per element: conflict-free shared loads
+  extern __shared__ float smf[];
+  __shared__ float wred[NT / 32];
+  __shared__ int s_to;
+  if (ctrl_done(ctrl) || *(volatile const int*)&ctrl->inner_done) return;
+  const int j0 = *(volatile const int*)&ctrl->inner_iter;
+  const int iter0 = *(volatile const int*)&ctrl->iter;
+  const int lowp0 = *(volatile const int*)&ctrl->lowp_sweeps;
+  const int max_iters = ctrl->max_iters, inner_max = ctrl->inner_max;
+  const float limf = (float)(ctrl->inner_rtol * ctrl->rnorm);
+  const int n0 = g.n[0], n1 = g.n[1], H = sh.halo, ld = (int)g.ld;
+  const int tx0 = (int)(blockIdx.x % sh.tiles_x) * sh.tx, ty0 = (int)(blockIdx.x / sh.tiles_x) * sh.ty;
+  const int tx1 = min(n0, tx0 + sh.tx), ty1 = min(n1, ty0 + sh.ty);
+  const int tw = tx1 - tx0, th = ty1 - ty0;
+  const int rx0 = max(0, tx0 - H), ry0 = max(0, ty0 - H);
+  const int RX = min(n0, tx1 + H) - rx0, RY = min(n1, ty1 + H) - ry0;
+  const int RA = RX * RY, P = blk_pitch(RX);
+  float* const es0 = smf;
+  float* const es1 = smf + (size_t)sh.ra_max * SP;
+  float* rs = smf + 2 * (size_t)sh.ra_max * SP;
+  // the whole region of e_j0 (written by the previous launch) and of r
+  {
+    const TL* eb = (j0 & 1) ? e1 : e0;
+    for (int i = threadIdx.x; i < RA; i += NT) {
+      const int K = (rx0 + i % RX) + n0 * (ry0 + i / RX);
+      const int li = (i / RX) * P + i % RX;
+#pragma unroll
+      for (int e = 0; e < NEXP; ++e) {
+        const bool live = (g.live >> e) & 1ull;
+        es0[li * SP + e] = live ? ldcg_f(eb + (long long)e * ld + K) : 0.f;
+        rs[li * SP + e] = live ? to_f(rlp[(long long)e * ld + K]) : 0.f;
+      }
+    }
+  }
+  unsigned* count = &ctrl->bar_count;
+  float* partf = reinterpret_cast<float*>(partials);
+  int cur = 0, done = 0;
+  for (int m = 0;; ++m) {
+    float* ec = cur ? es1 : es0;
+    // halo of the current level (stored by the neighbours before the barrier) and the last
+    // super-step's partial step norms, in one round trip
+    float pv = 0.f;
+    if (m > 0) {
+      for (int i = threadIdx.x; i < (int)gridDim.x; i += NT) pv += __ldcg(partf + ((m - 1) & 1) * gridDim.x + i);
+      // the halo (region minus tile): the region's rows above and below the tile, then the
+      // columns left and right of the tile in its rows; every thread issues all loads of
+      // its halo element before storing any, so one round trip serves the whole halo
+      const TL* gb = ((j0 + m) & 1) ? e1 : e0;
+      const int nab = (ty0 - ry0) * RX, nbe = (ry0 + RY - ty1) * RX;
+      const int lw = tx0 - rx0, sw = lw + (rx0 + RX - tx1);
+      const int nh = nab + nbe + th * sw;
+      for (int i = threadIdx.x; i < nh; i += NT) {
+        int gx, gy;
+        if (i < nab) {
+          gx = rx0 + i % RX;
+          gy = ry0 + i / RX;
+        } else if (i < nab + nbe) {
+          gx = rx0 + (i - nab) % RX;
+          gy = ty1 + (i - nab) / RX;
+        } else {
+          const int k = i - nab - nbe, c = k % sw;
+          gy = ty0 + k / sw;
+          gx = c < lw ? rx0 + c : tx1 + (c - lw);
+        }
+        const int K = gx + n0 * gy;
+        const int li = (gy - ry0) * P + (gx - rx0);
+        float v[NEXP];
+#pragma unroll
+        for (int e = 0; e < NEXP; ++e) v[e] = ((g.live >> e) & 1ull) ? ldcg_f(gb + (long long)e * ld + K) : 0.f;
+#pragma unroll
+        for (int e = 0; e < NEXP; ++e) ec[li * SP + e] = v[e];
+      }
+    }
+    // fixed-order fold (the same in every thread of every block): warp sums, then the warp
+    // sums by one shuffle tree in each warp
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) pv += __shfl_xor_sync(0xffffffffu, pv, o);
+    if ((threadIdx.x & 31) == 0) wred[threadIdx.x >> 5] = pv;
+    __syncthreads();
+    float tot = (threadIdx.x & 31) < NT / 32 ? wred[threadIdx.x & 31] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    const float step = sqrtf(tot);
+    const int j = j0 + done, it = iter0 + done;
+    const bool budget = j >= inner_max || it >= max_iters;
+    const bool stop = budget || (m > 0 && (step <= limf || !(step == step) || isinf(step)));
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+      ctrl->inner_iter = j;
+      ctrl->iter = it;
+      ctrl->lowp_sweeps = lowp0 + done;
+      if (m > 0) ctrl->inner_step = (double)step;
+      if (stop) ctrl->inner_done = 1;
+    }
+    if (stop) {
+      // the whole tile into the buffer the outer sweep reads after j inner sweeps
+      TL* fb = (j & 1) ? e1 : e0;
+      for (int i = threadIdx.x; i < tw * th; i += NT) {
+        const int gx = tx0 + i % tw, gy = ty0 + i / tw;
+        const int li = (gy - ry0) * P + (gx - rx0);
+        const int K = gx + n0 * gy;
+#pragma unroll
+        for (int e = 0; e < NEXP; ++e)
+          if ((g.live >> e) & 1ull) fb[(long long)e * ld + K] = from_f<TL>(ec[li * SP + e]);
+      }
+      break;
+    }
+    const int h = min(H, min(inner_max - j, max_iters - it));
+    float snorm = 0.f;
+    TL* nbuf = ((j0 + m + 1) & 1) ? e1 : e0;   // the next super-step's buffer
+    for (int t = 1; t <= h; ++t) {
+      const float* src = cur ? es1 : es0;
+      float* dst = cur ? es0 : es1;
+      const int grow = H - t;
+      const int ax0 = max(0, tx0 - grow), ay0 = max(0, ty0 - grow);
+      const int aw = min(n0, tx1 + grow) - ax0, ah = min(n1, ty1 + grow) - ay0;
+      // one element per thread; a warp takes an 8 x 4 patch of the area
+      const int npx = (aw + 7) >> 3, npatch = npx * ((ah + 3) >> 2);
+      const int dx = threadIdx.x & 7, dy = (threadIdx.x >> 3) & 3;
+      auto sweep = [&](auto last_c) {
+        constexpr bool LAST = decltype(last_c)::value;
+        for (int pch = threadIdx.x >> 5; pch < npatch; pch += NT / 32) {
+          const int ix = (pch % npx) * 8 + dx, iy = (pch / npx) * 4 + dy;
+          if (ix >= aw || iy >= ah) continue;
+          const int gx = ax0 + ix, gy = ay0 + iy;
+          const int li = (gy - ry0) * P + (gx - rx0);
+          // a1: the traces of the four faces (own and neighbour exports from shared memory)
+          float tr[NIN];
+#pragma unroll
+          for (int f = 0; f < NLF; ++f) {
+            const int a = f >> 1;
+            const int c = a ? gy : gx, nn = a ? n1 : n0;
+            const bool bnd = (f & 1) ? (c == nn - 1) : (c == 0);
+            const int kind = g.kind[f];
+            const int lin = li + ((f & 1) ? 1 : -1) * (a ? P : 1);
+            const int os = PER_AXIS ? a * NF : f * NF;
+            const int ns = PER_AXIS ? a * NF : (f ^ 1) * NF;
+            const float wo = kind == FK_OWN_D ? 1.f : kind == FK_SUM_D ? (!bnd ? 1.f : (g.bc_mirror ? 2.f : 0.f)) : 0.f;
+            const bool nbm = !bnd && (kind == FK_NBR_D || kind == FK_SUM_D);
+#pragma unroll
+            for (int q = 0; q < NF; ++q) {
+              const float nb = nbm ? src[lin * SP + ns + q] : 0.f;
+              tr[f * NF + q] = wo * src[li * SP + os + q] + nb;
+            }
+          }
+          // a3: e_new = r + L_E t, one accumulation chain per row in trace order (a chain
+          // reuses its accumulator register: twice the FMA issue rate of interleaving all rows
+          // per trace value).  Rows of slots that carry no value have zero operator rows and
+          // zero r, so they stay zero.
+          float acc[NEXP];
+#pragma unroll
+          for (int e = 0; e < NEXP; ++e) {
+            float v = rs[li * SP + e];
+#pragma unroll
+            for (int k = 0; k < NIN; ++k) v = fmaf(Lp.L[e][k], tr[k], v);
+            acc[e] = v;
+          }
+          // a4: rounded to the storage type.  In the last sweep: the step norm over the tile,
+          // and the tile elements within H of its edges (the neighbours' halo) go straight to
+          // the next super-step's global buffer
+          bool in_tile = false, strip = false;
+          if constexpr (LAST) {
+            in_tile = gx >= tx0 && gx < tx1 && gy >= ty0 && gy < ty1;
+            strip = in_tile && (gx - tx0 < H || tx1 - 1 - gx < H || gy - ty0 < H || ty1 - 1 - gy < H);
+          }
+          const int K = gx + n0 * gy;
+#pragma unroll
+          for (int e = 0; e < NEXP; ++e) {
+            const TL nt = from_f<TL>(acc[e]);
+            const float nv = to_f(nt);
+            if constexpr (LAST) {
+              const float d = nv - src[li * SP + e];
+              if (in_tile) snorm = fmaf(d, d, snorm);
+              if (strip && ((g.live >> e) & 1ull)) nbuf[(long long)e * ld + K] = nt;
+            }
+            dst[li * SP + e] = nv;
+          }
+        }
+      };
+      if (t == h) sweep(std::true_type{});
+      else sweep(std::false_type{});
+      __syncthreads();
+      cur ^= 1;
+    }
+    done += h;
+    const float blk = sum_partials<NT>(snorm, wred);
+    arrive_wait(partf + (m & 1) * gridDim.x, count, (unsigned)(m + 1), blk, ctrl, &s_to);
+    if (s_to) break;
+  }
+}
+
+// Launch k_inner_blk with halo m.blk_h (>= 2): the tile shape minimises the tile + halo area
+// over at most one tile per SM; returns cudaErrorNotSupported (nothing launched) when the
+// state does not fit in shared memory or the grid would not be co-resident.
+template <int NF, bool PER_AXIS, typename TL, int NT>
+cudaError_t launch_blk_v(MixedArgs& m, TL* rl, TL* e0, TL* e1) {
+  using LT = LTile<NF, 4, PER_AXIS>;
+  constexpr int SP = LT::NEXP | 1;
+  const LaunchArgs& a = m.base;
+  const int H = m.blk_h;
+  if (a.g.dim != 2 || H < 2 || !m.LE32h || a.g.n_exp != LT::NEXP || (long long)a.g.ld * LT::NEXP >= (1LL << 31))
+    return cudaErrorNotSupported;
+  auto k = k_inner_blk<NF, PER_AXIS, TL, NT>;
+  int dev = 0, sms = 0, smem_max = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  smem_max -= 1024;   // static shared memory of the kernel
+  const int n0 = a.g.n[0], n1 = a.g.n[1];
+  int cap = sms;
+  if (cap > m.max_grid) cap = m.max_grid;
+  if (cap > m.slots / 2) cap = m.slots / 2;
+  BlkShape sh{0, 0, 0, H, 0};
+  long long best = -1;
+  int grid = 0;
+  for (int txn = 1; txn <= n0 && txn <= cap; ++txn) {
+    const int tx = (n0 + txn - 1) / txn, tiles_x = (n0 + tx - 1) / tx;
+    const int tyn = cap / tiles_x;
+    if (tyn < 1) continue;
+    const int ty = (n1 + tyn - 1) / tyn, tiles_y = (n1 + ty - 1) / ty;
+    const long long area = (long long)blk_pitch(std::min(n0, tx + 2 * H)) * std::min(n1, ty + 2 * H);
+    if (best < 0 || area < best) {
+      best = area;
+      sh.tiles_x = tiles_x;
+      sh.tx = tx;
+      sh.ty = ty;
+      sh.ra_max = (int)area;
+      grid = tiles_x * tiles_y;
+    }
+  }
+  if (best < 0 || grid < 1) return cudaErrorNotSupported;
+  const size_t smem = (size_t)3 * sh.ra_max * SP * sizeof(float);
+  if (smem > (size_t)smem_max) return cudaErrorNotSupported;
+  cudaError_t e = allow_dynamic_smem(k);
+  if (e != cudaSuccess) return e;
+  int per = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, NT, smem);
+  if (e != cudaSuccess) return e;
+  if ((long long)per * sms < grid) return cudaErrorNotSupported;
+  LT L;
+  for (int r = 0; r < LT::NEXP; ++r)   // rows of slots that carry no value: zero
+    for (int q = 0; q < LT::NIN; ++q) L.L[r][q] = ((a.g.live >> r) & 1ull) ? m.LE32h[r * LT::NIN + q] : 0.f;
+  DevGeo gg = a.g;
+  const TL* rlc = rl;
+  Ctrl* ct = a.ctrl;
+  double* pp = a.partials;
+  e = cudaMemsetAsync(&a.ctrl->bar_count, 0, sizeof(unsigned), a.stream);
+  if (e != cudaSuccess) return e;
+  void* args[] = {&gg, &rlc, &e0, &e1, &ct, &pp, &sh, &L};
+  e = cudaLaunchCooperativeKernel((const void*)k, dim3((unsigned)grid), dim3(NT), args, smem, a.stream);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
 // Tile kernel shape: one element per thread (default) or, with IHDG_TILE_LPE=4 on 2D
 // meshes, four lanes per element (one face each) with shuffled traces.
 template <int NF, int NLF, bool PER_AXIS, typename TL>
@@ -772,7 +1060,7 @@ struct MixedRunner {
         size_t smem = ((size_t)a.g.n_exp * NIN + (size_t)NIN * BS) * sizeof(double);
         auto k = k_outer64<NF, NLF, TL>;
         if (smem > 32 * 1024) {
-          cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+          cudaError_t e = allow_dynamic_smem(k);
           if (e != cudaSuccess) return e;
         }
         k<<<grid_for(a.g.nel), BS, smem, a.stream>>>(a.g, a.op, a.F, m.E64, a.ring_stride, m.r64, rl, e0, e1, has_e,
@@ -781,7 +1069,7 @@ struct MixedRunner {
         size_t smem = (size_t)NIN * (NIN + 1) / 2 * sizeof(double) + (size_t)a.g.n_exp * NIN * sizeof(float);
         auto k = k_inner_first<NF, NLF, TL>;
         if (smem > 32 * 1024) {
-          cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+          cudaError_t e = allow_dynamic_smem(k);
           if (e != cudaSuccess) return e;
         }
         k<<<grid_for(a.g.nel), BS, smem, a.stream>>>(a.g, a.op, m.r64, e0, a.ctrl, a.partials, a.res_hist);
@@ -804,6 +1092,11 @@ struct MixedRunner {
         }
         if (!m.no_tile) {
           if constexpr (NLF == 4) {
+            if (m.blk_h >= 2) {
+              cudaError_t be = a.g.per_axis ? launch_blk_v<NF, true, TL, 1024>(m, rl, e0, e1)
+                                            : launch_blk_v<NF, false, TL, 1024>(m, rl, e0, e1);
+              if (be != cudaErrorNotSupported) return be;
+            }
             if (m.tile_lpe != 1) {
               cudaError_t re = a.g.per_axis ? launch_reg<NF, true, TL>(m, rl, e0, e1)
                                             : launch_reg<NF, false, TL>(m, rl, e0, e1);

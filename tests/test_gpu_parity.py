@@ -475,6 +475,82 @@ def test_mixed_tensor_core_inner(ctx, monkeypatch, case, grid, kernel, prec_name
     assert rel(u, U.reshape(pr.mesh.nel, -1)) < 1e-6
 
 
+
+def _blocked_case(ihdg, pde):
+    if pde == "convdiff":
+        mesh = ihdg.make_mesh(2, (37, 29), 3)
+        co = ihdg.make_coeffs(ihdg.CONVDIFF, beta=(1.0, 0.7), kappa=1e-3)
+        vol, bnd = ihdg.quadrature_points(mesh, co)
+        return mesh, co, W.convdiff_forcing(vol, 1e-3, (1.0, 0.7)), W.convdiff_exact(bnd)
+    if pde == "transport":
+        mesh = ihdg.make_mesh(2, (41, 23), 2)
+        co = ihdg.make_coeffs(ihdg.TRANSPORT, beta=(0.8, -0.6))
+        vol, bnd = ihdg.quadrature_points(mesh, co)
+        return mesh, co, W.transport2d_forcing(vol, (0.8, -0.6)), W.transport2d_exact(bnd)
+    mesh = ihdg.make_mesh(2, (33, 27), 2)
+    co = ihdg.make_coeffs(ihdg.SWE, Phi=1.0, dt=0.5 / 33 / 12, coriolis_f=0.2, friction=0.01)
+    return mesh, co, None, None
+
+
+def _blocked_run(ctx, ihdg, pde, case, opts):
+    mesh, co, f, g = case
+    if pde == "swe":
+        nodes = ihdg.node_points(mesh, co)
+        q = W.swe_bump(nodes, seed=2, width=0.15)
+        q = q.reshape(q.shape[0], -1).copy()
+        its, res = ctx.swe_steps(mesh, co, q, 1, opts)
+        return q, res
+    u, tr, res = ctx.solve(mesh, co, f, g, opts)
+    return u, res
+
+
+@pytest.mark.parametrize("pde", ["convdiff", "transport", "swe"])
+@pytest.mark.parametrize("H,grid", [(2, ""), (3, "6"), (4, "11")])
+def test_blocked_inner_matches_one_barrier_per_sweep(ctx, monkeypatch, pde, H, grid):
+    """Temporal blocking (H inner sweeps per grid barrier, halo recomputed in shared memory)
+    must produce the iterates of the one-barrier-per-sweep kernel.  The float64 outer sweeps
+    of the mixed path would repair a wrong inner correction, so the comparison fixes the
+    schedule (tol 0, 7 inner sweeps per outer step, a sweep budget that ends right after the
+    outer sweep that applies the second inner correction) and compares the results directly:
+    float32 rounding of a different summation order differs by ~1e-6 relative, a stale or
+    misplaced halo value by the size of the correction.  Grid caps give many small ragged
+    tiles; the three PDEs cover the per-face layout with Dirichlet data (conv.-diff.), the
+    per-axis layout (transport) and mirrored wall traces (shallow water)."""
+    ihdg = ih()
+    if grid:
+        monkeypatch.setenv("IHDG_PERSISTENT_GRID", grid)
+    case = _blocked_case(ihdg, pde)
+    out = {}
+    for sps in (1, H):
+        opts = ihdg.make_options(0.0, prec=ihdg.MIXED_FP32, max_iters=19, inner_max=7, inner_rtol=1e-30,
+                                 diverge_factor=-1.0, inner_kernel=ihdg.KERNEL_CUDA_CORES, sweeps_per_sync=sps)
+        out[sps] = _blocked_run(ctx, ihdg, pde, case, opts)
+    (u1, r1), (uh, rh) = out[1], out[H]
+    assert r1.status == rh.status == ihdg.NOT_CONVERGED
+    assert (r1.iterations, r1.fp64_sweeps, r1.lowp_sweeps) == (rh.iterations, rh.fp64_sweeps, rh.lowp_sweeps)
+    assert rel(uh, u1) < 2e-5, rel(uh, u1)
+
+
+@pytest.mark.parametrize("H", [2, 3, 4])
+def test_blocked_inner_converges_to_oracle(ctx, H):
+    """The blocked inner kernel in a complete mixed solve: the oracle's solution within the
+    mixed bar (1e-6), and no more float64 outer steps than the one-barrier-per-sweep kernel
+    needs plus one (a wrong inner solve would show as extra outer steps)."""
+    ihdg = ih()
+    n, p, kappa = (46, 38), 3, 1e-4
+    mesh = ihdg.make_mesh(2, n, p)
+    co = ihdg.make_coeffs(ihdg.CONVDIFF, beta=(1.0, 1.0), kappa=kappa)
+    vol, bnd = ihdg.quadrature_points(mesh, co)
+    f, g = W.convdiff_forcing(vol, kappa), W.convdiff_exact(bnd)
+    base = dict(prec=ihdg.MIXED_FP32, max_iters=20000, inner_kernel=ihdg.KERNEL_CUDA_CORES)
+    u1, _, r1 = ctx.solve(mesh, co, f, g, ihdg.make_options(1e-8, sweeps_per_sync=1, **base))
+    uh, _, rh = ctx.solve(mesh, co, f, g, ihdg.make_options(1e-8, sweeps_per_sync=H, **base))
+    assert r1.status == rh.status == ihdg.OK, rh.as_dict()
+    assert rh.fp64_sweeps <= r1.fp64_sweeps + 1, (rh.fp64_sweeps, r1.fp64_sweeps)
+    om = BoxMesh(2, n)
+    U = ConvDiff(Discretisation(om, p), np.array([1.0, 1.0]), kappa).iterate(f, g, 1e-8, max_iters=20000)[0]
+    assert rel(uh, U.reshape(om.nel, -1)) < 1e-6
+
 def test_mixed_convdiff(ctx):
     ihdg = ih()
     n, p, kappa = (12, 10), 3, 1e-4
