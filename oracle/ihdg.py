@@ -12,7 +12,9 @@ What is computed, following the paper:
   measures ||u^{k+1} - u^k||_{L2(Omega)} (the stopping test of Section 5.1,
   Eq. (tolerancecriteriarelerror)).
 * Section 3, Eqs. (transportLocalk1)/(transportLocale): scalar transport; and the NPC flux
-  of Section 3 (Eq. Ntaub and the trace formula after it) as the alternative.
+  of Section 3 (Eq. Ntaub and the trace formula after it) as the alternative.  TransportVar:
+  the same with a velocity field beta(x) that varies in space (the paper's experiments of
+  Section 5.1), every element with its own local matrix.
 * Section 3, Eq. (localSolverDD) and the trace formula below it: linearized shallow water,
   backward Euler in time.
 * Section 4.1, Eqs. (ErrorDDMCD1)/(ErrorDDMCD2) and the flux (general_flux_convdiff):
@@ -370,6 +372,129 @@ class Transport(Problem):
         inflow = ((b > 0) & ~hasL) | ((b < 0) & ~hasR)
         boundary = np.where(inflow, gfull - T, own - T)
         return np.where(hasL & hasR, interior, boundary)
+
+
+
+# =============================================================================
+class TransportVar(Problem):
+    """Steady transport beta.grad u = f with a velocity field beta(x) that varies in space
+    (Section 3, Eq. transport; beta continuous across the skeleton), upwind HDG flux.
+
+    Every element has its own local matrix.  The local equation (transportLocalk1) is used in
+    its integrated-by-parts form
+        (beta.grad u^{k+1}, v)_K + <|beta.n| (u^{k+1} - u_hat^k), v>_dK = (f, v)_K,
+    which equals the printed form -(u, div(beta v))_K + <beta.n u + |beta.n|(u - u_hat), v>_dK
+    under exact integration and needs beta, not div(beta), at the quadrature points.  Every
+    integral is a Gauss sum with beta sampled at the quadrature points.  The weighted trace
+    (transportLocale) is formed point by point on each face: the upwind side's u^k where
+    beta.n != 0 (g on the inflow boundary), so a face may be inflow in one part and outflow
+    in another.  beta_fn maps physical points (..., d) to velocities (..., d).
+    """
+
+    nc = 1
+
+    def __init__(self, disc, beta_fn):
+        m = disc.mesh
+        self.beta_fn = beta_fn
+        self.bq = np.asarray(beta_fn(disc.volume_points()), dtype=np.float64)            # (nel, nq, d)
+        self.bf = np.asarray(beta_fn(disc.face_points(np.arange(m.nface))), dtype=np.float64)  # (nface, nqf, d)
+        # beta . (outward normal of local face f) at that face's points, per element
+        self.bn = np.zeros((m.nel, 2 * disc.d, disc.nqf))
+        for f in range(2 * disc.d):
+            self.bn[:, f, :] = self.bf[m.elem_face[:, f]] @ disc.normal[f]
+        super().__init__(disc)
+
+    def local_matrix(self):
+        disc, ref, h = self.disc, self.disc.ref, self.mesh.h
+        wJ = ref.wq * disc.jac
+        # (beta.grad phi_j)(x_q), physical gradient of the reference basis
+        bgrad = sum(self.bq[:, :, a, None] * ((2.0 / h[a]) * ref.Dq[a])[None] for a in range(disc.d))
+        A = np.einsum("q,kqj,qi->kij", wJ, bgrad, ref.Bq)
+        for f in range(2 * disc.d):
+            w = np.abs(self.bn[:, f, :]) * (ref.face_w * disc.face_jac[f])[None, :]
+            A += np.einsum("kq,qj,qi->kij", w, ref.face_B[f], ref.face_B[f])
+        return A
+
+    def solve_local(self, rhs):
+        sol = np.linalg.solve(self.A, rhs[:, :, None])[:, :, 0]
+        return sol.reshape(-1, self.nc, self.disc.nb)
+
+    def volume_rhs(self, f_qp, U_prev=None):
+        return self.disc.load(f_qp)
+
+    def traces(self, U, g_qp):
+        m = self.mesh
+        L, R = self.face_side_values(U, [0])[0]
+        b = self.bf[np.arange(m.nface), :, m.face_axis]   # beta . (left element's outward normal)
+        hasL = (m.face_left >= 0)[:, None]
+        hasR = (m.face_right >= 0)[:, None]
+        gfull = np.zeros_like(L)
+        gfull[m.bface_ids] = g_qp
+        up_left = np.where(hasL, L, gfull)
+        up_right = np.where(hasR, R, gfull)
+        avg = np.where(hasL & hasR, 0.5 * (np.nan_to_num(L) + np.nan_to_num(R)), np.where(hasL, L, R))
+        return np.where(b > 0, up_left, np.where(b < 0, up_right, avg))
+
+    def trace_coupling(self):
+        """Per element and local face: (nel, nb, q^(d-1)) maps of the face trace to the rhs."""
+        disc, ref = self.disc, self.disc.ref
+        return [ref.face_B[f].T[None, :, :] * (np.abs(self.bn[:, f, :]) * (ref.face_w * disc.face_jac[f])[None, :])[:, None, :]
+                for f in range(2 * disc.d)]
+
+    def trace_rhs(self, T):
+        Te = self.elem_traces(T)
+        W = self.trace_coupling()
+        return sum(np.einsum("kiq,kq->ki", W[f], Te[:, f, :]) for f in range(2 * self.disc.d))
+
+    def norm2(self, dU):
+        return self.disc.mass_norm2(dU[:, 0, :])
+
+    def face_equations(self, vals, T, g):
+        """Conservation (transportGlobal) point by point: [[beta.n u + |beta.n|(u - u_hat)]] = 0
+        on interior faces where beta.n != 0, u_hat = {{u}} where beta.n = 0; on the boundary
+        u_hat = g where the flow enters and u_hat = u^- elsewhere."""
+        m = self.mesh
+        L, R = (np.nan_to_num(v) for v in vals[0])
+        b = self.bf[np.arange(m.nface), :, m.face_axis]
+        hasL = (m.face_left >= 0)[:, None]
+        hasR = (m.face_right >= 0)[:, None]
+        gfull = np.zeros_like(T)
+        gfull[m.bface_ids] = g
+        ab = np.abs(b)
+        interior = np.where(b != 0, b * L - b * R + ab * (L - T) + ab * (R - T), 0.5 * (L + R) - T)
+        own = np.where(hasL, L, R)
+        inflow = ((b > 0) & ~hasL) | ((b < 0) & ~hasR)
+        boundary = np.where(inflow, gfull - T, own - T)
+        return np.where(hasL & hasR, interior, boundary)
+
+    def direct_solve(self, f_qp, g_qp, U_prev=None):
+        """Static condensation of (HDGlocal) + (transportGlobal) with per-element local
+        matrices: U_K = A_K^{-1}(b_K + sum_f W_Kf T_f), then the face residuals are affine in
+        the face-point traces T; the square system is assembled by probing and solved densely."""
+        m, disc = self.mesh, self.disc
+        nqf = disc.nqf
+        nT = m.nface * nqf
+        b = self.volume_rhs(f_qp, U_prev)
+        U0 = np.linalg.solve(self.A, b[:, :, None])[:, :, 0]
+        W = self.trace_coupling()
+        Lf = [np.linalg.solve(self.A, W[f]) for f in range(2 * disc.d)]     # (nel, nb, nqf)
+        S = np.zeros((nT, nT))
+        r0 = -self._face_residuals(U0.reshape(-1, self.nc, disc.nb), np.zeros(nT), g_qp)
+        for col in range(nT):
+            e, j = divmod(col, nqf)
+            Ucol = np.zeros((m.nel, self.nvol))
+            for side, lf in ((m.face_left[e], 2 * m.face_axis[e] + 1), (m.face_right[e], 2 * m.face_axis[e])):
+                if side >= 0:
+                    Ucol[side] += Lf[lf][side][:, j]
+            Tcol = np.zeros(nT)
+            Tcol[col] = 1.0
+            S[:, col] = self._face_residuals(Ucol.reshape(-1, self.nc, disc.nb), Tcol, g_qp, homogeneous=True)
+        T = np.linalg.solve(S, r0).reshape(m.nface, nqf)
+        Te = self.elem_traces(T)
+        U = U0.copy()
+        for f in range(2 * disc.d):
+            U += np.einsum("kij,kj->ki", Lf[f], Te[:, f, :])
+        return U.reshape(-1, self.nc, disc.nb), T
 
 
 # =============================================================================

@@ -12,6 +12,9 @@ Workloads (the sizes are the ones the benchmarks and parity tests use):
   transport3d   3D steady transport, beta = (1,1,1)/sqrt(3), u = sin(pi x) sin(pi y) sin(pi z)
   swe_bump      2D linearized shallow water, Gaussian bump in phi with seeded 1% amplitude
                 noise per GLL node, zero velocity
+  e1, e2        transport with velocity fields that vary in space: beta = (1 + sin(pi y/2), 2)
+                on [0,2]^2 with discontinuous inflow data, and beta = (z, x, y) on [0,1]^3 with
+                u = sin(pi x) cos(pi y) sin(pi z) / pi
   serving       a seeded stream of convection-diffusion requests with Poisson arrivals
 """
 import math
@@ -39,6 +42,41 @@ def transport3d_forcing(X, beta=(1 / math.sqrt(3),) * 3):
     s = [np.sin(PI * X[..., a]) for a in range(3)]
     c = [np.cos(PI * X[..., a]) for a in range(3)]
     return PI * (beta[0] * c[0] * s[1] * s[2] + beta[1] * s[0] * c[1] * s[2] + beta[2] * s[0] * s[1] * c[2])
+
+
+# ----------------------------------------------------------------------------- variable beta
+# The two transport experiments of the paper's Section 5.1 (Table 1), with velocity fields
+# that vary in space.
+def e1_beta(X):
+    """2D: beta = (1 + sin(pi y / 2), 2) on [0,2]^2 (divergence-free)."""
+    y = X[..., 1]
+    return np.stack([1.0 + np.sin(PI * y / 2.0), np.full_like(y, 2.0)], axis=-1)
+
+
+def e1_inflow(X):
+    """2D inflow data: 1 on x = 0; sin^6(pi x) on y = 0 for 0 < x <= 1; 0 on y = 0 for x >= 1;
+    the forcing is zero.  Evaluated on boundary points (outflow points get values that the
+    upwind flux never reads)."""
+    x, y = X[..., 0], X[..., 1]
+    return np.where(x <= 0.0, 1.0, np.where((y <= 0.0) & (x <= 1.0), np.sin(PI * x) ** 6, 0.0))
+
+
+def e2_beta(X):
+    """3D: beta = (z, x, y) on [0,1]^3 (divergence-free, inflow faces x = 0, y = 0, z = 0)."""
+    return np.stack([X[..., 2], X[..., 0], X[..., 1]], axis=-1)
+
+
+def e2_exact(X):
+    """u = sin(pi x) cos(pi y) sin(pi z) / pi."""
+    return np.sin(PI * X[..., 0]) * np.cos(PI * X[..., 1]) * np.sin(PI * X[..., 2]) / PI
+
+
+def e2_forcing(X):
+    """f = beta.grad u for beta = (z, x, y) and u = sin(pi x) cos(pi y) sin(pi z) / pi."""
+    x, y, z = X[..., 0], X[..., 1], X[..., 2]
+    sx, cx, sy, cy, sz, cz = (np.sin(PI * x), np.cos(PI * x), np.sin(PI * y), np.cos(PI * y), np.sin(PI * z),
+                              np.cos(PI * z))
+    return z * cx * cy * sz - x * sx * sy * sz + y * sx * cy * cz
 
 
 # ----------------------------------------------------------------------------- conv.-diff.
