@@ -308,6 +308,55 @@ ihdg_status ihdg_submit(ihdg_ctx* ctx, const ihdg_mesh* mesh, const ihdg_coeffs*
 ihdg_status ihdg_poll(ihdg_ctx* ctx, ihdg_ticket ticket, ihdg_result* res);
 ihdg_status ihdg_fetch(ihdg_ctx* ctx, ihdg_ticket ticket, double* u_out, double* trace_out);
 
+/* Transport with a velocity field that varies in space (Section 3: beta.grad u = f with beta
+ * continuous across the skeleton; the paper's transport experiments of Section 5.1, Table 1,
+ * use such fields).  Every element has its own local matrix A_K, so the local solves of
+ * Algorithm 1 are factorised once per field into a plan: float64 LU on the host (threads over
+ * elements), and L_K = A_K^{-1} G_K (the trace coupling) and A_K^{-1} kept in device memory in
+ * float64 with float32 and bf16 copies of L_K.  A sweep is then u_K^{k+1} = A_K^{-1} b_K +
+ * L_K t_K(u^k) for every element: the device streams each element's own operator (a batched
+ * GEMV), so it is bound by HBM bandwidth.  The local equation is (transportLocalk1) in its
+ * integrated-by-parts form (beta.grad u, v)_K + <|beta.n| (u - u_hat^k), v>_dK = (f, v)_K
+ * (equal to the printed form under exact integration; beta, not div beta, is sampled), with
+ * the upwind trace of Eq. transportLocale.
+ *
+ * ihdg_face_quadrature_points: the Gauss points of EVERY global face (global face order),
+ * [n_face][nqf][dim] (host-only), where the caller samples beta on the skeleton.
+ *
+ * ihdg_var_plan_create: beta_vol [n_el][nqv][dim] at the volume quadrature points of
+ * ihdg_quadrature_points, beta_face [n_face][nqf][dim] at the points above (host arrays, read
+ * during the call).  Each beta component must keep one sign (or vanish) over all faces
+ * normal to its axis, so that each element face is an inflow or an outflow face as a whole
+ * (true for the paper's fields); otherwise IHDG_ERR_UNSUPPORTED.  Built for 2D p = 1..4 and
+ * 3D p = 1..2.  The plan allocates its device memory on the context's device
+ * (ihdg_var_plan_info reports how much) and is freed by ihdg_var_plan_destroy.
+ *
+ * ihdg_var_solve: f_qp [n_el][nqv] (forcing at the volume quadrature points), g_qp
+ * [n_bface][nqf] (inflow data at the boundary quadrature points, read on inflow faces only),
+ * options as for ihdg_solve with prec FP64, MIXED_FP32 or MIXED_BF16 (float32 / bf16 inner
+ * sweeps with float32 accumulation on the correction equation, float64 outer sweeps and
+ * stopping norm) and opts->u0 an optional initial guess [n_el][(p+1)^dim]; u_out
+ * [n_el][(p+1)^dim], trace_out [n_face][(p+1)^(dim-1)] (NULL = skip).  Host buffers, copies
+ * inside the call.  ihdg_var_solve_device: the same with device arrays, ordered on `stream`;
+ * returns after the solve has finished.  Errors as for ihdg_solve; IHDG_ERR_INVALID when the
+ * plan belongs to another context's device. */
+typedef struct ihdg_var_plan ihdg_var_plan;
+ihdg_status ihdg_face_quadrature_points(const ihdg_mesh* mesh, double* xyz);
+ihdg_status ihdg_var_plan_create(ihdg_ctx* ctx, const ihdg_mesh* mesh, const double* beta_vol,
+                                 const double* beta_face, ihdg_var_plan** out);
+void ihdg_var_plan_destroy(ihdg_var_plan* plan);
+ihdg_status ihdg_var_plan_info(const ihdg_var_plan* plan, size_t* device_bytes, double* setup_ms);
+ihdg_status ihdg_var_solve(ihdg_ctx* ctx, ihdg_var_plan* plan, const double* f_qp, const double* g_qp,
+                           const ihdg_options* opts, double* u_out, double* trace_out, ihdg_result* res);
+ihdg_status ihdg_var_solve_device(ihdg_ctx* ctx, ihdg_var_plan* plan, const double* d_f_qp,
+                                  const double* d_g_qp, const ihdg_options* opts, double* d_u_out,
+                                  double* d_trace_out, void* stream, ihdg_result* res);
+/* Host-only inspection of one element's float64 local solve as the plan builds it (no device
+ * needed): which = 0 L_K = A_K^{-1} G_K (nvol x n_in; column f*nf + r is face f's node r),
+ * 1 A_K^{-1} (nvol x nvol).  Row-major into data (NULL: query rows/cols only). */
+ihdg_status ihdg_var_host_operator(const ihdg_mesh* mesh, const double* beta_vol, const double* beta_face,
+                                   long long element, int which, int* rows, int* cols, double* data);
+
 /* Device peak rates that bound the sweep kernels where neither HBM bandwidth nor the bf16
  * tensor rate does.  No counterpart in the paper: these are roofline denominators.  Each is
  * the best of five timed launches of one probe kernel (after a warm-up launch) on `device`:

@@ -25,6 +25,7 @@
 #include "ihdg_kernels.h"
 #include "ihdg_mixed.h"
 #include "ihdg_ops.h"
+#include "ihdg_var.h"
 
 using namespace ihdg;
 
@@ -1115,6 +1116,142 @@ ihdg_status ihdg_swe_steps(ihdg_ctx* ctx, const ihdg_mesh* mesh, const ihdg_coef
   st = ihdg_swe_steps_device(ctx, mesh, co, d_q, nsteps, &o, iters_per_step, static_cast<char*>(ctx->scratch) + bq, ws, nullptr, res);
   if (st != IHDG_OK) return st;
   CK(cudaMemcpy(q, d_q, sizeof(double) * sz.n_el * sz.nvol, cudaMemcpyDeviceToHost), "copy q");
+  return IHDG_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Transport with a velocity field that varies in space: plans of per-element local solves.
+}  // extern "C"
+
+struct ihdg_var_plan {
+  int device = 0;
+  ihdg_mesh mesh{};
+  ihdg::VarDev dev;
+  long long n_el = 0, n_bface = 0, n_face = 0;
+  int nvol = 0, nqv = 0, nqf = 0, nf = 0;
+  double setup_ms = 0.0;
+};
+
+extern "C" {
+
+ihdg_status ihdg_face_quadrature_points(const ihdg_mesh* mesh, double* xyz) {
+  if (!mesh || !xyz) return IHDG_ERR_INVALID;
+  std::string err;
+  ihdg_status st = validate(*mesh, nullptr, err);
+  if (st != IHDG_OK) return st;
+  face_points(*mesh, xyz);
+  return IHDG_OK;
+}
+
+ihdg_status ihdg_var_plan_create(ihdg_ctx* ctx, const ihdg_mesh* mesh, const double* beta_vol, const double* beta_face,
+                                 ihdg_var_plan** out) {
+  if (!ctx) return IHDG_ERR_INVALID;
+  if (!mesh || !beta_vol || !beta_face || !out) return fail(ctx, IHDG_ERR_INVALID, "null argument");
+  *out = nullptr;
+  const auto t0 = std::chrono::steady_clock::now();
+  VarHost h;
+  std::string err;
+  ihdg_status st = build_var(*mesh, beta_vol, beta_face, h, err);
+  if (st != IHDG_OK) return fail(ctx, st, err);
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  auto pl = std::make_unique<ihdg_var_plan>();
+  pl->device = ctx->device;
+  pl->mesh = *mesh;
+  cudaError_t e = var_upload(h, pl->dev, 100000);
+  if (e != cudaSuccess) {
+    const ihdg_status code = e == cudaErrorMemoryAllocation ? IHDG_ERR_NOMEM : IHDG_ERR_CUDA;
+    return fail(ctx, code, std::string("variable-coefficient plan upload: ") + cudaGetErrorString(e));
+  }
+  pl->n_el = h.nel;
+  pl->n_bface = h.nbface;
+  pl->n_face = h.nface;
+  pl->nvol = h.nb;
+  pl->nqv = h.nqv;
+  pl->nqf = h.nqf;
+  pl->nf = h.nf;
+  pl->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  *out = pl.release();
+  ctx->err.clear();
+  return IHDG_OK;
+}
+
+void ihdg_var_plan_destroy(ihdg_var_plan* plan) {
+  if (!plan) return;
+  cudaSetDevice(plan->device);
+  var_free(plan->dev);
+  delete plan;
+}
+
+ihdg_status ihdg_var_plan_info(const ihdg_var_plan* plan, size_t* device_bytes, double* setup_ms) {
+  if (!plan) return IHDG_ERR_INVALID;
+  if (device_bytes) *device_bytes = plan->dev.bytes;
+  if (setup_ms) *setup_ms = plan->setup_ms;
+  return IHDG_OK;
+}
+
+ihdg_status ihdg_var_host_operator(const ihdg_mesh* mesh, const double* beta_vol, const double* beta_face,
+                                   long long element, int which, int* rows, int* cols, double* data) {
+  if (!mesh || !beta_vol || !beta_face || !rows || !cols) return IHDG_ERR_INVALID;
+  VarHost h;
+  std::string err;
+  ihdg_status st = build_var(*mesh, beta_vol, beta_face, h, err);
+  if (st != IHDG_OK) return st;
+  if (element < 0 || element >= h.nel || (which != 0 && which != 1)) return IHDG_ERR_INVALID;
+  *rows = h.nb;
+  *cols = which == 0 ? h.nin : h.nb;
+  if (!data) return IHDG_OK;
+  const int nc = *cols;
+  const double* src = which == 0 ? &h.L[(size_t)element * h.nin * h.nb] : &h.Ainv[(size_t)element * h.nb * h.nb];
+  for (int i = 0; i < h.nb; ++i)
+    for (int k = 0; k < nc; ++k) data[(size_t)i * nc + k] = src[(size_t)k * h.nb + i];   // stored column by column
+  return IHDG_OK;
+}
+
+ihdg_status ihdg_var_solve_device(ihdg_ctx* ctx, ihdg_var_plan* plan, const double* d_f, const double* d_g,
+                                  const ihdg_options* opts, double* d_u, double* d_tr, void* stream, ihdg_result* res) {
+  if (!ctx) return IHDG_ERR_INVALID;
+  if (!plan || !d_f || !d_g || !d_u) return fail(ctx, IHDG_ERR_INVALID, "null argument");
+  if (plan->device != ctx->device) return fail(ctx, IHDG_ERR_INVALID, "the plan belongs to another device");
+  ihdg_options o = defaults(opts);
+  ihdg_status st = check_opts(ctx, o);
+  if (st != IHDG_OK) return st;
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  std::string err;
+  st = var_solve(plan->dev, d_f, d_g, o, d_u, d_tr, static_cast<cudaStream_t>(stream), ctx->h_ctrl, err, res);
+  if (st != IHDG_OK) return fail(ctx, st, err);
+  ctx->err.clear();
+  return IHDG_OK;
+}
+
+ihdg_status ihdg_var_solve(ihdg_ctx* ctx, ihdg_var_plan* plan, const double* f_qp, const double* g_qp,
+                           const ihdg_options* opts, double* u_out, double* trace_out, ihdg_result* res) {
+  if (!ctx) return IHDG_ERR_INVALID;
+  if (!plan || !f_qp || !g_qp || !u_out) return fail(ctx, IHDG_ERR_INVALID, "null argument");
+  if (plan->device != ctx->device) return fail(ctx, IHDG_ERR_INVALID, "the plan belongs to another device");
+  ihdg_options o = defaults(opts);
+  ihdg_status st = check_opts(ctx, o);
+  if (st != IHDG_OK) return st;
+  const size_t bf = align256(sizeof(double) * plan->n_el * plan->nqv), bg = align256(sizeof(double) * plan->n_bface * plan->nqf);
+  const size_t bu = align256(sizeof(double) * plan->n_el * plan->nvol), bt = align256(sizeof(double) * plan->n_face * plan->nf);
+  const size_t bu0 = o.u0 ? bu : 0;
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  st = ensure_scratch(ctx, bf + bg + bu + bt + bu0);
+  if (st != IHDG_OK) return st;
+  char* s = static_cast<char*>(ctx->scratch);
+  double* d_f = reinterpret_cast<double*>(s);
+  double* d_g = reinterpret_cast<double*>(s + bf);
+  double* d_u = reinterpret_cast<double*>(s + bf + bg);
+  double* d_t = reinterpret_cast<double*>(s + bf + bg + bu);
+  double* d_u0 = o.u0 ? reinterpret_cast<double*>(s + bf + bg + bu + bt) : nullptr;
+  CK(cudaMemcpy(d_f, f_qp, sizeof(double) * plan->n_el * plan->nqv, cudaMemcpyHostToDevice), "copy f");
+  CK(cudaMemcpy(d_g, g_qp, sizeof(double) * plan->n_bface * plan->nqf, cudaMemcpyHostToDevice), "copy g");
+  if (o.u0) CK(cudaMemcpy(d_u0, o.u0, sizeof(double) * plan->n_el * plan->nvol, cudaMemcpyHostToDevice), "copy u0");
+  ihdg_options od = o;
+  od.u0 = d_u0;
+  st = ihdg_var_solve_device(ctx, plan, d_f, d_g, &od, d_u, trace_out ? d_t : nullptr, nullptr, res);
+  if (st != IHDG_OK) return st;
+  CK(cudaMemcpy(u_out, d_u, sizeof(double) * plan->n_el * plan->nvol, cudaMemcpyDeviceToHost), "copy u");
+  if (trace_out) CK(cudaMemcpy(trace_out, d_t, sizeof(double) * plan->n_face * plan->nf, cudaMemcpyDeviceToHost), "copy trace");
   return IHDG_OK;
 }
 

@@ -324,6 +324,51 @@ void quadrature_points(const ihdg_mesh& m, double* vol_xyz, double* bnd_xyz) {
   }
 }
 
+void face_points(const ihdg_mesh& m, double* xyz) {
+  Ref1D r = make_ref(m.p);
+  const int d = m.dim, q = r.q;
+  const int n0 = m.n[0], n1 = m.n[1], n2 = d == 3 ? m.n[2] : 1;
+  double h[3] = {1, 1, 1};
+  for (int a = 0; a < d; ++a) h[a] = (m.hi[a] - m.lo[a]) / m.n[a];
+  int nqf = 1;
+  for (int a = 1; a < d; ++a) nqf *= q;
+  long long fid = 0;
+  for (int ax = 0; ax < d; ++ax) {
+    const int e0 = n0 + (ax == 0), e1 = n1 + (ax == 1), e2 = n2 + (ax == 2 && d == 3);
+    for (int k = 0; k < e2; ++k)
+      for (int j = 0; j < e1; ++j)
+        for (int i = 0; i < e0; ++i, ++fid) {
+          const int c[3] = {i, j, k};
+          for (int g = 0; g < nqf; ++g) {
+            int gi[2] = {0, 0};
+            unflat(g, q, d - 1, gi);
+            int t = 0;
+            for (int a = 0; a < d; ++a) {
+              const double x = a == ax ? m.lo[a] + c[a] * h[a] : m.lo[a] + c[a] * h[a] + 0.5 * (r.xg[gi[t++]] + 1.0) * h[a];
+              xyz[((size_t)fid * nqf + g) * d + a] = x;
+            }
+          }
+        }
+  }
+}
+
+RefTables ref_tables(int p) {
+  Ref1D r = make_ref(p);
+  RefTables t;
+  t.p = r.p;
+  t.q = r.q;
+  t.nb1 = r.nb1;
+  t.xn = r.xn;
+  t.xg = r.xg;
+  t.wg = r.wg;
+  t.Lg = r.Lg;
+  t.Dg = r.Dg;
+  t.M1 = r.M1;
+  return t;
+}
+
+bool dense_solve(std::vector<double> A, int n, std::vector<double>& B, int m) { return lu_solve(std::move(A), n, B, m); }
+
 void node_points(const ihdg_mesh& m, double* xyz) {
   Ref1D r = make_ref(m.p);
   int d = m.dim, nb1 = r.nb1;

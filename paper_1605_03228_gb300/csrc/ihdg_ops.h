@@ -65,5 +65,19 @@ void node_points(const ihdg_mesh& mesh, double* xyz);
 long long count_faces(const ihdg_mesh& mesh, long long* n_bface);
 // Per boundary face: (element, local face) in boundary-face order.
 void boundary_faces(const ihdg_mesh& mesh, std::vector<long long>& elem, std::vector<int>& lf);
+// Quadrature points of every global face, [n_face][q^(dim-1)][dim], global face order.
+void face_points(const ihdg_mesh& mesh, double* xyz);
+
+// 1D reference tables of order p: GLL nodes xn (p+1), Gauss points xg and weights wg
+// (q = p+2), the Lagrange basis and its derivative at the Gauss points (Lg, Dg: q x (p+1),
+// row-major) and the exact 1D mass matrix M1 ((p+1) x (p+1)) on [-1, 1].
+struct RefTables {
+  int p = 0, q = 0, nb1 = 0;
+  std::vector<double> xn, xg, wg, Lg, Dg, M1;
+};
+RefTables ref_tables(int p);
+// Dense LU with partial pivoting: solves A X = B (A n x n, B n x m, both row-major; B is
+// overwritten with X).  Returns false for a singular A.
+bool dense_solve(std::vector<double> A, int n, std::vector<double>& B, int m);
 
 }  // namespace ihdg

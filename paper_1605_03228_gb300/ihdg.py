@@ -68,7 +68,9 @@ class Peaks(ctypes.Structure):
 EXPORTED = ["ihdg_create", "ihdg_destroy", "ihdg_last_error", "ihdg_problem_sizes", "ihdg_quadrature_points",
             "ihdg_node_points", "ihdg_solve", "ihdg_workspace_bytes", "ihdg_solve_device", "ihdg_swe_steps",
             "ihdg_swe_steps_device", "ihdg_host_operator", "ihdg_solve_device_static", "ihdg_server_start",
-            "ihdg_server_stop", "ihdg_submit", "ihdg_poll", "ihdg_fetch", "ihdg_autotune", "ihdg_measure_peaks"]
+            "ihdg_server_stop", "ihdg_submit", "ihdg_poll", "ihdg_fetch", "ihdg_autotune", "ihdg_measure_peaks",
+            "ihdg_face_quadrature_points", "ihdg_var_plan_create", "ihdg_var_plan_destroy", "ihdg_var_plan_info",
+            "ihdg_var_solve", "ihdg_var_solve_device", "ihdg_var_host_operator"]
 STATIC_SCRATCH_BYTES = 64 * 1024 * 1024
 
 _lib = None
@@ -112,10 +114,18 @@ def load(build_if_missing=True):
     L.ihdg_poll.argtypes = [VP, ctypes.c_longlong, P(Result)]
     L.ihdg_fetch.argtypes = [VP, ctypes.c_longlong, dp, dp]
     L.ihdg_measure_peaks.argtypes = [I, P(Peaks)]
+    L.ihdg_face_quadrature_points.argtypes = [P(Mesh), dp]
+    L.ihdg_var_plan_create.argtypes = [VP, P(Mesh), dp, dp, P(VP)]
+    L.ihdg_var_plan_destroy.argtypes = [VP]
+    L.ihdg_var_plan_info.argtypes = [VP, P(SZ), dp]
+    L.ihdg_var_solve.argtypes = [VP, VP, dp, dp, P(Options), dp, dp, P(Result)]
+    L.ihdg_var_solve_device.argtypes = [VP, VP, VP, VP, P(Options), VP, VP, VP, P(Result)]
+    L.ihdg_var_host_operator.argtypes = [P(Mesh), dp, dp, ctypes.c_longlong, I, P(I), P(I), dp]
     for name in EXPORTED:
         f = getattr(L, name)
-        if name not in ("ihdg_destroy", "ihdg_last_error"):
+        if name not in ("ihdg_destroy", "ihdg_last_error", "ihdg_var_plan_destroy"):
             f.restype = ctypes.c_int
+    L.ihdg_var_plan_destroy.restype = None
     _lib = L
     return L
 
@@ -195,6 +205,37 @@ def quadrature_points(mesh, coeffs):
     if st != OK:
         raise IHDGError(st, "ihdg_quadrature_points")
     return vol, bnd
+
+
+def face_quadrature_points(mesh):
+    """Gauss points of every global face, (n_face, q^(dim-1), dim), global face order."""
+    L = load()
+    co = make_coeffs(TRANSPORT, beta=(1.0, 0.0, 0.0))
+    s = problem_sizes(mesh, co)
+    nqf = (mesh.p + 2) ** (mesh.dim - 1)
+    xyz = np.zeros((s.n_face, nqf, mesh.dim))
+    st = L.ihdg_face_quadrature_points(ctypes.byref(mesh), _dptr(xyz))
+    if st != OK:
+        raise IHDGError(st, "ihdg_face_quadrature_points")
+    return xyz
+
+
+def var_host_operator(mesh, beta_vol, beta_face, element, which):
+    """ihdg_var_host_operator: one element's L_K (which 0) or A_K^{-1} (which 1), host float64."""
+    L = load()
+    bv = np.ascontiguousarray(beta_vol, dtype=np.float64)
+    bf = np.ascontiguousarray(beta_face, dtype=np.float64)
+    r, c = ctypes.c_int(0), ctypes.c_int(0)
+    st = L.ihdg_var_host_operator(ctypes.byref(mesh), _dptr(bv), _dptr(bf), int(element), int(which), ctypes.byref(r),
+                                  ctypes.byref(c), None)
+    if st != OK:
+        raise IHDGError(st, "ihdg_var_host_operator")
+    out = np.zeros((r.value, c.value))
+    st = L.ihdg_var_host_operator(ctypes.byref(mesh), _dptr(bv), _dptr(bf), int(element), int(which), ctypes.byref(r),
+                                  ctypes.byref(c), _dptr(out))
+    if st != OK:
+        raise IHDGError(st, "ihdg_var_host_operator")
+    return out
 
 
 def node_points(mesh, coeffs):
@@ -306,6 +347,17 @@ class Context:
         self._check(st, "ihdg_solve_device_static")
         return res
 
+    # ---------------------------------------------------------------- variable beta
+    def var_plan(self, mesh, beta_vol, beta_face):
+        """ihdg_var_plan_create: per-element local solves of transport with a velocity field
+        sampled at the volume and face quadrature points.  Returns a VarPlan."""
+        bv = np.ascontiguousarray(beta_vol, dtype=np.float64)
+        bf = np.ascontiguousarray(beta_face, dtype=np.float64)
+        h = ctypes.c_void_p()
+        st = self.L.ihdg_var_plan_create(self.h, ctypes.byref(mesh), _dptr(bv), _dptr(bf), ctypes.byref(h))
+        self._check(st, "ihdg_var_plan_create")
+        return VarPlan(self, mesh, h)
+
     # ---------------------------------------------------------------- serving
     def server_start(self, hbm_budget_bytes, slots):
         self._check(self.L.ihdg_server_start(self.h, ctypes.c_size_t(hbm_budget_bytes), slots), "ihdg_server_start")
@@ -358,3 +410,53 @@ class Context:
                                           ctypes.c_size_t(ws_bytes), ctypes.c_void_p(stream), ctypes.byref(res))
         self._check(st, "ihdg_swe_steps_device")
         return list(its)[:nsteps], res
+
+
+class VarPlan:
+    """An ihdg_var_plan: the per-element local solves of one velocity field on one device."""
+
+    def __init__(self, ctx, mesh, h):
+        self.ctx, self.mesh, self.h = ctx, mesh, h
+        co = make_coeffs(TRANSPORT, beta=(1.0, 0.0, 0.0))
+        self.sizes = problem_sizes(mesh, co)
+
+    def close(self):
+        if self.h:
+            self.ctx.L.ihdg_var_plan_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        """(device bytes, host set-up time in ms)."""
+        b = ctypes.c_size_t(0)
+        ms = ctypes.c_double(0.0)
+        self.ctx._check(self.ctx.L.ihdg_var_plan_info(self.h, ctypes.byref(b), ctypes.byref(ms)), "ihdg_var_plan_info")
+        return b.value, ms.value
+
+    def solve(self, f_qp, g_qp, opts, want_trace=True):
+        """Host-buffer solve: (u [n_el, (p+1)^dim], trace or None, Result)."""
+        s = self.sizes
+        f = np.ascontiguousarray(f_qp, dtype=np.float64)
+        g = np.ascontiguousarray(g_qp, dtype=np.float64)
+        u = np.zeros((s.n_el, (self.mesh.p + 1) ** self.mesh.dim))
+        tr = np.zeros((s.n_face, s.nface_nodes)) if want_trace else None
+        res = Result()
+        st = self.ctx.L.ihdg_var_solve(self.ctx.h, self.h, _dptr(f), _dptr(g), ctypes.byref(opts), _dptr(u),
+                                       _dptr(tr), ctypes.byref(res))
+        self.ctx._check(st, "ihdg_var_solve")
+        return u, tr, res
+
+    def solve_device(self, d_f, d_g, opts, d_u, d_tr=0, stream=0):
+        """Device-pointer solve (integer pointers).  Returns Result."""
+        res = Result()
+        st = self.ctx.L.ihdg_var_solve_device(self.ctx.h, self.h, ctypes.c_void_p(d_f), ctypes.c_void_p(d_g),
+                                              ctypes.byref(opts), ctypes.c_void_p(d_u),
+                                              ctypes.c_void_p(d_tr) if d_tr else None, ctypes.c_void_p(stream),
+                                              ctypes.byref(res))
+        self.ctx._check(st, "ihdg_var_solve_device")
+        return res

@@ -191,3 +191,63 @@ def test_export_form_matches_oracle_swe(p):
     pr = ShallowWater(Discretisation(om, p), 1.5, 0.01, 0.3, 0.1)
     nf = p + 1
     check_one_sweep(mesh, co, pr, ["sum"] * 4, [f * nf for f in range(4)], [(f ^ 1) * nf for f in range(4)], True)
+
+
+# ------------------------------------------------------------------ variable beta (host)
+def _var_case(d, field):
+    from oracle.refelem import lagrange_matrix
+    if d == 2:
+        n, p = (4, 3), 3
+        mesh = ihdg.make_mesh(2, n, p, hi=(2.0, 2.0))
+        om = BoxMesh(2, n, lo=[0, 0], hi=[2, 2])
+    else:
+        n, p = (2, 3, 2), 2
+        mesh = ihdg.make_mesh(3, n, p)
+        om = BoxMesh(3, n)
+    return mesh, om, p, field
+
+
+@pytest.mark.parametrize("d,field", [(2, "e1"), (2, "neg"), (2, "zero_y"), (3, "e2")])
+def test_var_operators_match_oracle(d, field):
+    """The plan's per-element local solve, built on the host from beta sampled at the library's
+    quadrature points, against the oracle's (TransportVar, its own tables): A_K^{-1} and
+    L_K = A_K^{-1} G_K, where the oracle's face-point coupling W_Kf times the face nodal basis
+    at the face Gauss points is G_K's block of face f (outflow and inflow faces; faces with
+    beta.n = 0 couple nothing)."""
+    import workloads as W
+    from oracle import Discretisation, TransportVar
+    from oracle.refelem import lagrange_matrix
+    fields = {"e1": W.e1_beta, "e2": W.e2_beta,
+              "neg": lambda X: np.stack([-(1.0 + 0.3 * np.sin(X[..., 1])), -0.5 - 0.2 * X[..., 0]], axis=-1),
+              "zero_y": lambda X: np.stack([1.0 + 0.5 * X[..., 1], 0.0 * X[..., 0]], axis=-1)}
+    mesh, om, p, _ = _var_case(d, field)
+    co = ihdg.make_coeffs(ihdg.TRANSPORT, beta=(1.0, 0.0, 0.0))
+    vol, _ = ihdg.quadrature_points(mesh, co)
+    fpts = ihdg.face_quadrature_points(mesh)
+    disc = Discretisation(om, p)
+    assert np.abs(fpts - disc.face_points(np.arange(om.nface))).max() < 1e-13
+    assert np.abs(vol - disc.volume_points()).max() < 1e-13
+    beta = fields[field]
+    pr = TransportVar(disc, beta)
+    B1 = lagrange_matrix(disc.ref.nodes1, disc.ref.xq1)
+    Bf = B1 if d == 2 else np.kron(B1, B1)
+    W_ = pr.trace_coupling()
+    for K in (0, om.nel // 2, om.nel - 1):
+        Ainv = np.linalg.inv(pr.A[K])
+        assert np.allclose(ihdg.var_host_operator(mesh, beta(vol), beta(fpts), K, 1), Ainv, rtol=0, atol=1e-10 * np.abs(Ainv).max())
+        G = np.concatenate([W_[f][K] @ Bf for f in range(2 * d)], axis=1)
+        Lk = Ainv @ G
+        got = ihdg.var_host_operator(mesh, beta(vol), beta(fpts), K, 0)
+        assert np.abs(got - Lk).max() < 1e-10 * max(1.0, np.abs(Lk).max())
+
+
+def test_var_plan_rejects_sign_change_and_needs_device():
+    import workloads as W
+    mesh = ihdg.make_mesh(2, (3, 3), 2)
+    co = ihdg.make_coeffs(ihdg.TRANSPORT, beta=(1.0, 0.0, 0.0))
+    vol, _ = ihdg.quadrature_points(mesh, co)
+    fpts = ihdg.face_quadrature_points(mesh)
+    sign_change = lambda X: np.stack([X[..., 1] - 0.45, np.ones_like(X[..., 0])], axis=-1)
+    with pytest.raises(ihdg.IHDGError) as ei:
+        ihdg.var_host_operator(mesh, sign_change(vol), sign_change(fpts), 0, 0)
+    assert ei.value.status == ihdg.ERR_UNSUPPORTED
