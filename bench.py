@@ -193,7 +193,80 @@ class DeviceProblem:
         return float(np.mean(times)), r
 
 
-def sub_results(args, ih, ctx, dev, flush, peaks):
+def var_result(ih, ctx, dev, flush, peaks, pk, n=64, p=2):
+    """Variable-coefficient transport: plan set-up, float64 and mixed (float32, bf16) time to
+    tolerance 1e-8 through ihdg_var_solve_device, and the rooflines of its two sweep kernels:
+    the low-precision inner sweep streams every element's operator from HBM (algorithmic bytes
+    = operator + e and r read + e written per element), the float64 sweep is bound by the
+    float64 FMA rate (2 n_in nvol flops per element for the GEMV)."""
+    import torch
+    mesh = ih.make_mesh(3, (n, n, n), p)
+    co = ih.make_coeffs(ih.TRANSPORT, beta=(1.0, 0.0, 0.0))
+    vol, bnd = ih.quadrature_points(mesh, co)
+    fpts = ih.face_quadrature_points(mesh)
+    t0 = time.perf_counter()
+    plan = ctx.var_plan(mesh, W.e2_beta(vol), W.e2_beta(fpts))
+    setup_s = time.perf_counter() - t0
+    try:
+        dbytes, _ = plan.info()
+        sz = ih.problem_sizes(mesh, co)
+        nb, nin = (p + 1) ** 3, 6 * (p + 1) ** 2
+        df = torch.from_numpy(np.ascontiguousarray(W.e2_forcing(vol))).to(dev)
+        dg = torch.from_numpy(np.ascontiguousarray(W.e2_exact(bnd))).to(dev)
+        du = torch.empty((sz.n_el, nb), dtype=torch.float64, device=dev)
+        stream = torch.cuda.current_stream(dev)
+        sp = stream.cuda_stream
+
+        def timed(o, steps, warm):
+            for _ in range(warm):
+                r = plan.solve_device(df.data_ptr(), dg.data_ptr(), o, du.data_ptr(), 0, sp)
+            ts = []
+            for _ in range(steps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                r = plan.solve_device(df.data_ptr(), dg.data_ptr(), o, du.data_ptr(), 0, sp)
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            return float(np.mean(ts)), r
+
+        tol = 1e-8
+        ms64, r64 = timed(ih.make_options(tol, max_iters=4000), 2, 1)
+        u64 = du.clone()
+        out = {"workload": f"3D transport beta=(z,x,y) {n}^3 p={p} u=sin(pi x)cos(pi y)sin(pi z)/pi tol {tol} "
+                           "(per-element local solves)",
+               "plan_setup_s": setup_s, "plan_device_bytes": int(dbytes),
+               "fp64_ms": ms64, "fp64_sweeps": r64.iterations, "fp64_status": ih.STATUS_NAMES[r64.status]}
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        for name, prec, lpb in (("mixed_fp32", ih.MIXED_FP32, 4), ("mixed_bf16", ih.MIXED_BF16, 2)):
+            o = ih.make_options(tol, max_iters=20000, prec=prec)
+            ms, r = timed(o, 3, 1)
+            relv = float(torch.linalg.norm(du - u64) / torch.linalg.norm(u64))
+            rp = plan.solve_device(df.data_ptr(), dg.data_ptr(), ih.make_options(tol, max_iters=20000, prec=prec, profile=1),
+                                   du.data_ptr(), 0, sp)
+            alg = sz.n_el * (nin * nb * lpb + 3 * nb * lpb)
+            ach = alg / (rp.lowp_sweep_ms * 1e-3) / 1e9 if rp.lowp_sweep_ms > 0 else None
+            out[name] = {"ms": ms, "sweeps": r.iterations, "fp64_sweeps": r.fp64_sweeps, "status": ih.STATUS_NAMES[r.status],
+                         "rel_l2_vs_fp64": relv, "speedup_vs_fp64": ms64 / ms,
+                         "element_dof_updates_per_s": sz.n_el * nb * r.iterations / (ms * 1e-3),
+                         "k_var_inner": {"avg_sweep_ms": rp.lowp_sweep_ms, "algorithmic_bytes_per_sweep": alg,
+                                         "achieved_gbs": ach, "bound": "hbm", "peak_gbs": hbm,
+                                         "frac": ach / hbm if ach else None}}
+        rp = plan.solve_device(df.data_ptr(), dg.data_ptr(), ih.make_options(tol, max_iters=4000, profile=1),
+                               du.data_ptr(), 0, sp)
+        fl = sz.n_el * 2.0 * nin * nb
+        out["k_var_sweep_fp64"] = {"avg_sweep_ms": rp.fp64_sweep_ms, "gemv_flops_per_sweep": fl,
+                                   "achieved_tflops": fl / (rp.fp64_sweep_ms * 1e-3) / 1e12 if rp.fp64_sweep_ms else None,
+                                   "bound": "fp64 fma", "peak_tflops": pk["fp64_fma_tflops"],
+                                   "frac": fl / (rp.fp64_sweep_ms * 1e-3) / 1e12 / pk["fp64_fma_tflops"]
+                                   if rp.fp64_sweep_ms else None}
+        return out
+    finally:
+        plan.close()
+
+
+def sub_results(args, ih, ctx, dev, flush, peaks, pk):
     """Compact driver-recorded results of the other listed workloads, each with its float64
     comparison: 3D transport 64^3 (bf16 tensor-core inner sweeps), shallow water 512^2 x 100
     steps (float32 inner sweeps), and the serving stream."""
@@ -238,6 +311,10 @@ def sub_results(args, ih, ctx, dev, flush, peaks):
         "speedup_mixed_vs_fp64": ms_64 / ms_m, "mixed_vs_fp64_rel_l2_after_100_steps": rel,
         "element_dof_updates_per_s": P.sz.n_el * P.sz.nvol * r_m.iterations / (ms_m * 1e-3)}
     del P
+    torch.cuda.synchronize(dev)
+    # transport with the 3D experiment's velocity field beta = (z, x, y) (Section 5.1), 64^3,
+    # p = 2: per-element local solves streamed by the batched-GEMV sweep
+    out["transport3d_var_64"] = var_result(ih, ctx, dev, flush, peaks, pk)
     torch.cuda.synchronize(dev)
     # serving stream
     sa = argparse.Namespace(**vars(args))
@@ -699,7 +776,7 @@ def main():
     line.update(extras)
     line["peaks_measured"] = {**pk, "by": "ihdg_measure_peaks (probe kernels, best of 5 after warm-up)"}
     if spec["name"] == "convdiff2d" and not args.no_workloads and world == 1 and not args.n and not args.prec:
-        line["workloads"] = sub_results(args, ih, ctx, dev, flush, peaks)
+        line["workloads"] = sub_results(args, ih, ctx, dev, flush, peaks, pk)
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -672,6 +672,31 @@ ihdg_status var_solve(VarDev& d, const double* f, const double* gb, const ihdg_o
   };
   const bool mixed = o.prec != IHDG_FP64;
   const bool bf16 = o.prec == IHDG_MIXED_BF16;
+  // profile: events around every sweep launch (synchronised), averaged per kind
+  struct Prof {
+    cudaEvent_t a = nullptr, b = nullptr;
+    double ms64 = 0.0, mslp = 0.0;
+    int n64 = 0, nlp = 0;
+    ~Prof() {
+      if (a) cudaEventDestroy(a);
+      if (b) cudaEventDestroy(b);
+    }
+  } pf;
+  const bool prof = o.profile != 0;
+  if (prof && (!ck(cudaEventCreate(&pf.a), "cudaEventCreate") || !ck(cudaEventCreate(&pf.b), "cudaEventCreate")))
+    return IHDG_ERR_CUDA;
+  auto timed = [&](auto&& launch, bool fp64) {
+    if (!prof) return launch();
+    cudaEventRecord(pf.a, s);
+    cudaError_t e = launch();
+    if (e != cudaSuccess) return e;
+    cudaEventRecord(pf.b, s);
+    e = cudaEventSynchronize(pf.b);
+    float t = 0.f;
+    cudaEventElapsedTime(&t, pf.a, pf.b);
+    if (fp64) { pf.ms64 += t; pf.n64 += 1; } else { pf.mslp += t; pf.nlp += 1; }
+    return e;
+  };
   const double* ufinal = nullptr;
   const double* rfinal = nullptr;
   if (!mixed) {
@@ -683,7 +708,9 @@ ihdg_status var_solve(VarDev& d, const double* f, const double* gb, const ihdg_o
       const int n = std::min(batch, left);
       if (n <= 0) break;
       for (int i = 0; i < n; ++i)
-        if (!ck(var_dispatch(d, [&](auto R) { return decltype(R)::template sweep<float>(d, 0, 0, s); }), "sweep kernel"))
+        if (!ck(timed([&] { return var_dispatch(d, [&](auto R) { return decltype(R)::template sweep<float>(d, 0, 0, s); }); },
+                      true),
+                "sweep kernel"))
           return IHDG_ERR_CUDA;
       launches += n;
       if (batch < 32) batch *= 2;
@@ -692,10 +719,12 @@ ihdg_status var_solve(VarDev& d, const double* f, const double* gb, const ihdg_o
   } else {
     int has_e = 0;
     for (;;) {
-      cudaError_t e = var_dispatch(d, [&](auto R) {
-        return bf16 ? decltype(R)::template sweep<__nv_bfloat16>(d, 1, has_e, s)
-                    : decltype(R)::template sweep<float>(d, 1, has_e, s);
-      });
+      cudaError_t e = timed([&] {
+        return var_dispatch(d, [&](auto R) {
+          return bf16 ? decltype(R)::template sweep<__nv_bfloat16>(d, 1, has_e, s)
+                      : decltype(R)::template sweep<float>(d, 1, has_e, s);
+        });
+      }, true);
       if (!ck(e, "outer sweep kernel")) return IHDG_ERR_CUDA;
       launches += 1;
       has_e = 1;
@@ -704,9 +733,11 @@ ihdg_status var_solve(VarDev& d, const double* f, const double* gb, const ihdg_o
       int batch = 4;
       for (;;) {
         for (int i = 0; i < batch; ++i) {
-          e = var_dispatch(d, [&](auto R) {
-            return bf16 ? decltype(R)::template inner<__nv_bfloat16>(d, s) : decltype(R)::template inner<float>(d, s);
-          });
+          e = timed([&] {
+            return var_dispatch(d, [&](auto R) {
+              return bf16 ? decltype(R)::template inner<__nv_bfloat16>(d, s) : decltype(R)::template inner<float>(d, s);
+            });
+          }, false);
           if (!ck(e, "inner sweep kernel")) return IHDG_ERR_CUDA;
         }
         launches += batch;
@@ -739,6 +770,12 @@ ihdg_status var_solve(VarDev& d, const double* f, const double* gb, const ihdg_o
     res->status = (ihdg_status)hc->status;
     res->solve_ms = ms;
     res->kernel_launches = launches;
+    // inner launches that found the loop stopped return at once; the average is over the
+    // sweeps the inner loop ran
+    res->fp64_sweep_ms = pf.n64 ? pf.ms64 / pf.n64 : 0.0;
+    res->lowp_sweep_ms = hc->lowp_sweeps ? pf.mslp / hc->lowp_sweeps : 0.0;
+    res->fp64_launches = pf.n64;
+    res->lowp_launches = pf.nlp;
   }
   return IHDG_OK;
 }

@@ -90,7 +90,7 @@ struct VarDev {
   int grid = 0, max_hist = 0;
 };
 
-// Allocate and upload a plan (operators built by build_var); frees nothing on failure.
+// Allocate and upload a plan (operators built by build_var); on failure nothing stays allocated.
 cudaError_t var_upload(const VarHost& h, VarDev& d, int max_hist);
 void var_free(VarDev& d);
 // One solve on `stream`: forcing, the float64 sweep loop or the mixed loop, u_out and the
