@@ -15,6 +15,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <cstdlib>
 #include <cstring>
 #include <type_traits>
 #include <sstream>
@@ -353,50 +354,138 @@ __global__ void __launch_bounds__(VNT) k_var_sweep(const VGeo g, const double* _
   }
 }
 
+// The TMA engine's untiled bulk copy, global -> this CTA's shared memory, its completion
+// counted in bytes on an mbarrier; bounded waits (the caller decides what to do on expiry).
+__device__ __forceinline__ uint32_t vsmem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void vbulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(dst), "l"(src), "r"(bytes), "r"(mbar) : "memory");
+}
+__device__ __forceinline__ bool vmbar_try(uint32_t mbar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+               "selp.u32 %0, 1, 0, p;\n\t}\n" : "=r"(ok) : "r"(mbar), "r"(parity) : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool vmbar_wait(uint32_t mbar, uint32_t parity, long long lim) {
+  const long long t0 = clock64();
+  while (!vmbar_try(mbar, parity))
+    if (clock64() - t0 > lim) return false;
+  return true;
+}
+
 // Low-precision inner sweep of the mixed path: e_{j+1} = r + L t(e_j) with float32 arithmetic
 // and TL storage of e, r and the operator; the inner loop stops when the step norm falls to
 // inner_rtol * ||r|| (Euclidean norms over all nodes), after inner_max sweeps, or at the sweep
-// budget.
+// budget.  Each warp streams the operators of its elements through a private ring of R stages
+// in shared memory: one stage holds the EPW consecutive elements the warp computes together
+// (their operator blocks are contiguous, each padded to lsb bytes, a multiple of 16), filled by
+// one bulk copy that lane 0 issues R batches ahead, so R - 1 copies stay in flight while the
+// warp gathers its traces and computes from shared memory.  Every wait is bounded: on expiry
+// the kernel sets ctrl->timeout, waits (bounded) for its own copies still in flight and stops
+// the loop.
 template <int D, int P, typename TL>
-__global__ void __launch_bounds__(VNT) k_var_inner(const VGeo g, const TL* __restrict__ L,
+__global__ void __launch_bounds__(VNT) k_var_inner(const VGeo g, const TL* __restrict__ L, const int lsb, const int R,
                                                    const int* __restrict__ facevol, const TL* __restrict__ rlp, TL* e0,
                                                    TL* e1, Ctrl* ctrl, double* partials) {
   using S = VShape<D, P>;
+  constexpr int NW = VNT / 32;
+  extern __shared__ __align__(128) unsigned char vsm[];
+  __shared__ __align__(8) unsigned long long s_mb[NW * 8];
   if (ctrl_done(ctrl) || *(volatile const int*)&ctrl->inner_done) return;
-  const int lane = threadIdx.x & 31, gl = lane % S::GS, grp = lane / S::GS;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, gl = lane % S::GS, grp = lane / S::GS;
   Slots<S> sl;
   sl.load(facevol, gl);
   // e_0 = r (the first correction from zero); e_j in e[j & 1] for j >= 1
   const int j = *(volatile const int*)&ctrl->inner_iter;
   const TL* ec = j == 0 ? rlp : ((j & 1) ? e1 : e0);
   TL* en = (j & 1) ? e0 : e1;
+  const int SB = S::EPW * lsb;
+  unsigned char* ring = vsm + (size_t)w * R * SB;
+  const uint32_t mb0 = vsmem(&s_mb[w * 8]);
+  if (lane == 0) {
+    for (int q = 0; q < R; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb0 + 8 * q) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  const long long gw = (long long)blockIdx.x * NW + w, GW = (long long)gridDim.x * NW;
+  const long long nbatch = (g.nel + S::EPW - 1) / S::EPW;
+  // failure-detection test hook: warp 0 of block ctrl->stall_block issues no copy, so its
+  // first wait runs out
+  const bool stall = (int)blockIdx.x == ctrl->stall_block && w == 0;
+  auto issue = [&](long long i) {   // lane 0: batch i of this warp into stage i % R
+    const long long b = gw + i * GW;
+    if (b >= nbatch || stall) return;
+    const long long k0 = b * S::EPW;
+    const long long cnt = g.nel - k0 < S::EPW ? g.nel - k0 : S::EPW;
+    vbulk_load(vsmem(ring + (size_t)(i % R) * SB), reinterpret_cast<const char*>(L) + k0 * lsb, (uint32_t)(cnt * lsb),
+               mb0 + 8 * (uint32_t)(i % R));
+  };
+  if (lane == 0)
+    for (int q = 0; q < R; ++q) issue(q);
+  const long long lim = ctrl->wait_cycles;
   float st = 0.f;
-  const long long first = (long long)blockIdx.x * S::EPB + (threadIdx.x >> 5) * S::EPW;
-  for (long long base = first; base < g.nel; base += (long long)gridDim.x * S::EPB) {
-    const long long K = base + grp;
-    const bool valid = K < g.nel;
+  long long fail = -1;
+  // the gather of batch i + 1 (its traces, r and e values, plain loads) is issued before batch
+  // i is computed, so its round trip overlaps the computation from shared memory
+  struct Pre {
+    long long K;
+    bool valid;
+    float t[S::TPL], s, old;
+  };
+  auto fetch = [&](long long i, Pre& q) {
+    const long long b = gw + i * GW;
+    q.K = b * S::EPW + grp;
+    q.valid = b < nbatch && q.K < g.nel;
     int c[3] = {0, 0, 0};
-    if (valid) vcoords(g, K, c);
-    float t[S::TPL];
-    vgather<S, TL, TL, float>(g, sl, ec, (const TL*)nullptr, K, c, valid, t);
-    const bool row = valid && gl < S::NB;
-    float s = 0.f, old = 0.f;
-    if (row) {
-      s = vld_or(rlp, K * S::NB + gl);
-      old = vld_or(ec, K * S::NB + gl);
+    if (q.valid) vcoords(g, q.K, c);
+    vgather<S, TL, TL, float>(g, sl, ec, (const TL*)nullptr, q.K, c, q.valid, q.t);
+    q.s = q.old = 0.f;
+    if (q.valid && gl < S::NB) {
+      q.s = vld_or(rlp, q.K * S::NB + gl);
+      q.old = vld_or(ec, q.K * S::NB + gl);
     }
-    const TL* Lk = L + (size_t)(valid ? K : 0) * S::NIN * S::NB + (gl < S::NB ? gl : 0);
+  };
+  Pre cur, nxt;
+  fetch(0, cur);
+  for (long long i = 0;; ++i) {
+    const long long b = gw + i * GW;
+    if (b >= nbatch) break;
+    fetch(i + 1, nxt);
+    const int stg = (int)(i % R);
+    const bool ok = __all_sync(0xffffffffu, vmbar_wait(mb0 + 8 * stg, (uint32_t)((i / R) & 1), lim));
+    if (!ok) {
+      fail = i;
+      break;
+    }
+    const TL* Ls = reinterpret_cast<const TL*>(ring + (size_t)stg * SB + (size_t)grp * lsb) + (gl < S::NB ? gl : 0);
+    float acc = cur.s;
 #pragma unroll
     for (int k = 0; k < S::NIN; ++k) {
-      const float tk = __shfl_sync(0xffffffffu, t[k / S::GS], k % S::GS, S::GS);
-      s = fmaf(vld(Lk + (size_t)k * S::NB), tk, s);
+      const float tk = __shfl_sync(0xffffffffu, cur.t[k / S::GS], k % S::GS, S::GS);
+      acc = fmaf(to_f(Ls[k * S::NB]), tk, acc);
     }
-    if (row) {
-      const TL nv = from_f<TL>(s);
-      const float d = to_f(nv) - old;
+    if (cur.valid && gl < S::NB) {
+      const TL nv = from_f<TL>(acc);
+      const float d = to_f(nv) - cur.old;
       st = fmaf(d, d, st);
-      en[K * S::NB + gl] = nv;
+      en[cur.K * S::NB + gl] = nv;
     }
+    __syncwarp();
+    if (lane == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(i + R);
+    }
+    cur = nxt;
+  }
+  if (fail >= 0) {   // a copy did not arrive in time: flag it, then wait for this warp's copies in flight
+    if (lane == 0) {
+      atomicExch(&ctrl->timeout, 1);
+      for (long long i = fail; !stall && i < fail + R && gw + i * GW < nbatch; ++i)   // ~1 s each at most
+        vmbar_wait(mb0 + 8 * (uint32_t)(i % R), (uint32_t)((i / R) & 1), 2000000000LL);
+    }
+    __syncwarp();
   }
   double tA, tB;
   if (var_arrive2(ctrl, partials, (double)st, 0.0, &tA, &tB)) {
@@ -406,9 +495,14 @@ __global__ void __launch_bounds__(VNT) k_var_inner(const VGeo g, const TL* __res
     ctrl->lowp_sweeps += 1;
     const double step = sqrt(tA);
     ctrl->inner_step = step;
-    if (step <= ctrl->inner_rtol * ctrl->rnorm || jn >= ctrl->inner_max || it >= ctrl->max_iters || !(step == step) ||
-        isinf(step))
+    if (*(volatile int*)&ctrl->timeout) {
       ctrl->inner_done = 1;
+      ctrl->done = 1;
+      ctrl->status = IHDG_ERR_TIMEOUT;
+    } else if (step <= ctrl->inner_rtol * ctrl->rnorm || jn >= ctrl->inner_max || it >= ctrl->max_iters ||
+               !(step == step) || isinf(step)) {
+      ctrl->inner_done = 1;
+    }
   }
 }
 
@@ -468,12 +562,15 @@ __global__ void k_var_trace(const VGeo g, const double* __restrict__ u, const in
   }
 }
 
-__global__ void k_var_convert(long long n, const double* __restrict__ x, float* __restrict__ y32,
-                              __nv_bfloat16* __restrict__ y16) {
+// float32 and bf16 copies of the operators, each element's block padded to ls32 / ls16 values
+__global__ void k_var_convert(long long nel, int per, const double* __restrict__ x, float* __restrict__ y32, int ls32,
+                              __nv_bfloat16* __restrict__ y16, int ls16) {
+  const long long n = nel * per;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long K = i / per, jx = i % per;
     const double v = x[i];
-    y32[i] = (float)v;
-    y16[i] = __float2bfloat16_rn((float)v);
+    y32[K * ls32 + jx] = (float)v;
+    y16[K * ls16 + jx] = __float2bfloat16_rn((float)v);
   }
 }
 
@@ -500,12 +597,32 @@ struct VarRun {
                                                       d.r64, rl, d.ctrl, d.partials, d.res_hist);
     return cudaGetLastError();
   }
+  // stages per warp: enough for ~100 KB of shared memory per block (two blocks per SM), 2..8
   template <typename TL>
   static cudaError_t inner(VarDev& d, cudaStream_t s) {
-    const TL* L = std::is_same<TL, float>::value ? (const TL*)d.L32 : (const TL*)d.L16;
-    k_var_inner<D, P, TL><<<d.grid, VNT, 0, s>>>(vgeo(d), L, d.facevol, static_cast<const TL*>(d.rlp),
-                                                 static_cast<TL*>(d.e[0]), static_cast<TL*>(d.e[1]), d.ctrl,
-                                                 d.partials);
+    using S = VShape<D, P>;
+    const bool f32 = std::is_same<TL, float>::value;
+    const TL* L = f32 ? (const TL*)d.L32 : (const TL*)d.L16;
+    const int lsb = f32 ? d.lsb32 : d.lsb16;
+    const int nw = VNT / 32, sb = S::EPW * lsb;
+    int R = (100 * 1024) / (nw * sb);
+    R = R < 2 ? 2 : (R > 8 ? 8 : R);
+    const size_t smem = (size_t)nw * R * sb;
+    auto k = k_var_inner<D, P, TL>;
+    cudaError_t e = allow_dynamic_smem(k);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, VNT, smem);
+    if (e != cudaSuccess) return e;
+    if (per < 1) return cudaErrorInvalidConfiguration;
+    const long long nbatch = (d.nel + S::EPW - 1) / S::EPW;
+    long long grid = (nbatch + nw - 1) / nw;
+    if (grid > (long long)per * sms) grid = (long long)per * sms;
+    if (grid > d.grid) grid = d.grid;   // the partials array holds d.grid blocks
+    k<<<(unsigned)grid, VNT, smem, s>>>(vgeo(d), L, lsb, R, d.facevol, static_cast<const TL*>(d.rlp),
+                                        static_cast<TL*>(d.e[0]), static_cast<TL*>(d.e[1]), d.ctrl, d.partials);
     return cudaGetLastError();
   }
   static cudaError_t trace(VarDev& d, const double* u, const double* gb, double* tr, cudaStream_t s) {
@@ -574,7 +691,11 @@ cudaError_t var_upload(const VarHost& h, VarDev& d, int max_hist) {
   // layout of the single allocation
   size_t at = 0;
   auto take = [&](size_t bytes) { size_t r = at; at += a256(bytes); return r; };
-  const size_t oL64 = take(nL * 8), oL32 = take(nL * 4), oL16 = take(nL * 2), oA = take(nA * 8);
+  const int per = h.nin * h.nb;
+  d.lsb32 = (per * 4 + 15) / 16 * 16;   // bytes per element block, multiples of 16 (bulk copies)
+  d.lsb16 = (per * 2 + 15) / 16 * 16;
+  const size_t oL64 = take(nL * 8), oL32 = take((size_t)h.nel * d.lsb32), oL16 = take((size_t)h.nel * d.lsb16);
+  const size_t oA = take(nA * 8);
   const size_t oWq = take(h.Wq.size() * 8), oFB = take(h.FBv.size() * 8), obw = take(std::max<size_t>(1, h.bw.size()) * 8);
   const size_t ofv = take(h.facevol.size() * 4), oM1 = take(h.M1.size() * 8), oPg = take(h.Pg.size() * 8);
   const size_t ou0 = take(nS * 8), ou1 = take(nS * 8), oV = take(nS * 8), or64 = take(nS * 8), orl = take(nS * 4);
@@ -618,9 +739,12 @@ cudaError_t var_upload(const VarHost& h, VarDev& d, int max_hist) {
   up(ofv, h.facevol.data(), h.facevol.size() * 4);
   up(oM1, h.M1.data(), h.M1.size() * 8);
   up(oPg, h.Pg.data(), h.Pg.size() * 8);
+  if (e == cudaSuccess) e = cudaMemset(b + oL32, 0, (size_t)h.nel * d.lsb32);
+  if (e == cudaSuccess) e = cudaMemset(b + oL16, 0, (size_t)h.nel * d.lsb16);
   if (e == cudaSuccess) {
     k_var_convert<<<(unsigned)std::min<size_t>((nL + 255) / 256, (size_t)sms * 16), 256>>>(
-        (long long)nL, d.L64, reinterpret_cast<float*>(b + oL32), reinterpret_cast<__nv_bfloat16*>(b + oL16));
+        (long long)h.nel, per, d.L64, reinterpret_cast<float*>(b + oL32), d.lsb32 / 4,
+        reinterpret_cast<__nv_bfloat16*>(b + oL16), d.lsb16 / 2);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -660,9 +784,18 @@ ihdg_status var_solve(VarDev& d, const double* f, const double* gb, const ihdg_o
   LaunchArgs la{};
   la.ctrl = d.ctrl;
   la.stream = s;
+  // bound of the inner kernel's waits for its operator copies (~1 s of SM clock); the
+  // failure-detection tests shorten it with IHDG_TEST_WAIT_CYCLES
+  long long wait_cycles = 2000000000LL;
+  int stall_block = -1;
+  if (const char* wv = std::getenv("IHDG_TEST_WAIT_CYCLES")) {
+    const long long v = std::atoll(wv);
+    if (v > 0) wait_cycles = v;
+  }
+  if (const char* sb = std::getenv("IHDG_TEST_STALL_BLOCK")) stall_block = std::atoi(sb);
   int launches = 0;
   if (!ck(cudaEventRecord(ev.a, s), "cudaEventRecord") ||
-      !ck(launch_ctrl_init(la, o.tol, o.diverge_factor, max_iters, o.inner_max, inner_rtol, 2000000000LL, -1), "ctrl init") ||
+      !ck(launch_ctrl_init(la, o.tol, o.diverge_factor, max_iters, o.inner_max, inner_rtol, wait_cycles, stall_block), "ctrl init") ||
       !ck(var_dispatch(d, [&](auto R) { return decltype(R)::forcing(d, f, gb, o.u0, s); }), "forcing kernel"))
     return IHDG_ERR_CUDA;
   launches += 2;
@@ -742,6 +875,10 @@ ihdg_status var_solve(VarDev& d, const double* f, const double* gb, const ihdg_o
         }
         launches += batch;
         if (!readback("inner loop")) return IHDG_ERR_CUDA;
+        if (hc->timeout) {
+          err = "inner sweep: an operator copy into shared memory did not complete in time";
+          return IHDG_ERR_TIMEOUT;
+        }
         if (hc->inner_done || hc->done) break;
         if (batch < 64) batch *= 2;
       }

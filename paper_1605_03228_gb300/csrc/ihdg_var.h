@@ -69,8 +69,9 @@ struct VarDev {
   void* mem = nullptr;          // one device allocation holding everything below
   size_t bytes = 0;
   const double* L64 = nullptr;  // [K][k][i]
-  const float* L32 = nullptr;
-  const void* L16 = nullptr;    // bf16
+  const float* L32 = nullptr;   // [K][k][i], each element's block padded to lsb32 bytes
+  const void* L16 = nullptr;    // bf16, padded to lsb16 bytes
+  int lsb32 = 0, lsb16 = 0;
   const double* Ainv = nullptr; // [K][j][i]
   const double* Wq = nullptr;   // [i][g]
   const double* FBv = nullptr;  // [f][i][g]

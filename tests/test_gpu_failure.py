@@ -73,3 +73,35 @@ def test_nan_forcing_is_reported_as_diverged(ctx, prec):
     f[100, 3] = np.nan
     u, _, r = ctx.solve(mesh, co, f, g, ih.make_options(1e-8, prec=getattr(ih, prec), max_iters=5000))
     assert r.status == ih.DIVERGED
+
+
+@pytest.mark.parametrize("prec", ["MIXED_FP32", "MIXED_BF16"])
+def test_operator_copy_wait_runs_out_and_plan_stays_usable(ctx, monkeypatch, prec):
+    """Variable-coefficient transport: the inner sweep streams each element's operator into
+    shared memory with bulk copies and waits for them with a bounded wait.  Under the test hook
+    one warp issues no copy (IHDG_TEST_STALL_BLOCK) and the bound is ~10 ms: its wait runs out,
+    the call returns IHDG_ERR_TIMEOUT, and the next solve on the same plan gives the same
+    result as before."""
+    from paper_1605_03228_gb300 import ihdg as ih
+    mesh = ih.make_mesh(2, (40, 36), 3, hi=(2.0, 2.0))
+    co = ih.make_coeffs(ih.TRANSPORT, beta=(1.0, 0.0, 0.0))
+    vol, bnd = ih.quadrature_points(mesh, co)
+    fpts = ih.face_quadrature_points(mesh)
+    plan = ctx.var_plan(mesh, W.e1_beta(vol), W.e1_beta(fpts))
+    try:
+        f, g = np.zeros(vol.shape[:2]), W.e1_inflow(bnd)
+        opts = ih.make_options(1e-10, prec=getattr(ih, prec), max_iters=20000)
+        u_ref, _, r_ref = plan.solve(f, g, opts, want_trace=False)
+        assert r_ref.status == ih.OK
+        monkeypatch.setenv("IHDG_TEST_WAIT_CYCLES", "20000000")
+        monkeypatch.setenv("IHDG_TEST_STALL_BLOCK", "0")
+        with pytest.raises(ih.IHDGError) as e:
+            plan.solve(f, g, opts, want_trace=False)
+        assert e.value.status == ih.ERR_TIMEOUT
+        monkeypatch.delenv("IHDG_TEST_STALL_BLOCK")
+        monkeypatch.delenv("IHDG_TEST_WAIT_CYCLES")
+        u, _, r = plan.solve(f, g, opts, want_trace=False)
+        assert r.status == ih.OK and r.iterations == r_ref.iterations
+        assert np.array_equal(u, u_ref)
+    finally:
+        plan.close()
