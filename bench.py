@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="convdiff2d",
-                    choices=["convdiff2d", "transport2d", "transport3d", "swe", "serving"])
+                    choices=["convdiff2d", "transport2d", "transport3d", "swe", "serving", "transport3d_var"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=0, help="override the elements per side (profiling cases)")
     ap.add_argument("--no-extras", action="store_true", help="skip the as-listed and float64 comparison solves")
@@ -92,6 +92,10 @@ def workload_spec(name):
                     desc="serving stream: 2D conv-diff requests, side log-uniform in [16,256], p in 1..4, "
                          "kappa log-uniform in [1e-4,1], beta angle uniform, seeded manufactured solutions, "
                          "Poisson arrivals, admitted by HBM footprint, mixed precision, tol 1e-8")
+    if name == "transport3d_var":
+        return dict(name="transport3d_var", dim=3, n=(64, 64, 64), p=2, pde="transport", tol=1e-8, prec="MIXED_FP32",
+                    desc="3D transport beta=(z,x,y) (Section 5.1) 64^3 p=2 u=sin(pi x)cos(pi y)sin(pi z)/pi tol 1e-8, "
+                         "per-element local solves, float32 inner sweeps + float64")
     if name == "swe":
         return dict(name="swe", dim=2, n=(512, 512), p=2, pde="swe", Phi=1.0, dt=1.0 / (512 * 12), listed_dt=1e-3,
                     nsteps=100, tol=1e-8, prec="MIXED_FP32",
@@ -193,7 +197,7 @@ class DeviceProblem:
         return float(np.mean(times)), r
 
 
-def var_result(ih, ctx, dev, flush, peaks, pk, n=64, p=2):
+def var_result(ih, ctx, dev, flush, peaks, pk, n=64, p=2, steps=3, warmup=1):
     """Variable-coefficient transport: plan set-up, float64 and mixed (float32, bf16) time to
     tolerance 1e-8 through ihdg_var_solve_device, and the rooflines of its two sweep kernels:
     the low-precision inner sweep streams every element's operator from HBM (algorithmic bytes
@@ -241,13 +245,14 @@ def var_result(ih, ctx, dev, flush, peaks, pk, n=64, p=2):
         hbm = peaks.get("hbm_gbs", 6800.0)
         for name, prec, lpb in (("mixed_fp32", ih.MIXED_FP32, 4), ("mixed_bf16", ih.MIXED_BF16, 2)):
             o = ih.make_options(tol, max_iters=20000, prec=prec)
-            ms, r = timed(o, 3, 1)
+            ms, r = timed(o, steps, warmup)
             relv = float(torch.linalg.norm(du - u64) / torch.linalg.norm(u64))
             rp = plan.solve_device(df.data_ptr(), dg.data_ptr(), ih.make_options(tol, max_iters=20000, prec=prec, profile=1),
                                    du.data_ptr(), 0, sp)
             alg = sz.n_el * (nin * nb * lpb + 3 * nb * lpb)
             ach = alg / (rp.lowp_sweep_ms * 1e-3) / 1e9 if rp.lowp_sweep_ms > 0 else None
             out[name] = {"ms": ms, "sweeps": r.iterations, "fp64_sweeps": r.fp64_sweeps, "status": ih.STATUS_NAMES[r.status],
+                         "kernel_launches": r.kernel_launches,
                          "rel_l2_vs_fp64": relv, "speedup_vs_fp64": ms64 / ms,
                          "element_dof_updates_per_s": sz.n_el * nb * r.iterations / (ms * 1e-3),
                          "k_var_inner": {"avg_sweep_ms": rp.lowp_sweep_ms, "algorithmic_bytes_per_sweep": alg,
@@ -264,6 +269,48 @@ def var_result(ih, ctx, dev, flush, peaks, pk, n=64, p=2):
         return out
     finally:
         plan.close()
+
+
+def var_traffic(n_el):
+    """DRAM bytes of one float32 inner sweep, scaled from the committed capture's per-element
+    figure (that capture moved the algorithmic bytes, so traffic grows with the elements)."""
+    try:
+        tr = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        return tr["transport3d_var:k_var_inner"]["per_element_bytes"] * n_el
+    except Exception:
+        return None
+
+
+def run_var(args, spec, ih, ctx, dev, world, rank, dist):
+    """The variable-coefficient workload as the bench line: the mixed float32 solve's
+    element-DOF updates/s, the float64 solve beside it, and the inner sweep's HBM roofline."""
+    import torch
+    pk = ih.measure_peaks(int(os.environ.get("LOCAL_RANK", "0"))).as_dict()
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    r = var_result(ih, ctx, dev, flush, peaks, pk, n=spec["n"][0], p=spec["p"], steps=args.steps, warmup=args.warmup)
+    clk = clocks.stop()
+    m = r["mixed_fp32"]
+    ms, units = aggregate(m["ms"], m["element_dof_updates_per_s"] * m["ms"] * 1e-3, dist, dev)
+    ki = m["k_var_inner"]
+    line = {"metric": METRIC, "value": units / (ms * 1e-3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": spec["desc"], "l2": "flushed between steps (512 MB write, outside the timed events)"},
+            "roofline": {"kernel": "k_var_inner", "bound": "hbm", "achieved": ki["achieved_gbs"], "peak": ki["peak_gbs"],
+                         "unit": "GB/s", "frac": ki["frac"], "traffic": var_traffic(spec["n"][0] ** 3),
+                         "algorithmic_bytes_per_launch": ki["algorithmic_bytes_per_sweep"],
+                         "avg_launch_ms": ki["avg_sweep_ms"]},
+            "clocks": clk, "cpu_baseline": None, "e2e": None, "gpu_launches": m["kernel_launches"] * args.steps,
+            "details": r}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 def sub_results(args, ih, ctx, dev, flush, peaks, pk):
@@ -573,6 +620,12 @@ def main():
     dev = torch.device(f"cuda:{local}")
     torch.cuda.set_device(dev)
     ctx = ih.Context(local)
+    if spec["name"] == "transport3d_var":
+        run_var(args, spec, ih, ctx, dev, world, rank, dist)
+        ctx.close()
+        if dist is not None:
+            dist.destroy_process_group()
+        return
     if spec["name"] == "serving":
         run_serving(args, ih, ctx, world, rank)
         ctx.close()
@@ -600,7 +653,7 @@ def main():
         names = {ih.KERNEL_TENSOR_CORES: "tensor cores (tcgen05)", ih.KERNEL_CUDA_CORES: "CUDA cores",
                  ih.KERNEL_GLOBAL: "CUDA cores, global state"}
         tune = {"by": "ihdg_autotune", "inner_kernel": names.get(tuned.inner_kernel, "auto"),
-                "inner_rtol": tuned.inner_rtol, "best_solve_ms": tune_ms}
+                "inner_rtol": tuned.inner_rtol, "sweeps_per_sync": tuned.sweeps_per_sync, "best_solve_ms": tune_ms}
     nws = ih.workspace_bytes(mesh, co, opts)
     ws = torch.empty(nws + 256, dtype=torch.uint8, device=dev)
     wsp = (ws.data_ptr() + 255) // 256 * 256
@@ -649,15 +702,25 @@ def main():
     status = ih.STATUS_NAMES[r.status]
 
     # roofline of the dominant kernel: one profiled solve (events around every sweep launch)
-    rp = step(ih.make_options(spec["tol"], max_iters=4000, prec=prec, profile=1, inner_max=args.inner_max,
-                              inner_rtol=args.inner_rtol))
+    po = ih.make_options(spec["tol"], max_iters=4000, prec=prec, profile=1, inner_max=args.inner_max,
+                         inner_rtol=opts.inner_rtol, inner_kernel=opts.inner_kernel, sweeps_per_sync=opts.sweeps_per_sync)
+    rp = step(po)
     lp_bytes = 2 if prec == ih.MIXED_BF16 else 4
     if prec == ih.FP64:
         kern, kms = "k_sweep64", rp.fp64_sweep_ms
         # read E^k, E^(k-1), F, write E^(k+1): 4 float64 words per export value
         bytes_per_launch = sz.n_el * sz.n_exp * 8 * 4
     else:
-        kern, kms = "k_inner", rp.lowp_sweep_ms
+        # the inner kernel the solve ran: tensor cores, the 2D CUDA-core kernels (temporally
+        # blocked unless one sweep per barrier was chosen), or the 3D shared-memory tile kernel
+        if opts.inner_kernel == ih.KERNEL_TENSOR_CORES or (opts.inner_kernel == ih.KERNEL_AUTO and
+                                                          (prec in (ih.MIXED_BF16, ih.MIXED_TF32) or spec["dim"] == 3)):
+            kern = "k_inner_tc"
+        elif spec["dim"] == 2:
+            kern = "k_inner_reg" if opts.sweeps_per_sync == 1 else "k_inner_blk"
+        else:
+            kern = "k_inner_tile"
+        kms = rp.lowp_sweep_ms
         # read e_j, r, write e_(j+1): 3 low-precision words per export value
         bytes_per_launch = sz.n_el * sz.n_exp * lp_bytes * 3
     peaks = {}
