@@ -313,6 +313,71 @@ def run_var(args, spec, ih, ctx, dev, world, rank, dist):
         print(json.dumps(line), flush=True)
 
 
+def var_group_result(ih, ctx, dev, nplans=48, seed=7):
+    """Many small variable-coefficient problems of uneven size and order: each solved alone
+    (one solve after another on the stream) against all of them in one grouped solve (one
+    launch per shape class and sweep step); the results are bitwise the same."""
+    import torch
+    rng = np.random.default_rng(seed)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    plans, bufs = [], []
+    try:
+        for i in range(nplans):
+            if i % 8 == 7:
+                n, p, d = int(rng.integers(4, 10)), 2, 3
+            else:
+                n, p, d = int(rng.integers(8, 41)), int(rng.integers(2, 4)), 2
+            mesh = ih.make_mesh(d, (n,) * d, p, hi=(2.0,) * d if d == 2 else (1.0,) * d)
+            co = ih.make_coeffs(ih.TRANSPORT, beta=(1.0, 0.0, 0.0))
+            vol, bnd = ih.quadrature_points(mesh, co)
+            fpts = ih.face_quadrature_points(mesh)
+            if d == 2:
+                plan = ctx.var_plan(mesh, W.e1_beta(vol), W.e1_beta(fpts))
+                f, g = np.zeros(vol.shape[:2]), W.e1_inflow(bnd)
+            else:
+                plan = ctx.var_plan(mesh, W.e2_beta(vol), W.e2_beta(fpts))
+                f, g = W.e2_forcing(vol), W.e2_exact(bnd)
+            plans.append(plan)
+            s = plan.sizes
+            bufs.append((torch.from_numpy(np.ascontiguousarray(f)).to(dev), torch.from_numpy(np.ascontiguousarray(g)).to(dev),
+                         torch.empty((s.n_el, (p + 1) ** d), dtype=torch.float64, device=dev)))
+        out = {"problems": nplans, "meshes": "2D beta=(1+sin(pi y/2),2) side 8..40 p 2..3, every 8th 3D beta=(z,x,y) side 4..9 p 2"}
+        for name, prec in (("fp64", ih.FP64), ("mixed_fp32", ih.MIXED_FP32)):
+            o = ih.make_options(1e-10, max_iters=20000, prec=prec)
+
+            def alone():
+                for pl, (df, dg, du) in zip(plans, bufs):
+                    pl.solve_device(df.data_ptr(), dg.data_ptr(), o, du.data_ptr(), 0, sp)
+
+            def grouped():
+                return ctx.var_solve_group(plans, [b[0].data_ptr() for b in bufs], [b[1].data_ptr() for b in bufs], o,
+                                           [b[2].data_ptr() for b in bufs], None, sp)
+
+            alone()
+            u_alone = [b[2].clone() for b in bufs]
+            res = grouped()
+            same = all(bool(torch.equal(a, b[2])) for a, b in zip(u_alone, bufs))
+            ts = {}
+            for lab, fn in (("alone", alone), ("grouped", grouped)):
+                times = []
+                for _ in range(3):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    fn()
+                    e1.record(stream)
+                    e1.synchronize()
+                    times.append(e0.elapsed_time(e1))
+                ts[lab] = float(np.min(times))
+            out[name] = {"alone_ms": ts["alone"], "grouped_ms": ts["grouped"], "speedup": ts["alone"] / ts["grouped"],
+                         "bitwise_equal": same, "statuses": sorted({ih.STATUS_NAMES[r.status] for r in res}),
+                         "launches_grouped": res[0].kernel_launches}
+        return out
+    finally:
+        for pl in plans:
+            pl.close()
+
+
 def sub_results(args, ih, ctx, dev, flush, peaks, pk):
     """Compact driver-recorded results of the other listed workloads, each with its float64
     comparison: 3D transport 64^3 (bf16 tensor-core inner sweeps), shallow water 512^2 x 100
@@ -362,6 +427,8 @@ def sub_results(args, ih, ctx, dev, flush, peaks, pk):
     # transport with the 3D experiment's velocity field beta = (z, x, y) (Section 5.1), 64^3,
     # p = 2: per-element local solves streamed by the batched-GEMV sweep
     out["transport3d_var_64"] = var_result(ih, ctx, dev, flush, peaks, pk)
+    torch.cuda.synchronize(dev)
+    out["transport_var_group"] = var_group_result(ih, ctx, dev)
     torch.cuda.synchronize(dev)
     # serving stream
     sa = argparse.Namespace(**vars(args))

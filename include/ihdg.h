@@ -79,8 +79,8 @@ typedef enum {
 } ihdg_precision;
 
 /* Inner-sweep kernel of the mixed path.  AUTO: tensor cores for bf16, tf32 and 3D float32,
- * the register-resident CUDA-core kernel for 2D float32 (or what ihdg_autotune chose for the
- * problem on this context).  TENSOR_CORES: tcgen05 local apply wherever the element shape
+ * the CUDA-core kernel for 2D float32, temporally blocked (opts.sweeps_per_sync) -- or what
+ * ihdg_autotune chose for the problem on this context.  TENSOR_CORES: tcgen05 local apply wherever the element shape
  * fits (n_in <= 64, n_exp <= 32), else the CUDA-core kernels.  CUDA_CORES: register- or
  * shared-memory-resident state.  GLOBAL: global-memory state (any size). */
 typedef enum {
@@ -351,6 +351,23 @@ ihdg_status ihdg_var_solve(ihdg_ctx* ctx, ihdg_var_plan* plan, const double* f_q
 ihdg_status ihdg_var_solve_device(ihdg_ctx* ctx, ihdg_var_plan* plan, const double* d_f_qp,
                                   const double* d_g_qp, const ihdg_options* opts, double* d_u_out,
                                   double* d_trace_out, void* stream, ihdg_result* res);
+/* Several plans solved together (the paper solves one problem at a time; no counterpart):
+ * every sweep step is one grouped launch per (dim, p) class covering all the class's plans,
+ * so problems of uneven size and order share launches, and small problems that could not fill
+ * the GPU alone fill it together.  Each block of a grouped launch works for one plan exactly as
+ * that block of the plan's own launch would (same grid, element mapping, fixed-order
+ * reductions, loop decisions), so every plan's u, trace, iteration count and status are
+ * bitwise those of ihdg_var_solve_device with the same options; the plans advance through
+ * their float64 / mixed phases independently and stop on their own tolerance.  n plans of
+ * the context's device (1..64; distinct plans), device arrays d_f_qp[i], d_g_qp[i],
+ * d_u_out[i] (and d_trace_out[i] unless d_trace_out or the entry is NULL) laid out as for
+ * ihdg_var_solve_device; opts is shared (opts->u0 must be NULL); res: n results (solve_ms is
+ * the whole group's device time).  Allocates a few KB of device descriptors per call.  Errors
+ * as for ihdg_var_solve_device. */
+ihdg_status ihdg_var_solve_group(ihdg_ctx* ctx, int n, ihdg_var_plan* const* plans,
+                                 const double* const* d_f_qp, const double* const* d_g_qp,
+                                 const ihdg_options* opts, double* const* d_u_out,
+                                 double* const* d_trace_out, void* stream, ihdg_result* res);
 /* Host-only inspection of one element's float64 local solve as the plan builds it (no device
  * needed): which = 0 L_K = A_K^{-1} G_K (nvol x n_in; column f*nf + r is face f's node r),
  * 1 A_K^{-1} (nvol x nvol).  Row-major into data (NULL: query rows/cols only). */

@@ -1223,6 +1223,38 @@ ihdg_status ihdg_var_solve_device(ihdg_ctx* ctx, ihdg_var_plan* plan, const doub
   return IHDG_OK;
 }
 
+ihdg_status ihdg_var_solve_group(ihdg_ctx* ctx, int n, ihdg_var_plan* const* plans, const double* const* d_f,
+                                 const double* const* d_g, const ihdg_options* opts, double* const* d_u,
+                                 double* const* d_tr, void* stream, ihdg_result* res) {
+  if (!ctx) return IHDG_ERR_INVALID;
+  if (n < 1 || n > 64) return fail(ctx, IHDG_ERR_INVALID, "n must be in 1..64");
+  if (!plans || !d_f || !d_g || !d_u || !res) return fail(ctx, IHDG_ERR_INVALID, "null argument");
+  ihdg_options o = defaults(opts);
+  ihdg_status st = check_opts(ctx, o);
+  if (st != IHDG_OK) return st;
+  if (o.u0) return fail(ctx, IHDG_ERR_INVALID, "a grouped solve takes no initial guess (opts->u0 must be NULL)");
+  std::vector<VarDev*> ds;
+  std::vector<const double*> fv, gv;
+  std::vector<double*> uv, tv;
+  for (int i = 0; i < n; ++i) {
+    if (!plans[i] || !d_f[i] || !d_g[i] || !d_u[i]) return fail(ctx, IHDG_ERR_INVALID, "null argument");
+    if (plans[i]->device != ctx->device) return fail(ctx, IHDG_ERR_INVALID, "a plan belongs to another device");
+    for (int j = 0; j < i; ++j)
+      if (plans[j] == plans[i]) return fail(ctx, IHDG_ERR_INVALID, "a plan appears twice in the group");
+    ds.push_back(&plans[i]->dev);
+    fv.push_back(d_f[i]);
+    gv.push_back(d_g[i]);
+    uv.push_back(d_u[i]);
+    tv.push_back(d_tr ? d_tr[i] : nullptr);
+  }
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  std::string err;
+  st = var_solve_group(ds, fv, gv, o, uv, tv, static_cast<cudaStream_t>(stream), err, res);
+  if (st != IHDG_OK) return fail(ctx, st, err);
+  ctx->err.clear();
+  return IHDG_OK;
+}
+
 ihdg_status ihdg_var_solve(ihdg_ctx* ctx, ihdg_var_plan* plan, const double* f_qp, const double* g_qp,
                            const ihdg_options* opts, double* u_out, double* trace_out, ihdg_result* res) {
   if (!ctx) return IHDG_ERR_INVALID;

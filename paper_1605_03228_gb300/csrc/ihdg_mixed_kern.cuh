@@ -928,37 +928,35 @@ __global__ void __launch_bounds__(NT, 1) k_inner_blk(const DevGeo g, const TL* _
               tr[f * NF + q] = wo * src[li * SP + os + q] + nb;
             }
           }
-          // a3: e_new = r + L_E t, one accumulation chain per row in trace order (a chain
-          // reuses its accumulator register: twice the FMA issue rate of interleaving all rows
-          // per trace value).  Rows of slots that carry no value have zero operator rows and
-          // zero r, so they stay zero.
-          float acc[NEXP];
-#pragma unroll
-          for (int e = 0; e < NEXP; ++e) {
-            float v = rs[li * SP + e];
-#pragma unroll
-            for (int k = 0; k < NIN; ++k) v = fmaf(Lp.L[e][k], tr[k], v);
-            acc[e] = v;
-          }
-          // a4: rounded to the storage type.  In the last sweep: the step norm over the tile,
-          // and the tile elements within H of its edges (the neighbours' halo) go straight to
-          // the next super-step's global buffer
           bool in_tile = false, strip = false;
           if constexpr (LAST) {
             in_tile = gx >= tx0 && gx < tx1 && gy >= ty0 && gy < ty1;
             strip = in_tile && (gx - tx0 < H || tx1 - 1 - gx < H || gy - ty0 < H || ty1 - 1 - gy < H);
           }
           const int K = gx + n0 * gy;
-#pragma unroll
-          for (int e = 0; e < NEXP; ++e) {
-            const TL nt = from_f<TL>(acc[e]);
+          // a4: rounded to the storage type.  In the last sweep: the step norm over the tile,
+          // and the tile elements within H of its edges (the neighbours' halo) go straight to
+          // the next super-step's global buffer
+          auto finish = [&](int e, float v) {
+            const TL nt = from_f<TL>(v);
             const float nv = to_f(nt);
             if constexpr (LAST) {
               const float d = nv - src[li * SP + e];
               if (in_tile) snorm = fmaf(d, d, snorm);
               if (strip && ((g.live >> e) & 1ull)) nbuf[(long long)e * ld + K] = nt;
             }
-            dst[li * SP + e] = nv;
+            return nv;
+          };
+          // a3: e_new = r + L_E t, one accumulation chain per row in trace order (a chain
+          // reuses its accumulator register: twice the FMA issue rate of interleaving all rows
+          // per trace value).  Rows of slots that carry no value have zero operator rows and
+          // zero r, so they stay zero.
+#pragma unroll
+          for (int e = 0; e < NEXP; ++e) {
+            float v = rs[li * SP + e];
+#pragma unroll
+            for (int k = 0; k < NIN; ++k) v = fmaf(Lp.L[e][k], tr[k], v);
+            dst[li * SP + e] = finish(e, v);
           }
         }
       };
@@ -980,7 +978,7 @@ __global__ void __launch_bounds__(NT, 1) k_inner_blk(const DevGeo g, const TL* _
 template <int NF, bool PER_AXIS, typename TL, int NT>
 cudaError_t launch_blk_v(MixedArgs& m, TL* rl, TL* e0, TL* e1) {
   using LT = LTile<NF, 4, PER_AXIS>;
-  constexpr int SP = LT::NEXP | 1;
+  constexpr int SP = LT::NEXP | 1;   // as in k_inner_blk
   const LaunchArgs& a = m.base;
   const int H = m.blk_h;
   if (a.g.dim != 2 || H < 2 || !m.LE32h || a.g.n_exp != LT::NEXP || (long long)a.g.ld * LT::NEXP >= (1LL << 31))

@@ -179,9 +179,11 @@ __device__ __forceinline__ double mass_norm(double x, int gl, const double* sM1,
   return group_sum<S::GS>(gl < S::NB ? jac * x * z : 0.0);
 }
 
-// Fixed-order block and grid reduction of two doubles; true in thread 0 of the last block to
-// arrive, which then holds the totals.
-__device__ bool var_arrive2(Ctrl* ctrl, double* partials, double a, double b, double* ta, double* tb) {
+// Fixed-order block and grid reduction of two doubles over the nblk blocks of one problem
+// (bid: this block's number among them); true in thread 0 of the last block to arrive, which
+// then holds the totals.
+__device__ bool var_arrive2(Ctrl* ctrl, double* partials, double a, double b, double* ta, double* tb, int bid,
+                            int nblk) {
   __shared__ double sa[VNT / 32], sb[VNT / 32];
   __shared__ int s_last;
 #pragma unroll
@@ -201,17 +203,17 @@ __device__ bool var_arrive2(Ctrl* ctrl, double* partials, double a, double b, do
       A += sa[i];
       B += sb[i];
     }
-    partials[2 * blockIdx.x] = A;
-    partials[2 * blockIdx.x + 1] = B;
+    partials[2 * bid] = A;
+    partials[2 * bid + 1] = B;
     __threadfence();
     const unsigned t = atomicAdd(&ctrl->ticket, 1u);
-    s_last = (t == gridDim.x - 1);
+    s_last = (t == (unsigned)nblk - 1);
   }
   __syncthreads();
   if (!s_last) return false;
   __threadfence();
   double A = 0.0, B = 0.0;
-  for (int i = threadIdx.x; i < (int)gridDim.x; i += VNT) {
+  for (int i = threadIdx.x; i < nblk; i += VNT) {
     A += __ldcg(partials + 2 * i);
     B += __ldcg(partials + 2 * i + 1);
   }
@@ -286,29 +288,50 @@ __global__ void __launch_bounds__(VNT) k_var_forcing(const VGeo g, const double*
 // ||u^{k+1} - u^k||_M.  MODE 1 (mixed outer sweep): u' = u + e, r = V + L t(u') - u', written
 // in float64 and as the low-precision residual and first correction; its norm ||r||_M is the
 // stopping residual of the exact sweep from u'.
+template <typename TL>
+struct VSweepArgs {
+  VGeo g;
+  const double* L;
+  const double* M1;
+  const int* facevol;
+  const double* V;
+  double* u0p;
+  double* u1p;
+  const TL* e0;
+  const TL* e1;
+  double* r64;
+  TL* rlp;
+  Ctrl* ctrl;
+  double* partials;
+  double* res_hist;
+  int nblk;   // blocks of this problem's launch
+};
+
 template <int D, int P, int MODE, typename TL>
-__global__ void __launch_bounds__(VNT) k_var_sweep(const VGeo g, const double* __restrict__ L,
-                                                   const double* __restrict__ M1, const int* __restrict__ facevol,
-                                                   const double* __restrict__ V, double* u0p, double* u1p, const TL* e0,
-                                                   const TL* e1, int has_e, double* r64, TL* rlp, Ctrl* ctrl,
-                                                   double* partials, double* res_hist) {
+__device__ __forceinline__ void var_sweep_body(const VSweepArgs<TL>& A, int bid) {
   using S = VShape<D, P>;
   __shared__ double sM1[S::NB1 * S::NB1];
+  const VGeo& g = A.g;
+  Ctrl* ctrl = A.ctrl;
   if (ctrl_done(ctrl)) return;
-  for (int i = threadIdx.x; i < S::NB1 * S::NB1; i += VNT) sM1[i] = M1[i];
+  // the mixed outer sweep runs once per inner loop: first, or after the inner loop has stopped
+  const int outer0 = *(volatile const int*)&ctrl->outer;
+  if (MODE == 1 && outer0 > 0 && !*(volatile const int*)&ctrl->inner_done) return;
+  for (int i = threadIdx.x; i < S::NB1 * S::NB1; i += VNT) sM1[i] = A.M1[i];
   const int lane = threadIdx.x & 31, gl = lane % S::GS, grp = lane / S::GS;
   Slots<S> sl;
-  sl.load(facevol, gl);
+  sl.load(A.facevol, gl);
   __syncthreads();
-  const int k0 = MODE == 0 ? ctrl_iter(ctrl) : *(volatile const int*)&ctrl->outer;
-  const double* ucur = (k0 & 1) ? u1p : u0p;
-  double* unext = (k0 & 1) ? u0p : u1p;
-  // the correction of the last inner loop: after j >= 1 inner sweeps it is in e[j & 1]
+  const int k0 = MODE == 0 ? ctrl_iter(ctrl) : outer0;
+  const double* ucur = (k0 & 1) ? A.u1p : A.u0p;
+  double* unext = (k0 & 1) ? A.u0p : A.u1p;
+  // the correction of the last inner loop (none before the first outer step): after j >= 1
+  // inner sweeps it is in e[j & 1]
   const TL* ec = nullptr;
-  if (MODE == 1 && has_e) ec = (*(volatile const int*)&ctrl->inner_iter & 1) ? e1 : e0;
+  if (MODE == 1 && outer0 > 0) ec = (*(volatile const int*)&ctrl->inner_iter & 1) ? A.e1 : A.e0;
   double accM = 0.0, acc2 = 0.0;
-  const long long first = (long long)blockIdx.x * S::EPB + (threadIdx.x >> 5) * S::EPW;
-  for (long long base = first; base < g.nel; base += (long long)gridDim.x * S::EPB) {
+  const long long first = (long long)bid * S::EPB + (threadIdx.x >> 5) * S::EPW;
+  for (long long base = first; base < g.nel; base += (long long)A.nblk * S::EPB) {
     const long long K = base + grp;
     const bool valid = K < g.nel;
     int c[3] = {0, 0, 0};
@@ -320,9 +343,9 @@ __global__ void __launch_bounds__(VNT) k_var_sweep(const VGeo g, const double* _
     if (row) {
       uo = ucur[K * S::NB + gl];
       if (ec) uo += (double)vld_or(ec, K * S::NB + gl);
-      s = V[K * S::NB + gl];
+      s = A.V[K * S::NB + gl];
     }
-    const double* Lk = L + (size_t)(valid ? K : 0) * S::NIN * S::NB + (gl < S::NB ? gl : 0);
+    const double* Lk = A.L + (size_t)(valid ? K : 0) * S::NIN * S::NB + (gl < S::NB ? gl : 0);
 #pragma unroll
     for (int k = 0; k < S::NIN; ++k) {
       const double tk = __shfl_sync(0xffffffffu, t[k / S::GS], k % S::GS, S::GS);
@@ -336,15 +359,15 @@ __global__ void __launch_bounds__(VNT) k_var_sweep(const VGeo g, const double* _
         unext[K * S::NB + gl] = s;
       } else {
         unext[K * S::NB + gl] = uo;
-        r64[K * S::NB + gl] = dlt;
-        rlp[K * S::NB + gl] = from_f<TL>((float)dlt);
+        A.r64[K * S::NB + gl] = dlt;
+        A.rlp[K * S::NB + gl] = from_f<TL>((float)dlt);
         acc2 += dlt * dlt;
       }
     }
   }
   double tM, t2;
-  if (var_arrive2(ctrl, partials, accM, acc2, &tM, &t2)) {
-    decide(ctrl, tM, res_hist, true);
+  if (var_arrive2(ctrl, A.partials, accM, acc2, &tM, &t2, bid, A.nblk)) {
+    decide(ctrl, tM, A.res_hist, true);
     if (MODE == 1) {
       ctrl->rnorm = sqrt(t2);
       ctrl->outer = k0 + 1;
@@ -352,6 +375,34 @@ __global__ void __launch_bounds__(VNT) k_var_sweep(const VGeo g, const double* _
       ctrl->inner_done = 0;
     }
   }
+}
+
+// Float64 sweep of one problem.  MODE 0 (the plain iteration): u^{k+1} = V + L t(u^k), stopping
+// residual ||u^{k+1} - u^k||_M.  MODE 1 (mixed outer sweep): u' = u + e, r = V + L t(u') - u',
+// written in float64 and as the low-precision residual; its norm ||r||_M is the stopping
+// residual of the exact sweep from u'.
+template <int D, int P, int MODE, typename TL>
+__global__ void __launch_bounds__(VNT) k_var_sweep(const VSweepArgs<TL> A) {
+  var_sweep_body<D, P, MODE, TL>(A, (int)blockIdx.x);
+}
+
+// Index of the problem that block b belongs to in a grouped launch (off: prefix sums of the
+// problems' block counts, n + 1 entries).
+__device__ __forceinline__ int group_item(const int* off, int n, int b) {
+  int i = 0;
+  while (i + 1 < n && __ldg(off + i + 1) <= b) ++i;
+  return i;
+}
+
+// The same sweep for several problems of one shape in one launch: each problem keeps its own
+// grid (block b - off[i] of nblk), reduction and loop state, so its result is bitwise the one
+// of its own launch.
+template <int D, int P, int MODE, typename TL>
+__global__ void __launch_bounds__(VNT) k_var_sweep_group(const VSweepArgs<TL>* __restrict__ items,
+                                                         const int* __restrict__ off, int n) {
+  const int i = group_item(off, n, (int)blockIdx.x);
+  const VSweepArgs<TL> A = items[i];
+  var_sweep_body<D, P, MODE, TL>(A, (int)blockIdx.x - __ldg(off + i));
 }
 
 // The TMA engine's untiled bulk copy, global -> this CTA's shared memory, its completion
@@ -385,22 +436,40 @@ __device__ __forceinline__ bool vmbar_wait(uint32_t mbar, uint32_t parity, long 
 // warp gathers its traces and computes from shared memory.  Every wait is bounded: on expiry
 // the kernel sets ctrl->timeout, waits (bounded) for its own copies still in flight and stops
 // the loop.
+template <typename TL>
+struct VInnerArgs {
+  VGeo g;
+  const TL* L;
+  int lsb, R;
+  const int* facevol;
+  const TL* rlp;
+  TL* e0;
+  TL* e1;
+  Ctrl* ctrl;
+  double* partials;
+  int nblk;   // blocks of this problem's launch
+};
+
 template <int D, int P, typename TL>
-__global__ void __launch_bounds__(VNT) k_var_inner(const VGeo g, const TL* __restrict__ L, const int lsb, const int R,
-                                                   const int* __restrict__ facevol, const TL* __restrict__ rlp, TL* e0,
-                                                   TL* e1, Ctrl* ctrl, double* partials) {
+__device__ __forceinline__ void var_inner_body(const VInnerArgs<TL>& A, int bid) {
   using S = VShape<D, P>;
   constexpr int NW = VNT / 32;
   extern __shared__ __align__(128) unsigned char vsm[];
   __shared__ __align__(8) unsigned long long s_mb[NW * 8];
-  if (ctrl_done(ctrl) || *(volatile const int*)&ctrl->inner_done) return;
+  const VGeo& g = A.g;
+  const TL* __restrict__ L = A.L;
+  const TL* __restrict__ rlp = A.rlp;
+  const int lsb = A.lsb, R = A.R;
+  Ctrl* ctrl = A.ctrl;
+  // nothing to do before the first outer step, after the inner loop stopped, or when done
+  if (ctrl_done(ctrl) || *(volatile const int*)&ctrl->inner_done || *(volatile const int*)&ctrl->outer == 0) return;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, gl = lane % S::GS, grp = lane / S::GS;
   Slots<S> sl;
-  sl.load(facevol, gl);
+  sl.load(A.facevol, gl);
   // e_0 = r (the first correction from zero); e_j in e[j & 1] for j >= 1
   const int j = *(volatile const int*)&ctrl->inner_iter;
-  const TL* ec = j == 0 ? rlp : ((j & 1) ? e1 : e0);
-  TL* en = (j & 1) ? e0 : e1;
+  const TL* ec = j == 0 ? rlp : ((j & 1) ? A.e1 : A.e0);
+  TL* en = (j & 1) ? A.e0 : A.e1;
   const int SB = S::EPW * lsb;
   unsigned char* ring = vsm + (size_t)w * R * SB;
   const uint32_t mb0 = vsmem(&s_mb[w * 8]);
@@ -409,11 +478,11 @@ __global__ void __launch_bounds__(VNT) k_var_inner(const VGeo g, const TL* __res
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncwarp();
-  const long long gw = (long long)blockIdx.x * NW + w, GW = (long long)gridDim.x * NW;
+  const long long gw = (long long)bid * NW + w, GW = (long long)A.nblk * NW;
   const long long nbatch = (g.nel + S::EPW - 1) / S::EPW;
   // failure-detection test hook: warp 0 of block ctrl->stall_block issues no copy, so its
   // first wait runs out
-  const bool stall = (int)blockIdx.x == ctrl->stall_block && w == 0;
+  const bool stall = bid == ctrl->stall_block && w == 0;
   auto issue = [&](long long i) {   // lane 0: batch i of this warp into stage i % R
     const long long b = gw + i * GW;
     if (b >= nbatch || stall) return;
@@ -488,7 +557,7 @@ __global__ void __launch_bounds__(VNT) k_var_inner(const VGeo g, const TL* __res
     __syncwarp();
   }
   double tA, tB;
-  if (var_arrive2(ctrl, partials, (double)st, 0.0, &tA, &tB)) {
+  if (var_arrive2(ctrl, A.partials, (double)st, 0.0, &tA, &tB, bid, A.nblk)) {
     const int jn = j + 1, it = ctrl->iter + 1;
     ctrl->inner_iter = jn;
     ctrl->iter = it;
@@ -504,6 +573,20 @@ __global__ void __launch_bounds__(VNT) k_var_inner(const VGeo g, const TL* __res
       ctrl->inner_done = 1;
     }
   }
+}
+
+template <int D, int P, typename TL>
+__global__ void __launch_bounds__(VNT) k_var_inner(const VInnerArgs<TL> A) {
+  var_inner_body<D, P, TL>(A, (int)blockIdx.x);
+}
+
+// The inner sweep of several problems of one shape in one launch (as k_var_sweep_group).
+template <int D, int P, typename TL>
+__global__ void __launch_bounds__(VNT) k_var_inner_group(const VInnerArgs<TL>* __restrict__ items,
+                                                         const int* __restrict__ off, int n) {
+  const int i = group_item(off, n, (int)blockIdx.x);
+  const VInnerArgs<TL> A = items[i];
+  var_inner_body<D, P, TL>(A, (int)blockIdx.x - __ldg(off + i));
 }
 
 // u_out = the final state (plain) or the last outer state plus its exact-sweep residual
@@ -584,45 +667,92 @@ struct VarRun {
     return cudaGetLastError();
   }
   template <typename TL>
-  static cudaError_t sweep(VarDev& d, int mode, int has_e, cudaStream_t s) {
-    const VGeo g = vgeo(d);
-    TL* e0 = static_cast<TL*>(d.e[0]);
-    TL* e1 = static_cast<TL*>(d.e[1]);
-    TL* rl = static_cast<TL*>(d.rlp);
-    if (mode == 0)
-      k_var_sweep<D, P, 0, TL><<<d.grid, VNT, 0, s>>>(g, d.L64, d.M1, d.facevol, d.V, d.u[0], d.u[1], e0, e1, 0,
-                                                      d.r64, rl, d.ctrl, d.partials, d.res_hist);
-    else
-      k_var_sweep<D, P, 1, TL><<<d.grid, VNT, 0, s>>>(g, d.L64, d.M1, d.facevol, d.V, d.u[0], d.u[1], e0, e1, has_e,
-                                                      d.r64, rl, d.ctrl, d.partials, d.res_hist);
+  static VSweepArgs<TL> sweep_args(VarDev& d) {
+    VSweepArgs<TL> A{};
+    A.g = vgeo(d);
+    A.L = d.L64;
+    A.M1 = d.M1;
+    A.facevol = d.facevol;
+    A.V = d.V;
+    A.u0p = d.u[0];
+    A.u1p = d.u[1];
+    A.e0 = static_cast<const TL*>(d.e[0]);
+    A.e1 = static_cast<const TL*>(d.e[1]);
+    A.r64 = d.r64;
+    A.rlp = static_cast<TL*>(d.rlp);
+    A.ctrl = d.ctrl;
+    A.partials = d.partials;
+    A.res_hist = d.res_hist;
+    A.nblk = d.grid;
+    return A;
+  }
+  template <typename TL>
+  static cudaError_t sweep(VarDev& d, int mode, cudaStream_t s) {
+    const VSweepArgs<TL> A = sweep_args<TL>(d);
+    if (mode == 0) k_var_sweep<D, P, 0, TL><<<d.grid, VNT, 0, s>>>(A);
+    else k_var_sweep<D, P, 1, TL><<<d.grid, VNT, 0, s>>>(A);
     return cudaGetLastError();
   }
-  // stages per warp: enough for ~100 KB of shared memory per block (two blocks per SM), 2..8
+  // the inner kernel's launch shape: stages per warp for ~100 KB of shared memory per block (two
+  // blocks per SM), 2..8; grid capped by residency and by the partials array (d.grid blocks)
   template <typename TL>
-  static cudaError_t inner(VarDev& d, cudaStream_t s) {
+  static cudaError_t inner_args(VarDev& d, VInnerArgs<TL>* A, size_t* smem) {
     using S = VShape<D, P>;
     const bool f32 = std::is_same<TL, float>::value;
-    const TL* L = f32 ? (const TL*)d.L32 : (const TL*)d.L16;
     const int lsb = f32 ? d.lsb32 : d.lsb16;
     const int nw = VNT / 32, sb = S::EPW * lsb;
     int R = (100 * 1024) / (nw * sb);
     R = R < 2 ? 2 : (R > 8 ? 8 : R);
-    const size_t smem = (size_t)nw * R * sb;
+    *smem = (size_t)nw * R * sb;
     auto k = k_var_inner<D, P, TL>;
+    auto kg = k_var_inner_group<D, P, TL>;
     cudaError_t e = allow_dynamic_smem(k);
+    if (e == cudaSuccess) e = allow_dynamic_smem(kg);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, VNT, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, VNT, *smem);
     if (e != cudaSuccess) return e;
     if (per < 1) return cudaErrorInvalidConfiguration;
     const long long nbatch = (d.nel + S::EPW - 1) / S::EPW;
     long long grid = (nbatch + nw - 1) / nw;
     if (grid > (long long)per * sms) grid = (long long)per * sms;
-    if (grid > d.grid) grid = d.grid;   // the partials array holds d.grid blocks
-    k<<<(unsigned)grid, VNT, smem, s>>>(vgeo(d), L, lsb, R, d.facevol, static_cast<const TL*>(d.rlp),
-                                        static_cast<TL*>(d.e[0]), static_cast<TL*>(d.e[1]), d.ctrl, d.partials);
+    if (grid > d.grid) grid = d.grid;
+    *A = VInnerArgs<TL>{};
+    A->g = vgeo(d);
+    A->L = f32 ? (const TL*)d.L32 : (const TL*)d.L16;
+    A->lsb = lsb;
+    A->R = R;
+    A->facevol = d.facevol;
+    A->rlp = static_cast<const TL*>(d.rlp);
+    A->e0 = static_cast<TL*>(d.e[0]);
+    A->e1 = static_cast<TL*>(d.e[1]);
+    A->ctrl = d.ctrl;
+    A->partials = d.partials;
+    A->nblk = (int)grid;
+    return cudaSuccess;
+  }
+  template <typename TL>
+  static cudaError_t inner(VarDev& d, cudaStream_t s) {
+    VInnerArgs<TL> A;
+    size_t smem = 0;
+    cudaError_t e = inner_args<TL>(d, &A, &smem);
+    if (e != cudaSuccess) return e;
+    k_var_inner<D, P, TL><<<(unsigned)A.nblk, VNT, smem, s>>>(A);
+    return cudaGetLastError();
+  }
+  // grouped launches over device descriptor arrays (items, off: n + 1 prefix sums of blocks)
+  template <typename TL>
+  static cudaError_t sweep_group(const void* items, const int* off, int n, int blocks, int mode, cudaStream_t s) {
+    const auto* it = static_cast<const VSweepArgs<TL>*>(items);
+    if (mode == 0) k_var_sweep_group<D, P, 0, TL><<<blocks, VNT, 0, s>>>(it, off, n);
+    else k_var_sweep_group<D, P, 1, TL><<<blocks, VNT, 0, s>>>(it, off, n);
+    return cudaGetLastError();
+  }
+  template <typename TL>
+  static cudaError_t inner_group(const void* items, const int* off, int n, int blocks, size_t smem, cudaStream_t s) {
+    k_var_inner_group<D, P, TL><<<blocks, VNT, smem, s>>>(static_cast<const VInnerArgs<TL>*>(items), off, n);
     return cudaGetLastError();
   }
   static cudaError_t trace(VarDev& d, const double* u, const double* gb, double* tr, cudaStream_t s) {
@@ -841,7 +971,7 @@ ihdg_status var_solve(VarDev& d, const double* f, const double* gb, const ihdg_o
       const int n = std::min(batch, left);
       if (n <= 0) break;
       for (int i = 0; i < n; ++i)
-        if (!ck(timed([&] { return var_dispatch(d, [&](auto R) { return decltype(R)::template sweep<float>(d, 0, 0, s); }); },
+        if (!ck(timed([&] { return var_dispatch(d, [&](auto R) { return decltype(R)::template sweep<float>(d, 0, s); }); },
                       true),
                 "sweep kernel"))
           return IHDG_ERR_CUDA;
@@ -850,17 +980,15 @@ ihdg_status var_solve(VarDev& d, const double* f, const double* gb, const ihdg_o
     }
     ufinal = d.u[hc->iter & 1];
   } else {
-    int has_e = 0;
     for (;;) {
       cudaError_t e = timed([&] {
         return var_dispatch(d, [&](auto R) {
-          return bf16 ? decltype(R)::template sweep<__nv_bfloat16>(d, 1, has_e, s)
-                      : decltype(R)::template sweep<float>(d, 1, has_e, s);
+          return bf16 ? decltype(R)::template sweep<__nv_bfloat16>(d, 1, s)
+                      : decltype(R)::template sweep<float>(d, 1, s);
         });
       }, true);
       if (!ck(e, "outer sweep kernel")) return IHDG_ERR_CUDA;
       launches += 1;
-      has_e = 1;
       if (!readback("outer sweep")) return IHDG_ERR_CUDA;
       if (hc->done) break;
       int batch = 4;
@@ -913,6 +1041,219 @@ ihdg_status var_solve(VarDev& d, const double* f, const double* gb, const ihdg_o
     res->lowp_sweep_ms = hc->lowp_sweeps ? pf.mslp / hc->lowp_sweeps : 0.0;
     res->fp64_launches = pf.n64;
     res->lowp_launches = pf.nlp;
+  }
+  return IHDG_OK;
+}
+
+}  // namespace ihdg
+
+namespace ihdg {
+
+// Several plans solved together: every sweep step is one grouped launch per (dim, p) class
+// over all the class's plans (each block works for one plan, as that block of the plan's own
+// launch), so problems of any size and order share launches while each keeps its own grid,
+// reductions and loop state.  Forcing, output and trace stay per plan (once per solve).
+ihdg_status var_solve_group(std::vector<VarDev*>& ds, const std::vector<const double*>& f,
+                            const std::vector<const double*>& gb, const ihdg_options& o,
+                            const std::vector<double*>& u_out, const std::vector<double*>& tr_out, cudaStream_t s,
+                            std::string& err, ihdg_result* res) {
+  NvtxRange nv("ihdg variable-coefficient grouped solve");
+  const int n = (int)ds.size();
+  auto ck = [&](cudaError_t e, const char* where) {
+    if (e != cudaSuccess) {
+      err = std::string(where) + ": " + cudaGetErrorString(e);
+      return false;
+    }
+    return true;
+  };
+  if (o.prec == IHDG_MIXED_TF32) {
+    err = "variable-coefficient transport takes FP64, MIXED_FP32 or MIXED_BF16";
+    return IHDG_ERR_UNSUPPORTED;
+  }
+  const bool mixed = o.prec != IHDG_FP64, bf16 = o.prec == IHDG_MIXED_BF16;
+  const double inner_rtol = o.inner_rtol > 0.0 ? o.inner_rtol : (bf16 ? 0.2 : 2e-3);
+  long long wait_cycles = 2000000000LL;
+  if (const char* wv = std::getenv("IHDG_TEST_WAIT_CYCLES")) {
+    const long long v = std::atoll(wv);
+    if (v > 0) wait_cycles = v;
+  }
+  // resources released on every return path
+  struct Res {
+    void* dbuf = nullptr;
+    Ctrl* hc = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~Res() {
+      if (dbuf) cudaFree(dbuf);
+      if (hc) cudaFreeHost(hc);
+      if (a) cudaEventDestroy(a);
+      if (b) cudaEventDestroy(b);
+    }
+  } rs;
+  if (!ck(cudaMallocHost(&rs.hc, sizeof(Ctrl) * n), "pinned loop state") || !ck(cudaEventCreate(&rs.a), "event") ||
+      !ck(cudaEventCreate(&rs.b), "event"))
+    return IHDG_ERR_CUDA;
+  // classes of equal shape and their descriptor tables (host images, one device buffer)
+  struct Cls {
+    int dim, p;
+    std::vector<int> plans;
+    std::vector<unsigned char> sw, in;   // VSweepArgs / VInnerArgs images
+    std::vector<int> soff, ioff;
+    size_t smem = 0;
+    size_t o_sw = 0, o_in = 0, o_soff = 0, o_ioff = 0;
+  };
+  std::vector<Cls> cls;
+  for (int i = 0; i < n; ++i) {
+    int c = -1;
+    for (int k = 0; k < (int)cls.size(); ++k)
+      if (cls[k].dim == ds[i]->dim && cls[k].p == ds[i]->p) c = k;
+    if (c < 0) {
+      cls.push_back(Cls{ds[i]->dim, ds[i]->p, {}, {}, {}, {0}, {0}});
+      c = (int)cls.size() - 1;
+    }
+    cls[c].plans.push_back(i);
+  }
+  for (auto& C : cls) {
+    for (int i : C.plans) {
+      VarDev& d = *ds[i];
+      cudaError_t e = var_dispatch(d, [&](auto R) -> cudaError_t {
+        using Run = decltype(R);
+        auto put = [](std::vector<unsigned char>& v, const void* p, size_t b) {
+          v.insert(v.end(), static_cast<const unsigned char*>(p), static_cast<const unsigned char*>(p) + b);
+        };
+        if (bf16) {
+          const auto A = Run::template sweep_args<__nv_bfloat16>(d);
+          put(C.sw, &A, sizeof(A));
+          VInnerArgs<__nv_bfloat16> I;
+          cudaError_t r = mixed ? Run::template inner_args<__nv_bfloat16>(d, &I, &C.smem) : cudaSuccess;
+          if (r != cudaSuccess) return r;
+          put(C.in, &I, sizeof(I));
+          C.ioff.push_back(C.ioff.back() + (mixed ? I.nblk : 0));
+        } else {
+          const auto A = Run::template sweep_args<float>(d);
+          put(C.sw, &A, sizeof(A));
+          VInnerArgs<float> I;
+          cudaError_t r = mixed ? Run::template inner_args<float>(d, &I, &C.smem) : cudaSuccess;
+          if (r != cudaSuccess) return r;
+          put(C.in, &I, sizeof(I));
+          C.ioff.push_back(C.ioff.back() + (mixed ? I.nblk : 0));
+        }
+        C.soff.push_back(C.soff.back() + d.grid);
+        return cudaSuccess;
+      });
+      if (!ck(e, "grouped launch set-up")) return IHDG_ERR_CUDA;
+    }
+  }
+  size_t at = 0;
+  auto take = [&](size_t b) { size_t r = at; at += (b + 255) & ~size_t(255); return r; };
+  for (auto& C : cls) {
+    C.o_sw = take(C.sw.size());
+    C.o_in = take(C.in.size());
+    C.o_soff = take(C.soff.size() * sizeof(int));
+    C.o_ioff = take(C.ioff.size() * sizeof(int));
+  }
+  if (!ck(cudaMalloc(&rs.dbuf, at), "grouped launch descriptors")) return IHDG_ERR_CUDA;
+  char* db = static_cast<char*>(rs.dbuf);
+  for (auto& C : cls) {
+    if (!ck(cudaMemcpy(db + C.o_sw, C.sw.data(), C.sw.size(), cudaMemcpyHostToDevice), "descriptors") ||
+        !ck(cudaMemcpy(db + C.o_in, C.in.data(), C.in.size(), cudaMemcpyHostToDevice), "descriptors") ||
+        !ck(cudaMemcpy(db + C.o_soff, C.soff.data(), C.soff.size() * sizeof(int), cudaMemcpyHostToDevice), "descriptors") ||
+        !ck(cudaMemcpy(db + C.o_ioff, C.ioff.data(), C.ioff.size() * sizeof(int), cudaMemcpyHostToDevice), "descriptors"))
+      return IHDG_ERR_CUDA;
+  }
+  // loop state and forcing of every plan
+  int launches = 0;
+  if (!ck(cudaEventRecord(rs.a, s), "event")) return IHDG_ERR_CUDA;
+  for (int i = 0; i < n; ++i) {
+    VarDev& d = *ds[i];
+    LaunchArgs la{};
+    la.ctrl = d.ctrl;
+    la.stream = s;
+    const int max_iters = std::min(o.max_iters, d.max_hist);
+    if (!ck(launch_ctrl_init(la, o.tol, o.diverge_factor, max_iters, o.inner_max, inner_rtol, wait_cycles, -1), "ctrl init") ||
+        !ck(var_dispatch(d, [&](auto R) { return decltype(R)::forcing(d, f[i], gb[i], nullptr, s); }), "forcing kernel"))
+      return IHDG_ERR_CUDA;
+    launches += 2;
+  }
+  auto readback = [&](const char* where) {
+    for (int i = 0; i < n; ++i)
+      if (!ck(cudaMemcpyAsync(rs.hc + i, ds[i]->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s), where)) return false;
+    return ck(cudaStreamSynchronize(s), where);
+  };
+  auto all_done = [&]() {
+    for (int i = 0; i < n; ++i)
+      if (!rs.hc[i].done) return false;
+    return true;
+  };
+  auto launch_all = [&](int which) -> bool {   // 0 float64 sweep, 1 outer sweep, 2 inner sweep
+    for (auto& C : cls) {
+      VarDev& d0 = *ds[C.plans[0]];
+      const int np = (int)C.plans.size();
+      cudaError_t e = var_dispatch(d0, [&](auto R) -> cudaError_t {
+        using Run = decltype(R);
+        if (which < 2)
+          return bf16 ? Run::template sweep_group<__nv_bfloat16>(db + C.o_sw, (const int*)(db + C.o_soff), np, C.soff.back(), which, s)
+                      : Run::template sweep_group<float>(db + C.o_sw, (const int*)(db + C.o_soff), np, C.soff.back(), which, s);
+        return bf16 ? Run::template inner_group<__nv_bfloat16>(db + C.o_in, (const int*)(db + C.o_ioff), np, C.ioff.back(), C.smem, s)
+                    : Run::template inner_group<float>(db + C.o_in, (const int*)(db + C.o_ioff), np, C.ioff.back(), C.smem, s);
+      });
+      if (!ck(e, which == 2 ? "grouped inner sweep" : "grouped sweep")) return false;
+      ++launches;
+    }
+    return true;
+  };
+  if (!mixed) {
+    int batch = 2;
+    for (;;) {
+      if (!readback("grouped sweep loop")) return IHDG_ERR_CUDA;
+      if (all_done()) break;
+      for (int i = 0; i < batch; ++i)
+        if (!launch_all(0)) return IHDG_ERR_CUDA;
+      if (batch < 32) batch *= 2;
+    }
+  } else {
+    int batch = 4;
+    for (;;) {
+      if (!launch_all(1)) return IHDG_ERR_CUDA;   // plans whose inner loop has stopped (or first)
+      for (int i = 0; i < batch; ++i)
+        if (!launch_all(2)) return IHDG_ERR_CUDA;
+      if (!readback("grouped mixed loop")) return IHDG_ERR_CUDA;
+      for (int i = 0; i < n; ++i)
+        if (rs.hc[i].timeout) {
+          err = "inner sweep: an operator copy into shared memory did not complete in time";
+          return IHDG_ERR_TIMEOUT;
+        }
+      if (all_done()) break;
+      if (batch < 64) batch *= 2;
+    }
+  }
+  for (int i = 0; i < n; ++i) {
+    VarDev& d = *ds[i];
+    const Ctrl& hc = rs.hc[i];
+    const double* uf = mixed ? d.u[hc.outer & 1] : d.u[hc.iter & 1];
+    const long long nS = d.nel * d.nb;
+    k_var_output<<<(unsigned)std::min<long long>((nS + 255) / 256, 4096), 256, 0, s>>>(nS, uf, mixed ? d.r64 : nullptr,
+                                                                                         u_out[i]);
+    if (!ck(cudaGetLastError(), "output kernel")) return IHDG_ERR_CUDA;
+    ++launches;
+    if (tr_out[i]) {
+      if (!ck(var_dispatch(d, [&](auto R) { return decltype(R)::trace(d, u_out[i], gb[i], tr_out[i], s); }), "trace kernel"))
+        return IHDG_ERR_CUDA;
+      ++launches;
+    }
+  }
+  if (!ck(cudaEventRecord(rs.b, s), "event") || !readback("grouped solve")) return IHDG_ERR_CUDA;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, rs.a, rs.b);
+  for (int i = 0; i < n; ++i) {
+    ihdg_result& r = res[i];
+    std::memset(&r, 0, sizeof(r));
+    r.iterations = rs.hc[i].iter;
+    r.fp64_sweeps = rs.hc[i].fp64_sweeps;
+    r.lowp_sweeps = rs.hc[i].lowp_sweeps;
+    r.residual = rs.hc[i].res;
+    r.status = (ihdg_status)rs.hc[i].status;
+    r.solve_ms = ms;
+    r.kernel_launches = launches;
   }
   return IHDG_OK;
 }

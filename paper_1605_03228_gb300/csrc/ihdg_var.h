@@ -99,4 +99,12 @@ void var_free(VarDev& d);
 ihdg_status var_solve(VarDev& d, const double* f_qp, const double* g_qp, const ihdg_options& o, double* u_out,
                       double* trace_out, cudaStream_t stream, Ctrl* h_ctrl, std::string& err, ihdg_result* res);
 
+// Several plans solved together with one grouped launch per (dim, p) class per sweep step;
+// each plan's result is the one of its own solve (same grids, reductions and decisions).
+// solve_ms of every result is the group's device time.
+ihdg_status var_solve_group(std::vector<VarDev*>& plans, const std::vector<const double*>& f_qp,
+                            const std::vector<const double*>& g_qp, const ihdg_options& o,
+                            const std::vector<double*>& u_out, const std::vector<double*>& trace_out,
+                            cudaStream_t stream, std::string& err, ihdg_result* res);
+
 }  // namespace ihdg

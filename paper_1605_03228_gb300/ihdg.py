@@ -70,7 +70,7 @@ EXPORTED = ["ihdg_create", "ihdg_destroy", "ihdg_last_error", "ihdg_problem_size
             "ihdg_swe_steps_device", "ihdg_host_operator", "ihdg_solve_device_static", "ihdg_server_start",
             "ihdg_server_stop", "ihdg_submit", "ihdg_poll", "ihdg_fetch", "ihdg_autotune", "ihdg_measure_peaks",
             "ihdg_face_quadrature_points", "ihdg_var_plan_create", "ihdg_var_plan_destroy", "ihdg_var_plan_info",
-            "ihdg_var_solve", "ihdg_var_solve_device", "ihdg_var_host_operator"]
+            "ihdg_var_solve", "ihdg_var_solve_device", "ihdg_var_host_operator", "ihdg_var_solve_group"]
 STATIC_SCRATCH_BYTES = 64 * 1024 * 1024
 
 _lib = None
@@ -121,6 +121,7 @@ def load(build_if_missing=True):
     L.ihdg_var_solve.argtypes = [VP, VP, dp, dp, P(Options), dp, dp, P(Result)]
     L.ihdg_var_solve_device.argtypes = [VP, VP, VP, VP, P(Options), VP, VP, VP, P(Result)]
     L.ihdg_var_host_operator.argtypes = [P(Mesh), dp, dp, ctypes.c_longlong, I, P(I), P(I), dp]
+    L.ihdg_var_solve_group.argtypes = [VP, I, P(VP), P(VP), P(VP), P(Options), P(VP), P(VP), VP, P(Result)]
     for name in EXPORTED:
         f = getattr(L, name)
         if name not in ("ihdg_destroy", "ihdg_last_error", "ihdg_var_plan_destroy"):
@@ -357,6 +358,18 @@ class Context:
         st = self.L.ihdg_var_plan_create(self.h, ctypes.byref(mesh), _dptr(bv), _dptr(bf), ctypes.byref(h))
         self._check(st, "ihdg_var_plan_create")
         return VarPlan(self, mesh, h)
+
+    def var_solve_group(self, plans, d_f, d_g, opts, d_u, d_tr=None, stream=0):
+        """ihdg_var_solve_group: device-pointer solves of several plans together (integer
+        pointers, one per plan).  Returns a list of Result."""
+        n = len(plans)
+        arr = lambda xs: (ctypes.c_void_p * n)(*[ctypes.c_void_p(int(x) if x else 0) for x in xs])
+        res = (Result * n)()
+        pl = (ctypes.c_void_p * n)(*[p.h for p in plans])
+        st = self.L.ihdg_var_solve_group(self.h, n, pl, arr(d_f), arr(d_g), ctypes.byref(opts), arr(d_u),
+                                         arr(d_tr) if d_tr is not None else None, ctypes.c_void_p(stream), res)
+        self._check(st, "ihdg_var_solve_group")
+        return list(res)
 
     # ---------------------------------------------------------------- serving
     def server_start(self, hbm_budget_bytes, slots):

@@ -213,3 +213,41 @@ def case_big(n, p):
     vol, bnd = ihdg.quadrature_points(mesh, co)
     fpts = ihdg.face_quadrature_points(mesh)
     return mesh, W.e2_beta(vol), W.e2_beta(fpts), W.e2_forcing(vol), W.e2_exact(bnd), None, None
+
+
+@pytest.mark.parametrize("prec_name", ["FP64", "MIXED_FP32", "MIXED_BF16"])
+def test_var_group_equals_alone(ctx, prec_name):
+    """Several plans of uneven size and order solved together (one grouped launch per shape
+    class and sweep step) give bitwise the results of their own solves: each block of a
+    grouped launch works for one plan as that block of the plan's own launch would."""
+    ihdg = ih()
+    cases = [("e1", 2, (8, 8), 3), ("swirl", 2, (13, 9), 3), ("e1", 2, (5, 7), 2), ("neg", 2, (6, 7), 4),
+             ("e2", 3, (4, 3, 5), 2), ("e2", 3, (6, 6, 6), 2), ("e2", 3, (3, 3, 3), 1)]
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.current_stream().cuda_stream
+    opts = ihdg.make_options(1e-10, max_iters=20000, prec=getattr(ihdg, prec_name))
+    plans, bufs, alone = [], [], []
+    try:
+        for field, d, n, p in cases:
+            mesh, bv, bf, f, g, pr, disc = case(field, d, n, p)
+            plan = ctx.var_plan(mesh, bv, bf)
+            plans.append(plan)
+            df = torch.from_numpy(np.ascontiguousarray(f)).to(dev)
+            dg = torch.from_numpy(np.ascontiguousarray(g)).to(dev)
+            s = plan.sizes
+            nb = (p + 1) ** d
+            du = torch.empty((s.n_el, nb), dtype=torch.float64, device=dev)
+            dt = torch.empty((s.n_face, s.nface_nodes), dtype=torch.float64, device=dev)
+            r = plan.solve_device(df.data_ptr(), dg.data_ptr(), opts, du.data_ptr(), dt.data_ptr(), stream)
+            alone.append((du.cpu().numpy().copy(), dt.cpu().numpy().copy(), r.iterations, r.status))
+            du.fill_(np.nan)
+            dt.fill_(np.nan)
+            bufs.append((df, dg, du, dt))
+        res = ctx.var_solve_group(plans, [b[0].data_ptr() for b in bufs], [b[1].data_ptr() for b in bufs], opts,
+                                  [b[2].data_ptr() for b in bufs], [b[3].data_ptr() for b in bufs], stream)
+        for (u1, t1, it1, st1), (df, dg, du, dt), r in zip(alone, bufs, res):
+            assert r.status == st1 == ihdg.OK and r.iterations == it1
+            assert np.array_equal(du.cpu().numpy(), u1) and np.array_equal(dt.cpu().numpy(), t1)
+    finally:
+        for pl in plans:
+            pl.close()
