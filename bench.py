@@ -778,15 +778,8 @@ def main():
         # read E^k, E^(k-1), F, write E^(k+1): 4 float64 words per export value
         bytes_per_launch = sz.n_el * sz.n_exp * 8 * 4
     else:
-        # the inner kernel the solve ran: tensor cores, the 2D CUDA-core kernels (temporally
-        # blocked unless one sweep per barrier was chosen), or the 3D shared-memory tile kernel
-        if opts.inner_kernel == ih.KERNEL_TENSOR_CORES or (opts.inner_kernel == ih.KERNEL_AUTO and
-                                                          (prec in (ih.MIXED_BF16, ih.MIXED_TF32) or spec["dim"] == 3)):
-            kern = "k_inner_tc"
-        elif spec["dim"] == 2:
-            kern = "k_inner_reg" if opts.sweeps_per_sync == 1 else "k_inner_blk"
-        else:
-            kern = "k_inner_tile"
+        # the inner kernel the solve ran, as the library reports it
+        kern = ih.INNER_KERNEL_NAMES.get(rp.inner_kernel_used) or "inner kernel not recorded"
         kms = rp.lowp_sweep_ms
         # read e_j, r, write e_(j+1): 3 low-precision words per export value
         bytes_per_launch = sz.n_el * sz.n_exp * lp_bytes * 3
@@ -800,8 +793,10 @@ def main():
     traffic = None
     try:
         tr = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-        ent = tr.get(f"{spec['name']}:{kern}")
-        if ent and ent.get("per_launch_bytes"):
+        ent = tr.get(f"{spec['name']}:{kern}") or {}
+        if ent.get("per_element_bytes"):
+            traffic = ent["per_element_bytes"] * sz.n_el
+        elif ent.get("per_launch_bytes") and ent.get("n_el") == sz.n_el:
             traffic = ent["per_launch_bytes"]
     except Exception:
         pass

@@ -155,6 +155,10 @@ typedef struct {
                               the loop already stopped and returned at once) */
   double latency_ms;       /* serving: submit -> results on the host */
   double queue_ms;         /* serving: submit -> admitted to a slot */
+  int inner_kernel_used;   /* mixed: the kernel that ran the inner sweeps (0 none or not
+                              recorded, 1 tensor cores k_inner_tc, 2 temporally blocked
+                              k_inner_blk, 3 register-resident k_inner_reg, 4 shared-memory
+                              tile k_inner_tile, 5 global state k_inner_persist) */
 } ihdg_result;
 
 typedef struct {

@@ -288,6 +288,7 @@ ihdg_status device_iterate(ihdg_ctx* ctx, Plan* pl, const ihdg_options& o, const
   a.partials = reinterpret_cast<double*>(ws + L.partials);
   a.res_hist = reinterpret_cast<double*>(ws + L.res_hist);
   a.stream = stream;
+  int inner_used = 0;
   // every event this call creates is destroyed on every return path (errors included)
   struct Events {
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -427,6 +428,7 @@ ihdg_status device_iterate(ihdg_ctx* ctx, Plan* pl, const ihdg_options& o, const
     m.slots = partials_needed(pl->g.nel);
     ihdg_status st = run_mixed(ctx->h_ctrl, m, o, &Eu, &Eu2, &Et, &Et2, ctx->err, &tm);
     if (st != IHDG_OK) return fail(ctx, st, ctx->err);
+    inner_used = m.ran;
   }
   if (d_u) { CK(launch_reconstruct(a, Eu, Eu2, d_u), "reconstruct kernel"); tm.launches += 1; }
   if (d_tr) {
@@ -452,6 +454,7 @@ ihdg_status device_iterate(ihdg_ctx* ctx, Plan* pl, const ihdg_options& o, const
     res->residual = hc->res;
     res->status = (ihdg_status)hc->status;
     res->solve_ms = ms;
+    res->inner_kernel_used = inner_used;
   }
   return IHDG_OK;
 }
@@ -1082,6 +1085,7 @@ ihdg_status ihdg_swe_steps_device(ihdg_ctx* ctx, const ihdg_mesh* mesh, const ih
     tot.fp64_launches += r.fp64_launches;
     tot.lowp_launches += r.lowp_launches;
     tot.kernel_launches += r.kernel_launches;
+    if (r.inner_kernel_used) tot.inner_kernel_used = r.inner_kernel_used;
     if (r.status > tot.status) tot.status = r.status;
   }
   CK(cudaStreamSynchronize(s), "swe steps");

@@ -605,6 +605,11 @@ cudaError_t launch_trace_out(const LaunchArgs& a, const double* E, const double*
                                                 alpha[0], alpha[1], alpha[2], nface, tr);
   return cudaGetLastError();
 }
-int partials_needed(long long nel) { return 2 * (int)grid_for(nel) + 2; }
+// two halves (ping-pong) of one slot per block; at least 512 blocks, so that the persistent
+// kernels may size their grids by SM count on small meshes too
+int partials_needed(long long nel) {
+  const long long g = grid_for(nel);
+  return 2 * (int)(g > 512 ? g : 512) + 2;
+}
 
 }  // namespace ihdg

@@ -70,6 +70,7 @@ ihdg_status run_mixed(Ctrl* hc, MixedArgs& m, const ihdg_options& o, const doubl
     const int before = hc->iter;
     if (!ck(mlaunch(mm, which, he, 1), which == 0 ? "outer sweep kernel" : which == 1 ? "residual kernel" : "inner sweep kernel"))
       return false;
+    m.ran = mm.ran;
     tm->launches += 1;
     if (!tm->on) return true;
     if (!ck(cudaEventRecord(tm->b, a.stream), "event") || !ck(cudaEventSynchronize(tm->b), "event") ||

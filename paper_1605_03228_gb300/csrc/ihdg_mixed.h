@@ -38,6 +38,7 @@ struct MixedArgs {
   int lt_kind = 0;          // operator layout now in dLT: 0 none, 1 register kernel, 2 tensor-core B
   int blk_h = 0;            // >= 2: 2D CUDA-core inner sweeps temporally blocked, this many per barrier
   const float* LE32h = nullptr;  // host copy of the float32 operator (n_exp x n_in)
+  int ran = 0;              // inner kernel of the last inner launch (ihdg_result.inner_kernel_used codes)
 };
 
 // One launch of the mixed loop's kernel `which` (0 outer float64 sweep, 1 residual check + first

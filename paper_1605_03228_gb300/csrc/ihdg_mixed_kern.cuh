@@ -225,65 +225,118 @@ __device__ double barrier_sum(double* part, unsigned* count, unsigned nb, double
 }
 
 
-// Persistent inner loop on the correction equation: e_{j+1} = r + L_E t(e_j), until the
+// Low-precision operator passed by value: the kernel reads it from the parameter (constant)
+// bank, so every multiply-add takes its matrix entry straight from there.
+template <int NF, int NLF, bool PER_AXIS>
+struct LTile {
+  static constexpr int NIN = NF * NLF;
+  static constexpr int NEXP = PER_AXIS ? NF * (NLF / 2) : NF * NLF;
+  float L[NEXP][NIN];
+};
+
+// Persistent inner loop on the correction equation with the state in global memory (meshes
+// whose state fits neither registers nor shared memory): e_{j+1} = r + L_E t(e_j), until the
 // step norm falls below inner_rtol * ||r||, inner_max sweeps, or the sweep budget.  One
-// cooperative launch runs many sweeps; each sweep ends with a grid barrier after which every
-// block sums the per-block partials in the same fixed order, so all blocks take the same
-// decision.  Block 0 records the loop state.
-template <int NF, int NLF, typename TL>
-__global__ void __launch_bounds__(PBS) k_inner_persist(DevGeo g, OpsDev op, const TL* __restrict__ rlp, TL* e0,
-                                                       TL* e1, Ctrl* ctrl, double* partials) {
+// element per thread and grid-stride pass, software-pipelined: all loads of the next element
+// (its own exports, also the reference of the step norm; the neighbours' facing exports, an
+// in-bounds stand-in where none is read; r) are issued before the current element's operator
+// apply, so every warp keeps its next element's bytes in flight while it computes (operators
+// of up to 20 trace values; larger ones load and compute one element at a time).  Element
+// coordinates advance by the grid stride written as mixed-radix digits (no division per
+// element); ALL: every export slot carries a value (no per-slot tests).  The operator comes
+// from the parameter bank, one accumulation chain per row.  Each sweep ends with a grid
+// barrier after which every block sums the per-block partials in the same fixed order, so all
+// blocks take the same decision; block 0 records the loop state.
+template <int NF, int NLF, bool PER_AXIS, bool ALL, typename TL>
+__global__ void __launch_bounds__(PBS, NF * NLF <= 20 ? 2 : 1)
+    k_inner_persist(const DevGeo g, const TL* __restrict__ rlp, TL* e0, TL* e1, Ctrl* ctrl, double* partials,
+                    const LTile<NF, NLF, PER_AXIS> Lp) {
   constexpr int NIN = NF * NLF;
+  constexpr int NEXP = LTile<NF, NLF, PER_AXIS>::NEXP;
+  constexpr bool PIPE = NIN <= 20;   // the next element's loads fit beside the current element's values
   __shared__ double s_tot;
   __shared__ int s_to, s_stop;
   __shared__ float wsum_p[PBS / 32];
-  extern __shared__ float sf[];
   if (ctrl_done(ctrl) || *(volatile const int*)&ctrl->inner_done) return;
   int j = *(volatile const int*)&ctrl->inner_iter;
   const int iter0 = *(volatile const int*)&ctrl->iter;
   const int lowp0 = *(volatile const int*)&ctrl->lowp_sweeps;
   const int max_iters = ctrl->max_iters, inner_max = ctrl->inner_max;
   const double lim = ctrl->inner_rtol * ctrl->rnorm;
-  for (int i = threadIdx.x; i < g.n_exp * NIN; i += PBS) sf[i] = op.LE32[i];
-  __syncthreads();
-  const long long stride = (long long)gridDim.x * PBS;
+  const long long stride = (long long)gridDim.x * PBS, ld = g.ld, nel = g.nel;
+  const long long Kfirst = (long long)blockIdx.x * PBS + threadIdx.x;
+  int cfirst[3], ds[3];
+  coords(g, Kfirst, cfirst);
+  coords(g, stride, ds);   // the stride as digits (ds[0] < n0, ds[1] < n1)
+  auto live = [&](int e) { return ALL || ((g.live >> e) & 1ull); };
   for (int s = 0;; ++s) {
     const TL* __restrict__ ec = (j & 1) ? e1 : e0;
     TL* __restrict__ en = (j & 1) ? e0 : e1;
     float acc = 0.f;
-    for (long long K = (long long)blockIdx.x * PBS + threadIdx.x; K < g.nel; K += stride) {
-      int c[3];
-      coords(g, K, c);
-      float t[NIN];
-      gather_lp<NF, NLF, TL, float>(g, ec, K, c, [&](int q, float v) { t[q] = v; });
+    float ov[NEXP], rv[NEXP], nv[NLF][NF];
+    // all loads of element K at coordinates c (a thread past the end loads nothing)
+    auto fetch = [&](long long K, const int* c) {
+      const bool in = K < nel;
+      const long long Ks = in ? K : 0;
 #pragma unroll
-      for (int c0 = 0; c0 < NIN; c0 += CH) {
-        float rv[CH], ov[CH];
+      for (int e = 0; e < NEXP; ++e) {
+        ov[e] = (in && live(e)) ? ldcg_f(ec + e * ld + Ks) : 0.f;
+        rv[e] = (in && live(e)) ? to_f(rlp[e * ld + Ks]) : 0.f;
+      }
 #pragma unroll
-        for (int i = 0; i < CH; ++i) {
-          const int e = c0 + i;
-          rv[i] = 0.f;
-          ov[i] = 0.f;
-          if (e < g.n_exp && row_live(g, e, NF)) {
-            const long long at = (long long)e * g.ld + K;
-            rv[i] = to_f(rlp[at]);
-            ov[i] = ldcg_f(ec + at);
-          }
-        }
+      for (int f = 0; f < NLF; ++f) {
+        const int kind = g.kind[f];
+        const bool nbm = in && !on_bnd(g, c, f) && (kind == FK_NBR_D || kind == FK_SUM_D);
+        const int ns = PER_AXIS ? (f >> 1) * NF : (f ^ 1) * NF;
+        const TL* nb = ec + (long long)ns * ld + (nbm ? nbr_of(g, Ks, f) : Ks);
 #pragma unroll
-        for (int i = 0; i < CH; ++i) {
-          const int e = c0 + i;
-          if (e < g.n_exp && row_live(g, e, NF)) {
-            float v = rv[i];
-            const float* row = sf + e * NIN;
+        for (int q = 0; q < NF; ++q) nv[f][q] = ldcg_f(nb + q * ld);
+      }
+    };
+    long long K = Kfirst;
+    int c[3] = {cfirst[0], cfirst[1], cfirst[2]};
+    if (PIPE) fetch(K, c);
+    while (K < nel) {
+      if (!PIPE) fetch(K, c);
+      // a1: this element's traces; its exports and r stay for the rows
+      float t[NIN], oc[NEXP], rc[NEXP];
 #pragma unroll
-            for (int q = 0; q < NIN; ++q) v = fmaf(row[q], t[q], v);
-            const TL nv = from_f<TL>(v);
-            const float dl = to_f(nv) - ov[i];
-            acc = fmaf(dl, dl, acc);
-            en[(long long)e * g.ld + K] = nv;
-          }
-        }
+      for (int f = 0; f < NLF; ++f) {
+        const int kind = g.kind[f];
+        const bool bnd = on_bnd(g, c, f);
+        const bool nbm = !bnd && (kind == FK_NBR_D || kind == FK_SUM_D);
+        const float wo = kind == FK_OWN_D ? 1.f : kind == FK_SUM_D ? (!bnd ? 1.f : (g.bc_mirror ? 2.f : 0.f)) : 0.f;
+        const int os = PER_AXIS ? (f >> 1) * NF : f * NF;
+#pragma unroll
+        for (int q = 0; q < NF; ++q) t[f * NF + q] = wo * ov[os + q] + (nbm ? nv[f][q] : 0.f);
+      }
+#pragma unroll
+      for (int e = 0; e < NEXP; ++e) {
+        oc[e] = ov[e];
+        rc[e] = rv[e];
+      }
+      const long long Kc = K;
+      // the next element: coordinates by digit addition with carries, then its loads
+      K += stride;
+      c[0] += ds[0];
+      int cy = c[0] >= g.n[0];
+      if (cy) c[0] -= g.n[0];
+      c[1] += ds[1] + cy;
+      cy = c[1] >= g.n[1];
+      if (cy) c[1] -= g.n[1];
+      c[2] += ds[2] + cy;
+      if (PIPE) fetch(K, c);
+      // a3 + a4: e_new = r + L_E t, rounded to the storage type; the step norm
+#pragma unroll
+      for (int e = 0; e < NEXP; ++e) {
+        if (!live(e)) continue;
+        float v = rc[e];
+#pragma unroll
+        for (int k = 0; k < NIN; ++k) v = fmaf(Lp.L[e][k], t[k], v);
+        const TL nt = from_f<TL>(v);
+        const float dl = to_f(nt) - oc[e];
+        acc = fmaf(dl, dl, acc);
+        en[e * ld + Kc] = nt;
       }
     }
     const int it = iter0 + s + 1;
@@ -315,15 +368,6 @@ __global__ void __launch_bounds__(PBS) k_inner_persist(DevGeo g, OpsDev op, cons
     if (s_stop) break;
   }
 }
-
-// Low-precision operator passed by value: the kernel reads it from the parameter (constant)
-// bank, so every multiply-add takes its matrix entry straight from there.
-template <int NF, int NLF, bool PER_AXIS>
-struct LTile {
-  static constexpr int NIN = NF * NLF;
-  static constexpr int NEXP = PER_AXIS ? NF * (NLF / 2) : NF * NLF;
-  float L[NEXP][NIN];
-};
 
 // Persistent inner loop with block-resident state.  Block b owns elements
 // [b*epb, b*epb + epb); their own exports e_j and the residual r stay in shared memory
@@ -1042,6 +1086,41 @@ cudaError_t launch_tile(MixedArgs& m, TL* rl, TL* e0, TL* e1) {
   return launch_tile_v<NF, NLF, PER_AXIS, TL, 512, 1>(m, rl, e0, e1);
 }
 
+// Cooperative launch of k_inner_persist: as many co-resident blocks as the elements need.
+template <int NF, int NLF, bool PER_AXIS, typename TL>
+cudaError_t launch_persist(MixedArgs& m, TL* rl, TL* e0, TL* e1) {
+  using LT = LTile<NF, NLF, PER_AXIS>;
+  const LaunchArgs& a = m.base;
+  if (!m.LE32h || a.g.n_exp != LT::NEXP) return cudaErrorNotSupported;
+  const size_t smem = 0;
+  const unsigned long long all = LT::NEXP >= 64 ? ~0ull : (1ull << LT::NEXP) - 1;
+  auto k = (a.g.live & all) == all ? k_inner_persist<NF, NLF, PER_AXIS, true, TL>
+                                   : k_inner_persist<NF, NLF, PER_AXIS, false, TL>;
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, PBS, smem);
+  if (e != cudaSuccess) return e;
+  if (per < 1) return cudaErrorInvalidConfiguration;
+  long long need = (a.g.nel + PBS - 1) / PBS;
+  long long cap = (long long)per * sms;
+  int grid = (int)(need < cap ? need : cap);
+  if (grid > m.max_grid) grid = m.max_grid;
+  LT L;
+  for (int r = 0; r < LT::NEXP; ++r)
+    for (int q = 0; q < LT::NIN; ++q) L.L[r][q] = m.LE32h[r * LT::NIN + q];
+  DevGeo gg = a.g;
+  const TL* rlc = rl;
+  Ctrl* ct = a.ctrl;
+  double* pp = a.partials;
+  void* args[] = {&gg, &rlc, &e0, &e1, &ct, &pp, &L};
+  e = cudaMemsetAsync(&a.ctrl->bar_count, 0, sizeof(unsigned), a.stream);
+  if (e != cudaSuccess) return e;
+  e = cudaLaunchCooperativeKernel((const void*)k, dim3(grid), dim3(PBS), args, smem, a.stream);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
 inline unsigned grid_for(long long n) { return (unsigned)((n + BS - 1) / BS); }
 
 template <typename TL>
@@ -1084,7 +1163,7 @@ struct MixedRunner {
             ce = a.g.per_axis ? launch_tc<NF, NLF, true, TC_TF32X4>(m, rl, e0, e1)
                               : launch_tc<NF, NLF, false, TC_TF32X4>(m, rl, e0, e1);
           }
-          if (ce != cudaErrorNotSupported) return ce;
+          if (ce != cudaErrorNotSupported) return m.ran = 1, ce;
           // shapes the tensor-core kernel does not take (n_in > 64 or n_exp > 32) fall through
           // to the CUDA-core kernels in full float32
         }
@@ -1093,41 +1172,21 @@ struct MixedRunner {
             if (m.blk_h >= 2) {
               cudaError_t be = a.g.per_axis ? launch_blk_v<NF, true, TL, 1024>(m, rl, e0, e1)
                                             : launch_blk_v<NF, false, TL, 1024>(m, rl, e0, e1);
-              if (be != cudaErrorNotSupported) return be;
+              if (be != cudaErrorNotSupported) return m.ran = 2, be;
             }
             if (m.tile_lpe != 1) {
               cudaError_t re = a.g.per_axis ? launch_reg<NF, true, TL>(m, rl, e0, e1)
                                             : launch_reg<NF, false, TL>(m, rl, e0, e1);
-              if (re != cudaErrorNotSupported) return re;
+              if (re != cudaErrorNotSupported) return m.ran = 3, re;
             }
           }
           cudaError_t te = a.g.per_axis ? launch_tile<NF, NLF, true, TL>(m, rl, e0, e1)
                                         : launch_tile<NF, NLF, false, TL>(m, rl, e0, e1);
-          if (te != cudaErrorNotSupported) return te;
+          if (te != cudaErrorNotSupported) return m.ran = 4, te;
         }
-        // persistent cooperative launch: as many co-resident blocks as the elements need
-        size_t smem = (size_t)a.g.n_exp * NIN * sizeof(float);
-        auto k = k_inner_persist<NF, NLF, TL>;
-        int dev = 0, sms = 0, per = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, PBS, smem);
-        if (e != cudaSuccess) return e;
-        if (per < 1) return cudaErrorInvalidConfiguration;
-        long long need = (a.g.nel + PBS - 1) / PBS;
-        long long cap = (long long)per * sms;
-        int grid = (int)(need < cap ? need : cap);
-        if (grid > m.max_grid) grid = m.max_grid;
-        DevGeo gg = a.g;
-        OpsDev oo = a.op;
-        const TL* rlc = rl;
-        Ctrl* ct = a.ctrl;
-        double* pp = a.partials;
-        void* args[] = {&gg, &oo, &rlc, &e0, &e1, &ct, &pp};
-        e = cudaMemsetAsync(&a.ctrl->bar_count, 0, sizeof(unsigned), a.stream);
-        if (e != cudaSuccess) return e;
-        e = cudaLaunchCooperativeKernel((const void*)k, dim3(grid), dim3(PBS), args, smem, a.stream);
-        if (e != cudaSuccess) return e;
+        m.ran = 5;
+        return a.g.per_axis ? launch_persist<NF, NLF, true, TL>(m, rl, e0, e1)
+                            : launch_persist<NF, NLF, false, TL>(m, rl, e0, e1);
       }
       return cudaGetLastError();
     }

@@ -18,6 +18,9 @@ STATUS_NAMES = {0: "OK", 1: "ERR_INVALID", 2: "ERR_NOMEM", 3: "ERR_CUDA", 4: "NO
 TRANSPORT, CONVDIFF, SWE = 0, 1, 2
 FLUX_UPWIND, FLUX_NPC = 0, 1
 KERNEL_AUTO, KERNEL_TENSOR_CORES, KERNEL_CUDA_CORES, KERNEL_GLOBAL = 0, 1, 2, 3
+# Result.inner_kernel_used: the kernel that ran a mixed solve's inner sweeps
+INNER_KERNEL_NAMES = {0: None, 1: "k_inner_tc", 2: "k_inner_blk", 3: "k_inner_reg", 4: "k_inner_tile",
+                      5: "k_inner_persist"}
 FP64, MIXED_FP32, MIXED_TF32, MIXED_BF16 = 0, 1, 2, 3
 
 
@@ -45,7 +48,7 @@ class Result(ctypes.Structure):
                 ("residual", ctypes.c_double), ("status", ctypes.c_int), ("setup_ms", ctypes.c_double),
                 ("solve_ms", ctypes.c_double), ("fp64_sweep_ms", ctypes.c_double), ("lowp_sweep_ms", ctypes.c_double),
                 ("fp64_launches", ctypes.c_int), ("lowp_launches", ctypes.c_int), ("kernel_launches", ctypes.c_int),
-                ("latency_ms", ctypes.c_double), ("queue_ms", ctypes.c_double)]
+                ("latency_ms", ctypes.c_double), ("queue_ms", ctypes.c_double), ("inner_kernel_used", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -423,12 +423,19 @@ def test_mixed_inner_kernel_variants(ctx, monkeypatch, kernel, grid, lpe):
     u_b, _, rb = ctx.solve(mesh, co, f, g, opts)
     assert ra.status == rb.status == ihdg.OK
     assert rel(u_b, u_a) < 1e-9
+    # the result names the kernel that ran: global state, or a tile kernel (temporally
+    # blocked, register-resident or shared-memory tile)
+    used = rb.inner_kernel_used
+    assert (used == 5) if kernel == "global" else (used in (2, 3, 4)), used
 
 
 TC_CASES = [("t3d_p1", "", "tc", "MIXED_BF16"), ("t3d_p2", "", "tc", "MIXED_BF16"), ("cd2d_p3", "", "tc", "MIXED_BF16"),
             ("t2d_p2", "1", "tc", "MIXED_BF16"), ("t3d_p1", "", "tile", "MIXED_BF16"), ("cd2d_p3", "", "tile", "MIXED_BF16"),
             ("t3d_p1", "", "tc", "MIXED_FP32"), ("t3d_p2", "", "tc", "MIXED_FP32"), ("cd2d_p3", "", "tc", "MIXED_FP32"),
-            ("t2d_p2", "1", "tc", "MIXED_FP32"), ("t3d_p2", "", "tc", "MIXED_TF32"), ("cd2d_p3", "", "tc", "MIXED_TF32")]
+            ("t2d_p2", "1", "tc", "MIXED_FP32"), ("t3d_p2", "", "tc", "MIXED_TF32"), ("cd2d_p3", "", "tc", "MIXED_TF32"),
+            ("cd2d_p3", "", "global", "MIXED_FP32"), ("cd2d_p3", "3", "global", "MIXED_BF16"),
+            ("t3d_p2", "", "global", "MIXED_FP32"), ("t3d_p1", "2", "global", "MIXED_BF16"),
+            ("t2d_p2", "", "global", "MIXED_FP32")]
 
 
 @pytest.mark.parametrize("case,grid,kernel,prec_name", TC_CASES)
@@ -437,7 +444,9 @@ def test_mixed_tensor_core_inner(ctx, monkeypatch, case, grid, kernel, prec_name
     tiles of 128 elements with a float32 accumulator in tensor memory) reach the oracle's
     float64 solution at the mixed bar, for every operand mode: bf16 (kind::f16), float32 as
     four tf32 passes on hi/lo splits, and one tf32 pass; and so do bf16 sweeps on the CUDA
-    cores (kernel "tile").  The meshes leave a ragged last tile
+    cores (kernel "tile") and the global-state kernel (kernel "global": per-face and per-axis
+    export layouts, 2D and 3D, float32 and bf16 state, grids of 2 and 3 blocks looping over
+    the elements).  The meshes leave a ragged last tile
     (element counts not multiples of 128) and some of a block's four tile groups without a
     tile; a grid of one block makes its groups loop over several tiles per sweep."""
     ihdg = ih()
@@ -472,6 +481,9 @@ def test_mixed_tensor_core_inner(ctx, monkeypatch, case, grid, kernel, prec_name
     u, tr, res = ctx.solve(mesh, co, f, g, ihdg.make_options(tol, prec=getattr(ihdg, prec_name), max_iters=20000))
     assert res.status == ihdg.OK, res.as_dict()
     assert res.lowp_sweeps > 0
+    assert res.inner_kernel_used == {"tc": 1, "global": 5}.get(kernel, res.inner_kernel_used)
+    if kernel == "tile":
+        assert res.inner_kernel_used in (2, 3, 4)
     assert rel(u, U.reshape(pr.mesh.nel, -1)) < 1e-6
 
 
