@@ -17,5 +17,5 @@ contraction results the paper states (Theorem 1 and the remark after it).
 """
 from .mesh import BoxMesh
 from .refelem import RefElement, gll_nodes, gauss_rule, lagrange_matrix, lagrange_deriv_matrix
-from .ihdg import (Discretisation, Transport, TransportVar, ConvDiff, ShallowWater,
+from .ihdg import (Discretisation, Transport, TransportVar, ConvDiff, ShallowWater, ShallowWaterCN,
                    STATUS_OK, STATUS_NOT_CONVERGED, STATUS_DIVERGED)

@@ -16,7 +16,10 @@ What is computed, following the paper:
   the same with a velocity field beta(x) that varies in space (the paper's experiments of
   Section 5.1), every element with its own local matrix.
 * Section 3, Eq. (localSolverDD) and the trace formula below it: linearized shallow water,
-  backward Euler in time.
+  backward Euler in time; ShallowWaterCN: the same spatial HDG operator with the
+  Crank-Nicolson rule the paper's shallow-water experiments use (Section 5, linearized
+  shallow water subsection), written as the trapezoidal average of the implicit and explicit
+  spatial residuals.
 * Section 4.1, Eqs. (ErrorDDMCD1)/(ErrorDDMCD2) and the flux (general_flux_convdiff):
   convection-diffusion in first-order form with the upwind stabilisation.
 
@@ -730,3 +733,31 @@ class ShallowWater(Problem):
         """One backward-Euler step with the iHDG iteration warm-started from q^m."""
         U, T, k, res, status = self.iterate(None, None, tol, max_iters, U0=U_m, U_prev=U_m)
         return U, T, k, res, status
+
+    def step_direct(self, U_m):
+        """One time step by the direct (static condensation) solve."""
+        U, T = self.direct_solve(None, None, U_prev=U_m)
+        return U
+
+
+class ShallowWaterCN(ShallowWater):
+    """Linearized shallow water, one Crank-Nicolson step of size dt (the time rule of the
+    paper's shallow-water experiments): with N(q) = S q - sum_f W_f T_f(q) the element's HDG
+    spatial residual (S: the local matrix without its time-derivative part; T(q): the trace
+    of Section 3's formula evaluated from q), the step solves
+        (M/dt)(q^{m+1} - q^m) = -(N(q^{m+1}) + N(q^m)) / 2.
+    Multiplied by 2 this is a local problem with the time-derivative part 2M/dt (the
+    backward-Euler local matrix at dt/2) and the right-hand side
+        (2M/dt) q^m - N(q^m) = 2 (2M/dt) q^m - A q^m + sum_f W_f T_f(q^m),
+    where A = 2M/dt + S is that local matrix.  The iHDG iteration is Algorithm 1 on this
+    local problem, warm-started from q^m; the stopping test is on q^{m+1}'s iterates.
+    """
+
+    def __init__(self, disc, Phi, dt, coriolis=0.0, friction=0.0):
+        super().__init__(disc, Phi, 0.5 * dt, coriolis, friction)
+        self.dt_step = float(dt)
+
+    def volume_rhs(self, f_qp, U_prev):
+        mass = super().volume_rhs(f_qp, U_prev)            # (2M/dt) q^m, Phi-weighted rows
+        Aq = U_prev.reshape(self.mesh.nel, -1) @ self.A.T   # A q^m per element
+        return 2.0 * mass - Aq + self.trace_rhs(self.traces(U_prev))
