@@ -422,6 +422,12 @@ def sub_results(args, ih, ctx, dev, flush, peaks, pk):
         "fp64_ms": ms_64, "fp64_sweeps_per_step": float(np.mean(P.its)), "fp64_status": ih.STATUS_NAMES[r_64.status],
         "speedup_mixed_vs_fp64": ms_64 / ms_m, "mixed_vs_fp64_rel_l2_after_100_steps": rel,
         "element_dof_updates_per_s": P.sz.n_el * P.sz.nvol * r_m.iterations / (ms_m * 1e-3)}
+    # the same 100 steps with the Crank-Nicolson rule of the paper's shallow-water experiments
+    P.co.time_scheme = ih.CRANK_NICOLSON
+    ms_cn, r_cn = P.timed(om, 1, 1, flush)
+    out["swe_512"]["crank_nicolson_mixed_fp32"] = {
+        "ms": ms_cn, "sweeps_per_step": float(np.mean(P.its)), "status": ih.STATUS_NAMES[r_cn.status],
+        "rel_l2_vs_backward_euler_after_100_steps": float(torch.linalg.norm(P.dA - q_m) / torch.linalg.norm(q_m))}
     del P
     torch.cuda.synchronize(dev)
     # transport with the 3D experiment's velocity field beta = (z, x, y) (Section 5.1), 64^3,

@@ -67,6 +67,16 @@ typedef enum { IHDG_TRANSPORT = 0, IHDG_CONVDIFF = 1, IHDG_SWE = 2 } ihdg_pde;
  * flux (the paper gives NPC's tau for transport only). */
 typedef enum { IHDG_FLUX_UPWIND = 0, IHDG_FLUX_NPC = 1 } ihdg_flux;
 
+/* Time rule of the shallow-water steps.  BACKWARD_EULER: the local problem of Section 3 (Eq.
+ * localSolverDD) with M/dt.  CRANK_NICOLSON: the rule of the paper's shallow-water experiments
+ * (Section 5, linearized shallow water): (M/dt)(q^{m+1} - q^m) = -(N(q^{m+1}) + N(q^m))/2, N
+ * the HDG spatial residual.  The system is linear and autonomous, so the step is computed as
+ * q^{m+1} = 2 q^{m+1/2} - q^m with q^{m+1/2} the backward-Euler step of size dt/2, iterated
+ * from q^m to tolerance tol/2: its iterates map one to one onto the Crank-Nicolson iterates
+ * (k-th iterate 2 q^{m+1/2,k} - q^m, increments twice as large), so the iteration count and
+ * the stopping decision are the Crank-Nicolson iteration's.  Other PDEs: must be 0. */
+typedef enum { IHDG_BACKWARD_EULER = 0, IHDG_CRANK_NICOLSON = 1 } ihdg_time_scheme;
+
 /* Arithmetic of the sweep.  FP64: every step in float64.  MIXED_*: defect correction --
  * float64 outer sweeps form the residual r = S(E) - E and its float64 norm; inner sweeps on
  * the correction equation e = r + G(e) run in float32 (CUDA cores), TF32 or BF16 (tcgen05
@@ -114,6 +124,9 @@ typedef struct {
                            tau = tau_gamma (p+1)(p+2)/h on both sides of every face, h the
                            element size along the face normal, which the paper takes for the
                            diffusion-dominated limit (Section 4.2); other PDEs: must be 0 */
+  ihdg_time_scheme time_scheme;   /* shallow water: BACKWARD_EULER (0, the default) or
+                                     CRANK_NICOLSON; other PDEs: must be 0 (else
+                                     IHDG_ERR_UNSUPPORTED) */
 } ihdg_coeffs;
 
 typedef struct {
@@ -264,10 +277,11 @@ ihdg_status ihdg_autotune(ihdg_ctx* ctx, const ihdg_mesh* mesh, const ihdg_coeff
                           ihdg_options* tuned, double* best_ms);
 
 /* Linearized shallow water (Section 3, Eq. localSolverDD), walls on the whole boundary:
- * advance q (in/out, [n_el][3][(p+1)^2] volume layout (phi, u, v), host) by nsteps
- * backward-Euler steps of coeffs->dt; each step runs the iHDG iteration warm-started from
- * the previous step.  iters_per_step (host, length nsteps) may be NULL.  res reports the
- * totals and the status of the worst step. */
+ * advance q (in/out, [n_el][3][(p+1)^2] volume layout (phi, u, v), host) by nsteps steps of
+ * coeffs->dt with coeffs->time_scheme (backward Euler, or the Crank-Nicolson rule of the
+ * paper's shallow-water experiments, Section 5); each step runs the iHDG iteration
+ * warm-started from the previous step.  iters_per_step (host, length nsteps) may be NULL.
+ * res reports the totals and the status of the worst step. */
 ihdg_status ihdg_swe_steps(ihdg_ctx* ctx, const ihdg_mesh* mesh, const ihdg_coeffs* coeffs,
                            double* q_inout, int nsteps, const ihdg_options* opts,
                            int* iters_per_step, ihdg_result* res);

@@ -1056,9 +1056,18 @@ ihdg_status ihdg_swe_steps_device(ihdg_ctx* ctx, const ihdg_mesh* mesh, const ih
   ihdg_status st = check_opts(ctx, o);
   if (st != IHDG_OK) return st;
   CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  // Crank-Nicolson: the backward-Euler half step (operators at dt/2) to tolerance tol/2, then
+  // q^{m+1} = 2 q^{m+1/2} - q^m (see ihdg_time_scheme)
+  const bool cn = co->time_scheme == IHDG_CRANK_NICOLSON;
+  ihdg_coeffs cs = *co;
+  if (cn) {
+    cs.dt = 0.5 * co->dt;
+    cs.time_scheme = IHDG_BACKWARD_EULER;
+    o.tol = 0.5 * o.tol;
+  }
   Plan* pl = nullptr;
   double setup_ms = 0.0;
-  st = get_plan(ctx, *mesh, *co, pl, &setup_ms);
+  st = get_plan(ctx, *mesh, cs, pl, &setup_ms);
   if (st != IHDG_OK) return st;
   Layout L = layout_for(pl->g, o, true);
   if (ws_bytes < L.total) return fail(ctx, IHDG_ERR_NOMEM, "workspace smaller than ihdg_workspace_bytes()");
@@ -1073,7 +1082,13 @@ ihdg_status ihdg_swe_steps_device(ihdg_ctx* ctx, const ihdg_mesh* mesh, const ih
     ihdg_result r{};
     st = device_iterate(ctx, pl, o, src, d_q, qn, nullptr, ws, L, s, &r);
     if (st != IHDG_OK) return st;
-    CK(cudaMemcpyAsync(d_q, qn, qbytes, cudaMemcpyDeviceToDevice, s), "copy q");
+    if (cn) {
+      CK(launch_cn_extrapolate(d_q, qn, (long long)pl->g.nel * pl->g.nvol, s), "Crank-Nicolson kernel");
+      r.kernel_launches += 1;
+      r.residual *= 2.0;   // the Crank-Nicolson iterate's increment
+    } else {
+      CK(cudaMemcpyAsync(d_q, qn, qbytes, cudaMemcpyDeviceToDevice, s), "copy q");
+    }
     if (iters_per_step) iters_per_step[m] = r.iterations;
     tot.iterations += r.iterations;
     tot.fp64_sweeps += r.fp64_sweeps;

@@ -605,6 +605,21 @@ cudaError_t launch_trace_out(const LaunchArgs& a, const double* E, const double*
                                                 alpha[0], alpha[1], alpha[2], nface, tr);
   return cudaGetLastError();
 }
+// Crank-Nicolson step of a linear autonomous system from its backward-Euler half step:
+// q^{m+1} = 2 q^{m+1/2} - q^m, elementwise (grid-stride, coalesced float64).
+__global__ void __launch_bounds__(256) k_cn_extrapolate(double* __restrict__ q, const double* __restrict__ qh, long long n) {
+  for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < n; i += (long long)gridDim.x * 256)
+    q[i] = 2.0 * qh[i] - q[i];
+}
+
+cudaError_t launch_cn_extrapolate(double* q, const double* qh, long long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  k_cn_extrapolate<<<(unsigned)blocks, 256, 0, s>>>(q, qh, n);
+  return cudaGetLastError();
+}
+
 // two halves (ping-pong) of one slot per block; at least 512 blocks, so that the persistent
 // kernels may size their grids by SM count on small meshes too
 int partials_needed(long long nel) {

@@ -79,6 +79,8 @@ cudaError_t launch_sweep64(const LaunchArgs& a, int count);
 // not co-resident (then launch_sweep64 in batches)
 cudaError_t launch_sweep64_persist(const LaunchArgs& a);
 cudaError_t launch_reconstruct(const LaunchArgs& a, const double* E, const double* E2, double* u);
+// q <- 2 qh - q over n values (the Crank-Nicolson step from the backward-Euler half step qh)
+cudaError_t launch_cn_extrapolate(double* q, const double* qh, long long n, cudaStream_t s);
 cudaError_t launch_trace_out(const LaunchArgs& a, const double* E, const double* E2, const double* u, int pde,
                              const double* beta, const double* alpha, long long nface, double* tr);
 

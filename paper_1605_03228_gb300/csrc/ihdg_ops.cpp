@@ -216,6 +216,11 @@ ihdg_status validate(const ihdg_mesh& m, const ihdg_coeffs* co, std::string& err
   if (co->flux == IHDG_FLUX_NPC && co->pde != IHDG_TRANSPORT) { err = "the NPC flux is defined for transport only"; return IHDG_ERR_UNSUPPORTED; }
   if (!(co->tau_gamma >= 0.0) || !std::isfinite(co->tau_gamma)) { err = "coeffs.tau_gamma must be finite and >= 0"; return IHDG_ERR_INVALID; }
   if (co->tau_gamma > 0.0 && co->pde != IHDG_CONVDIFF) { err = "the mesh-dependent stabilisation is for convection-diffusion"; return IHDG_ERR_UNSUPPORTED; }
+  if (co->time_scheme != IHDG_BACKWARD_EULER && co->time_scheme != IHDG_CRANK_NICOLSON) {
+    err = "coeffs.time_scheme must be IHDG_BACKWARD_EULER or IHDG_CRANK_NICOLSON";
+    return IHDG_ERR_INVALID;
+  }
+  if (co->time_scheme != IHDG_BACKWARD_EULER && co->pde != IHDG_SWE) { err = "a time rule applies to shallow water only"; return IHDG_ERR_UNSUPPORTED; }
   if (co->pde == IHDG_CONVDIFF) {
     if (!(co->kappa > 0) || !std::isfinite(co->kappa)) { err = "coeffs.kappa must be > 0"; return IHDG_ERR_INVALID; }
     if (!(co->nu >= 0) || !std::isfinite(co->nu)) { err = "coeffs.nu must be >= 0"; return IHDG_ERR_INVALID; }

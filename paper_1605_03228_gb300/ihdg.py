@@ -18,6 +18,7 @@ STATUS_NAMES = {0: "OK", 1: "ERR_INVALID", 2: "ERR_NOMEM", 3: "ERR_CUDA", 4: "NO
 TRANSPORT, CONVDIFF, SWE = 0, 1, 2
 FLUX_UPWIND, FLUX_NPC = 0, 1
 KERNEL_AUTO, KERNEL_TENSOR_CORES, KERNEL_CUDA_CORES, KERNEL_GLOBAL = 0, 1, 2, 3
+BACKWARD_EULER, CRANK_NICOLSON = 0, 1
 # Result.inner_kernel_used: the kernel that ran a mixed solve's inner sweeps
 INNER_KERNEL_NAMES = {0: None, 1: "k_inner_tc", 2: "k_inner_blk", 3: "k_inner_reg", 4: "k_inner_tile",
                       5: "k_inner_persist"}
@@ -33,7 +34,7 @@ class Coeffs(ctypes.Structure):
     _fields_ = [("pde", ctypes.c_int), ("beta", ctypes.c_double * 3), ("kappa", ctypes.c_double),
                 ("nu", ctypes.c_double), ("Phi", ctypes.c_double), ("coriolis_f", ctypes.c_double),
                 ("friction", ctypes.c_double), ("dt", ctypes.c_double), ("flux", ctypes.c_int),
-                ("tau_gamma", ctypes.c_double)]
+                ("tau_gamma", ctypes.c_double), ("time_scheme", ctypes.c_int)]
 
 
 class Options(ctypes.Structure):
@@ -146,9 +147,10 @@ def make_mesh(dim, n, p, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0)):
 
 
 def make_coeffs(pde, beta=(0.0, 0.0, 0.0), kappa=0.0, nu=0.0, Phi=0.0, coriolis_f=0.0, friction=0.0, dt=0.0,
-                flux=0, tau_gamma=0.0):
+                flux=0, tau_gamma=0.0, time_scheme=0):
     c = Coeffs()
     c.pde = pde
+    c.time_scheme = time_scheme
     c.flux = flux
     c.tau_gamma = tau_gamma
     for a in range(3):

@@ -88,6 +88,12 @@ def test_invalid_arguments_rejected():
     assert L.ihdg_problem_sizes(ctypes.byref(m2), ctypes.byref(tau_tr), ctypes.byref(s)) == ihdg.ERR_UNSUPPORTED
     npc_cd = ihdg.make_coeffs(ihdg.CONVDIFF, beta=(1, 1), kappa=0.1, flux=ihdg.FLUX_NPC)
     assert L.ihdg_problem_sizes(ctypes.byref(m2), ctypes.byref(npc_cd), ctypes.byref(s)) == ihdg.ERR_UNSUPPORTED
+    cn_tr = ihdg.make_coeffs(ihdg.TRANSPORT, beta=(1, 1), time_scheme=ihdg.CRANK_NICOLSON)
+    assert L.ihdg_problem_sizes(ctypes.byref(m2), ctypes.byref(cn_tr), ctypes.byref(s)) == ihdg.ERR_UNSUPPORTED
+    bad_ts = ihdg.make_coeffs(ihdg.SWE, Phi=1.0, dt=0.01, time_scheme=7)
+    assert L.ihdg_problem_sizes(ctypes.byref(m2), ctypes.byref(bad_ts), ctypes.byref(s)) == ihdg.ERR_INVALID
+    cn_swe = ihdg.make_coeffs(ihdg.SWE, Phi=1.0, dt=0.01, time_scheme=ihdg.CRANK_NICOLSON)
+    assert L.ihdg_problem_sizes(ctypes.byref(m2), ctypes.byref(cn_swe), ctypes.byref(s)) == ihdg.OK
     m = ihdg.make_mesh(2, (2, 2), 5)
     c = ihdg.make_coeffs(ihdg.TRANSPORT, beta=(1, 1))
     assert L.ihdg_problem_sizes(ctypes.byref(m), ctypes.byref(c), ctypes.byref(s)) == ihdg.ERR_UNSUPPORTED
