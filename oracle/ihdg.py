@@ -289,6 +289,9 @@ class Transport(Problem):
           -(u, div(beta v))_K + <beta.n u + |beta.n|(u - u_hat^k), v>_dK = (f, v)_K
       Weighted trace (transportLocale): |beta.n| u_hat = {{beta.n u}} + |beta.n| {{u}},
       i.e. the upwind value; g on the inflow boundary.
+    nu >= 0 adds the L2 term nu (u^{k+1}, v)_K to the local equation: the term a backward-
+      Euler step of the time-dependent equation adds with nu = 1/dt (the remark on
+      time-dependent transport after Theorem 1), the step's u^m/dt going into the forcing.
     NPC flux (flux="npc", Section 3, Eq. Ntaub):
       Local equation -(u, div(beta v))_K + <beta.n u + tau (u - u_hat^k), v>_dK = (f, v)_K
       with tau = |beta.n| (1 + sgn(beta.n))/2 - beta.n: 0 on outflow faces, |beta.n| on
@@ -299,11 +302,12 @@ class Transport(Problem):
 
     nc = 1
 
-    def __init__(self, disc, beta, flux="upwind"):
+    def __init__(self, disc, beta, flux="upwind", nu=0.0):
         self.beta = np.asarray(beta, dtype=np.float64)[: disc.d]
         if flux not in ("upwind", "npc"):
             raise ValueError("flux must be 'upwind' or 'npc'")
         self.flux = flux
+        self.nu = float(nu)
         super().__init__(disc)
 
     def bn(self, f):
@@ -325,7 +329,7 @@ class Transport(Problem):
         A = -sum(self.beta[a] * disc.K[a] for a in range(disc.d))
         for f in range(2 * disc.d):
             A = A + (self.bn(f) + self.tau(f)) * disc.Mf[f]
-        return A
+        return A + self.nu * disc.M
 
     def volume_rhs(self, f_qp, U_prev=None):
         return self.disc.load(f_qp)
