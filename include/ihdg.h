@@ -112,7 +112,11 @@ typedef struct {
   ihdg_pde pde;
   double beta[3];       /* transport / convection-diffusion velocity (constant) */
   double kappa;         /* convection-diffusion diffusivity, > 0 */
-  double nu;            /* convection-diffusion reaction, >= 0 */
+  double nu;            /* reaction nu (u, v)_K in the local equation, >= 0 (transport and
+                           convection-diffusion).  A backward-Euler step of the time-dependent
+                           equation is a solve with nu + 1/dt and the forcing f + u^m/dt, warm-
+                           started from u^m (opts.u0): the remarks on time-dependent transport
+                           (after Theorem 1) and convection-diffusion (Section 4.1) */
   double Phi;           /* shallow water mean geopotential, > 0 */
   double coriolis_f;    /* shallow water Coriolis parameter (constant) */
   double friction;      /* shallow water bottom friction gamma >= 0 */
@@ -135,7 +139,9 @@ typedef struct {
   ihdg_precision prec;
   double diverge_factor;   /* DIVERGED when residual > factor * its running minimum;
                               <= 0 disables the check (default 1e6 when == 0) */
-  int inner_max;           /* mixed: inner sweeps per outer step cap (0 = automatic) */
+  int inner_max;           /* mixed: inner sweeps per outer step cap (0 = automatic: 400;
+                              32 for shallow-water steps, whose warm-started inner loops
+                              stall above their stopping ratio) */
   double inner_rtol;       /* mixed: inner stop when step norm <= inner_rtol * ||r||
                               (0 = auto: 2e-3 float32, 1e-2 tf32, 0.2 bf16, or the autotuned value) */
   const double* u0;        /* optional initial guess, volume layout (host for ihdg_solve,

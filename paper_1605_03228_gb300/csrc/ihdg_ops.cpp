@@ -235,6 +235,7 @@ ihdg_status validate(const ihdg_mesh& m, const ihdg_coeffs* co, std::string& err
     double s = 0;
     for (int a = 0; a < m.dim; ++a) s += std::fabs(co->beta[a]);
     if (!(s > 0)) { err = "transport needs a nonzero beta"; return IHDG_ERR_INVALID; }
+    if (!(co->nu >= 0) || !std::isfinite(co->nu)) { err = "coeffs.nu must be >= 0"; return IHDG_ERR_INVALID; }
   }
   return IHDG_OK;
 }
@@ -547,6 +548,9 @@ ihdg_status build_ops(const ihdg_mesh& m, const ihdg_coeffs& co, Ops& o, std::st
       else o.face_kind[f] = FK_NONE;
     }
     for (int a = 0; a < d; ++a) add_vol(K[a], 0, 0, -co.beta[a]);       // -(u, beta.grad v)
+    // nu (u, v): a reaction term, or the L2 term 1/dt (u, v) of a backward-Euler step of the
+    // time-dependent equation (the remark on time-dependent transport after Theorem 1)
+    if (co.nu != 0.0) add_vol(M, 0, 0, co.nu);
     for (int f = 0; f < nlf; ++f) {
       double bn = nsign(f) * co.beta[f / 2];
       // stabilisation: upwind |beta.n|; NPC (Eq. Ntaub) |beta.n|(1 + sgn(beta.n))/2 - beta.n,

@@ -128,6 +128,81 @@ def test_transport_npc_fp64(ctx, d, n, p, beta):
     assert rel(tr, oracle_trace_at_nodes(disc, T)) < 1e-10
 
 
+@pytest.mark.parametrize("d,p,beta,prec_name", [(2, 2, (1.0, 0.5), "FP64"), (2, 3, (-0.3, 1.0), "FP64"),
+                                                (3, 2, (0.6, -0.4, 0.7), "FP64"), (2, 3, (1.0, 0.5), "MIXED_FP32")])
+def test_time_dependent_transport_step(ctx, d, p, beta, prec_name):
+    """A backward-Euler step of time-dependent transport through ihdg_solve (the remark after
+    Theorem 1): reaction nu = 1/dt, forcing u^m/dt at the quadrature points, warm start u^m.
+    From a polynomial u^m the exact step Q = P - dt DP + dt^2 D^2 P (D = beta.grad) is in the
+    element space, so the GPU reproduces it to the float64 (or mixed) bar; and on random
+    data it matches the oracle's step and iteration count."""
+    ihdg = ih()
+    dt, n = 0.05, (5, 4, 3)[:d]
+    mesh = ihdg.make_mesh(d, n, p)
+    co = ihdg.make_coeffs(ihdg.TRANSPORT, beta=beta, nu=1.0 / dt)
+    vol, bnd = ihdg.quadrature_points(mesh, co)
+    nodes = ihdg.node_points(mesh, co)
+    b = np.asarray(beta, dtype=float)
+
+    def P(X):
+        v = X[..., 0] ** 2 + 2 * X[..., 0] * X[..., 1] - X[..., 1]
+        return v + X[..., 0] * X[..., 2] if d == 3 else v
+
+    def DP(X):
+        v = b[0] * (2 * X[..., 0] + 2 * X[..., 1]) + b[1] * (2 * X[..., 0] - 1)
+        return v + b[0] * X[..., 2] + b[2] * X[..., 0] if d == 3 else v
+
+    d2 = 2 * b[0] ** 2 + 4 * b[0] * b[1] + (2 * b[0] * b[2] if d == 3 else 0.0)
+    Q = lambda X: P(X) - dt * DP(X) + dt * dt * d2
+    u0 = np.ascontiguousarray(P(nodes))
+    o = ihdg.make_options(1e-12, prec=getattr(ihdg, prec_name), max_iters=4000)
+    o.u0 = u0.ctypes.data
+    u, tr, res = ctx.solve(mesh, co, P(vol) / dt, Q(bnd), o)
+    assert res.status == ihdg.OK, res.as_dict()
+    bar = 1e-10 if prec_name == "FP64" else 1e-6
+    assert rel(u, Q(nodes)) < bar
+    # random data against the oracle's step
+    rng = np.random.default_rng(13)
+    f = rng.standard_normal(vol.shape[:2])
+    g = rng.standard_normal(bnd.shape[:2])
+    u0r = np.ascontiguousarray(rng.standard_normal(u.shape))
+    o.u0 = u0r.ctypes.data
+    o.tol = 1e-10
+    u2, _, res2 = ctx.solve(mesh, co, f, g, o)
+    om = BoxMesh(d, n)
+    disc = Discretisation(om, p)
+    U, T, K, r, st = Transport(disc, b, nu=1.0 / dt).iterate(f, g, 1e-10, U0=u0r.reshape(om.nel, 1, -1))
+    assert res2.status == ihdg.OK and st == STATUS_OK
+    if prec_name == "FP64":
+        assert abs(res2.iterations - K) <= 1
+    assert rel(u2, U.reshape(om.nel, -1)) < (1e-9 if prec_name == "FP64" else 1e-6)
+
+
+def test_time_dependent_convdiff_steps_converge_faster(ctx):
+    """The remark on time-dependent convection-diffusion (Section 4.1): the L2 term 1/dt
+    (reaction nu + 1/dt) makes the iteration converge in fewer sweeps; GPU counts equal the
+    oracle's."""
+    ihdg = ih()
+    n, p = (8, 8), 2
+    mesh = ihdg.make_mesh(2, n, p)
+    om = BoxMesh(2, n)
+    disc = Discretisation(om, p)
+    rng = np.random.default_rng(5)
+    counts = []
+    for nu in (0.0, 8.0, 32.0):
+        co = ihdg.make_coeffs(ihdg.CONVDIFF, beta=(1.0, 1.0), kappa=1e-2, nu=nu)
+        vol, bnd = ihdg.quadrature_points(mesh, co)
+        f = rng.standard_normal(vol.shape[:2])
+        g = np.zeros(bnd.shape[:2])
+        u, _, res = ctx.solve(mesh, co, f, g, ihdg.make_options(1e-10, max_iters=3000))
+        U, T, K, r, st = ConvDiff(disc, np.array([1.0, 1.0]), 1e-2, nu).iterate(f, g, 1e-10, max_iters=3000)
+        assert res.status == ihdg.OK and st == STATUS_OK
+        assert abs(res.iterations - K) <= 1
+        assert rel(u, U.reshape(om.nel, -1)) < 1e-8
+        counts.append(res.iterations)
+    assert counts[0] > counts[1] > counts[2], counts
+
+
 @pytest.mark.parametrize("prec_name", ["MIXED_FP32", "MIXED_BF16"])
 def test_transport_npc_mixed(ctx, prec_name):
     """NPC flux through the mixed-precision path (outer float64, inner low precision)."""
