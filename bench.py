@@ -629,6 +629,8 @@ def run_serving(args, ih, ctx, world, rank, emit=True):
     finally:
         ctx.server_stop()
     lat = np.array([r.latency_ms for r, _ in done])
+    que = np.array([r.queue_ms for r, _ in done])
+    svc = lat - que   # admitted to a slot -> results on the host
     updates = sum(d * r.iterations for r, d in done)
     status = {}
     for r, _ in done:
@@ -643,6 +645,8 @@ def run_serving(args, ih, ctx, world, rank, emit=True):
                        "status_counts": status, "l2": "not flushed: requests stream through the server"},
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "mean": float(lat.mean())},
+            "service_ms": {"p50": float(np.percentile(svc, 50)), "p99": float(np.percentile(svc, 99))},
+            "queue_ms": {"p50": float(np.percentile(que, 50)), "p99": float(np.percentile(que, 99))},
             "requests_per_s": args.requests / wall,
             "e2e": {"value": value, "unit": UNIT, "note": "host buffers in and out through ihdg_submit/ihdg_fetch",
                     "h2d_bytes_per_step": None, "d2h_bytes_per_step": None},
@@ -651,7 +655,8 @@ def run_serving(args, ih, ctx, world, rank, emit=True):
     if not emit:
         return {"workload": line["config"]["workload"], "requests": args.requests, "slots": args.slots,
                 "offered_load": args.load, "capacity_req_per_s": cap, "requests_per_s": line["requests_per_s"],
-                "latency_ms": line["latency_ms"], "status_counts": status,
+                "latency_ms": line["latency_ms"], "service_ms": line["service_ms"], "queue_ms": line["queue_ms"],
+                "status_counts": status,
                 "element_dof_updates_per_s": value}
     if rank == 0:
         print(json.dumps(line), flush=True)

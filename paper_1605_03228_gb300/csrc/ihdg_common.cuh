@@ -29,6 +29,16 @@ constexpr int BS = 128;   // threads per block of the element kernels
 constexpr int PBS = 256;  // threads per block of the persistent kernels
 
 __device__ __forceinline__ void coords(const DevGeo& g, long long K, int* c) {
+  if (g.nel <= 0xffffffffLL && K <= 0xffffffffLL) {
+    // every mesh of up to 2^32 elements: 32-bit unsigned division (a 64-bit division is a
+    // long instruction sequence, and the sweeps take coordinates per element)
+    const unsigned k = (unsigned)K, n0 = (unsigned)g.n[0], n1 = (unsigned)g.n[1];
+    const unsigned t = k / n0, t2 = t / n1;
+    c[0] = (int)(k - t * n0);
+    c[1] = (int)(t - t2 * n1);
+    c[2] = (int)t2;
+    return;
+  }
   c[0] = (int)(K % g.n[0]);
   long long t = K / g.n[0];
   c[1] = (int)(t % g.n[1]);

@@ -315,6 +315,13 @@ __global__ void __launch_bounds__(128 * TcShape<NF, NLF, PER_AXIS, MODE>::G, 1)
     }
     float acc = 0.f;
     for (int tile = tile0; tile < ntiles; tile += tstride) {
+      // the epilogue's residual loads, issued with this tile's gathers (one round trip)
+      const int K = tile * 128 + gt;
+      const bool valid = K < nel;
+      RAW rr[NEXP];
+      const RAW* rb = reinterpret_cast<const RAW*>(rlp);
+#pragma unroll
+      for (int e = 0; e < NEXP; ++e) rr[e] = rb[e * ld + (valid ? K : 0)];
       if (tile != tile0) gather_pack(tile, ec);
       tc::fence_proxy_async();
       tc::fence_before();
@@ -341,13 +348,6 @@ __global__ void __launch_bounds__(128 * TcShape<NF, NLF, PER_AXIS, MODE>::G, 1)
         tc::commit(mbar);
       }
       __syncwarp();
-      // the epilogue's residual loads while the MMAs run
-      const int K = tile * 128 + gt;
-      const bool valid = K < nel;
-      RAW rr[NEXP];
-      const RAW* rb = reinterpret_cast<const RAW*>(rlp);
-#pragma unroll
-      for (int e = 0; e < NEXP; ++e) rr[e] = rb[e * ld + (valid ? K : 0)];
       // the group agrees on the outcome of the (bounded) wait, so all its threads take one path
       const int ok = tc::mbar_wait(mbar, phase) ? 1 : 0;
       const int bad = tc::group_or(bar_id, !ok);
