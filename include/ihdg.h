@@ -177,7 +177,8 @@ typedef struct {
   int inner_kernel_used;   /* mixed: the kernel that ran the inner sweeps (0 none or not
                               recorded, 1 tensor cores k_inner_tc, 2 temporally blocked
                               k_inner_blk, 3 register-resident k_inner_reg, 4 shared-memory
-                              tile k_inner_tile, 5 global state k_inner_persist) */
+                              tile k_inner_tile, 5 global state k_inner_persist, 6 tensor
+                              cores with TMA-staged gathers k_inner_tcs) */
 } ihdg_result;
 
 typedef struct {

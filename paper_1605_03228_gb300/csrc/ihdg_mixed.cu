@@ -26,12 +26,20 @@ size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 MixedLayout mixed_layout(const DevGeo& g, int prec) {
   MixedLayout L{};
   L.lp_bytes = prec == IHDG_MIXED_BF16 ? 2 : 4;
+  // guard band of the correction arrays: the staged tensor-core kernel copies windows of 136
+  // values starting up to one layer (the largest element-number step) plus 8 below an
+  // element's number, and as far above it; the guards keep those windows inside the region
+  // (what they read there lands only in masked rows)
+  long long step = 1;
+  for (int a = 0; a < g.dim; ++a) step = g.stride[a] > step ? g.stride[a] : step;
+  L.pad = (step + 8 + 7) / 8 * 8 + 136;
   size_t one = a256((size_t)g.n_exp * g.ld * L.lp_bytes);
+  size_t onep = a256(((size_t)g.n_exp * g.ld + 2 * (size_t)L.pad) * L.lp_bytes);
   L.rlp = 0;
   L.e0 = one;
-  L.e1 = 2 * one;
-  L.lt = 3 * one;
-  L.total = 3 * one + MIXED_LT_BYTES;   // + the register kernel's or the tensor-core kernel's operator
+  L.e1 = one + onep;
+  L.lt = one + 2 * onep;
+  L.total = one + 2 * onep + MIXED_LT_BYTES;   // + the register kernel's or the tensor-core kernel's operator
   return L;
 }
 
@@ -40,8 +48,9 @@ void mixed_bind(MixedArgs& m, char* region, const MixedLayout& L, int prec) {
   m.E64 = m.base.ring + m.base.ring_stride;   // ring slots 1 and 2
   m.r64 = m.base.ring;                        // ring slot 0 (E^0 is dead once the outer loop runs)
   m.rlp = region + L.rlp;
-  m.e[0] = region + L.e0;
-  m.e[1] = region + L.e1;
+  m.e[0] = region + L.e0 + (size_t)L.pad * L.lp_bytes;
+  m.e[1] = region + L.e1 + (size_t)L.pad * L.lp_bytes;
+  m.e_pad = L.pad;
   m.dLT = reinterpret_cast<float*>(region + L.lt);
 }
 

@@ -19,6 +19,7 @@ constexpr size_t MIXED_LT_BYTES = 16384;   // operator scratch in the mixed work
 struct MixedLayout {
   size_t rlp, e0, e1, lt, total;   // byte offsets inside the mixed region
   int lp_bytes;                // bytes per low-precision value
+  long long pad = 0;           // guard values before and after each correction array
 };
 
 struct MixedArgs {
@@ -39,6 +40,8 @@ struct MixedArgs {
   int blk_h = 0;            // >= 2: 2D CUDA-core inner sweeps temporally blocked, this many per barrier
   const float* LE32h = nullptr;  // host copy of the float32 operator (n_exp x n_in)
   int ran = 0;              // inner kernel of the last inner launch (ihdg_result.inner_kernel_used codes)
+  long long e_pad = 0;      // guard values below e[0], e[1] and above their last slot
+  int tc_staged = 0;        // the last tensor-core launch ran the staged-gather variant
 };
 
 // One launch of the mixed loop's kernel `which` (0 outer float64 sweep, 1 residual check + first

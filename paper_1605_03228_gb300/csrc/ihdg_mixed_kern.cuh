@@ -1163,7 +1163,7 @@ struct MixedRunner {
             ce = a.g.per_axis ? launch_tc<NF, NLF, true, TC_TF32X4>(m, rl, e0, e1)
                               : launch_tc<NF, NLF, false, TC_TF32X4>(m, rl, e0, e1);
           }
-          if (ce != cudaErrorNotSupported) return m.ran = 1, ce;
+          if (ce != cudaErrorNotSupported) return m.ran = m.tc_staged ? 6 : 1, ce;
           // shapes the tensor-core kernel does not take (n_in > 64 or n_exp > 32) fall through
           // to the CUDA-core kernels in full float32
         }

@@ -3,10 +3,12 @@
 // in parallel.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <type_traits>
 #include <vector>
@@ -386,9 +388,344 @@ __global__ void __launch_bounds__(128 * TcShape<NF, NLF, PER_AXIS, MODE>::G, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem0), "r"(S::TCOLS) : "memory");
 }
 
+// ---------------------------------------------------------------------------------------
+// Staged variant for the per-axis export layout (transport) with bf16 storage: the traces of
+// a tile of 128 consecutive elements are runs of consecutive element numbers in each export
+// slot -- the element's own exports at K on outflow faces, the upstream neighbour's at
+// K -+ (element-number step of the axis) on inflow faces -- so one thread of the group copies
+// them global -> shared memory with tiled TMA tensor copies (cp.async.bulk.tensor.2d over the
+// correction array seen as a [slots x ld] bf16 tensor, completion counted in bytes on a
+// per-stage mbarrier): one box of all slots' own runs (128 values each), and per inflow axis
+// one box of its slots' windows of 136 values from the 8-aligned number at or below the run's
+// start (a tensor copy's inner coordinate must be a multiple of 8 bf16 values; the run begins
+// delta = start mod 8 values into the window; coordinates outside the tensor read zeros).
+// Two stages per group: while a tile is packed, multiplied and written back, the next tile's
+// copies are in flight, and no register holds a gathered value before it is packed.  The rest
+// (A in the core-matrix layout, MMA, epilogue, lagged decision, bounded waits) is
+// k_inner_tc's.
+template <int NF, int NLF>
+struct TcsShape {
+  using S = TcShape<NF, NLF, true, TC_BF16>;
+  static constexpr int D = NLF / 2;
+  static constexpr int NEXP = S::NEXP;                // D * NF slots
+  static constexpr int NBW = 136;                     // values per inflow window
+  static constexpr int OWNB = NEXP * 256;             // own runs: 128 bf16 per slot
+  static constexpr int WB = (NF * NBW * 2 + 127) / 128 * 128;   // one axis's inflow windows
+  static constexpr int STAGE = OWNB + D * WB;         // a multiple of 128 (tensor-copy alignment)
+  static constexpr int GROUPB = S::ABYTES + 2 * STAGE;
+  static constexpr int FIT = (227 * 1024 - 4096 - S::BBYTES) / GROUPB;
+  static constexpr int G = FIT >= 4 ? 4 : (FIT < 1 ? 1 : FIT);
+  static constexpr int SMEM = S::BBYTES + G * GROUPB;
+  static constexpr uint32_t TCOLS = G * 32 <= 32 ? 32 : G * 32 <= 64 ? 64 : G * 32 <= 128 ? 128 : 256;
+  static constexpr bool OK = S::OK && FIT >= 1 && NLF % 2 == 0;
+};
+
+namespace tc {
+__device__ __forceinline__ void expect_bytes(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(dst), "l"(src), "r"(bytes), "r"(mbar) : "memory");
+}
+// tiled tensor copy of a 2D box (x: element number, y: slot) global -> shared memory;
+// coordinates outside the tensor read zeros
+__device__ __forceinline__ void tensor_g2s(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t mbar) {
+  asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+               ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mbar) : "memory");
+}
+// values other SMs stored with ordinary stores (made visible by the grid barrier) become
+// visible to this thread's bulk copies
+__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+}  // namespace tc
+
+template <int NF, int NLF>
+__global__ void __launch_bounds__(128 * TcsShape<NF, NLF>::G, 1)
+    k_inner_tcs(const DevGeo g, const __nv_bfloat16* __restrict__ rlp, __nv_bfloat16* e0, __nv_bfloat16* e1,
+                Ctrl* ctrl, double* partials, const unsigned char* __restrict__ Bg,
+                const __grid_constant__ CUtensorMap own0, const __grid_constant__ CUtensorMap own1,
+                const __grid_constant__ CUtensorMap win0m, const __grid_constant__ CUtensorMap win1m) {
+  using TL = __nv_bfloat16;
+  using RAW = unsigned short;
+  using S = TcShape<NF, NLF, true, TC_BF16>;
+  using Z = TcsShape<NF, NLF>;
+  constexpr int G = Z::G, NT = 128 * G, NIN = S::NIN, NEXP = S::NEXP, KP = S::KP, NP = S::NP, ROWB = S::ROWB;
+  constexpr int D = Z::D, KSTEP = S::KSTEP;
+  static_assert(Z::OK, "tile shape");
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  __shared__ __align__(8) unsigned long long s_mbar[G];        // MMA completion, per group
+  __shared__ __align__(8) unsigned long long s_stage[2 * G];   // copy completion, per group and stage
+  __shared__ uint32_t s_tmem;
+  __shared__ float wsum[NT / 32];
+  __shared__ int s_to, s_stop;
+  if (ctrl_done(ctrl) || *(volatile const int*)&ctrl->inner_done) return;
+  const int jj0 = *(volatile const int*)&ctrl->inner_iter;
+  const int iter0 = *(volatile const int*)&ctrl->iter;
+  const int lowp0 = *(volatile const int*)&ctrl->lowp_sweeps;
+  const int max_iters = ctrl->max_iters, inner_max = ctrl->inner_max;
+  const float limf = (float)(ctrl->inner_rtol * ctrl->rnorm);
+  const int tid = threadIdx.x, gr = tid >> 7, gt = tid & 127, wq = (tid >> 5) & 3;
+  unsigned char* sB = tc_smem;
+  unsigned char* sA = tc_smem + S::BBYTES + gr * Z::GROUPB;
+  unsigned char* sStage = sA + S::ABYTES;                       // two stages of Z::STAGE bytes
+  if (tid < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(&s_tmem)),
+                 "r"(Z::TCOLS) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid < 3 * G) {
+    const uint32_t mb = tid < G ? tc::smem_u32(&s_mbar[tid]) : tc::smem_u32(&s_stage[tid - G]);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(Bg);
+    uint4* dst = reinterpret_cast<uint4*>(sB);
+    for (int i = tid; i < S::BBYTES / 16; i += NT) dst[i] = src[i];
+  }
+  tc::fence_proxy_async();
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem0 = s_tmem;
+  const uint32_t tcol = tmem0 + (uint32_t)(gr * 32);
+  const uint32_t tld = tcol + ((uint32_t)(wq * 32) << 16);
+  const uint32_t mbar = tc::smem_u32(&s_mbar[gr]);
+  const uint32_t smb[2] = {tc::smem_u32(&s_stage[2 * gr]), tc::smem_u32(&s_stage[2 * gr + 1])};
+  const uint32_t aaddr = tc::smem_u32(sA), baddr = tc::smem_u32(sB);
+  const uint32_t stage_addr = tc::smem_u32(sStage);
+  constexpr uint32_t IDESC = tc::idesc_bf16(128, NP);
+  const int bar_id = 1 + gr;
+  uint32_t phase = 0, sphase[2] = {0u, 0u};
+  int pending[2] = {0, 0};
+  const int ld = (int)g.ld, nel = (int)g.nel;
+  const int ntiles = (nel + 127) / 128;
+  const int tile0 = blockIdx.x * G + gr, tstride = gridDim.x * G;
+  unsigned* count = &ctrl->bar_count;
+  float* partf = reinterpret_cast<float*>(partials);
+  int failed = 0;
+  // per axis: which face takes the element's own exports (outflow) and where the upstream
+  // neighbour of an inflow face sits (-1: below, +1: above, 0: no inflow face)
+  bool own_ax[D];
+  int up[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    const int k0 = g.kind[2 * a], k1 = g.kind[2 * a + 1];
+    own_ax[a] = k0 == FK_OWN_D || k1 == FK_OWN_D;
+    up[a] = k0 == FK_NBR_D ? -1 : (k1 == FK_NBR_D ? 1 : 0);
+  }
+  // start of the inflow window of axis a for the tile at K0 (8-aligned, at or below the run)
+  auto win0 = [&](int a, int K0) -> int {
+    const int x = K0 + up[a] * (int)g.stride[a];
+    return x - (((x % 8) + 8) % 8);
+  };
+  // one thread of the group: the copies of tile T into stage st -- one box of all slots'
+  // own runs [NEXP x 128] at (K0, 0), and per inflow axis one box of its slots' windows
+  // [NF x 136] at (window start, a NF)
+  auto issue = [&](int T, int st, int parity) {
+    const int K0 = T * 128;
+    const CUtensorMap* mo = parity ? &own1 : &own0;
+    const CUtensorMap* mw = parity ? &win1m : &win0m;
+    uint32_t bytes = (uint32_t)Z::OWNB;
+#pragma unroll
+    for (int a = 0; a < D; ++a) bytes += up[a] != 0 ? (uint32_t)(NF * Z::NBW * 2) : 0u;
+    tc::expect_bytes(smb[st], bytes);
+    const uint32_t base = stage_addr + (uint32_t)(st * Z::STAGE);
+    tc::tensor_g2s(base, mo, K0, 0, smb[st]);
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+      if (up[a] != 0) tc::tensor_g2s(base + Z::OWNB + a * Z::WB, mw, win0(a, K0), a * NF, smb[st]);
+  };
+  auto widen = [](RAW r) -> float { return __uint_as_float((unsigned)r << 16); };
+  for (int s = 0;; ++s) {
+    const TL* __restrict__ ec = ((jj0 + s) & 1) ? e1 : e0;
+    TL* __restrict__ en = ((jj0 + s) & 1) ? e0 : e1;
+    float pv = 0.f;
+    if (s > 0)
+      for (int i = tid; i < (int)gridDim.x; i += NT) pv += __ldcg(partf + ((s - 1) & 1) * gridDim.x + i);
+    // lagged loop decision (as in k_inner_tc)
+    {
+      const float tot = sum_partials<NT>(pv, wsum);
+      if (tid == 0) {
+        const float step = sqrtf(tot);
+        const bool budget = jj0 + s >= inner_max || iter0 + s >= max_iters;
+        const bool stop = budget || (s > 0 && (step <= limf || !(step == step) || isinf(step)));
+        s_stop = stop ? 1 : 0;
+        if (blockIdx.x == 0) {
+          ctrl->inner_iter = jj0 + s;
+          ctrl->iter = iter0 + s;
+          ctrl->lowp_sweeps = lowp0 + s;
+          if (s > 0) ctrl->inner_step = (double)step;
+          if (stop) ctrl->inner_done = 1;
+        }
+      }
+      __syncthreads();
+      if (s_stop) break;
+    }
+    const int par = (jj0 + s) & 1;   // which correction array is current
+    if (gt == 0 && tile0 < ntiles) {
+      tc::fence_proxy_async_global();
+      issue(tile0, 0, par);
+    }
+    pending[0] = tile0 < ntiles;
+    float acc = 0.f;
+    int i = 0;
+    for (int tile = tile0; tile < ntiles; tile += tstride, ++i) {
+      const int st = i & 1;
+      const int K0 = tile * 128, K = K0 + gt;
+      const bool valid = K < nel;
+      // the epilogue's residual, and the next tile's copies into the other stage (its last
+      // readers, the previous tile, passed the group barrier that ended that tile)
+      RAW rr[NEXP];
+      const RAW* rb = reinterpret_cast<const RAW*>(rlp);
+#pragma unroll
+      for (int e = 0; e < NEXP; ++e) rr[e] = rb[e * ld + (valid ? K : 0)];
+      if (tile + tstride < ntiles) {
+        if (gt == 0) issue(tile + tstride, st ^ 1, par);
+        pending[st ^ 1] = 1;
+      }
+      // this tile's copies (bounded wait; the group agrees on the outcome)
+      const int okc = tc::mbar_wait(smb[st], sphase[st]) ? 1 : 0;
+      if (okc) {
+        sphase[st] ^= 1u;
+        pending[st] = 0;
+      }
+      if (tc::group_or(bar_id, !okc)) { failed = 1; break; }
+      // a1: pack row gt of A from the stage (own runs at gt, inflow windows at gt + delta)
+      const RAW* own_s = reinterpret_cast<const RAW*>(sStage + st * Z::STAGE);
+      const RAW* nb_s = reinterpret_cast<const RAW*>(sStage + st * Z::STAGE + Z::OWNB);
+      {
+        int c[3] = {0, 0, 0};
+        if (valid) coords(g, K, c);
+        float t[KP];
+#pragma unroll
+        for (int k = NIN; k < KP; ++k) t[k] = 0.f;
+#pragma unroll
+        for (int f = 0; f < NLF; ++f) {
+          const int a = f >> 1, kind = g.kind[f];
+          const bool bnd = valid && on_bnd(g, c, f);
+          const int dl = up[a] != 0 ? (K0 + up[a] * (int)g.stride[a]) - win0(a, K0) : 0;
+          const bool use_own = valid && kind == FK_OWN_D;
+          const bool use_nb = valid && !bnd && kind == FK_NBR_D;
+          // the face's kind is the same in every thread: one shared load per value
+          if (kind == FK_OWN_D) {
+#pragma unroll
+            for (int q = 0; q < NF; ++q) t[f * NF + q] = use_own ? widen(own_s[(a * NF + q) * 128 + gt]) : 0.f;
+          } else if (kind == FK_NBR_D) {
+#pragma unroll
+            for (int q = 0; q < NF; ++q) t[f * NF + q] = use_nb ? widen(nb_s[a * (Z::WB / 2) + q * Z::NBW + gt + dl]) : 0.f;
+          } else {
+#pragma unroll
+            for (int q = 0; q < NF; ++q) t[f * NF + q] = 0.f;
+          }
+        }
+        unsigned char* row = sA + (gt >> 3) * ROWB + (gt & 7) * 16;
+#pragma unroll
+        for (int kc = 0; kc < KP / 8; ++kc) {
+          __align__(16) __nv_bfloat16 h[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) h[u] = __float2bfloat16_rn(t[kc * 8 + u]);
+          *reinterpret_cast<uint4*>(row + kc * 128) = *reinterpret_cast<uint4*>(h);
+        }
+      }
+      tc::fence_proxy_async();
+      tc::fence_before();
+      tc::group_bar(bar_id);
+      tc::fence_after();
+      // a3: D = A . B^T on the tensor cores
+      if (gt == 0) {
+#pragma unroll
+        for (int kk = 0; kk < KP / KSTEP; ++kk) {
+          const uint64_t ah = tc::sdesc(aaddr + kk * 256, 128, ROWB), bh = tc::sdesc(baddr + kk * 256, 128, ROWB);
+          tc::mma_bf16(tcol, ah, bh, IDESC, kk > 0 ? 1u : 0u);
+        }
+        tc::commit(mbar);
+      }
+      __syncwarp();
+      const int ok = tc::mbar_wait(mbar, phase) ? 1 : 0;
+      const int bad = tc::group_or(bar_id, !ok);
+      phase ^= 1u;
+      if (bad) { failed = 1; break; }
+      tc::fence_after();
+      // a4: e_{j+1} = r + D; the step norm against the current exports in the stage
+      float d[32];
+      tc::ld32(tld, d);
+      if (valid) {
+#pragma unroll
+        for (int e = 0; e < NEXP; ++e) {
+          if ((g.live >> e) & 1ull) {
+            const TL nv = from_f<TL>(widen(rr[e]) + d[e]);
+            const float dl = to_f(nv) - widen(own_s[e * 128 + gt]);
+            acc = fmaf(dl, dl, acc);
+            en[e * ld + K] = nv;
+          }
+        }
+      }
+      // every read of this stage and of A is done before either is written again
+      tc::fence_proxy_async();
+      tc::group_bar(bar_id);
+    }
+    if (__syncthreads_or(failed)) {
+      if (tid == 0) atomicExch(&ctrl->timeout, 1);
+      break;
+    }
+    const float blk = sum_partials<NT>(acc, wsum);
+    arrive_wait(partf + (s & 1) * gridDim.x, count, (unsigned)(s + 1), blk, ctrl, &s_to);
+    if (s_to) break;
+  }
+  // copies still in flight (only after an expired wait) land before the block exits; an
+  // expired MMA wait is waited for once more; then tensor memory is released
+  for (int st = 0; st < 2; ++st)
+    if (pending[st]) tc::mbar_wait(smb[st], sphase[st]);
+  if (failed) tc::mbar_wait(mbar, phase ^ 1u);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  if (tid < 32)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem0), "r"(Z::TCOLS) : "memory");
+}
+
 // Launch the tensor-core inner kernel.  B = L_E (and its low part) in the core-matrix layout
 // is built on the host and copied to the workspace once per solve.
 }  // namespace
+
+// Tensor maps of the staged tensor-core kernel over the correction arrays e0 and e1, each seen
+// as a bf16 tensor [nexp slots][ld values] (row stride ld * 2 bytes): boxes [nexp x 128] of
+// the own runs and [nf x nbw] of one axis's inflow windows, no swizzle, zeros outside.  The
+// encoder is the driver's cuTensorMapEncodeTiled, reached through the runtime's entry-point
+// query (no link to the driver library).  False when it is unavailable or refuses a map.
+inline bool encode_tcs_maps(CUtensorMap* maps, void* e0, void* e1, long long ld, int nexp, int nf, int nbw) {
+  using Enc = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*, const cuuint64_t*,
+                           const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                           CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static Enc enc = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      enc = reinterpret_cast<Enc>(fn);
+    tried = true;
+  }
+  if (!enc || nexp > 256 || nf > 256) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)nexp};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  const cuuint32_t box_own[2] = {128u, (cuuint32_t)nexp}, box_win[2] = {(cuuint32_t)nbw, (cuuint32_t)nf};
+  const cuuint32_t es[2] = {1u, 1u};
+  void* bases[2] = {e0, e1};
+  for (int i = 0; i < 2; ++i) {
+    if (enc(&maps[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, bases[i], dims, strides, box_own, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+    if (enc(&maps[2 + i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, bases[i], dims, strides, box_win, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  return true;
+}
 
 // host twin of tc::rna_tf32: round a finite float32 to 10 mantissa bits, ties away from zero
 inline float rna_tf32_host(float x) {
@@ -462,6 +799,43 @@ cudaError_t launch_tc(MixedArgs& m, void* rlv, void* e0v, void* e1v) {
     double* pp = a.partials;
     const unsigned char* bp = reinterpret_cast<const unsigned char*>(m.dLT);
     void* args[] = {&gg, &rlc, &e0, &e1, &ct, &pp, &bp};
+    m.tc_staged = 0;
+    if constexpr (MODE == TC_BF16 && PER_AXIS) {
+      // the staged variant when the correction arrays carry guard bands wide enough for its
+      // windows (IHDG_TC_STAGED=0 keeps the register-gather kernel)
+      using Z = TcsShape<NF, NLF>;
+      long long step = 1;
+      for (int ax = 0; ax < a.g.dim; ++ax) step = a.g.stride[ax] > step ? a.g.stride[ax] : step;
+      const char* env = std::getenv("IHDG_TC_STAGED");
+      const bool want = !(env && std::strcmp(env, "0") == 0);
+      if constexpr (Z::OK) {
+        CUtensorMap maps[4];
+        const bool have_maps = want && encode_tcs_maps(maps, e0, e1, a.g.ld, Z::NEXP, NF, Z::NBW);
+        if (have_maps && m.e_pad >= step + 8 + Z::NBW) {
+          auto ks = k_inner_tcs<NF, NLF>;
+          e = cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, Z::SMEM);
+          if (e != cudaSuccess) return e;
+          int pers = 0;
+          e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pers, ks, 128 * Z::G, Z::SMEM);
+          if (e != cudaSuccess) return e;
+          if (pers > (int)(512 / Z::TCOLS)) pers = (int)(512 / Z::TCOLS);
+          if (pers >= 1) {
+            long long gs = (long long)pers * sms;
+            const long long needs = (ntiles + Z::G - 1) / Z::G;
+            if (gs > needs) gs = needs;
+            if (gs > m.max_grid) gs = m.max_grid;
+            if (gs <= m.slots / 2) {
+              void* args_s[] = {&gg, &rlc, &e0, &e1, &ct, &pp, &bp, &maps[0], &maps[1], &maps[2], &maps[3]};
+              e = cudaLaunchCooperativeKernel((const void*)ks, dim3((unsigned)gs), dim3(128 * Z::G), args_s, Z::SMEM,
+                                              a.stream);
+              if (e != cudaSuccess) return e;
+              m.tc_staged = 1;
+              return cudaGetLastError();
+            }
+          }
+        }
+      }
+    }
     e = cudaLaunchCooperativeKernel((const void*)k, dim3((unsigned)grid), dim3(128 * G), args, S::SMEM, a.stream);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();

@@ -21,7 +21,7 @@ KERNEL_AUTO, KERNEL_TENSOR_CORES, KERNEL_CUDA_CORES, KERNEL_GLOBAL = 0, 1, 2, 3
 BACKWARD_EULER, CRANK_NICOLSON = 0, 1
 # Result.inner_kernel_used: the kernel that ran a mixed solve's inner sweeps
 INNER_KERNEL_NAMES = {0: None, 1: "k_inner_tc", 2: "k_inner_blk", 3: "k_inner_reg", 4: "k_inner_tile",
-                      5: "k_inner_persist"}
+                      5: "k_inner_persist", 6: "k_inner_tcs"}
 FP64, MIXED_FP32, MIXED_TF32, MIXED_BF16 = 0, 1, 2, 3
 
 

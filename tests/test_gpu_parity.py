@@ -8,6 +8,8 @@ Bars (written here, derived in the design notes):
     <= 1e-6 from the oracle's float64 solution at the same tolerance;
   * divergence is an integer outcome too: the same status at the same sweep.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -629,11 +631,38 @@ def test_mixed_tensor_core_inner(ctx, monkeypatch, case, grid, kernel, prec_name
     u, tr, res = ctx.solve(mesh, co, f, g, ihdg.make_options(tol, prec=getattr(ihdg, prec_name), max_iters=20000))
     assert res.status == ihdg.OK, res.as_dict()
     assert res.lowp_sweeps > 0
-    assert res.inner_kernel_used == {"tc": 1, "global": 5}.get(kernel, res.inner_kernel_used)
+    if kernel == "tc":
+        # transport in bf16 takes the staged-gather variant unless it is switched off
+        staged = prec_name == "MIXED_BF16" and not case.startswith("cd") and os.environ.get("IHDG_TC_STAGED") != "0"
+        assert res.inner_kernel_used == (6 if staged else 1), res.inner_kernel_used
+    if kernel == "global":
+        assert res.inner_kernel_used == 5
     if kernel == "tile":
         assert res.inner_kernel_used in (2, 3, 4)
     assert rel(u, U.reshape(pr.mesh.nel, -1)) < 1e-6
 
+
+
+@pytest.mark.parametrize("n,p", [((9, 7, 11), 1), ((6, 5, 7), 2), ((16, 12, 10), 2)])
+def test_tc_staged_gathers_equal_register_gathers(ctx, monkeypatch, n, p):
+    """The tensor-core kernel with TMA-staged gathers (bf16 transport) computes exactly what
+    the register-gather kernel computes: the same packed operands, tile assignment and
+    reductions, so the solutions and sweep counts are bitwise equal; the meshes put windows
+    into the guard bands (first and last layers) and leave a ragged last tile."""
+    ihdg = ih()
+    beta = tuple(np.array([1.0, -0.7, 0.5]) / np.linalg.norm([1.0, -0.7, 0.5]))
+    mesh = ihdg.make_mesh(3, n, p)
+    co = ihdg.make_coeffs(ihdg.TRANSPORT, beta=beta)
+    vol, bnd = ihdg.quadrature_points(mesh, co)
+    f, g = W.transport3d_forcing(vol, beta), W.transport3d_exact(bnd)
+    opts = ihdg.make_options(1e-9, prec=ihdg.MIXED_BF16, max_iters=20000, inner_kernel=ihdg.KERNEL_TENSOR_CORES)
+    u_s, t_s, r_s = ctx.solve(mesh, co, f, g, opts)
+    monkeypatch.setenv("IHDG_TC_STAGED", "0")
+    u_r, t_r, r_r = ctx.solve(mesh, co, f, g, opts)
+    assert r_s.status == r_r.status == ihdg.OK
+    assert r_s.inner_kernel_used == 6 and r_r.inner_kernel_used == 1
+    assert r_s.iterations == r_r.iterations and r_s.lowp_sweeps == r_r.lowp_sweeps
+    assert np.array_equal(u_s, u_r) and np.array_equal(t_s, t_r)
 
 
 def _blocked_case(ihdg, pde):
