@@ -574,23 +574,17 @@ __global__ void __launch_bounds__(128 * TcsShape<NF, NLF>::G, 1)
       const int st = i & 1;
       const int K0 = tile * 128, K = K0 + gt;
       const bool valid = K < nel;
-      // the epilogue's residual, and the next tile's copies into the other stage (its last
-      // readers, the previous tile, passed the group barrier that ended that tile)
+      // the epilogue's residual
       RAW rr[NEXP];
       const RAW* rb = reinterpret_cast<const RAW*>(rlp);
 #pragma unroll
       for (int e = 0; e < NEXP; ++e) rr[e] = rb[e * ld + (valid ? K : 0)];
-      if (tile + tstride < ntiles) {
-        if (gt == 0) issue(tile + tstride, st ^ 1, par);
-        pending[st ^ 1] = 1;
-      }
-      // this tile's copies (bounded wait; the group agrees on the outcome)
+      // this tile's copies (bounded wait; the group agrees on the outcome at the barrier)
       const int okc = tc::mbar_wait(smb[st], sphase[st]) ? 1 : 0;
       if (okc) {
         sphase[st] ^= 1u;
         pending[st] = 0;
       }
-      if (tc::group_or(bar_id, !okc)) { failed = 1; break; }
       // a1: pack row gt of A from the stage (own runs at gt, inflow windows at gt + delta)
       const RAW* own_s = reinterpret_cast<const RAW*>(sStage + st * Z::STAGE);
       const RAW* nb_s = reinterpret_cast<const RAW*>(sStage + st * Z::STAGE + Z::OWNB);
@@ -628,10 +622,18 @@ __global__ void __launch_bounds__(128 * TcsShape<NF, NLF>::G, 1)
           *reinterpret_cast<uint4*>(row + kc * 128) = *reinterpret_cast<uint4*>(h);
         }
       }
+      // one group barrier: A is complete, the copy wait's outcome is agreed, and every
+      // thread is past the previous tile (its stage reads, its accumulator reads)
       tc::fence_proxy_async();
       tc::fence_before();
-      tc::group_bar(bar_id);
+      const int badc = tc::group_or(bar_id, !okc);
       tc::fence_after();
+      if (badc) { failed = 1; break; }
+      // the next tile's copies into the other stage, read last by the previous tile
+      if (tile + tstride < ntiles) {
+        if (gt == 0) issue(tile + tstride, st ^ 1, par);
+        pending[st ^ 1] = 1;
+      }
       // a3: D = A . B^T on the tensor cores
       if (gt == 0) {
 #pragma unroll
@@ -661,9 +663,6 @@ __global__ void __launch_bounds__(128 * TcsShape<NF, NLF>::G, 1)
           }
         }
       }
-      // every read of this stage and of A is done before either is written again
-      tc::fence_proxy_async();
-      tc::group_bar(bar_id);
     }
     if (__syncthreads_or(failed)) {
       if (tid == 0) atomicExch(&ctrl->timeout, 1);
