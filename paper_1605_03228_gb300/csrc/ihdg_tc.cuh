@@ -591,9 +591,10 @@ __global__ void __launch_bounds__(128 * TcsShape<NF, NLF>::G, 1)
       {
         int c[3] = {0, 0, 0};
         if (valid) coords(g, K, c);
-        float t[KP];
+        // the stage holds bf16 already: A takes the bit patterns as they are (zeros where masked)
+        unsigned t[KP];
 #pragma unroll
-        for (int k = NIN; k < KP; ++k) t[k] = 0.f;
+        for (int k = NIN; k < KP; ++k) t[k] = 0u;
 #pragma unroll
         for (int f = 0; f < NLF; ++f) {
           const int a = f >> 1, kind = g.kind[f];
@@ -604,22 +605,21 @@ __global__ void __launch_bounds__(128 * TcsShape<NF, NLF>::G, 1)
           // the face's kind is the same in every thread: one shared load per value
           if (kind == FK_OWN_D) {
 #pragma unroll
-            for (int q = 0; q < NF; ++q) t[f * NF + q] = use_own ? widen(own_s[(a * NF + q) * 128 + gt]) : 0.f;
+            for (int q = 0; q < NF; ++q) t[f * NF + q] = use_own ? (unsigned)own_s[(a * NF + q) * 128 + gt] : 0u;
           } else if (kind == FK_NBR_D) {
 #pragma unroll
-            for (int q = 0; q < NF; ++q) t[f * NF + q] = use_nb ? widen(nb_s[a * (Z::WB / 2) + q * Z::NBW + gt + dl]) : 0.f;
+            for (int q = 0; q < NF; ++q) t[f * NF + q] = use_nb ? (unsigned)nb_s[a * (Z::WB / 2) + q * Z::NBW + gt + dl] : 0u;
           } else {
 #pragma unroll
-            for (int q = 0; q < NF; ++q) t[f * NF + q] = 0.f;
+            for (int q = 0; q < NF; ++q) t[f * NF + q] = 0u;
           }
         }
         unsigned char* row = sA + (gt >> 3) * ROWB + (gt & 7) * 16;
 #pragma unroll
         for (int kc = 0; kc < KP / 8; ++kc) {
-          __align__(16) __nv_bfloat16 h[8];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) h[u] = __float2bfloat16_rn(t[kc * 8 + u]);
-          *reinterpret_cast<uint4*>(row + kc * 128) = *reinterpret_cast<uint4*>(h);
+          const unsigned* v = t + kc * 8;
+          *reinterpret_cast<uint4*>(row + kc * 128) =
+              make_uint4(v[0] | (v[1] << 16), v[2] | (v[3] << 16), v[4] | (v[5] << 16), v[6] | (v[7] << 16));
         }
       }
       // one group barrier: A is complete, the copy wait's outcome is agreed, and every
@@ -629,12 +629,8 @@ __global__ void __launch_bounds__(128 * TcsShape<NF, NLF>::G, 1)
       const int badc = tc::group_or(bar_id, !okc);
       tc::fence_after();
       if (badc) { failed = 1; break; }
-      // the next tile's copies into the other stage, read last by the previous tile
-      if (tile + tstride < ntiles) {
-        if (gt == 0) issue(tile + tstride, st ^ 1, par);
-        pending[st ^ 1] = 1;
-      }
-      // a3: D = A . B^T on the tensor cores
+      // a3: D = A . B^T on the tensor cores; then the next tile's copies into the other stage,
+      // read last by the previous tile (after the MMAs: they are on the tile's critical path)
       if (gt == 0) {
 #pragma unroll
         for (int kk = 0; kk < KP / KSTEP; ++kk) {
@@ -642,6 +638,10 @@ __global__ void __launch_bounds__(128 * TcsShape<NF, NLF>::G, 1)
           tc::mma_bf16(tcol, ah, bh, IDESC, kk > 0 ? 1u : 0u);
         }
         tc::commit(mbar);
+      }
+      if (tile + tstride < ntiles) {
+        if (gt == 0) issue(tile + tstride, st ^ 1, par);
+        pending[st ^ 1] = 1;
       }
       __syncwarp();
       const int ok = tc::mbar_wait(mbar, phase) ? 1 : 0;
