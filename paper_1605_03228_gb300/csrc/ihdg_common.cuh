@@ -152,7 +152,10 @@ __device__ void decide(Ctrl* ctrl, double res2, double* res_hist, bool count_fp6
   if (k >= ctrl->max_iters) { ctrl->done = 1; ctrl->status = 4; }
 }
 
-__device__ __forceinline__ int ctrl_done(const Ctrl* c) { return *(volatile const int*)&c->done; }
+// the loop has stopped: finished, or a bounded wait ran out (later launches return at once)
+__device__ __forceinline__ int ctrl_done(const Ctrl* c) {
+  return *(volatile const int*)&c->done | *(volatile const int*)&c->timeout;
+}
 __device__ __forceinline__ int ctrl_iter(const Ctrl* c) { return *(volatile const int*)&c->iter; }
 
 }  // namespace

@@ -29,62 +29,50 @@ namespace ihdg {
 
 namespace {
 
-// Volume data of element K in float64: forcing/boundary (steady) or time-step data (SWE).
-// Writes V[i] = (A^{-1} b)_i for i < nvol through `put`.
-template <typename Out>
-__device__ __forceinline__ void volume_source(const DevGeo& g, const OpsDev& op, const SrcDev& src,
-                                              long long K, const int* c, Out&& put) {
-  for (int i = 0; i < g.nvol; ++i) {
-    double v = 0.0;
-    if (g.steady) {
-      const double* fk = src.f + K * g.nqv;
-      const double* row = op.PV + (long long)i * g.nqv;
-      for (int q = 0; q < g.nqv; ++q) v += row[q] * fk[q];
-      for (int f = 0; f < g.nlf; ++f) {
-        if (!on_bnd(g, c, f)) continue;
-        const double* gb = src.g + bface_of(g, c, f) * g.nqf;
-        const double* rb = op.PVb[f] + (long long)i * g.nqf;
-        for (int q = 0; q < g.nqf; ++q) v += rb[q] * gb[q];
-      }
-    } else {
-      const double* qk = src.q + K * g.nvol;
-      const double* row = op.PqV + (long long)i * g.nvol;
-      for (int q = 0; q < g.nvol; ++q) v += row[q] * qk[q];
-    }
-    put(i, v);
-  }
-}
-
 // ---------------------------------------------------------------------------------------
-// a2 (once per solve / per time step): export forcing F = R A^{-1} b.
+// a2 (once per solve / per time step): the volume source V = A^{-1} b and the export forcing
+// F = R A^{-1} b of every element in float64, from the forcing f at the quadrature points and
+// the boundary data g (steady problems) or from the time-step data q^m (shallow water).  The
+// block's input rows ([element][nin] in global memory) are first copied, coalesced, into
+// shared memory as columns [nin][element] (pitch BS + 1 doubles), so each thread reads its
+// element's inputs from there for every output row instead of re-fetching its row through
+// L1; the operator rows are the same for every thread.
 __global__ void __launch_bounds__(BS) k_forcing(DevGeo g, OpsDev op, SrcDev src, double* __restrict__ F,
                                                 double* __restrict__ V) {
-  const long long K = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (K >= g.nel) return;
+  extern __shared__ double s_in[];
+  constexpr int SPI = BS + 1;
+  const long long K0 = (long long)blockIdx.x * BS;
+  const int cnt = (int)(g.nel - K0 < BS ? g.nel - K0 : BS);
+  const int nin = g.steady ? g.nqv : g.nvol;
+  const double* in = (g.steady ? src.f : src.q) + K0 * nin;
+  for (int idx = threadIdx.x; idx < cnt * nin; idx += BS) {
+    const int e = idx / nin, q = idx - e * nin;
+    s_in[q * SPI + e] = in[idx];
+  }
+  __syncthreads();
+  if (threadIdx.x >= cnt) return;
+  const long long K = K0 + threadIdx.x;
+  const double* x = s_in + threadIdx.x;   // x[q * SPI]: this element's input q
   int c[3];
   coords(g, K, c);
-  // the volume source A^{-1} b, kept for the first sweep's residual and the reconstruction
-  volume_source(g, op, src, K, c, [&](int i, double v) { V[(long long)i * g.ld + K] = v; });
-  for (int e = 0; e < g.n_exp; ++e) {
-    if (!row_live(g, e, g.nf)) continue;
+  // row r of operator M (nin inputs) and boundary operators Mb, applied to this element
+  auto apply = [&](const double* M, const double* const* Mb, int r) {
     double v = 0.0;
-    if (g.steady) {
-      const double* fk = src.f + K * g.nqv;
-      const double* row = op.PF + (long long)e * g.nqv;
-      for (int q = 0; q < g.nqv; ++q) v += row[q] * fk[q];
+    const double* row = M + (long long)r * nin;
+    for (int q = 0; q < nin; ++q) v += row[q] * x[q * SPI];
+    if (g.steady)
       for (int f = 0; f < g.nlf; ++f) {
         if (!on_bnd(g, c, f)) continue;
         const double* gb = src.g + bface_of(g, c, f) * g.nqf;
-        const double* rb = op.PFb[f] + (long long)e * g.nqf;
+        const double* rb = Mb[f] + (long long)r * g.nqf;
         for (int q = 0; q < g.nqf; ++q) v += rb[q] * gb[q];
       }
-    } else {
-      const double* qk = src.q + K * g.nvol;
-      const double* row = op.PqF + (long long)e * g.nvol;
-      for (int q = 0; q < g.nvol; ++q) v += row[q] * qk[q];
-    }
-    F[(long long)e * g.ld + K] = v;
-  }
+    return v;
+  };
+  // the volume source, kept for the first sweep's residual and the reconstruction
+  for (int i = 0; i < g.nvol; ++i) V[(long long)i * g.ld + K] = apply(g.steady ? op.PV : op.PqV, op.PVb, i);
+  for (int e = 0; e < g.n_exp; ++e)
+    if (row_live(g, e, g.nf)) F[(long long)e * g.ld + K] = apply(g.steady ? op.PF : op.PqF, op.PFb, e);
 }
 
 // Initial export E^0 = R u^0 (u^0 in the volume layout [nel][nvol]).
@@ -585,7 +573,13 @@ cudaError_t launch_ctrl_init(const LaunchArgs& a, double tol, double div, int ma
   return cudaGetLastError();
 }
 cudaError_t launch_forcing(const LaunchArgs& a) {
-  k_forcing<<<grid_for(a.g.nel), BS, 0, a.stream>>>(a.g, a.op, a.src, a.F, a.V);
+  const int nin = a.g.steady ? a.g.nqv : a.g.nvol;
+  const size_t smem = (size_t)nin * (BS + 1) * sizeof(double);
+  if (smem > 48 * 1024) {
+    cudaError_t e = allow_dynamic_smem(k_forcing);
+    if (e != cudaSuccess) return e;
+  }
+  k_forcing<<<grid_for(a.g.nel), BS, smem, a.stream>>>(a.g, a.op, a.src, a.F, a.V);
   return cudaGetLastError();
 }
 cudaError_t launch_export0(const LaunchArgs& a, const double* u0, double* E0) {
