@@ -731,7 +731,8 @@ def main():
         names = {ih.KERNEL_TENSOR_CORES: "tensor cores (tcgen05)", ih.KERNEL_CUDA_CORES: "CUDA cores",
                  ih.KERNEL_GLOBAL: "CUDA cores, global state"}
         tune = {"by": "ihdg_autotune", "inner_kernel": names.get(tuned.inner_kernel, "auto"),
-                "inner_rtol": tuned.inner_rtol, "sweeps_per_sync": tuned.sweeps_per_sync, "best_solve_ms": tune_ms}
+                "inner_rtol": tuned.inner_rtol, "sweeps_per_sync": tuned.sweeps_per_sync,
+                "tile_shape": tuned.tile_shape, "best_solve_ms": tune_ms}
     nws = ih.workspace_bytes(mesh, co, opts)
     ws = torch.empty(nws + 256, dtype=torch.uint8, device=dev)
     wsp = (ws.data_ptr() + 255) // 256 * 256
@@ -781,7 +782,8 @@ def main():
 
     # roofline of the dominant kernel: one profiled solve (events around every sweep launch)
     po = ih.make_options(spec["tol"], max_iters=4000, prec=prec, profile=1, inner_max=args.inner_max,
-                         inner_rtol=opts.inner_rtol, inner_kernel=opts.inner_kernel, sweeps_per_sync=opts.sweeps_per_sync)
+                         inner_rtol=opts.inner_rtol, inner_kernel=opts.inner_kernel, sweeps_per_sync=opts.sweeps_per_sync,
+                         tile_shape=opts.tile_shape)
     rp = step(po)
     lp_bytes = 2 if prec == ih.MIXED_BF16 else 4
     if prec == ih.FP64:

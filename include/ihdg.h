@@ -154,6 +154,11 @@ typedef struct {
                               H >= 2: temporal blocking, every block sweeps its tile plus a halo
                               of H elements H times in shared memory (the same iterates; halo
                               work recomputed); 0: automatic (the autotuned value, else 4) */
+  int tile_shape;          /* mixed, temporally blocked 2D kernel: which tile shape, counted
+                              in order of increasing tile + halo area over at most one tile per
+                              SM (1: the smallest area, the automatic rule; 2, 3, ...: the
+                              next ones; past the last: the last); 0: automatic (the autotuned
+                              value, else 1) */
 } ihdg_options;
 
 typedef struct {

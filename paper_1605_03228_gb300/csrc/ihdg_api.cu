@@ -69,6 +69,7 @@ struct ihdg_ctx {
     int kernel;
     double rtol;
     int sps;
+    int shape;   // tile shape of the temporally blocked kernel (1-based rank)
   };
   std::map<std::string, Tuned> tuned;
 };
@@ -255,6 +256,7 @@ ihdg_status check_opts(ihdg_ctx* ctx, const ihdg_options& o) {
   if (o.max_iters > 100000000) return fail(ctx, IHDG_ERR_INVALID, "opts.max_iters too large");
   if (o.sweeps_per_sync < 0 || o.sweeps_per_sync > 8)
     return fail(ctx, IHDG_ERR_INVALID, "opts.sweeps_per_sync must be in 0..8");
+  if (o.tile_shape < 0 || o.tile_shape > 64) return fail(ctx, IHDG_ERR_INVALID, "opts.tile_shape must be in 0..64");
   if (o.inner_kernel < IHDG_KERNEL_AUTO || o.inner_kernel > IHDG_KERNEL_GLOBAL)
     return fail(ctx, IHDG_ERR_INVALID, "opts.inner_kernel is not a known kernel");
   return IHDG_OK;
@@ -314,12 +316,14 @@ ihdg_status device_iterate(ihdg_ctx* ctx, Plan* pl, const ihdg_options& o, const
   int inner_kernel = o.inner_kernel;
   double inner_rtol = o.inner_rtol;
   int sps = o.sweeps_per_sync;
-  if (o.prec != IHDG_FP64 && inner_kernel == IHDG_KERNEL_AUTO && inner_rtol <= 0.0 && sps <= 0) {
+  int shape = o.tile_shape;
+  if (o.prec != IHDG_FP64 && inner_kernel == IHDG_KERNEL_AUTO && inner_rtol <= 0.0 && sps <= 0 && shape <= 0) {
     auto it = ctx->tuned.find(tune_key(pl->mesh, pl->co, o.prec));
     if (it != ctx->tuned.end()) {
       inner_kernel = it->second.kernel;
       inner_rtol = it->second.rtol;
       sps = it->second.sps;
+      shape = it->second.shape;
     }
   }
   // Inner stop well above the low-precision rounding floor: an inner loop pushed towards its
@@ -424,6 +428,7 @@ ihdg_status device_iterate(ihdg_ctx* ctx, Plan* pl, const ihdg_options& o, const
       if (const char* h = std::getenv("IHDG_SWEEPS_PER_SYNC")) sps = std::atoi(h);
     if (sps <= 0) sps = 4;
     m.blk_h = sps >= 2 ? (sps > 8 ? 8 : sps) : 0;
+    m.blk_rank = shape >= 1 ? shape - 1 : 0;
     m.LE32h = pl->le32.data();
     m.slots = partials_needed(pl->g.nel);
     ihdg_status st = run_mixed(ctx->h_ctrl, m, o, &Eu, &Eu2, &Et, &Et2, ctx->err, &tm);
@@ -666,8 +671,10 @@ ihdg_status ihdg_autotune(ihdg_ctx* ctx, const ihdg_mesh* mesh, const ihdg_coeff
   // sweeps per grid barrier: the temporally blocked CUDA-core kernel exists for 2D meshes
   const int sps_2d[] = {1, 2, 3, 4};
   const int sps_1[] = {1};
+  // tile shapes of the temporally blocked kernel: the three of smallest tile + halo area
+  constexpr int NSHAPE = 3;
   double best = 1e300;
-  int best_k = IHDG_KERNEL_AUTO, best_s = 1;
+  int best_k = IHDG_KERNEL_AUTO, best_s = 1, best_shape = 1;
   double best_r = 0.0;
   for (int pass = 0; pass < 2; ++pass)          // pass 0 warms every kernel up (module loads)
     for (int k : kernels) {
@@ -675,30 +682,34 @@ ihdg_status ihdg_autotune(ihdg_ctx* ctx, const ihdg_mesh* mesh, const ihdg_coeff
       const int* sl = blk ? sps_2d : sps_1;
       const int ns = blk ? 4 : 1;
       for (int si = 0; si < ns; ++si)
-        for (int i = 0; i < (pass == 0 ? 1 : 5); ++i) {
-          ihdg_options oc = o;
-          oc.u0 = d_u0;
-          oc.inner_kernel = static_cast<ihdg_inner_kernel>(k);
-          oc.inner_rtol = ladder[pass == 0 ? 2 : i];
-          oc.sweeps_per_sync = sl[si];
-          oc.profile = 0;
-          ihdg_result r{};
-          st = ihdg_solve_device(ctx, mesh, co, d_f, d_g, &oc, d_u, nullptr, d_ws, ws, nullptr, &r);
-          if (st == IHDG_ERR_CUDA || st == IHDG_ERR_TIMEOUT || st == IHDG_ERR_NOMEM) return st;
-          if (pass == 0 || st != IHDG_OK || r.status != IHDG_OK) continue;
-          if (r.solve_ms < best) {
-            best = r.solve_ms;
-            best_k = k;
-            best_r = oc.inner_rtol;
-            best_s = sl[si];
+        for (int shape = 1; shape <= (sl[si] >= 2 ? NSHAPE : 1); ++shape)
+          for (int i = 0; i < (pass == 0 ? 1 : 5); ++i) {
+            ihdg_options oc = o;
+            oc.u0 = d_u0;
+            oc.inner_kernel = static_cast<ihdg_inner_kernel>(k);
+            oc.inner_rtol = ladder[pass == 0 ? 2 : i];
+            oc.sweeps_per_sync = sl[si];
+            oc.tile_shape = shape;
+            oc.profile = 0;
+            ihdg_result r{};
+            st = ihdg_solve_device(ctx, mesh, co, d_f, d_g, &oc, d_u, nullptr, d_ws, ws, nullptr, &r);
+            if (st == IHDG_ERR_CUDA || st == IHDG_ERR_TIMEOUT || st == IHDG_ERR_NOMEM) return st;
+            if (pass == 0 || st != IHDG_OK || r.status != IHDG_OK) continue;
+            if (r.solve_ms < best) {
+              best = r.solve_ms;
+              best_k = k;
+              best_r = oc.inner_rtol;
+              best_s = sl[si];
+              best_shape = shape;
+            }
           }
-        }
     }
   if (best_k == IHDG_KERNEL_AUTO) return fail(ctx, IHDG_NOT_CONVERGED, "no candidate converged");
-  ctx->tuned[tune_key(*mesh, *co, o.prec)] = {best_k, best_r, best_s};
+  ctx->tuned[tune_key(*mesh, *co, o.prec)] = {best_k, best_r, best_s, best_shape};
   tuned->inner_kernel = static_cast<ihdg_inner_kernel>(best_k);
   tuned->inner_rtol = best_r;
   tuned->sweeps_per_sync = best_s;
+  tuned->tile_shape = best_shape;
   if (best_ms) *best_ms = best;
   ctx->err.clear();
   return IHDG_OK;

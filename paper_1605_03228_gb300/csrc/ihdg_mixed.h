@@ -38,6 +38,7 @@ struct MixedArgs {
   int use_tc = 0;           // bf16: local apply on the tensor cores (tcgen05)
   int lt_kind = 0;          // operator layout now in dLT: 0 none, 1 register kernel, 2 tensor-core B
   int blk_h = 0;            // >= 2: 2D CUDA-core inner sweeps temporally blocked, this many per barrier
+  int blk_rank = 0;         // which tile shape of the blocked kernel (0: smallest tile + halo area)
   const float* LE32h = nullptr;  // host copy of the float32 operator (n_exp x n_in)
   int ran = 0;              // inner kernel of the last inner launch (ihdg_result.inner_kernel_used codes)
   long long e_pad = 0;      // guard values below e[0], e[1] and above their last slot

@@ -1037,27 +1037,31 @@ cudaError_t launch_blk_v(MixedArgs& m, TL* rl, TL* e0, TL* e1) {
   int cap = sms;
   if (cap > m.max_grid) cap = m.max_grid;
   if (cap > m.slots / 2) cap = m.slots / 2;
-  BlkShape sh{0, 0, 0, H, 0};
-  long long best = -1;
-  int grid = 0;
+  // the distinct tile shapes over at most one tile per SM whose state fits in shared memory,
+  // in order of increasing tile + halo area; m.blk_rank picks one (the autotuner times several)
+  struct Cand {
+    long long area;
+    int txn, tiles_x, tx, ty, grid;
+  };
+  std::vector<Cand> cands;
   for (int txn = 1; txn <= n0 && txn <= cap; ++txn) {
     const int tx = (n0 + txn - 1) / txn, tiles_x = (n0 + tx - 1) / tx;
     const int tyn = cap / tiles_x;
     if (tyn < 1) continue;
     const int ty = (n1 + tyn - 1) / tyn, tiles_y = (n1 + ty - 1) / ty;
     const long long area = (long long)blk_pitch(std::min(n0, tx + 2 * H)) * std::min(n1, ty + 2 * H);
-    if (best < 0 || area < best) {
-      best = area;
-      sh.tiles_x = tiles_x;
-      sh.tx = tx;
-      sh.ty = ty;
-      sh.ra_max = (int)area;
-      grid = tiles_x * tiles_y;
-    }
+    if ((size_t)3 * area * SP * sizeof(float) > (size_t)smem_max) continue;
+    bool dup = false;
+    for (const Cand& c : cands) dup = dup || (c.tx == tx && c.ty == ty);
+    if (!dup) cands.push_back({area, txn, tiles_x, tx, ty, tiles_x * tiles_y});
   }
-  if (best < 0 || grid < 1) return cudaErrorNotSupported;
+  if (cands.empty()) return cudaErrorNotSupported;
+  std::stable_sort(cands.begin(), cands.end(), [](const Cand& x, const Cand& y) { return x.area < y.area; });
+  const Cand& pick = cands[std::min((size_t)std::max(m.blk_rank, 0), cands.size() - 1)];
+  BlkShape sh{pick.tiles_x, pick.tx, pick.ty, H, (int)pick.area};
+  const int grid = pick.grid;
+  if (grid < 1) return cudaErrorNotSupported;
   const size_t smem = (size_t)3 * sh.ra_max * SP * sizeof(float);
-  if (smem > (size_t)smem_max) return cudaErrorNotSupported;
   cudaError_t e = allow_dynamic_smem(k);
   if (e != cudaSuccess) return e;
   int per = 0;

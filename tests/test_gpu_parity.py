@@ -720,6 +720,26 @@ def test_blocked_inner_matches_one_barrier_per_sweep(ctx, monkeypatch, pde, H, g
     assert rel(uh, u1) < 2e-5, rel(uh, u1)
 
 
+@pytest.mark.parametrize("pde", ["convdiff", "transport"])
+def test_blocked_tile_shapes_compute_the_same_iterates(ctx, pde):
+    """The blocked kernel's tile shape (opts.tile_shape: 1 the smallest tile + halo area, 2
+    and 3 the next ones, which the autotuner times) only changes which block computes an
+    element: with a fixed schedule every shape gives bitwise the same result."""
+    ihdg = ih()
+    case = _blocked_case(ihdg, pde)
+    out = []
+    for shape in (1, 2, 3):
+        opts = ihdg.make_options(0.0, prec=ihdg.MIXED_FP32, max_iters=19, inner_max=7, inner_rtol=1e-30,
+                                 diverge_factor=-1.0, inner_kernel=ihdg.KERNEL_CUDA_CORES, sweeps_per_sync=4,
+                                 tile_shape=shape)
+        u, r = _blocked_run(ctx, ihdg, pde, case, opts)
+        assert r.inner_kernel_used == 2
+        out.append((u, r))
+    for u, r in out[1:]:
+        assert (r.iterations, r.lowp_sweeps) == (out[0][1].iterations, out[0][1].lowp_sweeps)
+        assert np.array_equal(u, out[0][0])
+
+
 @pytest.mark.parametrize("H", [2, 3, 4])
 def test_blocked_inner_converges_to_oracle(ctx, H):
     """The blocked inner kernel in a complete mixed solve: the oracle's solution within the
@@ -885,6 +905,7 @@ def test_autotune_choice_converges_and_is_cached(ctx):
     tuned, best_ms = ctx.autotune(mesh, co, f, g, opts)
     assert tuned.inner_kernel in (ihdg.KERNEL_TENSOR_CORES, ihdg.KERNEL_CUDA_CORES)
     assert tuned.inner_rtol > 0 and best_ms > 0
+    assert 1 <= tuned.tile_shape <= 3 and 1 <= tuned.sweeps_per_sync <= 4
     assert tuned.prec == ihdg.MIXED_FP32 and tuned.tol == opts.tol
     u_t, _, r_t = ctx.solve(mesh, co, f, g, tuned)
     u_a, _, r_a = ctx.solve(mesh, co, f, g, opts)
