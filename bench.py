@@ -378,6 +378,75 @@ def var_group_result(ih, ctx, dev, nplans=48, seed=7):
             pl.close()
 
 
+def const_group_result(ih, ctx, dev, nprob=48, seed=11):
+    """Many small constant-coefficient float64 problems of uneven size and order (the serving
+    stream's conv.-diff. distribution, sides 16..64): each solved alone (ihdg_solve_device,
+    one after another on the stream) against all in one grouped call
+    (ihdg_solve_group_device); the results are bitwise the same."""
+    import torch
+    rng = np.random.default_rng(seed)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    probs = []
+    for _ in range(nprob):
+        side = int(round(np.exp(rng.uniform(np.log(16), np.log(64)))))
+        p = int(rng.integers(1, 5))
+        kappa = float(np.exp(rng.uniform(np.log(1e-4), np.log(1e-2))))
+        th = float(rng.uniform(0, 2 * np.pi))
+        beta = (float(np.cos(th)), float(np.sin(th)))
+        mesh = ih.make_mesh(2, (side, side), p)
+        co = ih.make_coeffs(ih.CONVDIFF, beta=beta, kappa=kappa)
+        vol, bnd = ih.quadrature_points(mesh, co)
+        f = W.convdiff_forcing(vol, kappa, beta)
+        g = W.convdiff_exact(bnd)
+        s = ih.problem_sizes(mesh, co)
+        probs.append((mesh, co, torch.from_numpy(np.ascontiguousarray(f)).to(dev),
+                      torch.from_numpy(np.ascontiguousarray(g)).to(dev),
+                      torch.zeros((s.n_el, s.nvol), dtype=torch.float64, device=dev)))
+    o = ih.make_options(1e-8, max_iters=4000)
+    meshes, coeffs = [q[0] for q in probs], [q[1] for q in probs]
+    nws = ctx.group_workspace_bytes(meshes, coeffs, o)
+    ws = torch.empty(nws + 256, dtype=torch.uint8, device=dev)
+    wsp = (ws.data_ptr() + 255) // 256 * 256
+    n1 = max(ih.workspace_bytes(q[0], q[1], o) for q in probs)
+    w1 = torch.empty(n1 + 256, dtype=torch.uint8, device=dev)
+    w1p = (w1.data_ptr() + 255) // 256 * 256
+
+    def alone():
+        return [ctx.solve_device(m, c, f.data_ptr(), g.data_ptr(), o, u.data_ptr(), 0, w1p, n1, sp)
+                for m, c, f, g, u in probs]
+
+    def grouped():
+        return ctx.solve_group_device(meshes, coeffs, [q[2].data_ptr() for q in probs],
+                                      [q[3].data_ptr() for q in probs], o, [q[4].data_ptr() for q in probs],
+                                      None, wsp, nws, sp)
+
+    ra = alone()
+    u_alone = [q[4].clone() for q in probs]
+    rg = grouped()
+    same = all(bool(torch.equal(a, q[4])) for a, q in zip(u_alone, probs))
+    same_counts = all((x.status, x.iterations) == (y.status, y.iterations) for x, y in zip(ra, rg))
+    ts = {}
+    for lab, fn in (("alone", alone), ("grouped", grouped)):
+        times = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        ts[lab] = float(np.min(times))
+    st = {}
+    for r in rg:
+        k = ih.STATUS_NAMES[r.status]
+        st[k] = st.get(k, 0) + 1
+    return {"problems": nprob, "meshes": "2D conv.-diff. side log-uniform 16..64, p 1..4, kappa log-uniform 1e-4..1e-2, "
+                                          "beta angle uniform; float64, tol 1e-8",
+            "alone_ms": ts["alone"], "grouped_ms": ts["grouped"], "speedup": ts["alone"] / ts["grouped"],
+            "bitwise_equal": same and same_counts, "status_counts": st}
+
+
 def sub_results(args, ih, ctx, dev, flush, peaks, pk):
     """Compact driver-recorded results of the other listed workloads, each with its float64
     comparison: 3D transport 64^3 (bf16 tensor-core inner sweeps), shallow water 512^2 x 100
@@ -435,6 +504,7 @@ def sub_results(args, ih, ctx, dev, flush, peaks, pk):
     out["transport3d_var_64"] = var_result(ih, ctx, dev, flush, peaks, pk)
     torch.cuda.synchronize(dev)
     out["transport_var_group"] = var_group_result(ih, ctx, dev)
+    out["convdiff_fp64_group"] = const_group_result(ih, ctx, dev)
     torch.cuda.synchronize(dev)
     # serving stream
     sa = argparse.Namespace(**vars(args))

@@ -288,6 +288,26 @@ ihdg_status ihdg_autotune(ihdg_ctx* ctx, const ihdg_mesh* mesh, const ihdg_coeff
                           const double* f_qp, const double* g_qp, const ihdg_options* opts,
                           ihdg_options* tuned, double* best_ms);
 
+/* Grouped float64 solves of many steady problems (no counterpart in the paper; every
+ * problem's sweeps are independent, Algorithm 1, so problems can share the GPU): n problems of
+ * any mesh sizes, orders and PDEs (transport, convection-diffusion; shallow water is stepped
+ * by ihdg_swe_steps*) solved in one call.  Problems of one element shape (dimension, nodes per
+ * face) run their whole loops in one cooperative launch as far as their blocks are
+ * co-resident, each exactly as in its own launch (bitwise the result, iteration count and
+ * status of ihdg_solve_device); larger ones run one by one; one readback at the end.
+ * opts->prec must be IHDG_FP64 (else IHDG_ERR_UNSUPPORTED) and opts->u0 NULL (zero initial
+ * guess).  d_f[i], d_g[i]: device forcing and boundary data of problem i (layouts of
+ * ihdg_solve); d_u[i]: device volume output [n_el][nvol]; d_tr: NULL, or per problem a device
+ * trace output or NULL.  d_workspace: 256-byte aligned device memory of at least
+ * ihdg_group_workspace_bytes(), owned by the caller.  res: n results (or NULL).  Errors as for
+ * ihdg_solve_device; host arrays are read during the call only. */
+ihdg_status ihdg_group_workspace_bytes(int n, const ihdg_mesh* meshes, const ihdg_coeffs* coeffs,
+                                       const ihdg_options* opts, size_t* bytes);
+ihdg_status ihdg_solve_group_device(ihdg_ctx* ctx, int n, const ihdg_mesh* meshes, const ihdg_coeffs* coeffs,
+                                    const double* const* d_f, const double* const* d_g, const ihdg_options* opts,
+                                    double* const* d_u, double* const* d_tr, void* d_workspace,
+                                    size_t workspace_bytes, void* stream, ihdg_result* res);
+
 /* Linearized shallow water (Section 3, Eq. localSolverDD), walls on the whole boundary:
  * advance q (in/out, [n_el][3][(p+1)^2] volume layout (phi, u, v), host) by nsteps steps of
  * coeffs->dt with coeffs->time_scheme (backward Euler, or the Crank-Nicolson rule of the

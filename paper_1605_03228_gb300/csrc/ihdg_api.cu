@@ -59,6 +59,7 @@ struct ihdg_ctx {
   std::string err;
   Server* server = nullptr;   // serving state (ihdg_server_start .. ihdg_server_stop)
   std::vector<std::unique_ptr<Plan>> plans;
+  int plan_pin = 0;   // > 0: a call holds plan pointers, nothing is evicted
   // device scratch of the host-pointer calls (inputs, outputs, workspace)
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
@@ -200,7 +201,7 @@ ihdg_status get_plan(ihdg_ctx* ctx, const ihdg_mesh& m, const ihdg_coeffs& co, P
     cudaFree(pl->dbuf);
     return st;
   }
-  if (ctx->plans.size() >= 16) {
+  while (ctx->plans.size() >= 16 && ctx->plan_pin == 0) {
     cudaFree(ctx->plans.front()->dbuf);
     ctx->plans.erase(ctx->plans.begin());
   }
@@ -1156,6 +1157,168 @@ ihdg_status ihdg_swe_steps(ihdg_ctx* ctx, const ihdg_mesh* mesh, const ihdg_coef
 
 // ---------------------------------------------------------------------------------------
 // Transport with a velocity field that varies in space: plans of per-element local solves.
+
+// ---------------------------------------------------------------------------------------
+// Grouped float64 solves: every problem's init kernels, then one cooperative launch per
+// element shape for the problems whose blocks fit together (each problem's loop exactly as
+// in its own launch), then the rest one by one, then every reconstruction; one readback.
+ihdg_status ihdg_group_workspace_bytes(int n, const ihdg_mesh* meshes, const ihdg_coeffs* coeffs,
+                                       const ihdg_options* opts, size_t* bytes) {
+  if (n < 0 || !bytes || (n > 0 && (!meshes || !coeffs))) return IHDG_ERR_INVALID;
+  size_t tot = sweep64_group_desc_bytes(n);
+  for (int i = 0; i < n; ++i) {
+    if (coeffs[i].pde == IHDG_SWE) return IHDG_ERR_INVALID;
+    size_t b = 0;
+    ihdg_status st = ihdg_workspace_bytes(&meshes[i], &coeffs[i], opts, &b);
+    if (st != IHDG_OK) return st;
+    tot += align256(b);
+  }
+  *bytes = tot;
+  return IHDG_OK;
+}
+
+ihdg_status ihdg_solve_group_device(ihdg_ctx* ctx, int n, const ihdg_mesh* meshes, const ihdg_coeffs* coeffs,
+                                    const double* const* d_f, const double* const* d_g, const ihdg_options* opts,
+                                    double* const* d_u, double* const* d_tr, void* d_ws, size_t ws_bytes,
+                                    void* stream, ihdg_result* res) {
+  if (!ctx) return IHDG_ERR_INVALID;
+  if (n < 0) return fail(ctx, IHDG_ERR_INVALID, "n must be >= 0");
+  if (n == 0) return IHDG_OK;
+  if (!meshes || !coeffs || !d_f || !d_g || !d_u || !d_ws) return fail(ctx, IHDG_ERR_INVALID, "null argument");
+  if (reinterpret_cast<uintptr_t>(d_ws) % 256 != 0) return fail(ctx, IHDG_ERR_INVALID, "workspace must be 256-byte aligned");
+  ihdg_options o = defaults(opts);
+  ihdg_status st = check_opts(ctx, o);
+  if (st != IHDG_OK) return st;
+  if (o.prec != IHDG_FP64) return fail(ctx, IHDG_ERR_UNSUPPORTED, "grouped solves run the float64 path (opts.prec = IHDG_FP64)");
+  if (o.u0) return fail(ctx, IHDG_ERR_UNSUPPORTED, "grouped solves start from the zero guess (opts.u0 = NULL)");
+  size_t need = 0;
+  st = ihdg_group_workspace_bytes(n, meshes, coeffs, &o, &need);
+  if (st != IHDG_OK) return fail(ctx, st, "invalid problem in the group");
+  if (ws_bytes < need) return fail(ctx, IHDG_ERR_NOMEM, "workspace smaller than ihdg_group_workspace_bytes()");
+  for (int i = 0; i < n; ++i)
+    if (!d_f[i] || !d_g[i] || !d_u[i]) return fail(ctx, IHDG_ERR_INVALID, "null argument");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // the plans stay in the context's cache for the whole call
+  struct Pin {
+    ihdg_ctx* c;
+    ~Pin() { c->plan_pin -= 1; }
+  } pin{ctx};
+  ctx->plan_pin += 1;
+  std::vector<Plan*> pl((size_t)n, nullptr);
+  std::vector<double> setup((size_t)n, 0.0);
+  std::vector<LaunchArgs> a((size_t)n);
+  std::vector<Layout> L((size_t)n);
+  char* ws = static_cast<char*>(d_ws);
+  char* desc = ws;
+  size_t at = sweep64_group_desc_bytes(n);
+  for (int i = 0; i < n; ++i) {
+    st = get_plan(ctx, meshes[i], coeffs[i], pl[(size_t)i], &setup[(size_t)i]);
+    if (st != IHDG_OK) return st;
+    L[(size_t)i] = layout_for(pl[(size_t)i]->g, o, false);
+    char* w = ws + at;
+    at += align256(L[(size_t)i].total);
+    LaunchArgs& ai = a[(size_t)i];
+    ai = LaunchArgs{};
+    ai.g = pl[(size_t)i]->g;
+    ai.op = pl[(size_t)i]->op;
+    ai.src = SrcDev{d_f[i], d_g[i], nullptr};
+    ai.u0 = nullptr;
+    ai.F = reinterpret_cast<double*>(w + L[(size_t)i].F);
+    ai.V = reinterpret_cast<double*>(w + L[(size_t)i].V);
+    ai.ring = reinterpret_cast<double*>(w + L[(size_t)i].ring);
+    ai.ring_stride = (long long)ai.g.n_exp * ai.g.ld;
+    ai.ctrl = reinterpret_cast<Ctrl*>(w + L[(size_t)i].ctrl);
+    ai.partials = reinterpret_cast<double*>(w + L[(size_t)i].partials);
+    ai.res_hist = reinterpret_cast<double*>(w + L[(size_t)i].res_hist);
+    ai.stream = s;
+    CK(launch_ctrl_init(ai, o.tol, o.diverge_factor, o.max_iters, o.inner_max, o.inner_rtol, 2000000000LL, -1),
+       "ctrl init");
+    CK(launch_forcing(ai), "forcing kernel");
+    CK(launch_export0(ai, nullptr, ai.ring), "initial export kernel");
+    CK(launch_first(ai), "first sweep kernel");
+  }
+  // one cooperative launch per element shape, as many problems as fit together (in order)
+  std::vector<int> rest;
+  std::vector<char> placed((size_t)n, 0);
+  for (int i = 0; i < n; ++i) {
+    if (placed[(size_t)i]) continue;
+    std::vector<LaunchArgs> cls;
+    std::vector<int> idx;
+    for (int j = i; j < n; ++j)
+      if (!placed[(size_t)j] && a[(size_t)j].g.dim == a[(size_t)i].g.dim && a[(size_t)j].g.nf == a[(size_t)i].g.nf) {
+        cls.push_back(a[(size_t)j]);
+        idx.push_back(j);
+        placed[(size_t)j] = 1;
+      }
+    size_t k = 0;
+    while (k < cls.size()) {
+      // the largest prefix of the remaining problems that is co-resident
+      size_t m = cls.size() - k;
+      cudaError_t e = cudaErrorNotSupported;
+      while (m > 0) {
+        e = launch_sweep64_persist_group(cls.data() + k, (int)m, desc, s);
+        if (e != cudaErrorNotSupported) break;
+        cudaGetLastError();
+        m = m > 1 ? m / 2 : 0;
+      }
+      if (e != cudaSuccess && e != cudaErrorNotSupported) return cuda_fail(ctx, e, "grouped sweep kernel");
+      if (m == 0) {   // too large for a persistent launch: its own loop below
+        rest.push_back(idx[k]);
+        k += 1;
+        continue;
+      }
+      // (the next launch's descriptor copy is stream-ordered after this launch)
+      k += m;
+    }
+  }
+  std::vector<Ctrl> hc((size_t)n);
+  for (int i : rest) {   // batches of launches with host checks, as the single solve does
+    LaunchArgs& ai = a[(size_t)i];
+    int batch = 2;
+    for (;;) {
+      CK(cudaMemcpyAsync(&hc[(size_t)i], ai.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s), "ctrl readback");
+      CK(cudaStreamSynchronize(s), "sweep loop");
+      if (hc[(size_t)i].done) break;
+      int left = hc[(size_t)i].max_iters - hc[(size_t)i].iter;
+      int nb = batch < left ? batch : left;
+      if (nb <= 0) break;
+      CK(launch_sweep64(ai, nb), "sweep kernel");
+      if (batch < 32) batch *= 2;
+    }
+  }
+  for (int i = 0; i < n; ++i)
+    CK(cudaMemcpyAsync(&hc[(size_t)i], a[(size_t)i].ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s), "ctrl readback");
+  CK(cudaStreamSynchronize(s), "grouped solves");
+  for (int i = 0; i < n; ++i) {
+    const LaunchArgs& ai = a[(size_t)i];
+    if (hc[(size_t)i].timeout) return fail(ctx, IHDG_ERR_TIMEOUT, "grouped float64 sweep: a grid barrier wait ran out");
+    const int K = hc[(size_t)i].iter;
+    const double* Et = ai.ring + (long long)(K % 3) * ai.ring_stride;
+    const double* Eu = ai.ring + (long long)((K + 2) % 3) * ai.ring_stride;
+    CK(launch_reconstruct(ai, Eu, nullptr, d_u[i]), "reconstruct kernel");
+    if (d_tr && d_tr[i]) {
+      const Plan* p = pl[(size_t)i];
+      double beta[3] = {p->co.beta[0], p->co.beta[1], p->co.beta[2]};
+      CK(launch_trace_out(ai, Et, nullptr, d_u[i], (int)p->co.pde, beta, p->ops.alpha_axis, count_faces(p->mesh, nullptr),
+                          d_tr[i]),
+         "trace kernel");
+    }
+    if (res) {
+      ihdg_result r{};
+      r.iterations = hc[(size_t)i].iter;
+      r.fp64_sweeps = hc[(size_t)i].fp64_sweeps;
+      r.residual = hc[(size_t)i].res;
+      r.status = (ihdg_status)hc[(size_t)i].status;
+      r.setup_ms = setup[(size_t)i];
+      res[i] = r;
+    }
+  }
+  CK(cudaStreamSynchronize(s), "grouped reconstructions");
+  ctx->err.clear();
+  return IHDG_OK;
+}
+
 }  // extern "C"
 
 struct ihdg_var_plan {

@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdio>
+#include <vector>
 
 #include "ihdg_dev.h"
 #include "ihdg_kernels.h"
@@ -222,12 +223,12 @@ __global__ void __launch_bounds__(BS) k_sweep64(DevGeo g, OpsDev op, const doubl
 // value, arrives with a release add and polls with acquire loads bounded by
 // ctrl->wait_cycles (then ctrl->timeout).  The total is valid in every thread.
 __device__ double barrier_sum64(double* part, unsigned* count, unsigned nb, double mine, Ctrl* ctrl, double* ws,
-                                double* s_out, int* s_flag) {
+                                double* s_out, int* s_flag, int bid, int nblk) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    part[blockIdx.x] = mine;
-    if ((int)blockIdx.x != ctrl->stall_block) red_release_add(count, 1u);
-    const unsigned target = nb * gridDim.x;
+    part[bid] = mine;
+    if (bid != ctrl->stall_block) red_release_add(count, 1u);
+    const unsigned target = nb * (unsigned)nblk;
     const long long lim = ctrl->wait_cycles;
     const long long t0 = clock64();
     while (ld_acquire_u32(count) < target) {
@@ -237,7 +238,7 @@ __device__ double barrier_sum64(double* part, unsigned* count, unsigned nb, doub
   }
   __syncthreads();
   double acc = 0.0;
-  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) acc += __ldcg(part + i);
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x) acc += __ldcg(part + i);
   const double t = block_sum(acc, ws);
   if (threadIdx.x == 0) *s_out = t;
   __syncthreads();
@@ -249,10 +250,23 @@ __device__ double barrier_sum64(double* part, unsigned* count, unsigned nb, doub
 // sum, then the loop decision, which every block takes identically from the same total
 // (decide()'s rules); block 0 records it in ctrl.  Per sweep this saves a launch and a host
 // check, which dominate on small meshes.
+// One problem's arguments of the persistent float64 loop (also one item of a grouped launch).
+struct P64Args {
+  DevGeo g;
+  OpsDev op;
+  const double* F;
+  double* ring;
+  long long ring_stride;
+  Ctrl* ctrl;
+  double* partials;
+  double* res_hist;
+};
+
+// The loop body of block bid of the nblk blocks that work for one problem.
 template <int NF, int NLF>
-__global__ void __launch_bounds__(BS) k_sweep64_persist(DevGeo g, OpsDev op, const double* __restrict__ F,
-                                                        double* ring, long long ring_stride, Ctrl* ctrl,
-                                                        double* partials, double* res_hist) {
+__device__ __forceinline__ void sweep64_persist_body(const DevGeo& g, const OpsDev& op, const double* __restrict__ F,
+                                                     double* ring, long long ring_stride, Ctrl* ctrl,
+                                                     double* partials, double* res_hist, int bid, int nblk) {
   constexpr int NIN = NF * NLF;
   constexpr int NQ = NIN * (NIN + 1) / 2;
   __shared__ double ws[BS / 32];
@@ -270,7 +284,7 @@ __global__ void __launch_bounds__(BS) k_sweep64_persist(DevGeo g, OpsDev op, con
   for (int i = threadIdx.x; i < g.n_exp * NIN; i += BS) sLE[i] = op.LE[i];
   for (int i = threadIdx.x; i < NQ; i += BS) sQ[i] = op.Qp[i];
   __syncthreads();
-  const long long K = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long K = (long long)bid * blockDim.x + threadIdx.x;
   int c[3] = {0, 0, 0};
   if (K < g.nel) coords(g, K, c);
   for (int s = 0;; ++s) {
@@ -311,8 +325,8 @@ __global__ void __launch_bounds__(BS) k_sweep64_persist(DevGeo g, OpsDev op, con
       }
     }
     const double blk = block_sum(acc, ws);
-    const double tot = barrier_sum64(partials + (size_t)(s & 1) * gridDim.x, &ctrl->bar_count, (unsigned)(s + 1),
-                                     blk, ctrl, ws, &s_tot, &s_to);
+    const double tot = barrier_sum64(partials + (size_t)(s & 1) * nblk, &ctrl->bar_count, (unsigned)(s + 1),
+                                     blk, ctrl, ws, &s_tot, &s_to, bid, nblk);
     if (s_to) break;
     // decide()'s rules, taken identically in every block
     const double res = sqrt(tot);
@@ -329,7 +343,7 @@ __global__ void __launch_bounds__(BS) k_sweep64_persist(DevGeo g, OpsDev op, con
       if (res < res_min) res_min = res;
       if (k >= max_iters) done = true;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (bid == 0 && threadIdx.x == 0) {
       ctrl->iter = k;
       ctrl->fp64_sweeps += 1;
       ctrl->res = res;
@@ -343,6 +357,33 @@ __global__ void __launch_bounds__(BS) k_sweep64_persist(DevGeo g, OpsDev op, con
     it = k;
     if (done) break;
   }
+}
+
+template <int NF, int NLF>
+__global__ void __launch_bounds__(BS) k_sweep64_persist(DevGeo g, OpsDev op, const double* __restrict__ F,
+                                                        double* ring, long long ring_stride, Ctrl* ctrl,
+                                                        double* partials, double* res_hist) {
+  sweep64_persist_body<NF, NLF>(g, op, F, ring, ring_stride, ctrl, partials, res_hist, (int)blockIdx.x,
+                                (int)gridDim.x);
+}
+
+// Several problems' float64 loops in one cooperative launch: blocks off[i] .. off[i+1]-1 work
+// for item i exactly as the blocks of its own launch would (the same block ids, count and
+// reduction order, so the results are bitwise those of solving it alone); each problem stops
+// on its own, and its blocks leave the launch when it does.
+template <int NF, int NLF>
+__global__ void __launch_bounds__(BS) k_sweep64_persist_group(const P64Args* __restrict__ items,
+                                                              const int* __restrict__ off, int n) {
+  int lo = 0, hi = n - 1;   // the item whose block range holds this block
+  const int b = (int)blockIdx.x;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(off + mid) <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  const P64Args& A = items[lo];   // read from global memory where used (no register copy)
+  const int base = __ldg(off + lo), nblk = __ldg(off + lo + 1) - base;
+  sweep64_persist_body<NF, NLF>(A.g, A.op, A.F, A.ring, A.ring_stride, A.ctrl, A.partials, A.res_hist, b - base, nblk);
 }
 
 // Volume reconstruction u = A^{-1} b + L_vol t(E) (+ L_vol t(E2) when E2 is given).
@@ -554,6 +595,57 @@ cudaError_t dispatch(const DevGeo& g, Args&&... args) {
   return cudaErrorNotSupported;
 }
 
+// Several problems of one element shape in one cooperative launch of the persistent float64
+// loop.  NotSupported when their blocks together are not co-resident.
+template <int NF, int NLF>
+cudaError_t run_sweep64_persist_group_t(const LaunchArgs* a, int n, void* d_desc, cudaStream_t st) {
+  constexpr int NIN = NF * NLF;
+  size_t smem = 0;
+  std::vector<P64Args> items((size_t)n);
+  std::vector<int> off((size_t)n + 1, 0);
+  for (int i = 0; i < n; ++i) {
+    const size_t sm = ((size_t)a[i].g.n_exp * NIN + NIN * (NIN + 1) / 2 + (size_t)NIN * BS) * sizeof(double);
+    smem = sm > smem ? sm : smem;
+    const long long grid = grid_for(a[i].g.nel);
+    if (grid > partials_needed(a[i].g.nel) / 2 - 1) return cudaErrorNotSupported;
+    off[(size_t)i + 1] = off[(size_t)i] + (int)grid;
+    items[(size_t)i] = {a[i].g, a[i].op, a[i].F, a[i].ring, a[i].ring_stride, a[i].ctrl, a[i].partials, a[i].res_hist};
+  }
+  auto kern = k_sweep64_persist_group<NF, NLF>;
+  if (smem > 32 * 1024) {
+    cudaError_t e = allow_dynamic_smem(kern);
+    if (e != cudaSuccess) return e;
+  }
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, BS, smem);
+  if (e != cudaSuccess) return e;
+  if (per < 1 || off[(size_t)n] > per * sms) return cudaErrorNotSupported;
+  for (int i = 0; i < n; ++i) {
+    e = cudaMemsetAsync(&a[i].ctrl->bar_count, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+  }
+  P64Args* d_items = static_cast<P64Args*>(d_desc);
+  int* d_off = reinterpret_cast<int*>(static_cast<char*>(d_desc) + sweep64_group_desc_items_bytes(n));
+  e = cudaMemcpyAsync(d_items, items.data(), sizeof(P64Args) * (size_t)n, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(d_off, off.data(), sizeof(int) * ((size_t)n + 1), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return e;
+  const P64Args* ci = d_items;
+  const int* co = d_off;
+  int nn = n;
+  void* args[] = {&ci, &co, &nn};
+  e = cudaLaunchCooperativeKernel((const void*)kern, dim3((unsigned)off[(size_t)n]), dim3(BS), args, smem, st);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+template <int NF, int NLF> struct Sweep64GroupFn {
+  static cudaError_t run(const LaunchArgs* a, int n, void* d_desc, cudaStream_t st) {
+    return run_sweep64_persist_group_t<NF, NLF>(a, n, d_desc, st);
+  }
+};
+
 template <int NF, int NLF> struct FirstFn { static cudaError_t run(const LaunchArgs& a) { return run_first_t<NF, NLF>(a); } };
 template <int NF, int NLF> struct Sweep64Fn { static cudaError_t run(const LaunchArgs& a, int n) { return run_sweep64_t<NF, NLF>(a, n); } };
 template <int NF, int NLF> struct Sweep64PersistFn { static cudaError_t run(const LaunchArgs& a) { return run_sweep64_persist_t<NF, NLF>(a); } };
@@ -589,6 +681,14 @@ cudaError_t launch_export0(const LaunchArgs& a, const double* u0, double* E0) {
 cudaError_t launch_first(const LaunchArgs& a) { return dispatch<FirstFn>(a.g, a); }
 cudaError_t launch_sweep64(const LaunchArgs& a, int count) { return dispatch<Sweep64Fn>(a.g, a, count); }
 cudaError_t launch_sweep64_persist(const LaunchArgs& a) { return dispatch<Sweep64PersistFn>(a.g, a); }
+size_t sweep64_group_desc_items_bytes(int n) { return ((sizeof(P64Args) * (size_t)n) + 255) / 256 * 256; }
+size_t sweep64_group_desc_bytes(int n) { return sweep64_group_desc_items_bytes(n) + ((sizeof(int) * ((size_t)n + 1)) + 255) / 256 * 256; }
+cudaError_t launch_sweep64_persist_group(const LaunchArgs* a, int n, void* d_desc, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  for (int i = 1; i < n; ++i)
+    if (a[i].g.dim != a[0].g.dim || a[i].g.nf != a[0].g.nf) return cudaErrorInvalidValue;
+  return dispatch<Sweep64GroupFn>(a[0].g, a, n, d_desc, st);
+}
 cudaError_t launch_reconstruct(const LaunchArgs& a, const double* E, const double* E2, double* u) {
   return dispatch<ReconFn>(a.g, a, E, E2, u);
 }

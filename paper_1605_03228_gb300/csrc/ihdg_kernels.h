@@ -78,6 +78,13 @@ cudaError_t launch_sweep64(const LaunchArgs& a, int count);
 // the whole float64 loop in one cooperative launch; cudaErrorNotSupported when the grid is
 // not co-resident (then launch_sweep64 in batches)
 cudaError_t launch_sweep64_persist(const LaunchArgs& a);
+// the persistent float64 loops of n problems of one element shape (dim, nf) in one cooperative
+// launch (bitwise each problem's own launch); d_desc: device scratch of
+// sweep64_group_desc_bytes(n) for the launch's descriptors.  NotSupported when the problems'
+// blocks together are not co-resident.
+size_t sweep64_group_desc_items_bytes(int n);
+size_t sweep64_group_desc_bytes(int n);
+cudaError_t launch_sweep64_persist_group(const LaunchArgs* a, int n, void* d_desc, cudaStream_t st);
 cudaError_t launch_reconstruct(const LaunchArgs& a, const double* E, const double* E2, double* u);
 // q <- 2 qh - q over n values (the Crank-Nicolson step from the backward-Euler half step qh)
 cudaError_t launch_cn_extrapolate(double* q, const double* qh, long long n, cudaStream_t s);

@@ -74,7 +74,8 @@ EXPORTED = ["ihdg_create", "ihdg_destroy", "ihdg_last_error", "ihdg_problem_size
             "ihdg_swe_steps_device", "ihdg_host_operator", "ihdg_solve_device_static", "ihdg_server_start",
             "ihdg_server_stop", "ihdg_submit", "ihdg_poll", "ihdg_fetch", "ihdg_autotune", "ihdg_measure_peaks",
             "ihdg_face_quadrature_points", "ihdg_var_plan_create", "ihdg_var_plan_destroy", "ihdg_var_plan_info",
-            "ihdg_var_solve", "ihdg_var_solve_device", "ihdg_var_host_operator", "ihdg_var_solve_group"]
+            "ihdg_var_solve", "ihdg_var_solve_device", "ihdg_var_host_operator", "ihdg_var_solve_group",
+            "ihdg_group_workspace_bytes", "ihdg_solve_group_device"]
 STATIC_SCRATCH_BYTES = 64 * 1024 * 1024
 
 _lib = None
@@ -375,6 +376,31 @@ class Context:
         st = self.L.ihdg_var_solve_group(self.h, n, pl, arr(d_f), arr(d_g), ctypes.byref(opts), arr(d_u),
                                          arr(d_tr) if d_tr is not None else None, ctypes.c_void_p(stream), res)
         self._check(st, "ihdg_var_solve_group")
+        return list(res)
+
+    def group_workspace_bytes(self, meshes, coeffs, opts):
+        """ihdg_group_workspace_bytes for the problems (meshes[i], coeffs[i])."""
+        n = len(meshes)
+        ms = (Mesh * n)(*meshes)
+        cs = (Coeffs * n)(*coeffs)
+        b = ctypes.c_size_t()
+        self._check(self.L.ihdg_group_workspace_bytes(n, ms, cs, ctypes.byref(opts), ctypes.byref(b)),
+                    "ihdg_group_workspace_bytes")
+        return b.value
+
+    def solve_group_device(self, meshes, coeffs, d_f, d_g, opts, d_u, d_tr, d_ws, ws_bytes, stream=0):
+        """ihdg_solve_group_device: float64 solves of several problems together (integer device
+        pointers, one per problem; d_tr None or a list with 0 for no trace).  Returns a list of
+        Result."""
+        n = len(meshes)
+        arr = lambda xs: (ctypes.c_void_p * n)(*[ctypes.c_void_p(int(x) if x else 0) for x in xs])
+        ms = (Mesh * n)(*meshes)
+        cs = (Coeffs * n)(*coeffs)
+        res = (Result * n)()
+        st = self.L.ihdg_solve_group_device(self.h, n, ms, cs, arr(d_f), arr(d_g), ctypes.byref(opts), arr(d_u),
+                                            arr(d_tr) if d_tr is not None else None, ctypes.c_void_p(d_ws),
+                                            ctypes.c_size_t(ws_bytes), ctypes.c_void_p(stream), res)
+        self._check(st, "ihdg_solve_group_device")
         return list(res)
 
     # ---------------------------------------------------------------- serving

@@ -916,3 +916,90 @@ def test_autotune_choice_converges_and_is_cached(ctx):
     assert rel(u_t, U.reshape(om.nel, -1)) < 1e-6
     t64, ms64 = ctx.autotune(mesh, co, f, g, ihdg.make_options(1e-8))
     assert t64.prec == ihdg.FP64 and t64.inner_kernel == ihdg.KERNEL_AUTO and ms64 == 0.0
+
+
+# ------------------------------------------------------------------------------ grouped float64 solves
+def _group_problems(ihdg, seed=3, n=14):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        if i % 5 == 4:
+            d, p = 3, int(rng.integers(1, 3))
+            side = int(rng.integers(3, 7))
+            beta = tuple(np.array([1.0, 0.6, 0.8]) / np.linalg.norm([1.0, 0.6, 0.8]))
+            mesh = ihdg.make_mesh(3, (side, side + 1, side), p)
+            co = ihdg.make_coeffs(ihdg.TRANSPORT, beta=beta)
+            vol, bnd = ihdg.quadrature_points(mesh, co)
+            f, g = W.transport3d_forcing(vol, beta), W.transport3d_exact(bnd)
+        elif i % 2:
+            p = int(rng.integers(1, 5))
+            side = int(rng.integers(8, 40))
+            kappa = float(10 ** rng.uniform(-3, -1))
+            mesh = ihdg.make_mesh(2, (side, side + 3), p)
+            co = ihdg.make_coeffs(ihdg.CONVDIFF, beta=(1.0, 0.7), kappa=kappa)
+            vol, bnd = ihdg.quadrature_points(mesh, co)
+            f, g = W.convdiff_forcing(vol, kappa, (1.0, 0.7)), W.convdiff_exact(bnd)
+        else:
+            p = int(rng.integers(1, 5))
+            side = int(rng.integers(6, 48))
+            mesh = ihdg.make_mesh(2, (side, side + 2), p)
+            co = ihdg.make_coeffs(ihdg.TRANSPORT, beta=(0.8, 0.6))
+            vol, bnd = ihdg.quadrature_points(mesh, co)
+            f, g = W.transport2d_forcing(vol, (0.8, 0.6)), W.transport2d_exact(bnd)
+        out.append((mesh, co, f, g))
+    return out
+
+
+def test_group_fp64_equals_alone(ctx):
+    """ihdg_solve_group_device: problems of different meshes, orders and PDEs (2D/3D
+    transport, conv.-diff. at several diffusivities) in one call give bitwise the results,
+    iteration counts and statuses of solving each alone with ihdg_solve_device."""
+    ihdg = ih()
+    probs = _group_problems(ihdg)
+    dev = torch.device("cuda:0")
+    opts = ihdg.make_options(1e-10, max_iters=3000)
+    sizes = [ihdg.problem_sizes(m, c) for m, c, _, _ in probs]
+    fs = [torch.from_numpy(np.ascontiguousarray(f)).to(dev) for _, _, f, _ in probs]
+    gs = [torch.from_numpy(np.ascontiguousarray(g)).to(dev) for _, _, _, g in probs]
+    ug = [torch.zeros((s.n_el, s.nvol), dtype=torch.float64, device=dev) for s in sizes]
+    tg = [torch.zeros((s.n_face, s.nface_nodes), dtype=torch.float64, device=dev) for s in sizes]
+    meshes, coeffs = [p[0] for p in probs], [p[1] for p in probs]
+    nws = ctx.group_workspace_bytes(meshes, coeffs, opts)
+    ws = torch.empty(nws + 256, dtype=torch.uint8, device=dev)
+    wsp = (ws.data_ptr() + 255) // 256 * 256
+    rg = ctx.solve_group_device(meshes, coeffs, [x.data_ptr() for x in fs], [x.data_ptr() for x in gs], opts,
+                                [x.data_ptr() for x in ug], [x.data_ptr() for x in tg], wsp, nws)
+    torch.cuda.synchronize()
+    statuses = set()
+    for i, (mesh, co, f, g) in enumerate(probs):
+        s = sizes[i]
+        nw = ihdg.workspace_bytes(mesh, co, opts)
+        w1 = torch.empty(nw + 256, dtype=torch.uint8, device=dev)
+        u1 = torch.zeros((s.n_el, s.nvol), dtype=torch.float64, device=dev)
+        t1 = torch.zeros((s.n_face, s.nface_nodes), dtype=torch.float64, device=dev)
+        r1 = ctx.solve_device(mesh, co, fs[i].data_ptr(), gs[i].data_ptr(), opts, u1.data_ptr(), t1.data_ptr(),
+                              (w1.data_ptr() + 255) // 256 * 256, nw, 0)
+        torch.cuda.synchronize()
+        assert (rg[i].status, rg[i].iterations) == (r1.status, r1.iterations), (i, rg[i].as_dict(), r1.as_dict())
+        assert torch.equal(ug[i], u1) and torch.equal(tg[i], t1), i
+        statuses.add(r1.status)
+    assert ihdg.OK in statuses
+
+
+def test_group_rejects_mixed_and_small_workspace(ctx):
+    ihdg = ih()
+    probs = _group_problems(ihdg, seed=4, n=2)
+    meshes, coeffs = [p[0] for p in probs], [p[1] for p in probs]
+    dev = torch.device("cuda:0")
+    opts = ihdg.make_options(1e-10)
+    nws = ctx.group_workspace_bytes(meshes, coeffs, opts)
+    ws = torch.empty(nws + 256, dtype=torch.uint8, device=dev)
+    wsp = (ws.data_ptr() + 255) // 256 * 256
+    dummy = [ws.data_ptr()] * 2
+    with pytest.raises(ihdg.IHDGError) as e1:
+        ctx.solve_group_device(meshes, coeffs, dummy, dummy, ihdg.make_options(1e-10, prec=ihdg.MIXED_FP32),
+                               dummy, None, wsp, nws)
+    assert e1.value.status == ihdg.ERR_UNSUPPORTED
+    with pytest.raises(ihdg.IHDGError) as e2:
+        ctx.solve_group_device(meshes, coeffs, dummy, dummy, opts, dummy, None, wsp, nws - 256)
+    assert e2.value.status == ihdg.ERR_NOMEM
