@@ -257,3 +257,24 @@ def test_var_plan_rejects_sign_change_and_needs_device():
     with pytest.raises(ihdg.IHDGError) as ei:
         ihdg.var_host_operator(mesh, sign_change(vol), sign_change(fpts), 0, 0)
     assert ei.value.status == ihdg.ERR_UNSUPPORTED
+
+
+def test_group_workspace_bytes_host_only():
+    """ihdg_group_workspace_bytes (host only): the per-problem workspaces, each rounded to 256
+    bytes, plus the grouped launch's descriptors; shallow water and bad counts are rejected."""
+    L = ihdg.load()
+    meshes = [ihdg.make_mesh(2, (9, 7), 2), ihdg.make_mesh(2, (12, 12), 4), ihdg.make_mesh(3, (3, 4, 5), 1)]
+    coeffs = [ihdg.make_coeffs(ihdg.TRANSPORT, beta=(1, 0.5)), ihdg.make_coeffs(ihdg.CONVDIFF, beta=(1, 1), kappa=0.01),
+              ihdg.make_coeffs(ihdg.TRANSPORT, beta=(1, 1, 1))]
+    opts = ihdg.make_options(1e-8)
+    n = len(meshes)
+    ms = (ihdg.Mesh * n)(*meshes)
+    cs = (ihdg.Coeffs * n)(*coeffs)
+    b = ctypes.c_size_t()
+    assert L.ihdg_group_workspace_bytes(n, ms, cs, ctypes.byref(opts), ctypes.byref(b)) == ihdg.OK
+    per = sum((ihdg.workspace_bytes(m, c, opts) + 255) // 256 * 256 for m, c in zip(meshes, coeffs))
+    assert per < b.value <= per + 64 * 1024
+    swe = (ihdg.Coeffs * 1)(ihdg.make_coeffs(ihdg.SWE, Phi=1.0, dt=0.01))
+    m1 = (ihdg.Mesh * 1)(meshes[0])
+    assert L.ihdg_group_workspace_bytes(1, m1, swe, ctypes.byref(opts), ctypes.byref(b)) == ihdg.ERR_INVALID
+    assert L.ihdg_group_workspace_bytes(-1, ms, cs, ctypes.byref(opts), ctypes.byref(b)) == ihdg.ERR_INVALID
