@@ -135,10 +135,10 @@ struct TcShape {
 
 // Group gr of the block handles tiles blockIdx.x * G + gr, + gridDim.x * G, ...; the
 // assignment is the same in every sweep, so each thread always owns the same elements.  A
-// group gathers its tile's traces into its A buffer(s), one thread issues the MMAs into the
-// group's 32 tensor-memory columns, and while they run the group loads the residual its
-// epilogue needs.  Groups synchronise among themselves with named barriers only, so the
-// block's tiles overlap their latencies.
+// group loads the residual its epilogue needs together with its tile's traces, packs the
+// traces into its A buffer(s), and one thread issues the MMAs into the group's 32
+// tensor-memory columns.  Groups synchronise among themselves with named barriers only, so
+// the block's tiles overlap their latencies.
 template <int NF, int NLF, bool PER_AXIS, int MODE>
 __global__ void __launch_bounds__(128 * TcShape<NF, NLF, PER_AXIS, MODE>::G, 1)
     k_inner_tc(const DevGeo g, const typename std::conditional<MODE == TC_BF16, __nv_bfloat16, float>::type* __restrict__ rlp,
