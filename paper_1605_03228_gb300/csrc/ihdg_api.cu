@@ -1205,6 +1205,15 @@ ihdg_status ihdg_solve_group_device(ihdg_ctx* ctx, int n, const ihdg_mesh* meshe
     ~Pin() { c->plan_pin -= 1; }
   } pin{ctx};
   ctx->plan_pin += 1;
+  // the failure-detection hooks of the single solve (a block that never arrives, a shorter
+  // bound of every wait), read the same way
+  long long wait_cycles = 2000000000LL;
+  int stall_block = -1;
+  if (const char* w = std::getenv("IHDG_TEST_WAIT_CYCLES")) {
+    const long long v = std::atoll(w);
+    if (v > 0) wait_cycles = v;
+  }
+  if (const char* b = std::getenv("IHDG_TEST_STALL_BLOCK")) stall_block = std::atoi(b);
   std::vector<Plan*> pl((size_t)n, nullptr);
   std::vector<double> setup((size_t)n, 0.0);
   std::vector<LaunchArgs> a((size_t)n);
@@ -1232,7 +1241,7 @@ ihdg_status ihdg_solve_group_device(ihdg_ctx* ctx, int n, const ihdg_mesh* meshe
     ai.partials = reinterpret_cast<double*>(w + L[(size_t)i].partials);
     ai.res_hist = reinterpret_cast<double*>(w + L[(size_t)i].res_hist);
     ai.stream = s;
-    CK(launch_ctrl_init(ai, o.tol, o.diverge_factor, o.max_iters, o.inner_max, o.inner_rtol, 2000000000LL, -1),
+    CK(launch_ctrl_init(ai, o.tol, o.diverge_factor, o.max_iters, o.inner_max, o.inner_rtol, wait_cycles, stall_block),
        "ctrl init");
     CK(launch_forcing(ai), "forcing kernel");
     CK(launch_export0(ai, nullptr, ai.ring), "initial export kernel");

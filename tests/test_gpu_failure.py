@@ -105,3 +105,32 @@ def test_operator_copy_wait_runs_out_and_plan_stays_usable(ctx, monkeypatch, pre
         assert np.array_equal(u, u_ref)
     finally:
         plan.close()
+
+
+def test_grouped_barrier_wait_runs_out_and_context_stays_usable(ctx, monkeypatch):
+    """Grouped float64 solves: a block that never arrives at its problem's grid barrier makes
+    that problem's bounded waits run out; the call returns IHDG_ERR_TIMEOUT, and the next
+    grouped call on the same context and workspace solves normally."""
+    import torch
+    from paper_1605_03228_gb300 import ihdg as ih
+    probs = [problem(ih, "cd2d"), problem(ih, "t3d")]
+    dev = torch.device("cuda:0")
+    opts = ih.make_options(1e-8, max_iters=5000)
+    meshes, coeffs = [p[0] for p in probs], [p[1] for p in probs]
+    fs = [torch.from_numpy(np.ascontiguousarray(p[2])).to(dev) for p in probs]
+    gs = [torch.from_numpy(np.ascontiguousarray(p[3])).to(dev) for p in probs]
+    sz = [ih.problem_sizes(m, c) for m, c in zip(meshes, coeffs)]
+    us = [torch.zeros((s.n_el, s.nvol), dtype=torch.float64, device=dev) for s in sz]
+    nws = ctx.group_workspace_bytes(meshes, coeffs, opts)
+    ws = torch.empty(nws + 256, dtype=torch.uint8, device=dev)
+    wsp = (ws.data_ptr() + 255) // 256 * 256
+    args = ([x.data_ptr() for x in fs], [x.data_ptr() for x in gs], opts, [x.data_ptr() for x in us], None, wsp, nws)
+    monkeypatch.setenv("IHDG_TEST_WAIT_CYCLES", "20000000")
+    monkeypatch.setenv("IHDG_TEST_STALL_BLOCK", "0")
+    with pytest.raises(ih.IHDGError) as e:
+        ctx.solve_group_device(meshes, coeffs, *args)
+    assert e.value.status == ih.ERR_TIMEOUT
+    monkeypatch.delenv("IHDG_TEST_WAIT_CYCLES")
+    monkeypatch.delenv("IHDG_TEST_STALL_BLOCK")
+    res = ctx.solve_group_device(meshes, coeffs, *args)
+    assert all(r.status == ih.OK for r in res)
