@@ -922,6 +922,45 @@ def test_full_size_transport3d_mixed_converged(ctx):
     assert rel(u[els], ref) < 1e-5, rel(u[els], ref)
 
 
+def test_full_size_swe_mixed_steps(ctx):
+    """The shallow-water workload itself: 512^2, p = 2, dt = h/12, two backward-Euler steps
+    from the seeded bump, mixed float32 inner sweeps with float64 outer sweeps in the bench's
+    launch shape, against the float64 oracle's state after two steps at 48 sampled elements
+    (tests/golden/swe_512_p2.json, written by the committed script beside it from oracle/
+    alone).  The float64 path matches the samples to 1e-10 with the oracle's per-step counts
+    (to one); the mixed state is within 1e-5 of them.  Both paths stop on ||q^k - q^(k-1)|| <
+    1e-8 at different iterates of a slowly contracting first step (374 sweeps), which leaves
+    them ~1e-6 apart; run to 1e-10 the mixed state is within the mixed bar (1e-6 relative L2)
+    of the float64 state over every node, which is the precision claim."""
+    import json
+    import os
+    ihdg = ih()
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "swe_512_p2.json")))
+    n, p = tuple(gold["n"]), gold["p"]
+    mesh = ihdg.make_mesh(2, n, p)
+    co = ihdg.make_coeffs(ihdg.SWE, Phi=gold["Phi"], dt=gold["dt"])
+    q0 = W.swe_bump(ihdg.node_points(mesh, co), seed=gold["bump_seed"])
+    q0 = q0.reshape(q0.shape[0], -1)
+    els, ref = np.array(gold["elements"]), np.array(gold["q"])
+    q64 = q0.copy()
+    its64, r64 = ctx.swe_steps(mesh, co, q64, gold["steps"], ihdg.make_options(gold["tol"], max_iters=4000))
+    assert r64.status == ihdg.OK
+    assert all(abs(int(a) - b) <= 1 for a, b in zip(its64, gold["iterations_per_step"])), (list(its64), gold)
+    assert rel(q64[els], ref) < 1e-10
+    qm = q0.copy()
+    itsm, rm = ctx.swe_steps(mesh, co, qm, gold["steps"], ihdg.make_options(gold["tol"], prec=ihdg.MIXED_FP32,
+                                                                               max_iters=4000))
+    assert rm.status == ihdg.OK and rm.lowp_sweeps > 0
+    assert rel(qm[els], ref) < 1e-5, rel(qm[els], ref)
+    tight = []
+    for prec in (ihdg.FP64, ihdg.MIXED_FP32):
+        q = q0.copy()
+        _, r = ctx.swe_steps(mesh, co, q, gold["steps"], ihdg.make_options(1e-10, prec=prec, max_iters=40000))
+        assert r.status == ihdg.OK, (prec, r.as_dict())
+        tight.append(q)
+    assert rel(tight[1], tight[0]) < 1e-6, rel(tight[1], tight[0])
+
+
 # ------------------------------------------------------------------------------ autotuner
 def test_autotune_choice_converges_and_is_cached(ctx):
     """ihdg_autotune times complete solves over the inner-kernel choices and a ladder of inner
