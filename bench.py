@@ -17,9 +17,11 @@ value = element-DOF updates/s = n_el * nvol * sweeps / step time.  L2 is flushed
 write) between timed steps, outside the timed events.
 
 Other workloads: --workload transport2d (8x8, p=2, float64, tol 1e-10),
-transport3d (64^3, p=2, bf16 inner + float64, tol 1e-8), swe (512^2, p=2, 100 steps).
+transport3d (64^3, p=2, bf16 inner + float64, tol 1e-8), swe (512^2, p=2, 100 steps),
+transport3d_var (64^3, p=2, beta = (z, x, y), per-element operators), serving (the request
+stream).  The default run adds these as compact sub-results, with the grouped solves.
 
---impl reference times the float64 CPU oracle (the reference arm of this build) on the
+--impl reference times the float64 CPU oracle (no reference implementation exists) on the
 same workload, each step a bounded sample of sweeps on the full mesh.
 
 Multi-GPU (torchrun, one rank per GPU): every rank solves its own replica (the solves are
