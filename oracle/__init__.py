@@ -10,6 +10,7 @@ Contents:
   mesh      uniform box meshes, faces and neighbours
   ihdg      the upwind HDG local problems (transport, convection-diffusion, linearized
             shallow water), Algorithm 1, and a static-condensation direct solve
+  krylov    restarted GMRES (Saad and Schultz) and GMRES around the iHDG sweep
 
 Every function is pinned by tests under tests/ against closed forms, brute force, the
 direct HDG solve, polynomial exactness, manufactured-solution convergence rates and the
@@ -19,3 +20,4 @@ from .mesh import BoxMesh
 from .refelem import RefElement, gll_nodes, gauss_rule, lagrange_matrix, lagrange_deriv_matrix
 from .ihdg import (Discretisation, Transport, TransportVar, ConvDiff, ShallowWater, ShallowWaterCN,
                    STATUS_OK, STATUS_NOT_CONVERGED, STATUS_DIVERGED)
+from .krylov import gmres, ihdg_gmres
