@@ -159,6 +159,15 @@ typedef struct {
                               SM (1: the smallest area, the automatic rule; 2, 3, ...: the
                               next ones; past the last: the last); 0: automatic (the autotuned
                               value, else 1) */
+  int krylov_restart;      /* 0: Algorithm 1 (the plain iteration).  m >= 1: GMRES(m) on the
+                              fixed-point system (I - T) E = F of one float64 sweep E -> T E + F
+                              (the iHDG sweep as preconditioner, Section 4.2, closing remark):
+                              restarted every m steps, at most max_iters steps in all (one
+                              homogeneous sweep each); tol bounds the residual relative to the
+                              initial one, ||F - (I - T) E||_2 <= tol ||F - (I - T) E^0||_2, in
+                              the export space.  float64 only (prec must be IHDG_FP64), m <= 4096;
+                              the workspace grows by (m + 1) export vectors.  result.residual is
+                              the true relative residual of the returned solution. */
 } ihdg_options;
 
 typedef struct {

@@ -15,7 +15,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libihdg.so")
 SOURCES = ["ihdg_mixed_f32.cu", "ihdg_mixed_bf16.cu", "ihdg_kernels.cu", "ihdg_tc_tf32x4.cu", "ihdg_tc_tf32.cu",
-           "ihdg_tc_bf16.cu", "ihdg_mixed.cu", "ihdg_api.cu", "ihdg_ops.cpp", "ihdg_probe.cu", "ihdg_var.cu", "ihdg_var_ops.cpp"]
+           "ihdg_tc_bf16.cu", "ihdg_mixed.cu", "ihdg_api.cu", "ihdg_ops.cpp", "ihdg_probe.cu", "ihdg_var.cu", "ihdg_var_ops.cpp",
+           "ihdg_krylov.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

@@ -23,6 +23,7 @@
 #include "../../include/ihdg.h"
 #include "ihdg_dev.h"
 #include "ihdg_kernels.h"
+#include "ihdg_krylov.h"
 #include "ihdg_mixed.h"
 #include "ihdg_ops.h"
 #include "ihdg_var.h"
@@ -213,7 +214,7 @@ ihdg_status get_plan(ihdg_ctx* ctx, const ihdg_mesh& m, const ihdg_coeffs& co, P
 
 // Workspace layout of one solve (offsets in bytes from the workspace base).
 struct Layout {
-  size_t ctrl, partials, res_hist, F, V, ring, qnext, mixed, total;
+  size_t ctrl, partials, res_hist, F, V, ring, qnext, mixed, kry, total;
   MixedLayout mx;
 };
 
@@ -233,6 +234,7 @@ Layout layout_for(const DevGeo& g, const ihdg_options& o, bool swe) {
     L.mx = mixed_layout(g, o.prec);
     L.mixed = take(L.mx.total);
   }
+  if (o.krylov_restart > 0) L.kry = take(krylov_bytes((long long)g.n_exp * g.ld, o.krylov_restart));
   L.total = at;
   return L;
 }
@@ -258,6 +260,10 @@ ihdg_status check_opts(ihdg_ctx* ctx, const ihdg_options& o) {
   if (o.sweeps_per_sync < 0 || o.sweeps_per_sync > 8)
     return fail(ctx, IHDG_ERR_INVALID, "opts.sweeps_per_sync must be in 0..8");
   if (o.tile_shape < 0 || o.tile_shape > 64) return fail(ctx, IHDG_ERR_INVALID, "opts.tile_shape must be in 0..64");
+  if (o.krylov_restart < 0 || o.krylov_restart > 4096)
+    return fail(ctx, IHDG_ERR_INVALID, "opts.krylov_restart must be in 0..4096");
+  if (o.krylov_restart > 0 && o.prec != IHDG_FP64)
+    return fail(ctx, IHDG_ERR_INVALID, "opts.krylov_restart needs opts.prec = IHDG_FP64");
   if (o.inner_kernel < IHDG_KERNEL_AUTO || o.inner_kernel > IHDG_KERNEL_GLOBAL)
     return fail(ctx, IHDG_ERR_INVALID, "opts.inner_kernel is not a known kernel");
   return IHDG_OK;
@@ -344,16 +350,35 @@ ihdg_status device_iterate(ihdg_ctx* ctx, Plan* pl, const ihdg_options& o, const
   CK(launch_ctrl_init(a, o.tol, o.diverge_factor, o.max_iters, o.inner_max, inner_rtol, wait_cycles, stall_block),
      "ctrl init");
   CK(launch_forcing(a), "forcing kernel");
-  CK(launch_export0(a, u0, a.ring), "initial export kernel");
-  CK(launch_first(a), "first sweep kernel");
-  tm.launches += 4;
+  tm.launches += 2;
   Ctrl* hc = ctx->h_ctrl;
   bool mixed = o.prec != IHDG_FP64;
+  const bool kry = o.krylov_restart > 0;
+  KryOut ko;
   const double* Eu = nullptr;     // exports whose traces fed the final local solve
   const double* Eu2 = nullptr;    //   (+ a second array, added; mixed path)
   const double* Et = nullptr;     // exports of u^K
   const double* Et2 = nullptr;
-  if (!mixed) {
+  if (kry) {
+    // GMRES around the sweep on (I - T) E = F from E^0 = the exports of u0 (or zero); the
+    // solution is a fixed point of the sweep, so its exports feed both the final local solve
+    // and the trace
+    NvtxRange nv_kry("ihdg GMRES");
+    double* Ex = a.ring;
+    CK(cudaMemsetAsync(Ex, 0, sizeof(double) * (size_t)a.ring_stride, stream), "memset");
+    if (u0) { CK(launch_export0(a, u0, Ex), "initial export kernel"); tm.launches += 1; }
+    if (run_krylov(a, o.krylov_restart, o.tol, o.max_iters, Ex, a.ring + a.ring_stride, ws + L.kry, &ko, ctx->err) !=
+        cudaSuccess)
+      return fail(ctx, IHDG_ERR_CUDA, ctx->err);
+    tm.launches += ko.launches;
+    Eu = Ex;
+    Et = Ex;
+  } else {
+    CK(launch_export0(a, u0, a.ring), "initial export kernel");
+    CK(launch_first(a), "first sweep kernel");
+    tm.launches += 2;
+  }
+  if (!kry && !mixed) {
     // the whole loop in one cooperative launch when its grid is co-resident (not in profile
     // mode, which times every sweep launch); otherwise, or after it, batches of launches
     if (!tm.on) {
@@ -396,7 +421,7 @@ ihdg_status device_iterate(ihdg_ctx* ctx, Plan* pl, const ihdg_options& o, const
     int K = hc->iter;
     Et = a.ring + (long long)(K % 3) * a.ring_stride;
     Eu = a.ring + (long long)((K + 2) % 3) * a.ring_stride;
-  } else {
+  } else if (!kry) {
     MixedArgs m{};
     m.base = a;
     mixed_bind(m, ws + L.mixed, L.mx, o.prec);
@@ -461,6 +486,13 @@ ihdg_status device_iterate(ihdg_ctx* ctx, Plan* pl, const ihdg_options& o, const
     res->status = (ihdg_status)hc->status;
     res->solve_ms = ms;
     res->inner_kernel_used = inner_used;
+    if (kry) {
+      res->iterations = ko.iters;
+      res->fp64_sweeps = ko.iters;
+      res->lowp_sweeps = 0;
+      res->residual = ko.res_true;
+      res->status = (ihdg_status)ko.status;
+    }
   }
   return IHDG_OK;
 }
@@ -550,6 +582,7 @@ ihdg_status ihdg_node_points(const ihdg_mesh* mesh, double* xyz) {
 
 ihdg_status ihdg_workspace_bytes(const ihdg_mesh* mesh, const ihdg_coeffs* co, const ihdg_options* opts, size_t* bytes) {
   if (!mesh || !co || !bytes) return IHDG_ERR_INVALID;
+  if (opts && (opts->krylov_restart < 0 || opts->krylov_restart > 4096)) return IHDG_ERR_INVALID;
   std::string err;
   Ops o;
   ihdg_status st = build_ops(*mesh, *co, o, err);
@@ -1190,6 +1223,8 @@ ihdg_status ihdg_solve_group_device(ihdg_ctx* ctx, int n, const ihdg_mesh* meshe
   ihdg_status st = check_opts(ctx, o);
   if (st != IHDG_OK) return st;
   if (o.prec != IHDG_FP64) return fail(ctx, IHDG_ERR_UNSUPPORTED, "grouped solves run the float64 path (opts.prec = IHDG_FP64)");
+  if (o.krylov_restart > 0)
+    return fail(ctx, IHDG_ERR_UNSUPPORTED, "grouped solves run Algorithm 1 (opts.krylov_restart = 0)");
   if (o.u0) return fail(ctx, IHDG_ERR_UNSUPPORTED, "grouped solves start from the zero guess (opts.u0 = NULL)");
   size_t need = 0;
   st = ihdg_group_workspace_bytes(n, meshes, coeffs, &o, &need);

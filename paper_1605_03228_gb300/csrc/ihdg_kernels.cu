@@ -76,6 +76,38 @@ __global__ void __launch_bounds__(BS) k_forcing(DevGeo g, OpsDev op, SrcDev src,
     if (row_live(g, e, g.nf)) F[(long long)e * g.ld + K] = apply(g.steady ? op.PF : op.PqF, op.PFb, e);
 }
 
+// Operator of the GMRES solve around the sweep (Section 4.2, closing remark): on the live
+// export rows, w = s (v - L_E t(v)) + F, i.e. s (I - T) v + F with T v = L_E t(v) the linear
+// part of one float64 sweep (its forcing F left out).  s = 1 with no forcing gives the Arnoldi
+// product (I - T) v; s = -1 with the forcing gives the residual F - (I - T) v.  Dead rows and
+// the padding columns of w are not written.  Returns at once when *done is set.
+template <int NF, int NLF>
+__global__ void __launch_bounds__(BS) k_kry_apply(DevGeo g, OpsDev op, const double* __restrict__ v,
+                                                  const double* __restrict__ F, double s, double* __restrict__ w,
+                                                  const int* __restrict__ done) {
+  constexpr int NIN = NF * NLF;
+  extern __shared__ double sdyn[];
+  if (done && *(const volatile int*)done) return;
+  for (int i = threadIdx.x; i < g.n_exp * NIN; i += BS) sdyn[i] = op.LE[i];
+  __syncthreads();
+  const long long K = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (K >= g.nel) return;
+  int c[3];
+  coords(g, K, c);
+  double t[NIN];
+  gather<NF, NLF, double, double>(g, v, K, c, [&](int q, double x) { t[q] = x; });
+  for (int e = 0; e < g.n_exp; ++e) {
+    if (!row_live(g, e, NF)) continue;
+    const double* row = sdyn + e * NIN;
+    double acc = 0.0;
+#pragma unroll
+    for (int q = 0; q < NIN; ++q) acc += row[q] * t[q];
+    double r = s * (v[(long long)e * g.ld + K] - acc);
+    if (F) r += F[(long long)e * g.ld + K];
+    w[(long long)e * g.ld + K] = r;
+  }
+}
+
 // Initial export E^0 = R u^0 (u^0 in the volume layout [nel][nvol]).
 __global__ void __launch_bounds__(BS) k_export0(DevGeo g, OpsDev op, const double* __restrict__ u0,
                                                 double* __restrict__ E0) {
@@ -646,6 +678,17 @@ template <int NF, int NLF> struct Sweep64GroupFn {
   }
 };
 
+template <int NF, int NLF>
+cudaError_t run_kry_apply_t(const LaunchArgs& a, const double* v, const double* F, double s, double* w, const int* done) {
+  const size_t smem = (size_t)a.g.n_exp * NF * NLF * sizeof(double);
+  k_kry_apply<NF, NLF><<<grid_for(a.g.nel), BS, smem, a.stream>>>(a.g, a.op, v, F, s, w, done);
+  return cudaGetLastError();
+}
+template <int NF, int NLF> struct KryApplyFn {
+  static cudaError_t run(const LaunchArgs& a, const double* v, const double* F, double s, double* w, const int* done) {
+    return run_kry_apply_t<NF, NLF>(a, v, F, s, w, done);
+  }
+};
 template <int NF, int NLF> struct FirstFn { static cudaError_t run(const LaunchArgs& a) { return run_first_t<NF, NLF>(a); } };
 template <int NF, int NLF> struct Sweep64Fn { static cudaError_t run(const LaunchArgs& a, int n) { return run_sweep64_t<NF, NLF>(a, n); } };
 template <int NF, int NLF> struct Sweep64PersistFn { static cudaError_t run(const LaunchArgs& a) { return run_sweep64_persist_t<NF, NLF>(a); } };
@@ -688,6 +731,9 @@ cudaError_t launch_sweep64_persist_group(const LaunchArgs* a, int n, void* d_des
   for (int i = 1; i < n; ++i)
     if (a[i].g.dim != a[0].g.dim || a[i].g.nf != a[0].g.nf) return cudaErrorInvalidValue;
   return dispatch<Sweep64GroupFn>(a[0].g, a, n, d_desc, st);
+}
+cudaError_t launch_kry_apply(const LaunchArgs& a, const double* v, const double* F, double s, double* w, const int* done) {
+  return dispatch<KryApplyFn>(a.g, a, v, F, s, w, done);
 }
 cudaError_t launch_reconstruct(const LaunchArgs& a, const double* E, const double* E2, double* u) {
   return dispatch<ReconFn>(a.g, a, E, E2, u);

@@ -85,6 +85,9 @@ cudaError_t launch_sweep64_persist(const LaunchArgs& a);
 size_t sweep64_group_desc_items_bytes(int n);
 size_t sweep64_group_desc_bytes(int n);
 cudaError_t launch_sweep64_persist_group(const LaunchArgs* a, int n, void* d_desc, cudaStream_t st);
+// w = s (I - T) v + F on the live export rows, T the linear part of one float64 sweep (F may
+// be null); nothing happens when *done (device) is set
+cudaError_t launch_kry_apply(const LaunchArgs& a, const double* v, const double* F, double s, double* w, const int* done);
 cudaError_t launch_reconstruct(const LaunchArgs& a, const double* E, const double* E2, double* u);
 // q <- 2 qh - q over n values (the Crank-Nicolson step from the backward-Euler half step qh)
 cudaError_t launch_cn_extrapolate(double* q, const double* qh, long long n, cudaStream_t s);

@@ -41,7 +41,8 @@ class Options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iters", ctypes.c_int), ("prec", ctypes.c_int),
                 ("diverge_factor", ctypes.c_double), ("inner_max", ctypes.c_int),
                 ("inner_rtol", ctypes.c_double), ("u0", ctypes.c_void_p), ("profile", ctypes.c_int),
-                ("inner_kernel", ctypes.c_int), ("sweeps_per_sync", ctypes.c_int), ("tile_shape", ctypes.c_int)]
+                ("inner_kernel", ctypes.c_int), ("sweeps_per_sync", ctypes.c_int), ("tile_shape", ctypes.c_int),
+                ("krylov_restart", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
@@ -161,8 +162,9 @@ def make_coeffs(pde, beta=(0.0, 0.0, 0.0), kappa=0.0, nu=0.0, Phi=0.0, coriolis_
 
 
 def make_options(tol, max_iters=2000, prec=FP64, diverge_factor=0.0, inner_max=0, inner_rtol=0.0, u0=None,
-                 profile=0, inner_kernel=0, sweeps_per_sync=0, tile_shape=0):
+                 profile=0, inner_kernel=0, sweeps_per_sync=0, tile_shape=0, krylov_restart=0):
     o = Options()
+    o.krylov_restart = krylov_restart
     o.tile_shape = tile_shape
     o.inner_kernel = inner_kernel
     o.sweeps_per_sync = sweeps_per_sync

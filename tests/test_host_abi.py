@@ -278,3 +278,24 @@ def test_group_workspace_bytes_host_only():
     m1 = (ihdg.Mesh * 1)(meshes[0])
     assert L.ihdg_group_workspace_bytes(1, m1, swe, ctypes.byref(opts), ctypes.byref(b)) == ihdg.ERR_INVALID
     assert L.ihdg_group_workspace_bytes(-1, ms, cs, ctypes.byref(opts), ctypes.byref(b)) == ihdg.ERR_INVALID
+
+
+def test_krylov_workspace_host_only():
+    """opts.krylov_restart = m (GMRES around the sweep) adds its basis, m + 1 export vectors of
+    n_exp x ld doubles, plus the small Hessenberg and reduction arrays, to the workspace;
+    values outside 0..4096 are rejected before any device work."""
+    mesh = ihdg.make_mesh(2, (20, 13), 3)
+    co = ihdg.make_coeffs(ihdg.CONVDIFF, beta=(1, 1), kappa=0.01)
+    s = ihdg.problem_sizes(mesh, co)
+    ld = (s.n_el + 31) // 32 * 32
+    nvec = s.n_exp * ld
+    nblk = (nvec + 1023) // 1024
+    w0 = ihdg.workspace_bytes(mesh, co, ihdg.make_options(1e-8))
+    for m in (1, 30, 4096):
+        wm = ihdg.workspace_bytes(mesh, co, ihdg.make_options(1e-8, krylov_restart=m))
+        basis = (m + 1) * nvec * 8
+        assert basis <= wm - w0 <= basis + (m + 1) * (m + 8) * 8 + (m + 1) * nblk * 8 + 16 * 256
+    for bad in (-1, 4097):
+        with pytest.raises(ihdg.IHDGError) as ei:
+            ihdg.workspace_bytes(mesh, co, ihdg.make_options(1e-8, krylov_restart=bad))
+        assert ei.value.status == ihdg.ERR_INVALID
