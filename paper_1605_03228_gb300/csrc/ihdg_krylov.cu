@@ -57,29 +57,34 @@ __global__ void k_kry_init(KryState* st, int m, int max_iters, double tol) {
   *st = s;
 }
 
-// part[i * nblk + block] = this block's share of V_i . w, i < nv
+// part[i * nblk + block] = this block's share of V_i . w over its DBS * EPT values, i < nv.
+// w's values are staged in shared memory; each warp takes one basis vector at a time (32
+// independent coalesced loads per lane) and reduces with shuffles, so the loop over vectors
+// has no block barrier.
 __global__ void __launch_bounds__(DBS) k_kry_dots(const double* __restrict__ V, long long ldv, int nv,
                                                   const double* __restrict__ w, long long n, double* __restrict__ part,
                                                   int nblk, const KryState* st, int force) {
-  __shared__ double ws[DBS / 32];
+  constexpr int R = DBS * EPT;   // values per block
+  constexpr int PL = R / 32;     // values per lane for one vector
+  __shared__ double sw[R];
   if (!force && kdone(st)) return;
-  const long long base = (long long)blockIdx.x * (DBS * EPT) + threadIdx.x;
-  double wv[EPT];
-#pragma unroll
-  for (int k = 0; k < EPT; ++k) {
-    const long long i = base + (long long)k * DBS;
-    wv[k] = i < n ? w[i] : 0.0;
-  }
-  for (int i = 0; i < nv; ++i) {
-    const double* vi = V + (long long)i * ldv;
+  const long long base = (long long)blockIdx.x * R;
+  for (int t = threadIdx.x; t < R; t += DBS) sw[t] = base + t < n ? w[base + t] : 0.0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool full = base + R <= n;
+  for (int i = warp; i < nv; i += DBS / 32) {
+    const double* vi = V + (long long)i * ldv + base;
     double acc = 0.0;
+    if (full) {
 #pragma unroll
-    for (int k = 0; k < EPT; ++k) {
-      const long long x = base + (long long)k * DBS;
-      if (x < n) acc += vi[x] * wv[k];
+      for (int k = 0; k < PL; ++k) acc += vi[lane + 32 * k] * sw[lane + 32 * k];
+    } else {
+      for (int k = 0; k < PL; ++k)
+        if (base + lane + 32 * k < n) acc += vi[lane + 32 * k] * sw[lane + 32 * k];
     }
-    const double t = block_sum(acc, ws);
-    if (threadIdx.x == 0) part[(long long)i * nblk + blockIdx.x] = t;
+    acc = warp_sum(acc);
+    if (lane == 0) part[(long long)i * nblk + blockIdx.x] = acc;
   }
 }
 
@@ -95,24 +100,50 @@ __global__ void __launch_bounds__(DBS) k_kry_sum(const double* __restrict__ part
   if (threadIdx.x == 0) out[blockIdx.x] = t;
 }
 
-// w -= sum_{i < nv} h_i V_i; with `part`, part[block] = this block's share of ||w||^2
+// w -= sum_{i < nv} h_i V_i (h staged in shared memory, nv doubles of dynamic shared memory;
+// four basis vectors per unrolled step, so 16 loads per thread are in flight); with `part`,
+// part[block] = this block's share of ||w||^2
 __global__ void __launch_bounds__(DBS) k_kry_update(double* __restrict__ w, const double* __restrict__ V, long long ldv,
                                                     int nv, const double* __restrict__ h, long long n,
                                                     double* __restrict__ part, const KryState* st) {
+  extern __shared__ double sh[];
   __shared__ double ws[DBS / 32];
   if (kdone(st)) return;
+  for (int i = threadIdx.x; i < nv; i += DBS) sh[i] = h[i];
+  __syncthreads();
   const long long base = (long long)blockIdx.x * (DBS * EPT) + threadIdx.x;
-  double acc = 0.0;
+  double v[EPT];
+  bool in[EPT];
 #pragma unroll
   for (int k = 0; k < EPT; ++k) {
-    const long long x = base + (long long)k * DBS;
-    if (x < n) {
-      double v = w[x];
-      for (int i = 0; i < nv; ++i) v -= h[i] * V[(long long)i * ldv + x];
-      w[x] = v;
-      acc += v * v;
+    in[k] = base + (long long)k * DBS < n;
+    v[k] = in[k] ? w[base + (long long)k * DBS] : 0.0;
+  }
+  int i = 0;
+  for (; i + 4 <= nv; i += 4) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const double* vi = V + (long long)(i + u) * ldv + base;
+      const double c = sh[i + u];
+#pragma unroll
+      for (int k = 0; k < EPT; ++k)
+        if (in[k]) v[k] -= c * vi[k * DBS];
     }
   }
+  for (; i < nv; ++i) {
+    const double* vi = V + (long long)i * ldv + base;
+    const double c = sh[i];
+#pragma unroll
+    for (int k = 0; k < EPT; ++k)
+      if (in[k]) v[k] -= c * vi[k * DBS];
+  }
+  double acc = 0.0;
+#pragma unroll
+  for (int k = 0; k < EPT; ++k)
+    if (in[k]) {
+      w[base + (long long)k * DBS] = v[k];
+      acc += v[k] * v[k];
+    }
   if (part) {
     const double t = block_sum(acc, ws);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
@@ -218,17 +249,20 @@ __global__ void k_kry_solve_y(const KryState* st, const double* __restrict__ H, 
   }
 }
 
-// x += sum_{i < st->j} y_i V_i
+// x += sum_{i < st->j} y_i V_i (y staged in shared memory: m doubles of dynamic shared memory)
 __global__ void __launch_bounds__(DBS) k_kry_combine(double* __restrict__ x, const double* __restrict__ V, long long ldv,
                                                      const double* __restrict__ y, long long n, const KryState* st) {
+  extern __shared__ double sy[];
   const int j = st->j;
+  for (int i = threadIdx.x; i < j; i += DBS) sy[i] = y[i];
+  __syncthreads();
   const long long base = (long long)blockIdx.x * (DBS * EPT) + threadIdx.x;
 #pragma unroll
   for (int k = 0; k < EPT; ++k) {
     const long long p = base + (long long)k * DBS;
     if (p < n) {
       double v = x[p];
-      for (int i = 0; i < j; ++i) v += y[i] * V[(long long)i * ldv + p];
+      for (int i = 0; i < j; ++i) v += sy[i] * V[(long long)i * ldv + p];
       x[p] = v;
     }
   }
@@ -301,10 +335,10 @@ cudaError_t run_krylov(const LaunchArgs& a, int m, double tol, int max_iters, do
     if (!ok(launch_kry_apply(a, V + (long long)j * n, nullptr, 1.0, w, dn), "apply")) return false;
     k_kry_dots<<<nblk, DBS, 0, s>>>(V, n, j + 1, w, n, part, nblk, st, 0);
     k_kry_sum<<<j + 1, DBS, 0, s>>>(part, nblk, h1, st);
-    k_kry_update<<<nblk, DBS, 0, s>>>(w, V, n, j + 1, h1, n, nullptr, st);
+    k_kry_update<<<nblk, DBS, sizeof(double) * (j + 1), s>>>(w, V, n, j + 1, h1, n, nullptr, st);
     k_kry_dots<<<nblk, DBS, 0, s>>>(V, n, j + 1, w, n, part, nblk, st, 0);
     k_kry_sum<<<j + 1, DBS, 0, s>>>(part, nblk, h2, st);
-    k_kry_update<<<nblk, DBS, 0, s>>>(w, V, n, j + 1, h2, n, part, st);
+    k_kry_update<<<nblk, DBS, sizeof(double) * (j + 1), s>>>(w, V, n, j + 1, h2, n, part, st);
     k_kry_finish<<<1, DBS, 0, s>>>(st, part, nblk, j, H, cs, sn, gv, h1, h2);
     k_kry_scale<<<nblk, DBS, 0, s>>>(w, n, st);
     launches += 9;
@@ -325,7 +359,7 @@ cudaError_t run_krylov(const LaunchArgs& a, int m, double tol, int max_iters, do
       if (batch < 32) batch *= 2;
     }
     k_kry_solve_y<<<1, 1, 0, s>>>(st, H, gv, y);
-    k_kry_combine<<<nblk, DBS, 0, s>>>(E, V, n, y, n, st);
+    k_kry_combine<<<nblk, DBS, sizeof(double) * m, s>>>(E, V, n, y, n, st);
     launches += 2;
     if (!ok(cudaSuccess, "combine")) return e;
     if (hs.done) break;
