@@ -448,6 +448,13 @@ typedef struct {
 } ihdg_peaks;
 ihdg_status ihdg_measure_peaks(int device, ihdg_peaks* out);
 
+/* Sizes in bytes of the public structs, for bindings that mirror them (no counterpart in the
+ * paper): out[0..5] = sizeof(ihdg_mesh), sizeof(ihdg_coeffs), sizeof(ihdg_options),
+ * sizeof(ihdg_result), sizeof(ihdg_sizes), sizeof(ihdg_peaks); the first min(n, 6) are
+ * written into the caller's host array.  Host only, no device work.  IHDG_ERR_INVALID when
+ * out is NULL or n < 0. */
+ihdg_status ihdg_abi_sizes(size_t* out, int n);
+
 #ifdef __cplusplus
 }
 #endif

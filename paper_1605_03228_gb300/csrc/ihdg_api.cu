@@ -542,6 +542,14 @@ void ihdg_destroy(ihdg_ctx* ctx) {
 
 const char* ihdg_last_error(const ihdg_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
+ihdg_status ihdg_abi_sizes(size_t* out, int n) {
+  if (!out || n < 0) return IHDG_ERR_INVALID;
+  const size_t sz[6] = {sizeof(ihdg_mesh), sizeof(ihdg_coeffs), sizeof(ihdg_options),
+                        sizeof(ihdg_result), sizeof(ihdg_sizes), sizeof(ihdg_peaks)};
+  for (int i = 0; i < n && i < 6; ++i) out[i] = sz[i];
+  return IHDG_OK;
+}
+
 ihdg_status ihdg_problem_sizes(const ihdg_mesh* mesh, const ihdg_coeffs* co, ihdg_sizes* out) {
   if (!mesh || !co || !out) return IHDG_ERR_INVALID;
   std::string err;

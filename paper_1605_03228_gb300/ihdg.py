@@ -76,7 +76,7 @@ EXPORTED = ["ihdg_create", "ihdg_destroy", "ihdg_last_error", "ihdg_problem_size
             "ihdg_server_stop", "ihdg_submit", "ihdg_poll", "ihdg_fetch", "ihdg_autotune", "ihdg_measure_peaks",
             "ihdg_face_quadrature_points", "ihdg_var_plan_create", "ihdg_var_plan_destroy", "ihdg_var_plan_info",
             "ihdg_var_solve", "ihdg_var_solve_device", "ihdg_var_host_operator", "ihdg_var_solve_group",
-            "ihdg_group_workspace_bytes", "ihdg_solve_group_device"]
+            "ihdg_group_workspace_bytes", "ihdg_solve_group_device", "ihdg_abi_sizes"]
 STATIC_SCRATCH_BYTES = 64 * 1024 * 1024
 
 _lib = None
@@ -104,6 +104,7 @@ def load(build_if_missing=True):
     L.ihdg_last_error.argtypes = [VP]
     L.ihdg_last_error.restype = ctypes.c_char_p
     L.ihdg_problem_sizes.argtypes = [P(Mesh), P(Coeffs), P(Sizes)]
+    L.ihdg_abi_sizes.argtypes = [P(ctypes.c_size_t), I]
     L.ihdg_quadrature_points.argtypes = [P(Mesh), dp, dp]
     L.ihdg_node_points.argtypes = [P(Mesh), dp]
     L.ihdg_solve.argtypes = [VP, P(Mesh), P(Coeffs), dp, dp, P(Options), dp, dp, P(Result)]

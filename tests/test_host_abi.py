@@ -299,3 +299,16 @@ def test_krylov_workspace_host_only():
         with pytest.raises(ihdg.IHDGError) as ei:
             ihdg.workspace_bytes(mesh, co, ihdg.make_options(1e-8, krylov_restart=bad))
         assert ei.value.status == ihdg.ERR_INVALID
+
+
+def test_binding_structs_match_the_c_abi():
+    """The ctypes mirrors of the public structs have the C sizes (a field added on one side
+    only, or a type mismatch, changes them)."""
+    L = ihdg.load()
+    out = (ctypes.c_size_t * 6)()
+    assert L.ihdg_abi_sizes(out, 6) == ihdg.OK
+    mirrors = [ihdg.Mesh, ihdg.Coeffs, ihdg.Options, ihdg.Result, ihdg.Sizes, ihdg.Peaks]
+    assert [ctypes.sizeof(m) for m in mirrors] == list(out)
+    assert L.ihdg_abi_sizes(None, 6) == ihdg.ERR_INVALID
+    part = (ctypes.c_size_t * 2)(0, 0)
+    assert L.ihdg_abi_sizes(part, 2) == ihdg.OK and part[1] == out[1]
