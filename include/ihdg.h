@@ -167,7 +167,9 @@ typedef struct {
                               initial one, ||F - (I - T) E||_2 <= tol ||F - (I - T) E^0||_2, in
                               the export space.  float64 only (prec must be IHDG_FP64), m <= 4096;
                               the workspace grows by (m + 1) export vectors.  result.residual is
-                              the true relative residual of the returned solution. */
+                              the true relative residual of the returned solution.  Taken by
+                              ihdg_solve*, ihdg_swe_steps*; the grouped, served and
+                              variable-coefficient calls return IHDG_ERR_UNSUPPORTED. */
 } ihdg_options;
 
 typedef struct {

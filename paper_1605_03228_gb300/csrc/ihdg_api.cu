@@ -1033,6 +1033,8 @@ extern "C" ihdg_status ihdg_submit(ihdg_ctx* ctx, const ihdg_mesh* mesh, const i
   r->opts.profile = 0;
   ihdg_status st = check_opts(ctx, r->opts);
   if (st != IHDG_OK) return st;
+  if (r->opts.krylov_restart > 0)
+    return fail(ctx, IHDG_ERR_UNSUPPORTED, "served requests run Algorithm 1 (opts.krylov_restart = 0)");
   st = prepare_plan(ctx, *mesh, *co, r->plan);
   if (st != IHDG_OK) return st;
   ihdg_sizes sz;

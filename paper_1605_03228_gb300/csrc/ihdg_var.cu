@@ -901,6 +901,10 @@ ihdg_status var_solve(VarDev& d, const double* f, const double* gb, const ihdg_o
     err = "variable-coefficient transport takes FP64, MIXED_FP32 or MIXED_BF16";
     return IHDG_ERR_UNSUPPORTED;
   }
+  if (o.krylov_restart != 0) {
+    err = "variable-coefficient solves run Algorithm 1 (opts.krylov_restart = 0)";
+    return IHDG_ERR_UNSUPPORTED;
+  }
   const int max_iters = std::min(o.max_iters, d.max_hist);
   double inner_rtol = o.inner_rtol > 0.0 ? o.inner_rtol : (o.prec == IHDG_MIXED_BF16 ? 0.2 : 2e-3);
   struct Ev {
@@ -1068,6 +1072,10 @@ ihdg_status var_solve_group(std::vector<VarDev*>& ds, const std::vector<const do
   };
   if (o.prec == IHDG_MIXED_TF32) {
     err = "variable-coefficient transport takes FP64, MIXED_FP32 or MIXED_BF16";
+    return IHDG_ERR_UNSUPPORTED;
+  }
+  if (o.krylov_restart != 0) {
+    err = "variable-coefficient solves run Algorithm 1 (opts.krylov_restart = 0)";
     return IHDG_ERR_UNSUPPORTED;
   }
   const bool mixed = o.prec != IHDG_FP64, bf16 = o.prec == IHDG_MIXED_BF16;
