@@ -2,8 +2,9 @@
 // products against a set of basis vectors, their fixed-order sums, the Gram-Schmidt update
 // with the norm of the result, scaling and the final combination x += V y; one-thread
 // kernels for the Hessenberg column (Givens rotations), the cycle start and the triangular
-// solve.  Every step kernel returns at once once the solve has stopped (KryState::done),
-// so the host launches steps in batches and reads the state back once per batch.
+// solve.  Every step kernel returns immediately after the solve has stopped
+// (KryState::done), so the host launches steps in batches and reads the state back once per
+// batch.
 #include <cuda_runtime.h>
 
 #include <cmath>
