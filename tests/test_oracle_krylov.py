@@ -12,7 +12,8 @@ GMRES alone, on small explicit matrices, against what its definition fixes:
 * A = I: one step.
 Around the sweep: the solution equals the oracle's static-condensation direct solve, both
 where the plain iteration converges (transport) and where it diverges (conv.-diff. with
-kappa = 1e-2 at h = 1/256, spectral radius > 5, the Section 5.3 regime).
+kappa = 1e-2 at h = 1/256, spectral radius > 5, the Section 5.3 regime; a shallow-water
+step beyond Theorem 3's time-step bound).
 """
 import numpy as np
 import pytest
@@ -136,3 +137,24 @@ def test_gmres_transport_equals_direct_solve(restart):
     # most as many steps as the plain iteration
     _, _, k, _, st2 = pr.iterate(f, g, 1e-13)
     assert st2 == STATUS_OK and its <= k
+
+
+def test_gmres_shallow_water_step_equals_the_direct_step():
+    """A backward-Euler shallow-water step at dt = 6 h / ((p+1)(p+2)), where Algorithm 1
+    diverges: GMRES around the sweep (the previous state enters the affine part only) equals
+    the direct step."""
+    from oracle import ShallowWater
+    n, p = 6, 2
+    h = 1.0 / n
+    disc = Discretisation(BoxMesh(2, (n, n)), p)
+    pr = ShallowWater(disc, 1.0, 6.0 * h / ((p + 1) * (p + 2)), 0.3, 0.05)
+    rng = np.random.default_rng(3)
+    U_m = rng.standard_normal((disc.mesh.nel, 3, disc.nb))
+    f0 = np.zeros((disc.mesh.nel, disc.nq))
+    g0 = np.zeros((disc.mesh.nbface, disc.nqf))
+    *_, st = pr.iterate(f0, g0, 1e-10, U_prev=U_m, max_iters=300)
+    assert st == STATUS_DIVERGED
+    U, _, its, st, _ = ihdg_gmres(pr, f0, g0, tol=1e-13, restart=100, max_iters=2000, U_prev=U_m)
+    Ud = pr.step_direct(U_m)
+    assert st == STATUS_OK
+    assert np.abs(U - Ud).max() <= 1e-9 * np.abs(Ud).max()
